@@ -1,0 +1,175 @@
+"""FP64 oracle for the bispectrum multipoles (Sec. II.C and III.B of the paper).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Steps and the passages they follow
+----------------------------------
+shells          thin shells of width dk about centres k_i (eq. shell), in integer
+                k_f units: shell s holds modes with lo_s <= |n| < lo_s + width,
+                lo_s = first + s*step - width/2.
+shell_field     F_k^(l)(x) = sum_{n in shell} F_l(n) e^{+ik.x} (eq. F_k), an
+                unnormalised inverse DFT of the shell-filtered field.
+triangle_sum    sum_x F_{k1}^(l) F_{k2}^(0) F_{k3}^(0) = N^3 sum over closed
+                triangles (eq. Factorize, discrete orthogonality).
+counts          N_T (eq. NT) as an exact integer: per-mode rounded FP64
+                convolution C_bc(n) of the shell indicators, summed over shell a.
+bispectrum      B^(l) = (2l+1) <F_l F_0 F_0>_T / I_33 - N^(l) (eqs. BispMono,
+                BispQuad) with the thin-shell shot noise of eq. SNbisp2thin:
+                (2l+1)/I_33 [<F_l F^w_0*>_{k1} + sum_{i=2,3} L_l(q^_1.q^_i)
+                <F_0 F^w_l*>_{ki}] - 2 S_3/I_33 delta_l0.  Cosines come from the
+                shell centres by the law of cosines (closure q_1+q_2+q_3 = 0).
+                Triangles are ordered by the largest side, k1 >= k2 >= k3
+                (Sec. II.C), i.e. shell indices a >= b >= c.
+
+Parity: shell fields, triangle sums and counts are pinned by brute-force
+enumeration; the thin-shell shot-noise term is "parity unpinned" (only a
+statistical check on unclustered catalogs stands behind it).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import power as _pw
+from .power import irfftn, rfftn
+
+
+def legendre_poly(l, mu):
+    mu = np.asarray(mu, dtype=np.float64)
+    if l == 0:
+        return np.ones_like(mu)
+    if l == 2:
+        return 0.5 * (3.0 * mu * mu - 1.0)
+    if l == 4:
+        return (35.0 * mu ** 4 - 30.0 * mu * mu + 3.0) / 8.0
+    raise ValueError(l)
+
+
+def shell_bounds(bshells):
+    """(lo_s, hi_s, centre_s) in k_f units for (first, step, width, S)."""
+    first, step, width, S = bshells
+    c = np.array([first + s * step for s in range(S)], dtype=np.float64)
+    lo = c - 0.5 * width
+    return lo, lo + width, c
+
+
+def shell_index(N, bshells):
+    """Shell of every half-spectrum mode (-1 outside all shells, at n = 0 and
+    on Nyquist planes) and the mode's full-grid weight."""
+    lo, hi, _ = shell_bounds(bshells)
+    nx, ny, nz = _pw.mode_vectors(N)
+    n2 = np.broadcast_to(nx * nx + ny * ny + nz * nz, (N, N, N // 2 + 1))
+    idx = np.full(n2.shape, -1, dtype=np.int64)
+    for s in range(len(lo)):
+        m = (n2 >= lo[s] ** 2) & (n2 < hi[s] ** 2)
+        idx[m] = s
+    nyq = (np.abs(nx) == N // 2) | (np.abs(ny) == N // 2) | (np.abs(nz) == N // 2)
+    idx[np.broadcast_to(nyq, idx.shape)] = -1
+    idx[n2 == 0] = -1
+    wt = np.broadcast_to(np.where(nx == 0, 1.0, 2.0), idx.shape)
+    return idx, wt
+
+
+def shell_field(Fl, sidx, s, N):
+    """F_k^(l)(x) for shell s: unnormalised inverse DFT of F_l on the shell."""
+    return irfftn(np.where(sidx == s, Fl, 0.0), (N, N, N)) * float(N) ** 3
+
+
+def triangle_list(S):
+    """All shell triples a >= b >= c (k1 >= k2 >= k3)."""
+    return [(a, b, c) for a in range(S) for b in range(a + 1) for c in range(b + 1)]
+
+
+class Counter:
+    """Exact N_T by rounded FP64 convolution of shell indicators."""
+
+    def __init__(self, N, bshells):
+        self.N = N
+        self.sidx, self.wt = shell_index(N, bshells)
+        self._j = {}
+        self._C = {}
+
+    def _jfield(self, s):
+        if s not in self._j:
+            self._j[s] = irfftn((self.sidx == s).astype(np.float64), (self.N,) * 3) * float(self.N) ** 3
+        return self._j[s]
+
+    def count(self, a, b, c):
+        key = (b, c)
+        if key not in self._C:
+            C = rfftn(self._jfield(b) * self._jfield(c)) / float(self.N) ** 3
+            self._C[key] = np.rint(C.real)
+        C = self._C[key]
+        m = self.sidx == a
+        return int(np.rint(np.sum(self.wt[m] * C[m])))
+
+
+def bispectrum(gal, ran, geom, bshells, ells=(0, 2, 4), tris=None):
+    """B^(l) for the given triangles (default: all a >= b >= c with N_T > 0)."""
+    g = _pw._geom(geom)
+    N = int(g["N"])
+    F, Fw, sc = _pw.fkp_grids(gal, ran, g, with_w2=True)
+    lmax = max(ells)
+    Fl = _pw.legendre(F, g, lmax=lmax)
+    Fwl = _pw.legendre(Fw, g, lmax=lmax)
+    return bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells, tris)
+
+
+def shell_means(Fl, Fwl, sidx, wt, S, ells):
+    """Shell means of Re F_l F^w_0* and Re F_0 F^w_l* and mode counts."""
+    sel = sidx >= 0
+    si = sidx[sel]
+    w = wt[sel]
+    nm = np.bincount(si, weights=w, minlength=S)
+    sn1, sn2 = {}, {}
+    for l in ells:
+        sn1[l] = np.bincount(si, weights=w * (Fl[l] * np.conj(Fwl[0])).real[sel], minlength=S) / nm
+        sn2[l] = np.bincount(si, weights=w * (Fl[0] * np.conj(Fwl[l])).real[sel], minlength=S) / nm
+    return nm, sn1, sn2
+
+
+def bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells=(0, 2, 4), tris=None):
+    S = bshells[3]
+    sidx, wt = shell_index(N, bshells)
+    _, _, cen = shell_bounds(bshells)
+    nm, sn1, sn2 = shell_means(Fl, Fwl, sidx, wt, S, ells)
+    counter = Counter(N, bshells)
+    cache = {}
+
+    def field(l, s):
+        if (l, s) not in cache:
+            cache[(l, s)] = shell_field(Fl[l], sidx, s, N)
+        return cache[(l, s)]
+
+    all_tris = triangle_list(S) if tris is None else list(tris)
+    out = dict(tri=[], NT=[], centre_closed=[], nmodes_shell=nm, I33=sc["I33"], S3=sc["S3"])
+    for l in ells:
+        out[f"T{l}"] = []
+        out[f"B{l}"] = []
+        out[f"N{l}"] = []
+    N3 = float(N) ** 3
+    for (a, b, c) in all_tris:
+        nt = counter.count(a, b, c)
+        if tris is None and nt == 0:
+            continue
+        out["tri"].append((a, b, c))
+        out["NT"].append(nt)
+        out["centre_closed"].append(bool(cen[b] + cen[c] >= cen[a]))
+        mu12 = np.clip((cen[c] ** 2 - cen[a] ** 2 - cen[b] ** 2) / (2 * cen[a] * cen[b]), -1.0, 1.0)
+        mu13 = np.clip((cen[b] ** 2 - cen[a] ** 2 - cen[c] ** 2) / (2 * cen[a] * cen[c]), -1.0, 1.0)
+        I0b, I0c = field(0, b), field(0, c)
+        for l in ells:
+            T = float(np.sum(field(l, a) * I0b * I0c))
+            pref = 2 * l + 1
+            noise = pref / sc["I33"] * (sn1[l][a] + float(legendre_poly(l, mu12)) * sn2[l][b]
+                                         + float(legendre_poly(l, mu13)) * sn2[l][c])
+            if l == 0:
+                noise -= 2.0 * sc["S3"] / sc["I33"]
+            out[f"T{l}"].append(T)
+            out[f"N{l}"].append(noise)
+            out[f"B{l}"].append(pref * T / (N3 * nt * sc["I33"]) - noise if nt > 0 else float("nan"))
+    for k in list(out):
+        if isinstance(out[k], list):
+            out[k] = np.asarray(out[k])
+    return out

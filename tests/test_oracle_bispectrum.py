@@ -1,0 +1,154 @@
+"""Pins for the FP64 bispectrum oracle: brute-force closed-triangle enumeration
+in k-space (eq. Factorize read right to left), explicit inverse DFTs for the
+shell fields (eq. F_k), exact integer triangle counts (eq. NT) and the thin-shell
+approximation of N_T."""
+import math
+
+import numpy as np
+import pytest
+
+import mockgen
+from oracle import bispectrum as ob
+from oracle import power as op
+
+
+def full_spectrum(Fh, N):
+    """Full-grid F(n) for n in (-N/2, N/2]^3 from the rfft half-spectrum of a
+    real field (F(-n) = F(n)*), as a dict keyed by integer mode tuples."""
+    out = {}
+    n1 = np.fft.fftfreq(N, 1.0 / N).astype(int)
+    for iz in range(N):
+        for iy in range(N):
+            for ix in range(N // 2 + 1):
+                v = Fh[iz, iy, ix]
+                n = (ix, n1[iy], n1[iz])
+                out[n] = v
+                out[(-n[0], -n[1], -n[2])] = np.conj(v)
+    return out
+
+
+def shell_modes(N, bshells, s):
+    lo, hi, _ = ob.shell_bounds(bshells)
+    r = np.arange(-(N // 2) + 1, N // 2)
+    nx, ny, nz = np.meshgrid(r, r, r, indexing="ij")
+    n2 = nx ** 2 + ny ** 2 + nz ** 2
+    m = (n2 >= lo[s] ** 2) & (n2 < hi[s] ** 2) & (n2 > 0)
+    return np.stack([nx[m], ny[m], nz[m]], 1)
+
+
+def test_shell_field_is_inverse_dft():
+    """F_k(x) = sum_{n in shell} F(n) e^{+2 pi i n.x/N}, by explicit summation."""
+    N = 12
+    bs = (2, 2, 2, 2)
+    f = mockgen.rng(2, 1).standard_normal((N, N, N))
+    Fh = op.rfftn(f)
+    sidx, _ = ob.shell_index(N, bs)
+    full = full_spectrum(Fh, N)
+    g = np.arange(N)
+    z, y, x = np.meshgrid(g, g, g, indexing="ij")
+    for s in range(2):
+        got = ob.shell_field(Fh, sidx, s, N)
+        ref = np.zeros((N, N, N), dtype=complex)
+        for n in shell_modes(N, bs, s):
+            ref += full[tuple(n)] * np.exp(2j * np.pi * (n[0] * x + n[1] * y + n[2] * z) / N)
+        assert np.max(np.abs(ref.imag)) < 1e-9
+        assert np.max(np.abs(got - ref.real)) < 1e-10 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N,bs", [(16, (1, 1, 1, 4)), (24, (2, 2, 2, 3))])
+def test_triangle_sums_and_counts_brute_force(N, bs):
+    """sum_x F_a^(l) F_b^(0) F_c^(0) / N^3 equals the k-space sum over closed
+    triangles n1+n2+n3 = 0 with n_i in shells a, b, c (eq. Factorize), and the
+    exact count N_T equals the number of such triangles (eq. NT)."""
+    f = mockgen.rng(3, N).standard_normal((N, N, N))
+    g = dict(N=N, L=100.0, assign=2, origin=(0, 0, 0), observer=(-40.0, 13.0, 77.0), compensate=False)
+    F = op.legendre(f, g, lmax=2)
+    sidx, _ = ob.shell_index(N, bs)
+    full = {l: full_spectrum(F[l], N) for l in (0, 2)}
+    S = bs[3]
+    shells = [shell_modes(N, bs, s) for s in range(S)]
+    lo, hi, _ = ob.shell_bounds(bs)
+    assert 3 * hi[-1] < N  # no aliasing of n1+n2+n3 = 0 mod N
+    counter = ob.Counter(N, bs)
+    for (a, b, c) in ob.triangle_list(S):
+        na, nb = shells[a], shells[b]
+        n3 = -(na[:, None, :] + nb[None, :, :])
+        q = (n3 ** 2).sum(-1)
+        ok = (q >= lo[c] ** 2) & (q < hi[c] ** 2)
+        ia, ib = np.nonzero(ok)
+        nt = ia.size
+        assert counter.count(a, b, c) == nt
+        if nt == 0:
+            continue
+        for l in (0, 2):
+            ref = 0.0
+            for i, j in zip(ia, ib):
+                m3 = tuple(n3[i, j])
+                ref += full[l][tuple(na[i])] * full[0][tuple(nb[j])] * full[0][m3]
+            T = np.sum(ob.shell_field(F[l], sidx, a, N) * ob.shell_field(F[0], sidx, b, N)
+                       * ob.shell_field(F[0], sidx, c, N)) / N ** 3
+            assert abs(ref.imag) < 1e-9 * max(1.0, abs(ref.real))
+            assert abs(T - ref.real) < 1e-9 * max(1.0, abs(ref.real)), (a, b, c, l)
+
+
+def test_counts_symmetric_and_thin_shell():
+    """N_T is symmetric in its shells and approaches 8 pi^2 k1 k2 k3 dk^3
+    (eq. NT, thin-shell form) for wide, well-closed triangles."""
+    N = 48
+    bs = (6, 3, 3, 4)  # centres 6, 9, 12, 15
+    c = ob.Counter(N, bs)
+    assert c.count(3, 2, 1) == c.count(2, 3, 1) == c.count(1, 3, 2)
+    _, _, cen = ob.shell_bounds(bs)
+    for (a, b, cc) in [(3, 2, 1), (2, 2, 1), (3, 3, 3)]:
+        approx = 8 * math.pi ** 2 * cen[a] * cen[b] * cen[cc] * 27
+        assert abs(c.count(a, b, cc) / approx - 1) < 0.12
+
+
+def test_bispectrum_plane_parallel_reduces_to_legendre_weighted_sum():
+    """Observer at infinity: F_l = L_l(mu) F_0, so T^(l) is the closed-triangle
+    sum of L_l(mu_1) F_0 F_0 F_0 (eqs. Bquad, Bispell4 in the plane-parallel
+    limit); checked by brute force on a 16^3 grid."""
+    N = 16
+    bs = (1, 1, 1, 4)
+    f = mockgen.rng(9, 0).standard_normal((N, N, N))
+    g = dict(N=N, L=50.0, assign=2, observer=None, los=(0, 0, 1), compensate=False)
+    F = op.legendre(f, g, lmax=4)
+    full0 = full_spectrum(F[0], N)
+    sidx, _ = ob.shell_index(N, bs)
+    shells = [shell_modes(N, bs, s) for s in range(4)]
+    lo, hi, _ = ob.shell_bounds(bs)
+    a, b, c = 3, 2, 2
+    na, nb = shells[a], shells[b]
+    n3 = -(na[:, None, :] + nb[None, :, :])
+    q = (n3 ** 2).sum(-1)
+    ia, ib = np.nonzero((q >= lo[c] ** 2) & (q < hi[c] ** 2))
+    for l in (2, 4):
+        ref = 0.0
+        for i, j in zip(ia, ib):
+            mu = na[i][2] / np.linalg.norm(na[i])
+            ref += ob.legendre_poly(l, mu) * full0[tuple(na[i])] * full0[tuple(nb[j])] * full0[tuple(n3[i, j])]
+        T = np.sum(ob.shell_field(F[l], sidx, a, N) * ob.shell_field(F[0], sidx, b, N)
+                   * ob.shell_field(F[0], sidx, c, N)) / N ** 3
+        assert abs(T - ref.real) < 1e-9 * max(1.0, abs(ref.real))
+
+
+def test_unclustered_bispectrum_shot_noise_statistical():
+    """Parity unpinned beyond statistics: for a Poisson-sampled unclustered
+    catalog the thin-shell shot-noise subtraction (eqs. Noise0, SNbisp2thin)
+    leaves B_0 consistent with zero, while the raw triangle average is not."""
+    N, L = 32, 400.0
+    bs = (3, 3, 3, 3)
+    geom = dict(N=N, L=L, assign=3, origin=(0.0, 0.0, 0.0), observer=(200.0, 200.0, -600.0), P_fkp=0.0)
+    raws, subs = [], []
+    for seed in range(4):
+        gal = mockgen.uniform_points(30000, 40.0, 360.0, seed=seed, stream=30)
+        ran = mockgen.uniform_points(300000, 40.0, 360.0, seed=seed, stream=31)
+        res = ob.bispectrum(gal, ran, geom, bs, ells=(0,), tris=[(2, 2, 2), (2, 1, 1), (1, 1, 1), (2, 2, 1)])
+        raws.append(res["B0"] + res["N0"])
+        subs.append(res["B0"])
+    raws, subs = np.array(raws), np.array(subs)
+    mean_sub = subs.mean(0)
+    err = subs.std(0, ddof=1) / math.sqrt(len(subs))
+    assert np.all(np.abs(mean_sub) < 4 * err + 1e-3 * np.abs(raws.mean(0)))
+    assert np.all(np.abs(raws.mean(0)) > 3 * err)
+    assert np.all(np.abs(mean_sub) < 0.3 * np.abs(raws.mean(0)))
