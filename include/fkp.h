@@ -1,0 +1,173 @@
+/*
+ * fkp.h - C ABI of the GB300 library for the FFT-based power-spectrum and
+ * bispectrum multipole estimators of Scoccimarro (2015), "Fast Estimators
+ * for Redshift-Space Clustering", arXiv:1506.02729.
+ *
+ * The library computes, for a galaxy catalog and its random catalog:
+ *   P_0, P_2, P_4 (Sec. III.A, eqs. P0_impl, P2_impl, P4_impl) and the
+ *   reduced-FFT hexadecapole P_4b (eqs. P4fast, P4_implb), and
+ *   B_0, B_2, B_4 for closed triangles (Sec. III.B, eqs. BispMono, BispQuad)
+ *   with the thin-shell shot noise of eq. SNbisp2thin and exact triangle
+ *   counts N_T (eq. NT).
+ *
+ * Conventions (the readings the library fixes where the paper is silent):
+ *   - Fourier sign e^{-ik.x}; the DFT phase origin is the box corner.
+ *   - alpha = W_g / W_r (weighted) by default, N_g/N_r on request.
+ *   - x^ (the line of sight) is taken at grid nodes about the observer.
+ *   - CIC (assign = 2) or TSC (assign = 3) with nodes at origin + i*L/N.
+ *   - Modes with any |n_a| = N/2 are excluded from every bin and shell.
+ *   - P bins are half-open [kmin + i dk, kmin + (i+1) dk), decided in FP64.
+ *   - P_4b = [35/2 <|F_2|^2> - 5 <Re F_2 F_0*> - 7/2 <|F_0|^2>] / I_22.
+ *   - I_33 = alpha sum_r nbar^2 w^3.
+ *   - Bispectrum shells: centre (first + s*step) k_f, width width*k_f.
+ *
+ * Errors: every int-returning call returns 0 on success or a negative
+ * FKP_E* code; fkp_last_error() then returns a thread-local message.
+ * Ownership: the caller owns every input array and every output array it
+ * passes; the library owns its device workspaces (allocated when a plan is
+ * created, freed by fkp_plan_destroy).  Input pointers are read only during
+ * the call.  A plan is used by one thread and one stream at a time.
+ */
+#ifndef FKP_H
+#define FKP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FKP_OK = 0,
+  FKP_EINVAL = -1,   /* bad sizes, bins, flags or NULL pointers            */
+  FKP_EGEOM = -2,    /* object too close to the box edge, or shells alias  */
+  FKP_ENOMEM = -3,   /* device allocation failed / over the HBM budget     */
+  FKP_ETIMEOUT = -4, /* a bounded device-side wait gave up                 */
+  FKP_ECUDA = -5,    /* a CUDA runtime call failed                         */
+  FKP_ESTATE = -6    /* call not valid in the plan's state                 */
+};
+
+/* What to compute (bit flags). */
+enum {
+  FKP_P0 = 1, FKP_P2 = 2, FKP_P4 = 4, FKP_P4B = 8,
+  FKP_B0 = 16, FKP_B2 = 32, FKP_B4 = 64
+};
+
+/* One catalog {x_j, w_j, nbar_j} (Sec. III.A, around eq. F0), structure of
+ * arrays of n float32 values.  w may be NULL: then w_j = 1/(1 + nbar_j P_fkp)
+ * (FKP weights).  on_device = 1: device pointers; 0: host pointers (pinned or
+ * pageable), copied in by the call. */
+typedef struct {
+  const float *x, *y, *z, *w, *nbar;
+  int64_t n;
+  int on_device;
+} fkp_catalog_t;
+
+/* Box, grid and observer.  The grid has N^3 nodes at origin + i*L/N.
+ * observer_at_infinity = 1 uses the constant unit vector los as x^.
+ * periodic = 0 rejects objects closer than assign/2 + 1 cells to a box face
+ * (FKP_EGEOM); periodic = 1 wraps node indices mod N.
+ * compensate = 1 divides every mode by prod_a sinc(pi n_a/N)^assign.
+ * alpha_mode: 0 = W_g/W_r, 1 = N_g/N_r. */
+typedef struct {
+  double L;
+  double origin[3];
+  double observer[3];
+  int observer_at_infinity;
+  double los[3];
+  int N;
+  int assign;
+  int compensate;
+  int periodic;
+  double P_fkp;
+  int alpha_mode;
+} fkp_geometry_t;
+
+/* P bins: edges kmin + i*dk, i = 0..nbins (h/Mpc), half-open. */
+typedef struct {
+  double kmin, dk;
+  int nbins;
+} fkp_pbins_t;
+
+/* Bispectrum shells in integer k_f units: shell s holds modes with
+ * c_s - width/2 <= |n| < c_s + width/2, c_s = first + s*step. */
+typedef struct {
+  int first, step, width, nshells;
+} fkp_bshells_t;
+
+/* Power-spectrum results.  Array pointers are caller-allocated host arrays
+ * of nbins entries (any may be NULL to skip).  Scalars are always filled.
+ * P_l follow eqs. P0_impl, P2_impl, P4_impl, P4_implb; mono_raw is
+ * <|F_0|^2>/I_22 before shot-noise subtraction. */
+typedef struct {
+  double *k_eff, *P0, *P2, *P4, *P4b, *mono_raw;
+  int64_t *nmodes;
+  double alpha, I22, I33, N0, N0_fkp, S3, W_g, W_r;
+  double Lab[6];        /* eq. Lab at k = 0, order xx yy zz xy yz zx */
+  int64_t n_gal, n_ran;
+  float timing_ms[8];   /* scalars, assign, xpass, ypass, zpass, bisp ifft, contraction, total */
+} fkp_power_out;
+
+/* Bispectrum results, ntri entries each (caller-allocated host arrays, any
+ * may be NULL).  Triangles are shell triples a >= b >= c (largest side
+ * first) with N_T > 0, in lexicographic (a, b, c) order. */
+typedef struct {
+  int16_t *tri;         /* [ntri][3] */
+  int64_t *NT;          /* exact closed-triangle counts (eq. NT)              */
+  uint8_t *centre_closed; /* 1 when c_b + c_c >= c_a                          */
+  double *B0, *B2, *B4; /* eqs. BispMono, BispQuad (shot noise subtracted)  */
+  double *N0, *N2, *N4; /* thin-shell shot noise of eq. SNbisp2thin          */
+  double *T0, *T2, *T4; /* raw sums sum_x F_a^(l) F_b^(0) F_c^(0) (eq. Factorize) */
+  double I33, S3;
+} fkp_bisp_out;
+
+/* Contraction precision for the triangle sums. */
+enum { FKP_CONTRACT_FP32 = 0, FKP_CONTRACT_BF16X3 = 1 };
+
+/* Context: binds a CUDA device.  hbm_budget_bytes = 0 means no limit.
+ * Returns FKP_EINVAL for a bad device index, FKP_ECUDA on runtime errors. */
+int fkp_context_create(int device, size_t hbm_budget_bytes, void **ctx);
+void fkp_context_destroy(void *ctx);
+
+/* Plan: validates geometry and bins, builds the FP64 bin look-up table
+ * (n^2 -> bin, eq. shell), the twiddle tables and, when B is wanted, the
+ * shell tables; allocates the device workspace.  bshells may be NULL when
+ * no FKP_B* flag is set.  FKP_EGEOM when B is wanted and 3*n_max >= N (the
+ * triangle sum of eq. Factorize would alias). */
+int fkp_plan_create(void *ctx, const fkp_geometry_t *geom, const fkp_pbins_t *pbins,
+                    const fkp_bshells_t *bshells, uint32_t want, void **plan);
+void fkp_plan_destroy(void *plan);
+
+/* Sizes the caller needs for its outputs and the plan's device footprint. */
+int fkp_plan_sizes(const void *plan, int *nbins, int *ntriangles, size_t *workspace_bytes);
+
+/* P_l of one survey (Sec. III.A).  Enqueues every step on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream), then synchronizes it and
+ * fills out.  FKP_EGEOM if an object lies too close to a box face
+ * (non-periodic plans). */
+int fkp_power(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
+              void *cuda_stream, fkp_power_out *out);
+
+/* The same estimator applied to a given real field F(x) (device pointer to
+ * N^3 float32, layout [z][y][x]), with caller-supplied I_22 and N_0.  Test
+ * hook for periodic-box checks. */
+int fkp_power_from_grid(void *plan, const float *F_device, double I22, double N0,
+                        void *cuda_stream, fkp_power_out *out);
+
+/* P_l and B_l of one survey (Sec. III.B).  contraction selects the plain
+ * FP32 path or the BF16 hi/lo tensor-core path. */
+int fkp_bispectrum(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
+                   int contraction, void *cuda_stream, fkp_power_out *pout, fkp_bisp_out *bout);
+
+/* Thread-local message for the last error on this thread. */
+const char *fkp_last_error(void);
+
+/* Library version string. */
+const char *fkp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FKP_H */

@@ -104,7 +104,8 @@ class Survey:
         self._nbar_scale = 1.0
         f = rr ** 2 * self.nbar(rr)
         self._nbar_scale = saved
-        return self.solid_angle() * np.trapezoid(f, rr)
+        trap = getattr(np, "trapezoid", None) or getattr(np, "trapz")
+        return self.solid_angle() * trap(f, rr)
 
     def __post_init__(self):
         self._nbar_scale = 1.0

@@ -1,0 +1,267 @@
+"""Python binding of libfkp.so, the GB300 library for the FKP power-spectrum
+and bispectrum multipole estimators of Scoccimarro (2015).
+
+The binding only marshals arguments: every step of the estimator runs in the
+library's CUDA kernels.  PyTorch tensors (or numpy arrays for host catalogs)
+are passed by pointer.  If the compiled library is missing the import of
+this package still succeeds, but every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfkp.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "fkp.h")
+
+FKP_P0, FKP_P2, FKP_P4, FKP_P4B = 1, 2, 4, 8
+FKP_B0, FKP_B2, FKP_B4 = 16, 32, 64
+FKP_CONTRACT_FP32, FKP_CONTRACT_BF16X3 = 0, 1
+ERRORS = {-1: "FKP_EINVAL", -2: "FKP_EGEOM", -3: "FKP_ENOMEM", -4: "FKP_ETIMEOUT", -5: "FKP_ECUDA",
+          -6: "FKP_ESTATE"}
+EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_plan_destroy", "fkp_plan_sizes",
+           "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version"]
+
+
+class FKPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Catalog(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("w", C.c_void_p), ("nbar", C.c_void_p),
+                ("n", C.c_int64), ("on_device", C.c_int)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("L", C.c_double), ("origin", C.c_double * 3), ("observer", C.c_double * 3),
+                ("observer_at_infinity", C.c_int), ("los", C.c_double * 3), ("N", C.c_int), ("assign", C.c_int),
+                ("compensate", C.c_int), ("periodic", C.c_int), ("P_fkp", C.c_double), ("alpha_mode", C.c_int)]
+
+
+class PBins(C.Structure):
+    _fields_ = [("kmin", C.c_double), ("dk", C.c_double), ("nbins", C.c_int)]
+
+
+class BShells(C.Structure):
+    _fields_ = [("first", C.c_int), ("step", C.c_int), ("width", C.c_int), ("nshells", C.c_int)]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class PowerOut(C.Structure):
+    _fields_ = [("k_eff", _DP), ("P0", _DP), ("P2", _DP), ("P4", _DP), ("P4b", _DP), ("mono_raw", _DP),
+                ("nmodes", C.POINTER(C.c_int64)), ("alpha", C.c_double), ("I22", C.c_double), ("I33", C.c_double),
+                ("N0", C.c_double), ("N0_fkp", C.c_double), ("S3", C.c_double), ("W_g", C.c_double),
+                ("W_r", C.c_double), ("Lab", C.c_double * 6), ("n_gal", C.c_int64), ("n_ran", C.c_int64),
+                ("timing_ms", C.c_float * 8)]
+
+
+class BispOut(C.Structure):
+    _fields_ = [("tri", C.POINTER(C.c_int16)), ("NT", C.POINTER(C.c_int64)), ("centre_closed", C.POINTER(C.c_uint8)),
+                ("B0", _DP), ("B2", _DP), ("B4", _DP), ("N0", _DP), ("N2", _DP), ("N4", _DP),
+                ("T0", _DP), ("T2", _DP), ("T4", _DP), ("I33", C.c_double), ("S3", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.fkp_context_create.argtypes = [C.c_int, C.c_size_t, C.POINTER(vp)]
+        L.fkp_context_destroy.argtypes = [vp]
+        L.fkp_context_destroy.restype = None
+        L.fkp_plan_create.argtypes = [vp, C.POINTER(Geometry), C.POINTER(PBins), C.POINTER(BShells), C.c_uint32,
+                                      C.POINTER(vp)]
+        L.fkp_plan_destroy.argtypes = [vp]
+        L.fkp_plan_destroy.restype = None
+        L.fkp_plan_sizes.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+        L.fkp_power.argtypes = [vp, C.POINTER(Catalog), C.POINTER(Catalog), vp, C.POINTER(PowerOut)]
+        L.fkp_power_from_grid.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.POINTER(PowerOut)]
+        L.fkp_bispectrum.argtypes = [vp, C.POINTER(Catalog), C.POINTER(Catalog), C.c_int, vp, C.POINTER(PowerOut),
+                                     C.POINTER(BispOut)]
+        L.fkp_last_error.restype = C.c_char_p
+        L.fkp_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise FKPError(rc, lib().fkp_last_error().decode())
+
+
+_contexts = {}
+
+
+def context(device=0, budget=0):
+    key = (device, budget)
+    if key not in _contexts:
+        h = C.c_void_p()
+        _check(lib().fkp_context_create(device, budget, C.byref(h)))
+        _contexts[key] = h
+    return _contexts[key]
+
+
+def _ptr(a):
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if a.dtype.__repr__() != "torch.float32" or not a.is_contiguous():
+            raise TypeError("catalog tensors must be contiguous float32")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return arr.ctypes.data, 0
+
+
+def make_catalog(cat):
+    """Catalog struct from a dict with x, y, z, nbar and optional w (torch
+    tensors on one device, or host arrays).  Returns (struct, keepalive)."""
+    keep = []
+    ptrs = {}
+    dev = None
+    n = None
+    for k in ("x", "y", "z", "w", "nbar"):
+        a = cat.get(k)
+        if a is None:
+            ptrs[k] = None
+            continue
+        if not hasattr(a, "data_ptr"):
+            a = np.ascontiguousarray(a, dtype=np.float32)
+        keep.append(a)
+        p, d = _ptr(a)
+        ptrs[k] = p
+        dev = d if dev is None else dev
+        if d != dev:
+            raise ValueError("catalog arrays must all be on the device or all on the host")
+        m = a.shape[0]
+        n = m if n is None else n
+        if m != n:
+            raise ValueError("catalog arrays differ in length")
+    c = Catalog(ptrs["x"], ptrs["y"], ptrs["z"], ptrs["w"], ptrs["nbar"], n or 0, dev or 0)
+    return c, keep
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def geometry(g):
+    """Geometry struct from a dict (keys of mockgen.Survey.geometry() plus
+    optional observer=None/los, compensate, periodic, alpha_mode)."""
+    obs = g.get("observer", (0.0, 0.0, 0.0))
+    inf = obs is None
+    return Geometry(float(g["L"]), (C.c_double * 3)(*g.get("origin", (0.0, 0.0, 0.0))),
+                    (C.c_double * 3)(*((0.0, 0.0, 0.0) if inf else obs)), 1 if inf else 0,
+                    (C.c_double * 3)(*g.get("los", (0.0, 0.0, 1.0))), int(g["N"]), int(g.get("assign", 2)),
+                    1 if g.get("compensate", True) else 0, 1 if g.get("periodic", False) else 0,
+                    float(g.get("P_fkp", 1e4)), int(g.get("alpha_mode", 0)))
+
+
+class Plan:
+    """One geometry, binning and set of outputs; owns the device workspace."""
+
+    def __init__(self, geom, pbins, bshells=None, want=FKP_P0 | FKP_P2 | FKP_P4 | FKP_P4B, device=0, budget=0):
+        self.geom = dict(geom)
+        self.want = want
+        self._g = geometry(geom)
+        self._pb = PBins(float(pbins[0]), float(pbins[1]), int(pbins[2]))
+        self._bs = BShells(*[int(v) for v in bshells]) if bshells is not None else None
+        self._h = C.c_void_p()
+        _check(lib().fkp_plan_create(context(device, budget), C.byref(self._g), C.byref(self._pb),
+                                     C.byref(self._bs) if self._bs is not None else None, want, C.byref(self._h)))
+        nb, nt, ws = C.c_int(), C.c_int(), C.c_size_t()
+        _check(lib().fkp_plan_sizes(self._h, C.byref(nb), C.byref(nt), C.byref(ws)))
+        self.nbins, self.ntri, self.workspace_bytes = nb.value, nt.value, ws.value
+
+    def close(self):
+        if self._h:
+            lib().fkp_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _pout(self):
+        nb = self.nbins
+        arr = {k: np.full(nb, np.nan) for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw")}
+        arr["nmodes"] = np.zeros(nb, dtype=np.int64)
+        o = PowerOut()
+        for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw"):
+            setattr(o, k, arr[k].ctypes.data_as(_DP))
+        o.nmodes = arr["nmodes"].ctypes.data_as(C.POINTER(C.c_int64))
+        return o, arr
+
+    @staticmethod
+    def _scalars(o, arr):
+        for k in ("alpha", "I22", "I33", "N0", "N0_fkp", "S3", "W_g", "W_r", "n_gal", "n_ran"):
+            arr[k] = getattr(o, k)
+        arr["Lab"] = np.array(list(o.Lab))
+        arr["timing_ms"] = np.array(list(o.timing_ms))
+        return arr
+
+    def power(self, gal, ran, stream=None):
+        """P_0, P_2, P_4, P_4b and the scalars for one survey."""
+        cg, k1 = make_catalog(gal)
+        cr, k2 = make_catalog(ran)
+        o, arr = self._pout()
+        _check(lib().fkp_power(self._h, C.byref(cg), C.byref(cr), _stream_handle(stream), C.byref(o)))
+        return self._scalars(o, arr)
+
+    def power_from_grid(self, F, I22=1.0, N0=0.0, stream=None):
+        """The estimator on a given device field F (torch float32 CUDA tensor
+        [N][N][N], layout [z][y][x])."""
+        if not (hasattr(F, "is_cuda") and F.is_cuda and F.is_contiguous()):
+            raise TypeError("F must be a contiguous CUDA float32 tensor")
+        o, arr = self._pout()
+        _check(lib().fkp_power_from_grid(self._h, F.data_ptr(), float(I22), float(N0), _stream_handle(stream),
+                                         C.byref(o)))
+        return self._scalars(o, arr)
+
+    def bispectrum(self, gal, ran, contraction=FKP_CONTRACT_FP32, stream=None):
+        """P_l and B_l (closed triangles a >= b >= c with N_T > 0)."""
+        cg, k1 = make_catalog(gal)
+        cr, k2 = make_catalog(ran)
+        o, parr = self._pout()
+        nt = self.ntri
+        b = {"tri": np.zeros((nt, 3), dtype=np.int16), "NT": np.zeros(nt, dtype=np.int64),
+             "centre_closed": np.zeros(nt, dtype=np.uint8)}
+        for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
+            b[k] = np.full(nt, np.nan)
+        bo = BispOut()
+        bo.tri = b["tri"].ctypes.data_as(C.POINTER(C.c_int16))
+        bo.NT = b["NT"].ctypes.data_as(C.POINTER(C.c_int64))
+        bo.centre_closed = b["centre_closed"].ctypes.data_as(C.POINTER(C.c_uint8))
+        for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
+            setattr(bo, k, b[k].ctypes.data_as(_DP))
+        _check(lib().fkp_bispectrum(self._h, C.byref(cg), C.byref(cr), int(contraction), _stream_handle(stream),
+                                    C.byref(o), C.byref(bo)))
+        b["I33"], b["S3"] = bo.I33, bo.S3
+        return self._scalars(o, parr), b
+
+
+def version():
+    return lib().fkp_version().decode()

@@ -1,0 +1,476 @@
+// fkp_capi.cu - the C ABI of include/fkp.h: contexts, plans (validation,
+// FP64 look-up tables, twiddles, workspace) and the host-side sequencing of
+// the kernels on one CUDA stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fkp.h"
+#include "fkp_internal.h"
+
+using namespace fkp;
+
+// ----------------------------------------------------------------------------
+// errors
+// ----------------------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+int fkp::set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+extern "C" const char* fkp_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char* fkp_version(void) { return "fkp-gb300 0.1 (sm_103a)"; }
+
+#define CK(call)                                                                                \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return set_error(FKP_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ----------------------------------------------------------------------------
+// context
+// ----------------------------------------------------------------------------
+
+extern "C" int fkp_context_create(int device, size_t hbm_budget_bytes, void** out) {
+  if (!out) return set_error(FKP_EINVAL, "fkp_context_create: out is NULL");
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return set_error(FKP_EINVAL, "fkp_context_create: bad device %d", device);
+  CK(cudaSetDevice(device));
+  auto* c = new Context();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device));
+  *out = c;
+  return FKP_OK;
+}
+
+extern "C" void fkp_context_destroy(void* ctx) { delete static_cast<Context*>(ctx); }
+
+// ----------------------------------------------------------------------------
+// plan
+// ----------------------------------------------------------------------------
+
+static bool radix_plan(int n, FftPlan& p) {
+  p.n = n;
+  p.nst = 0;
+  int m = n;
+  auto push = [&](int r) {
+    if (p.nst >= 8) return false;
+    p.radix[p.nst++] = r;
+    return true;
+  };
+  while (m % 8 == 0) { if (!push(8)) return false; m /= 8; }
+  while (m % 4 == 0) { if (!push(4)) return false; m /= 4; }
+  while (m % 2 == 0) { if (!push(2)) return false; m /= 2; }
+  while (m % 5 == 0) { if (!push(5)) return false; m /= 5; }
+  while (m % 3 == 0) { if (!push(3)) return false; m /= 3; }
+  return m == 1;
+}
+
+// Field list and k_z-power groups for multipoles up to lmax (0, 2 or 4).
+// Field (i, j, k) is grid * xh_x^i xh_y^j xh_z^k with i + j + k = ell; group
+// (ell, p) holds the fields with k = p, each with coefficient multinomial
+// ell!/(i! j! k!) (the multiplicities 1, 2 of eq. delta2b and 1, 4, 6, 12 of
+// eq. delta4b) and its k_x^i k_y^j monomial.
+void fkp::build_moments(int lmax, MomentTable& mt) {
+  memset(&mt, 0, sizeof(mt));
+  auto fact = [](int n) { int f = 1; for (int i = 2; i <= n; ++i) f *= i; return f; };
+  int q = 0, g = 0;
+  for (int ell = 0; ell <= lmax; ell += 2) {
+    for (int p = 0; p <= ell; ++p) {
+      mt.g_ell[g] = ell;
+      mt.g_p[g] = p;
+      int nm = 0;
+      for (int j = 0; j <= ell - p; ++j) {
+        const int i = ell - p - j;
+        mt.e[q][0] = (unsigned char)i;
+        mt.e[q][1] = (unsigned char)j;
+        mt.e[q][2] = (unsigned char)p;
+        mt.g_field[g][nm] = q;
+        mt.g_coef[g][nm] = (float)(fact(ell) / (fact(i) * fact(j) * fact(p)));
+        mt.g_ei[g][nm] = (unsigned char)i;
+        mt.g_ej[g][nm] = (unsigned char)j;
+        ++nm;
+        ++q;
+      }
+      mt.g_nmem[g] = nm;
+      ++g;
+    }
+  }
+  mt.nfields = q;
+  mt.ngroups = g;
+}
+
+static bool smooth235(int n) {
+  if (n <= 0) return false;
+  for (int f : {2, 3, 5}) while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+void* fkp::Plan::alloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  buffers.push_back(p);
+  bytes_total += bytes;
+  return p;
+}
+
+fkp::Plan::~Plan() {
+  for (void* p : buffers) cudaFree(p);
+  for (void* p : staging) cudaFree(p);
+  if (h_pinned) cudaFreeHost(h_pinned);
+  for (auto& e : ev) if (e) cudaEventDestroy(e);
+}
+
+extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp_pbins_t* pb,
+                               const fkp_bshells_t* bs, uint32_t want, void** out) {
+  auto* ctx = static_cast<Context*>(vctx);
+  if (!ctx || !geom || !pb || !out) return set_error(FKP_EINVAL, "fkp_plan_create: NULL argument");
+  const int N = geom->N;
+  if (N < 8 || N > 512 || (N & 1) || !smooth235(N))
+    return set_error(FKP_EINVAL, "grid N=%d must be even, 8 <= N <= 512 and a product of 2, 3, 5", N);
+  if (geom->assign != 2 && geom->assign != 3) return set_error(FKP_EINVAL, "assign must be 2 (CIC) or 3 (TSC)");
+  if (!(geom->L > 0)) return set_error(FKP_EINVAL, "box side L must be positive");
+  if (pb->nbins < 1 || pb->nbins > kMaxBins || !(pb->dk > 0) || !(pb->kmin >= 0))
+    return set_error(FKP_EINVAL, "bad P bins (nbins in [1,%d], dk > 0, kmin >= 0)", kMaxBins);
+  const bool wantB = (want & (FKP_B0 | FKP_B2 | FKP_B4)) != 0;
+  if (wantB) {
+    if (!bs || bs->nshells < 1 || bs->nshells > kMaxShells || bs->width < 1 || bs->step < 1 ||
+        bs->first < 1 || 2 * bs->first < bs->width)
+      return set_error(FKP_EINVAL, "bad bispectrum shells");
+    const double nmax = bs->first + (bs->nshells - 1) * (double)bs->step + 0.5 * bs->width;
+    if (3.0 * nmax >= N) return set_error(FKP_EGEOM, "3*n_max = %.1f >= N = %d: triangle sums would alias", 3 * nmax, N);
+    if (nmax >= N / 2) return set_error(FKP_EGEOM, "shells reach the Nyquist plane");
+  }
+  if (geom->observer_at_infinity) {
+    const double l2 = geom->los[0] * geom->los[0] + geom->los[1] * geom->los[1] + geom->los[2] * geom->los[2];
+    if (!(l2 > 0)) return set_error(FKP_EINVAL, "los must be nonzero when the observer is at infinity");
+  }
+  CK(cudaSetDevice(ctx->device));
+  auto* P = new Plan();
+  P->ctx = ctx;
+  P->geom = *geom;
+  P->pb = *pb;
+  if (bs) P->bs = *bs;
+  P->want = want;
+  P->wantB = wantB;
+  int lmax = 0;
+  if (want & (FKP_P2 | FKP_P4B | FKP_B2)) lmax = 2;
+  if (want & (FKP_P4 | FKP_B4)) lmax = 4;
+  P->lmax = lmax;
+  build_moments(lmax, P->mt);
+  if (!radix_plan(N, P->fp)) { delete P; return set_error(FKP_EINVAL, "no radix plan for N=%d", N); }
+
+  // geometry as the kernels see it
+  GeomDev& g = P->g;
+  g.N = N;
+  g.NH = N / 2 + 1;
+  g.H = (float)(geom->L / N);
+  g.invH = (float)(N / geom->L);
+  g.ox = (float)geom->origin[0];
+  g.oy = (float)geom->origin[1];
+  g.oz = (float)geom->origin[2];
+  g.rx = (float)(geom->origin[0] - geom->observer[0]);
+  g.ry = (float)(geom->origin[1] - geom->observer[1]);
+  g.rz = (float)(geom->origin[2] - geom->observer[2]);
+  g.los_inf = geom->observer_at_infinity ? 1 : 0;
+  {
+    const double l = std::sqrt(geom->los[0] * geom->los[0] + geom->los[1] * geom->los[1] + geom->los[2] * geom->los[2]);
+    g.lx = l > 0 ? (float)(geom->los[0] / l) : 0.f;
+    g.ly = l > 0 ? (float)(geom->los[1] / l) : 0.f;
+    g.lz = l > 0 ? (float)(geom->los[2] / l) : 1.f;
+  }
+  g.assign = geom->assign;
+  g.periodic = geom->periodic ? 1 : 0;
+  g.P_fkp = (float)geom->P_fkp;
+  g.alpha_mode = geom->alpha_mode;
+
+  // FP64 tables on the host
+  const double kf = 2.0 * M_PI / geom->L;
+  const int n2max = 3 * (N / 2) * (N / 2);
+  std::vector<short> lut(n2max + 1, -1);
+  double min_gap = 1e300;
+  for (int n2 = 1; n2 <= n2max; ++n2) {
+    const double k = kf * std::sqrt((double)n2);
+    long b = (long)std::floor((k - pb->kmin) / pb->dk);
+    if (b < -1) b = -1;
+    if (b > pb->nbins) b = pb->nbins;
+    while (b >= 0 && k < pb->kmin + pb->dk * b) --b;
+    while (b < pb->nbins && b >= -1 && k >= pb->kmin + pb->dk * (b + 1)) ++b;
+    if (b >= 0 && b < pb->nbins) {
+      lut[n2] = (short)b;
+      const double lo = pb->kmin + pb->dk * b, hi = pb->kmin + pb->dk * (b + 1);
+      min_gap = std::min(min_gap, std::min(std::fabs(k - lo), std::fabs(hi - k)) / k);
+    }
+  }
+  P->min_edge_gap = min_gap;
+  std::vector<float2> tw(N);
+  for (int m = 0; m < N; ++m) {
+    const double a = 2.0 * M_PI * (double)m / (double)N;
+    tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  std::vector<float> winv(3 * N, 1.0f);
+  if (geom->compensate) {
+    for (int i = 0; i < N; ++i) {
+      const int n = i <= N / 2 ? i : i - N;
+      const double t = M_PI * n / N;
+      const double s = n == 0 ? 1.0 : std::sin(t) / t;
+      const double w = std::pow(s, geom->assign);
+      for (int a = 0; a < 3; ++a) winv[a * N + i] = (float)(1.0 / w);
+    }
+  }
+
+  // device workspace
+  const size_t N3 = (size_t)N * N * N;
+  const size_t half = (size_t)N * N * (N / 2 + 1);
+  P->nblk_cat = std::max(1, ctx->nsm * 8);
+  P->nblk_z = yz_tiles(N) * N;
+  bool ok = true;
+  auto A = [&](size_t bytes) { void* p = P->alloc(bytes); if (!p) ok = false; return p; };
+  P->d_grid = (unsigned long long*)A(N3 * 8);
+  if (wantB) P->d_gridw = (unsigned long long*)A(N3 * 8);
+  P->d_S1 = (float2*)A(half * sizeof(float2) * P->mt.nfields);
+  P->d_S2 = (float2*)A(half * sizeof(float2) * P->mt.ngroups);
+  P->d_tw = (float2*)A(sizeof(float2) * N);
+  P->d_lut = (short*)A(sizeof(short) * (n2max + 1));
+  P->d_winv = (float*)A(sizeof(float) * 3 * N);
+  P->d_scpart = (double*)A(sizeof(double) * SC_NSUM * 2 * P->nblk_cat);
+  P->d_labpart = (double*)A(sizeof(double) * LAB_NSUM * P->nblk_cat);
+  P->d_ds = (double*)A(sizeof(double) * (DS_COUNT + LAB_NSUM + 8));
+  P->d_err = (int*)A(sizeof(int) * 4);
+  P->d_zpart = (float*)A(sizeof(float) * BQ_N * pb->nbins * (size_t)P->nblk_z);
+  P->d_zpartc = (int*)A(sizeof(int) * pb->nbins * (size_t)P->nblk_z);
+  P->d_bins = (double*)A(sizeof(double) * BQ_N * pb->nbins);
+  P->d_binc = (long long*)A(sizeof(long long) * pb->nbins);
+  if (!ok) {
+    const size_t tot = P->bytes_total;
+    delete P;
+    return set_error(FKP_ENOMEM, "device allocation failed (plan needs about %.2f GB)", tot / 1e9);
+  }
+  if (ctx->budget && P->bytes_total > ctx->budget) {
+    const size_t tot = P->bytes_total;
+    delete P;
+    return set_error(FKP_ENOMEM, "plan needs %.2f GB, over the HBM budget", tot / 1e9);
+  }
+  if (wantB) {
+    int rc = bisp_plan_init(P);
+    if (rc) { delete P; return rc; }
+  }
+  CK(cudaMemcpy(P->d_tw, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P->d_lut, lut.data(), sizeof(short) * (n2max + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P->d_winv, winv.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice));
+  const size_t hbytes = sizeof(double) * (BQ_N * pb->nbins + pb->nbins + DS_COUNT + LAB_NSUM + 8) + 64;
+  CK(cudaMallocHost(&P->h_pinned, hbytes));
+  for (auto& e : P->ev) CK(cudaEventCreate(&e));
+  *out = P;
+  return FKP_OK;
+}
+
+extern "C" void fkp_plan_destroy(void* plan) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P) return;
+  cudaSetDevice(P->ctx->device);
+  delete P;
+}
+
+extern "C" int fkp_plan_sizes(const void* plan, int* nbins, int* ntri, size_t* ws) {
+  auto* P = static_cast<const Plan*>(plan);
+  if (!P) return set_error(FKP_EINVAL, "NULL plan");
+  if (nbins) *nbins = P->pb.nbins;
+  if (ntri) *ntri = P->ntri;
+  if (ws) *ws = P->bytes_total;
+  return FKP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// catalogs: device views, copying host arrays into plan-owned staging
+// ----------------------------------------------------------------------------
+
+int fkp::stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, cudaStream_t s) {
+  if (!c) return set_error(FKP_EINVAL, "NULL catalog");
+  if (c->n < 0) return set_error(FKP_EINVAL, "negative catalog size");
+  if (c->n > 0 && (!c->x || !c->y || !c->z || !c->nbar))
+    return set_error(FKP_EINVAL, "catalog needs x, y, z and nbar (w may be NULL)");
+  out.n = c->n;
+  if (c->on_device || c->n == 0) {
+    out.x = c->x; out.y = c->y; out.z = c->z; out.w = c->w; out.nbar = c->nbar;
+    return FKP_OK;
+  }
+  const size_t need = (size_t)c->n * sizeof(float) * 5;
+  if (P->staging_bytes[slot] < need) {
+    if (P->staging[slot]) cudaFree(P->staging[slot]);
+    P->staging[slot] = nullptr;
+    P->staging_bytes[slot] = 0;
+    if (cudaMalloc(&P->staging[slot], need) != cudaSuccess)
+      return set_error(FKP_ENOMEM, "cannot stage a host catalog of %lld objects", (long long)c->n);
+    P->staging_bytes[slot] = need;
+  }
+  float* base = static_cast<float*>(P->staging[slot]);
+  const size_t n = (size_t)c->n;
+  const float* src[5] = {c->x, c->y, c->z, c->w, c->nbar};
+  const float* dst[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int a = 0; a < 5; ++a) {
+    if (!src[a]) continue;
+    float* d = base + a * n;
+    CK(cudaMemcpyAsync(d, src[a], n * sizeof(float), cudaMemcpyHostToDevice, s));
+    dst[a] = d;
+  }
+  out.x = dst[0]; out.y = dst[1]; out.z = dst[2]; out.w = dst[3]; out.nbar = dst[4];
+  return FKP_OK;
+}
+
+// ----------------------------------------------------------------------------
+// P_l
+// ----------------------------------------------------------------------------
+
+// Enqueues scalars and gridding of both catalogs into d_grid (and d_gridw).
+int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s) {
+  const int N = P->g.N;
+  const size_t N3 = (size_t)N * N * N;
+  const int nb = P->nblk_cat;
+  auto nblocks = [&](long long n) { return (int)std::max<long long>(1, std::min<long long>(nb, (n + 255) / 256)); };
+  const int nbg = nblocks(gal.n), nbr = nblocks(ran.n);
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
+  CK(cudaEventRecord(P->ev[0], s));
+  CK(launch_scalars(gal, 0, P->g.P_fkp, P->d_scpart, nbg, s));
+  CK(launch_scalars(ran, 1, P->g.P_fkp, P->d_scpart + (size_t)nbg * SC_NSUM, nbr, s));
+  CK(launch_scalars_finalize(P->d_scpart, nbg, nbr, gal.n, ran.n, P->g.alpha_mode, P->d_ds, s));
+  CK(cudaEventRecord(P->ev[1], s));
+  CK(cudaMemsetAsync(P->d_grid, 0, N3 * 8, s));
+  if (P->d_gridw) CK(cudaMemsetAsync(P->d_gridw, 0, N3 * 8, s));
+  const double* obs = P->geom.observer;
+  CK(launch_assign(gal, 0, P->g, obs, P->d_ds, P->d_grid, P->d_gridw, P->d_err, nullptr, nbg, s));
+  CK(launch_assign(ran, 1, P->g, obs, P->d_ds, P->d_grid, P->d_gridw, P->d_err, P->d_labpart, nbr, s));
+  CK(launch_lab_finalize(P->d_labpart, ran.n > 0 ? nbr : 0, P->d_ds + DS_COUNT, s));
+  CK(cudaEventRecord(P->ev[2], s));
+  return FKP_OK;
+}
+
+// Enqueues the three FFT passes, recombination and binning of one base grid.
+int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s) {
+  CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
+  CK(cudaEventRecord(P->ev[3], s));
+  CK(launch_ypass(P->d_S1, P->g, P->mt, P->fp, P->d_tw, P->d_S2, s));
+  CK(cudaEventRecord(P->ev[4], s));
+  ZParams zp;
+  zp.nbins = P->pb.nbins;
+  zp.lmax = P->lmax;
+  zp.kf = (float)(2.0 * M_PI / P->geom.L);
+  zp.lut = P->d_lut;
+  zp.winv = P->d_winv;
+  CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, s));
+  CK(launch_reduce_bins(P->d_zpart, P->d_zpartc, P->nblk_z, P->pb.nbins, P->d_bins, P->d_binc, s));
+  CK(cudaEventRecord(P->ev[5], s));
+  return FKP_OK;
+}
+
+// Copies bins and scalars back, synchronizes and fills out.
+int fkp::finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_scalars, double I22u, double N0u) {
+  const int nb = P->pb.nbins;
+  double* h = static_cast<double*>(P->h_pinned);
+  double* hb = h;
+  long long* hc = reinterpret_cast<long long*>(h + BQ_N * nb);
+  double* hds = h + BQ_N * nb + nb;
+  int* herr = reinterpret_cast<int*>(hds + DS_COUNT + LAB_NSUM + 8);
+  CK(cudaMemcpyAsync(hb, P->d_bins, sizeof(double) * BQ_N * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hc, P->d_binc, sizeof(long long) * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hds, P->d_ds, sizeof(double) * (DS_COUNT + LAB_NSUM), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (have_scalars && herr[0] != 0)
+    return set_error(FKP_EGEOM, "an object lies within assign/2+1 cells of a box face (or is not finite); "
+                                "enlarge the box or set periodic=1 (flags 0x%x)", herr[0]);
+  if (!out) return FKP_OK;
+  double I22 = I22u, N0 = N0u;
+  if (have_scalars) {
+    out->alpha = hds[DS_ALPHA];
+    out->I22 = I22 = hds[DS_I22];
+    out->I33 = hds[DS_I33];
+    out->N0 = N0 = hds[DS_N0];
+    out->N0_fkp = hds[DS_N0FKP];
+    out->S3 = hds[DS_S3];
+    out->W_g = hds[DS_WG];
+    out->W_r = hds[DS_WR];
+    out->n_gal = (int64_t)hds[DS_NG];
+    out->n_ran = (int64_t)hds[DS_NR];
+    for (int a = 0; a < 6; ++a) out->Lab[a] = hds[DS_WR] > 0 ? hds[DS_COUNT + a] / hds[DS_WR] : 0.0;
+  } else {
+    out->alpha = 0; out->I22 = I22; out->I33 = 0; out->N0 = N0; out->N0_fkp = 0; out->S3 = 0;
+    out->W_g = out->W_r = 0; out->n_gal = out->n_ran = 0;
+    for (int a = 0; a < 6; ++a) out->Lab[a] = 0;
+  }
+  for (int b = 0; b < nb; ++b) {
+    const double n = (double)hc[b];
+    const double s00 = hb[BQ_F00 * nb + b], s20 = hb[BQ_F20 * nb + b], s40 = hb[BQ_F40 * nb + b],
+                 s22 = hb[BQ_F22 * nb + b], sk = hb[BQ_K * nb + b];
+    const double nan = std::nan("");
+    if (out->nmodes) out->nmodes[b] = hc[b];
+    if (out->k_eff) out->k_eff[b] = n > 0 ? sk / n : nan;
+    if (out->mono_raw) out->mono_raw[b] = n > 0 ? s00 / n / I22 : nan;
+    if (out->P0) out->P0[b] = n > 0 ? (s00 / n - N0) / I22 : nan;
+    if (out->P2) out->P2[b] = n > 0 && P->lmax >= 2 ? 5.0 * s20 / n / I22 : nan;
+    if (out->P4) out->P4[b] = n > 0 && P->lmax >= 4 ? 9.0 * s40 / n / I22 : nan;
+    if (out->P4b) out->P4b[b] = n > 0 && P->lmax >= 2 ? (17.5 * s22 - 5.0 * s20 - 3.5 * s00) / n / I22 : nan;
+  }
+  float t = 0.f;
+  for (int i = 0; i < 8; ++i) out->timing_ms[i] = 0.f;
+  if (cudaEventElapsedTime(&t, P->ev[0], P->ev[1]) == cudaSuccess) out->timing_ms[0] = t;
+  if (cudaEventElapsedTime(&t, P->ev[1], P->ev[2]) == cudaSuccess) out->timing_ms[1] = t;
+  if (cudaEventElapsedTime(&t, P->ev[2], P->ev[3]) == cudaSuccess) out->timing_ms[2] = t;
+  if (cudaEventElapsedTime(&t, P->ev[3], P->ev[4]) == cudaSuccess) out->timing_ms[3] = t;
+  if (cudaEventElapsedTime(&t, P->ev[4], P->ev[5]) == cudaSuccess) out->timing_ms[4] = t;
+  if (cudaEventElapsedTime(&t, P->ev[0], P->ev[5]) == cudaSuccess) out->timing_ms[7] = t;
+  cudaGetLastError();  // events not recorded on this path leave a benign error
+  return FKP_OK;
+}
+
+extern "C" int fkp_power(void* plan, const fkp_catalog_t* gal, const fkp_catalog_t* ran, void* stream,
+                         fkp_power_out* out) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P) return set_error(FKP_EINVAL, "NULL plan");
+  CK(cudaSetDevice(P->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CatDev g, r;
+  int rc = stage_catalog(P, gal, 0, g, s);
+  if (rc) return rc;
+  rc = stage_catalog(P, ran, 1, r, s);
+  if (rc) return rc;
+  if (r.n == 0) return set_error(FKP_EINVAL, "the random catalog is empty");
+  rc = enqueue_grids(P, g, r, s);
+  if (rc) return rc;
+  rc = enqueue_fft_bin(P, P->d_grid, nullptr, s);
+  if (rc) return rc;
+  return finish_power(P, s, out, true, 0, 0);
+}
+
+extern "C" int fkp_power_from_grid(void* plan, const float* F, double I22, double N0, void* stream,
+                                   fkp_power_out* out) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P || !F) return set_error(FKP_EINVAL, "NULL plan or grid");
+  CK(cudaSetDevice(P->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
+  CK(cudaEventRecord(P->ev[0], s));
+  CK(cudaEventRecord(P->ev[1], s));
+  CK(cudaEventRecord(P->ev[2], s));
+  int rc = enqueue_fft_bin(P, nullptr, F, s);
+  if (rc) return rc;
+  return finish_power(P, s, out, false, I22, N0);
+}

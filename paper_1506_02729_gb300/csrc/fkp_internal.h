@@ -1,0 +1,90 @@
+// fkp_internal.h - host-side structures of the library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/fkp.h"
+#include "fkp_kernels.cuh"
+
+namespace fkp {
+
+struct Context {
+  int device = 0;
+  size_t budget = 0;
+  int nsm = 1;
+};
+
+struct Plan {
+  Context* ctx = nullptr;
+  fkp_geometry_t geom{};
+  fkp_pbins_t pb{};
+  fkp_bshells_t bs{};
+  uint32_t want = 0;
+  bool wantB = false;
+  int lmax = 0;
+  MomentTable mt{};
+  FftPlan fp{};
+  GeomDev g{};
+  double min_edge_gap = 0;
+  int nblk_cat = 0, nblk_z = 0;
+
+  // power workspace
+  unsigned long long *d_grid = nullptr, *d_gridw = nullptr;
+  float2 *d_S1 = nullptr, *d_S2 = nullptr, *d_tw = nullptr;
+  short* d_lut = nullptr;
+  float* d_winv = nullptr;
+  double *d_scpart = nullptr, *d_labpart = nullptr, *d_ds = nullptr;
+  int* d_err = nullptr;
+  float* d_zpart = nullptr;
+  int* d_zpartc = nullptr;
+  double* d_bins = nullptr;
+  long long* d_binc = nullptr;
+
+  // bispectrum workspace and tables
+  int ntri = 0;
+  void* bisp = nullptr;
+
+  // host catalogs staged on the device (slot 0 galaxies, 1 randoms)
+  void* staging[2] = {nullptr, nullptr};
+  size_t staging_bytes[2] = {0, 0};
+  void* h_pinned = nullptr;
+  cudaEvent_t ev[12] = {};
+
+  std::vector<void*> buffers;
+  size_t bytes_total = 0;
+  void* alloc(size_t bytes);
+  ~Plan();
+};
+
+int set_error(int code, const char* fmt, ...);
+void build_moments(int lmax, MomentTable& mt);
+int stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, cudaStream_t s);
+int enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s);
+int enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s);
+int finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_scalars, double I22, double N0);
+int bisp_plan_init(Plan* P);
+void bisp_plan_free(Plan* P);
+
+// launch wrappers (k_power.cu)
+size_t xpass_smem(int N, int nfields);
+size_t yz_smem(int N);
+size_t zpass_smem(int N, int nbins);
+int yz_tiles(int N);
+cudaError_t launch_scalars(const CatDev& c, int is_ran, float Pfkp, double* part, int nblk, cudaStream_t s);
+cudaError_t launch_scalars_finalize(const double* part, int nbg, int nbr, long long ng, long long nr, int amode,
+                                    double* ds, cudaStream_t s);
+cudaError_t launch_assign(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
+                          unsigned long long* grid, unsigned long long* gridw, int* err, double* labpart, int nblk,
+                          cudaStream_t s);
+cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
+cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
+                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s);
+cudaError_t launch_ypass(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+                         const float2* tw, float2* S2, cudaStream_t s);
+cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+                         const float2* tw, const ZParams& zp, float* part, int* partc, cudaStream_t s);
+cudaError_t launch_reduce_bins(const float* part, const int* partc, int nblk, int nbins, double* out,
+                               long long* outc, cudaStream_t s);
+
+}  // namespace fkp

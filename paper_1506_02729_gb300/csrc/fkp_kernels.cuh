@@ -1,0 +1,75 @@
+// fkp_kernels.cuh - parameter blocks and launch wrappers shared by the
+// kernel translation units and the C-ABI host code.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fkp_fft.cuh"
+
+namespace fkp {
+
+constexpr int kMaxFields = 22;   // 1 + 6 + 15 moment fields per base grid
+constexpr int kMaxGroups = 9;    // 1 + 3 + 5 k_z-power groups per base grid
+constexpr int kMaxMembers = 5;   // fields per group
+constexpr int kMaxBins = 512;    // P bins
+constexpr int kMaxShells = 64;   // bispectrum shells
+constexpr double kFixScale = 1099511627776.0;       // 2^40: fixed-point scale of the grids
+constexpr float kFixScaleF = 1099511627776.0f;
+constexpr float kFixInvF = 9.094947017729282379e-13f;  // 2^-40
+
+// Geometry as the kernels see it.
+struct GeomDev {
+  int N, NH;           // grid side, N/2 + 1
+  float H, invH;       // cell size and its inverse
+  float ox, oy, oz;    // origin (box corner)
+  float rx, ry, rz;    // node 0 relative to the observer: origin - observer
+  int los_inf;         // observer at infinity
+  float lx, ly, lz;    // unit line of sight when los_inf
+  int assign;          // 2 CIC, 3 TSC
+  int periodic;
+  float P_fkp;
+  int alpha_mode;
+};
+
+// Moment fields of one base grid: field q is grid * xh_x^e[q][0] xh_y^e[q][1] xh_z^e[q][2].
+// Group g collects the fields of multipole ell with k_z power p:
+// G_g(kx,ky,z) = sum_m coef[m] nx^i ny^j Q~_{field[m]}(kx,ky,z).
+struct MomentTable {
+  int nfields;
+  int ngroups;
+  unsigned char e[kMaxFields][3];
+  int g_ell[kMaxGroups];
+  int g_p[kMaxGroups];
+  int g_nmem[kMaxGroups];
+  int g_field[kMaxGroups][kMaxMembers];
+  float g_coef[kMaxGroups][kMaxMembers];
+  unsigned char g_ei[kMaxGroups][kMaxMembers];
+  unsigned char g_ej[kMaxGroups][kMaxMembers];
+};
+
+// Number of per-block FP64 partial sums the scalar kernels produce.
+// gal: n, sum w, sum w^2, sum w^3 ; ran: n, sum w, sum w^2, sum w^3, sum nbar w^2, sum nbar^2 w^3
+enum { SC_G_W = 0, SC_G_W2, SC_G_W3, SC_R_W, SC_R_W2, SC_R_W3, SC_R_NW2, SC_R_N2W3, SC_NSUM };
+// L^ab partial sums (randoms): sum w xh_a xh_b, order xx yy zz xy yz zx
+enum { LAB_NSUM = 6 };
+// Device scalars written by the finalize kernel (FP64).
+enum { DS_ALPHA = 0, DS_I22, DS_I33, DS_N0, DS_N0FKP, DS_S3, DS_WG, DS_WR, DS_NG, DS_NR, DS_COUNT };
+// Per-bin quantities accumulated by the z-pass.
+enum { BQ_K = 0, BQ_F00, BQ_F20, BQ_F40, BQ_F22, BQ_N };
+
+// z-pass parameters.
+struct ZParams {
+  int nbins;
+  int lmax;          // 0, 2 or 4
+  float kf;          // 2 pi / L
+  const short* lut;  // n^2 -> bin or -1
+  const float* winv; // [3][N]: 1/sinc^p per axis index (ones when not compensating)
+};
+
+// Catalog on the device.
+struct CatDev {
+  const float *x, *y, *z, *w, *nbar;
+  long long n;
+};
+
+}  // namespace fkp

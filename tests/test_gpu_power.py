@@ -1,0 +1,178 @@
+"""GPU parity of the power-spectrum path (C ABI) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import mockgen
+from oracle import power as op
+from tests.helpers import P_TOL, p_errors, to_device
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _fkp():
+    import paper_1506_02729_gb300 as fkp
+    return fkp
+
+
+def _bins_small(L):
+    kf = 2 * math.pi / L
+    return (0.5 * kf, kf, 32)  # bins centred on integer multiples of k_f up to k_N
+
+
+@pytest.fixture(scope="module")
+def small_mock():
+    sv = mockgen.survey_small()
+    gal, ran = mockgen.catalog(sv, 0)
+    return sv, gal, ran
+
+
+def _oracle_power(gal, ran, geom, bins):
+    return op.power(gal, ran, geom, bins)
+
+
+def test_small_survey_matches_oracle(small_mock):
+    """L=1000, 64^3, CIC, octant survey: P_0, P_2, P_4, P_4b, nmodes, k_eff,
+    alpha, I_22, N_0, L^ab against the FP64 oracle."""
+    fkp = _fkp()
+    sv, gal, ran = small_mock
+    geom = sv.geometry()
+    bins = _bins_small(sv.L)
+    ref = _oracle_power(gal, ran, geom, bins)
+    plan = fkp.Plan(geom, bins)
+    got = plan.power(to_device(gal), to_device(ran))
+    assert np.array_equal(got["nmodes"], ref["nmodes"])
+    err = p_errors(got, ref)
+    assert max(err.values()) < P_TOL, err
+    m = ref["nmodes"] > 0
+    assert np.max(np.abs(got["k_eff"][m] / ref["k_eff"][m] - 1)) < 1e-6
+    for k in ("alpha", "I22", "I33", "N0", "N0_fkp", "S3", "W_g", "W_r"):
+        assert abs(got[k] / ref[k] - 1) < 1e-9, k
+    assert np.max(np.abs(got["Lab"] - ref["Lab"])) < 1e-6
+    assert abs(got["Lab"][:3].sum() - 1) < 1e-6
+
+
+@pytest.mark.parametrize("N,assign", [(60, 3), (48, 2), (90, 3)])
+def test_ragged_grids_match_oracle(small_mock, N, assign):
+    """Non-power-of-two grids (radix 2, 3, 5 stages and ragged kx tiles),
+    both assignment orders."""
+    fkp = _fkp()
+    sv0, gal, ran = small_mock
+    sv = mockgen.survey_small(N=N, assign=assign)
+    geom = sv.geometry()
+    kf = 2 * math.pi / sv.L
+    bins = (0.0, 1.7 * kf, 14)
+    ref = _oracle_power(gal, ran, geom, bins)
+    got = fkp.Plan(geom, bins).power(to_device(gal), to_device(ran))
+    assert np.array_equal(got["nmodes"], ref["nmodes"])
+    err = p_errors(got, ref)
+    assert max(err.values()) < P_TOL, err
+
+
+def test_host_catalogs_equal_device_catalogs(small_mock):
+    """The host-pointer path (copies inside the call) gives bitwise the same
+    grid, so the same P_l."""
+    fkp = _fkp()
+    sv, gal, ran = small_mock
+    plan = fkp.Plan(sv.geometry(), _bins_small(sv.L))
+    a = plan.power(gal, ran)
+    b = plan.power(to_device(gal), to_device(ran))
+    for k in ("P0", "P2", "P4", "P4b", "k_eff"):
+        assert np.allclose(a[k], b[k], rtol=1e-6, atol=0, equal_nan=True), k
+    assert a["alpha"] == b["alpha"] and a["I22"] == b["I22"]
+
+
+def test_repeat_runs_agree(small_mock):
+    fkp = _fkp()
+    sv, gal, ran = small_mock
+    plan = fkp.Plan(sv.geometry(), _bins_small(sv.L))
+    g, r = to_device(gal), to_device(ran)
+    a = plan.power(g, r)
+    b = plan.power(g, r)
+    for k in ("P0", "P2", "P4", "P4b"):
+        assert np.allclose(a[k], b[k], rtol=1e-6, atol=0, equal_nan=True), k
+
+
+def test_periodic_kaiser_from_grid():
+    """Plane-parallel field with |F_0|^2 = A(|n|)(1+f mu^2)^2 through
+    fkp_power_from_grid against the oracle on the same float32 field."""
+    fkp = _fkp()
+    N, L, f = 64, 1000.0, 0.7
+
+    def amp(nx, ny, nz):
+        n2 = nx * nx + ny * ny + nz * nz
+        mu2 = np.where(n2 > 0, nz * nz / np.where(n2 > 0, n2, 1), 0.0)
+        return (1.0 + np.sqrt(n2)) ** -1.5 * (1 + f * mu2) ** 2 * 1e6
+
+    field = mockgen.random_phase_field(N, amp, seed=5).astype(np.float32)
+    geom = dict(N=N, L=L, assign=2, observer=None, los=(0, 0, 1), compensate=False, periodic=True)
+    kf = 2 * math.pi / L
+    bins = (0.5 * kf, kf, 31)
+    ref = op.power_from_grid(field.astype(np.float64), geom, bins, I22=1.0, N0=0.0)
+    got = fkp.Plan(geom, bins).power_from_grid(torch.from_numpy(field).cuda(), 1.0, 0.0)
+    assert np.array_equal(got["nmodes"], ref["nmodes"])
+    err = p_errors(got, ref)
+    assert max(err.values()) < P_TOL, err
+
+
+def test_radial_observer_inside_box_from_grid():
+    """Observer inside the box (radial x^ varies over the grid) on a random
+    smooth field: every multipole against the oracle."""
+    fkp = _fkp()
+    N, L = 48, 600.0
+    field = mockgen.random_phase_field(N, lambda nx, ny, nz: 1.0 / (1.0 + nx * nx + ny * ny + nz * nz), seed=8)
+    field = field.astype(np.float32)
+    geom = dict(N=N, L=L, assign=3, origin=(0.0, 0.0, 0.0), observer=(210.0, -90.0, 333.0), compensate=True,
+                periodic=True)
+    kf = 2 * math.pi / L
+    bins = (0.5 * kf, kf, 23)
+    ref = op.power_from_grid(field.astype(np.float64), geom, bins, I22=2.0, N0=0.5)
+    got = fkp.Plan(geom, bins).power_from_grid(torch.from_numpy(field).cuda(), 2.0, 0.5)
+    err = p_errors(got, ref)
+    assert max(err.values()) < P_TOL, err
+
+
+def test_object_near_box_face_is_rejected():
+    fkp = _fkp()
+    sv = mockgen.survey_small()
+    gal = mockgen.uniform_points(100, 100.0, 500.0, seed=1)
+    ran = mockgen.uniform_points(1000, 100.0, 500.0, seed=2)
+    gal["x"][5] = sv.origin[0] + 0.5 * sv.L / sv.N  # inside the first cell
+    plan = fkp.Plan(sv.geometry(), _bins_small(sv.L))
+    with pytest.raises(fkp.FKPError) as e:
+        plan.power(to_device(gal), to_device(ran))
+    assert e.value.code == -2
+    # the plan stays usable afterwards
+    gal["x"][5] = 300.0
+    plan.power(to_device(gal), to_device(ran))
+
+
+def test_bad_plans_are_rejected():
+    fkp = _fkp()
+    with pytest.raises(fkp.FKPError):
+        fkp.Plan(dict(L=100.0, N=98), (0.0, 0.1, 4))  # 98 = 2 * 7^2
+    with pytest.raises(fkp.FKPError):
+        fkp.Plan(dict(L=100.0, N=64, assign=4), (0.0, 0.1, 4))
+    with pytest.raises(fkp.FKPError):
+        fkp.Plan(dict(L=100.0, N=64), (0.0, -0.1, 4))
+
+
+@pytest.mark.slow
+def test_boss_512_full_size_matches_oracle():
+    """The benchmark workload: L=3500, 512^3, TSC, 7e5 galaxies and 3.5e7
+    randoms, 60 bins of 0.005 h/Mpc: every P_l bin against the FP64 oracle."""
+    fkp = _fkp()
+    sv = mockgen.survey_boss()
+    gal, ran = mockgen.catalog(sv, 0)
+    geom = sv.geometry()
+    bins = (0.0, 0.005, 60)
+    got = fkp.Plan(geom, bins).power(to_device(gal), to_device(ran))
+    ref = op.power(gal, ran, geom, bins)
+    assert np.array_equal(got["nmodes"], ref["nmodes"])
+    err = p_errors(got, ref)
+    assert max(err.values()) < P_TOL, err
+    for k in ("alpha", "I22", "N0"):
+        assert abs(got[k] / ref[k] - 1) < 1e-9, k
