@@ -255,7 +255,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   P->d_labpart = (double*)A(sizeof(double) * LAB_NSUM * P->nblk_cat);
   P->d_ds = (double*)A(sizeof(double) * (DS_COUNT + LAB_NSUM + 8));
   P->d_err = (int*)A(sizeof(int) * 4);
-  P->d_zpart = (float*)A(sizeof(float) * BQ_N * pb->nbins * (size_t)P->nblk_z);
+  P->d_zpart = (double*)A(sizeof(double) * BQ_N * pb->nbins * (size_t)P->nblk_z);
   P->d_zpartc = (int*)A(sizeof(int) * pb->nbins * (size_t)P->nblk_z);
   P->d_bins = (double*)A(sizeof(double) * BQ_N * pb->nbins);
   P->d_binc = (long long*)A(sizeof(long long) * pb->nbins);

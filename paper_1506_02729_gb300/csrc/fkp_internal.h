@@ -36,7 +36,7 @@ struct Plan {
   float* d_winv = nullptr;
   double *d_scpart = nullptr, *d_labpart = nullptr, *d_ds = nullptr;
   int* d_err = nullptr;
-  float* d_zpart = nullptr;
+  double* d_zpart = nullptr;
   int* d_zpartc = nullptr;
   double* d_bins = nullptr;
   long long* d_binc = nullptr;
@@ -83,8 +83,8 @@ cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const Ge
 cudaError_t launch_ypass(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, float2* S2, cudaStream_t s);
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, const ZParams& zp, float* part, int* partc, cudaStream_t s);
-cudaError_t launch_reduce_bins(const float* part, const int* partc, int nblk, int nbins, double* out,
+                         const float2* tw, const ZParams& zp, double* part, int* partc, cudaStream_t s);
+cudaError_t launch_reduce_bins(const double* part, const int* partc, int nblk, int nbins, double* out,
                                long long* outc, cudaStream_t s);
 
 }  // namespace fkp

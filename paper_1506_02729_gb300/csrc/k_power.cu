@@ -371,22 +371,22 @@ __global__ void __launch_bounds__(kTX * kRuns) k_ypass(const float2* __restrict_
 // ----------------------------------------------------------------------------
 // z-pass: for a tile of TX consecutive kx at one ky, FFT each group along z,
 // recombine F_0, F_2, F_4, compensate and bin.  Each thread owns a run of
-// consecutive k_z, along which |n| is monotone, and adds a run's sums to the
-// block's bins only when the bin changes.
+// consecutive k_z, along which |n| is monotone, sums a run in FP32 and adds
+// it to the block's FP64 bins (shared-memory atomics) only when the bin changes.
 // Per-block partials: part[(q * nbins + b) * nblk + blk], counts likewise.
 // ----------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
                                                        FftPlan fp, const float2* __restrict__ tw, ZParams zp,
-                                                       float* __restrict__ part, int* __restrict__ partc) {
+                                                       double* __restrict__ part, int* __restrict__ partc) {
   extern __shared__ float2 smem[];
   const int N = g.N, NH = g.NH;
   const int pst = N + 1;
   float2* A = smem;
   float2* B = smem + kTX * pst;
-  float* sb = reinterpret_cast<float*>(B + kTX * pst);  // [BQ_N][nbins]
+  double* sb = reinterpret_cast<double*>(B + kTX * pst);  // [BQ_N][nbins]
   int* sc = reinterpret_cast<int*>(sb + BQ_N * zp.nbins);
-  for (int t = threadIdx.x; t < BQ_N * zp.nbins; t += blockDim.x) sb[t] = 0.f;
+  for (int t = threadIdx.x; t < BQ_N * zp.nbins; t += blockDim.x) sb[t] = 0.0;
   for (int t = threadIdx.x; t < zp.nbins; t += blockDim.x) sc[t] = 0;
   const int ky = blockIdx.y;
   const int kx0 = blockIdx.x * kTX;
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict_
       if (curb >= 0) {
         atomicAdd(sc + curb, cnt);
 #pragma unroll
-        for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * zp.nbins + curb, acc[q]);
+        for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * zp.nbins + curb, (double)acc[q]);
       }
       curb = b;
       cnt = 0;
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict_
   if (curb >= 0) {
     atomicAdd(sc + curb, cnt);
 #pragma unroll
-    for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * zp.nbins + curb, acc[q]);
+    for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * zp.nbins + curb, (double)acc[q]);
   }
   __syncthreads();
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
@@ -508,14 +508,14 @@ __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict_
 }
 
 // One block per (quantity, bin): fixed-order FP64 tree sum over the blocks.
-__global__ void __launch_bounds__(256) k_reduce_bins(const float* __restrict__ part, const int* __restrict__ partc,
+__global__ void __launch_bounds__(256) k_reduce_bins(const double* __restrict__ part, const int* __restrict__ partc,
                                                      int nblk, int nbins, double* __restrict__ out,
                                                      long long* __restrict__ outc) {
   __shared__ double sh[32];
   const int row = blockIdx.x;  // 0 .. BQ_N*nbins (float rows) then nbins (count rows)
   double s = 0.0;
   if (row < BQ_N * nbins) {
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += (double)part[(size_t)row * nblk + b];
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)row * nblk + b];
     s = block_sum_f64(s, sh);
     if (threadIdx.x == 0) out[row] = s;
   } else {
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(256) k_reduce_bins(const float* __restrict__ p
 
 size_t xpass_smem(int N, int nfields) { return sizeof(float2) * (((N + 1) / 2) + 1 + 2 * ((nfields + 1) / 2) * N); }
 size_t yz_smem(int N) { return sizeof(float2) * 2 * kTX * (N + 1); }
-size_t zpass_smem(int N, int nbins) { return yz_smem(N) + sizeof(float) * BQ_N * nbins + sizeof(int) * nbins; }
+size_t zpass_smem(int N, int nbins) { return yz_smem(N) + sizeof(double) * BQ_N * nbins + sizeof(int) * nbins; }
 int yz_tiles(int N) { return (N / 2 + 1 + kTX - 1) / kTX; }
 
 cudaError_t launch_scalars(const CatDev& c, int is_ran, float Pfkp, double* part, int nblk, cudaStream_t s) {
@@ -591,7 +591,7 @@ cudaError_t launch_ypass(const float2* S1, const GeomDev& g, const MomentTable& 
 }
 
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, const ZParams& zp, float* part, int* partc, cudaStream_t s) {
+                         const float2* tw, const ZParams& zp, double* part, int* partc, cudaStream_t s) {
   const size_t sm = zpass_smem(g.N, zp.nbins);
   cudaFuncSetAttribute(k_zpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(yz_tiles(g.N), g.N);
@@ -599,7 +599,7 @@ cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& 
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_bins(const float* part, const int* partc, int nblk, int nbins, double* out, long long* outc,
+cudaError_t launch_reduce_bins(const double* part, const int* partc, int nblk, int nbins, double* out, long long* outc,
                                cudaStream_t s) {
   k_reduce_bins<<<(BQ_N + 1) * nbins, 256, 0, s>>>(part, partc, nblk, nbins, out, outc);
   return cudaGetLastError();
