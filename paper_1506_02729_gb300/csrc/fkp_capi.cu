@@ -133,6 +133,7 @@ void* fkp::Plan::alloc(size_t bytes) {
 }
 
 fkp::Plan::~Plan() {
+  bisp_plan_free(this);
   for (void* p : buffers) cudaFree(p);
   for (void* p : staging) cudaFree(p);
   if (h_pinned) cudaFreeHost(h_pinned);
@@ -375,6 +376,12 @@ int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf,
   zp.kf = (float)(2.0 * M_PI / P->geom.L);
   zp.lut = P->d_lut;
   zp.winv = P->d_winv;
+  zp.mode = 0;
+  zp.nshells = 0;
+  zp.nsh2 = 0;
+  zp.slut = nullptr;
+  zp.E = nullptr;
+  zp.mm = 0;
   CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, s));
   CK(launch_reduce_bins(P->d_zpart, P->d_zpartc, P->nblk_z, P->pb.nbins, P->d_bins, P->d_binc, s));
   CK(cudaEventRecord(P->ev[5], s));

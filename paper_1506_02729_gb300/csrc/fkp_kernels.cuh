@@ -56,6 +56,9 @@ enum { LAB_NSUM = 6 };
 enum { DS_ALPHA = 0, DS_I22, DS_I33, DS_N0, DS_N0FKP, DS_S3, DS_WG, DS_WR, DS_NG, DS_NR, DS_COUNT };
 // Per-bin quantities accumulated by the z-pass.
 enum { BQ_K = 0, BQ_F00, BQ_F20, BQ_F40, BQ_F22, BQ_N };
+// Per-shell quantities of the F^w pass (same slots): Re F_0 F^w_0*, Re F_2 F^w_0*,
+// Re F_4 F^w_0*, Re F_0 F^w_2*, Re F_0 F^w_4*.
+enum { SQ_00 = 0, SQ_20, SQ_40, SQ_02, SQ_04 };
 
 // z-pass parameters.
 struct ZParams {
@@ -64,6 +67,12 @@ struct ZParams {
   float kf;          // 2 pi / L
   const short* lut;  // n^2 -> bin or -1
   const float* winv; // [3][N]: 1/sinc^p per axis index (ones when not compensating)
+  int mode;          // 0 P bins, 1 P bins + export, 2 F^w shell sums
+  int nshells;
+  int nsh2;          // slut covers n^2 < nsh2
+  const signed char* slut;  // n^2 -> shell or -1
+  float2* E;         // [3][2mm+1][2mm+1][mm+1]: F_0, F_2, F_4 on the shells
+  int mm;            // largest |n_a| inside the outermost shell
 };
 
 // Catalog on the device.

@@ -1,16 +1,506 @@
 // k_bisp.cu - the bispectrum hot path (Sec. III.B of the paper).
+//
+//   counts     exact N_T (eq. NT) by integer enumeration of closed triangles,
+//              one block per cubic-symmetry orbit of q_1 (48-element group),
+//   export     F_0, F_2, F_4 on the shells (z-pass MODE 1, k_power.cu),
+//   shot noise shell means of Re F_l F^w_0* and Re F_0 F^w_l* (z-pass MODE 2)
+//              for the thin-shell form of eq. SNbisp2thin,
+//   shell IFFT F_k^(l)(x) = sum_{q in shell} F_l(q) e^{+iq.x} (eq. F_k): pruned
+//              z and y passes over |n_a| <= mm, then a complex-to-real x pass,
+//   contract   T^(l)(a,b,c) = sum_x F_a^(l) F_b^(0) F_c^(0) (eq. Factorize) in
+//              FP32 with compensated accumulation, FP64 across x slices,
+//   finalize   B^(l) = (2l+1) T^(l) / (N^3 N_T I_33) - N^(l) (eqs. BispMono,
+//              BispQuad) on the host in FP64.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "fkp_internal.h"
 
 namespace fkp {
 
-int bisp_plan_init(Plan* P) {
-  (void)P;
-  return set_error(FKP_ESTATE, "bispectrum path not built in this version");
+constexpr int kCTK = 64;     // x points per contraction chunk
+constexpr int kCA = 16;      // outputs (values of a) per contraction thread
+
+struct ContractItem {
+  int ell_i, b, c, a0, na;
+  int out[kCA];              // triangle index * 3 + ell_i, or -1
+};
+
+struct BispState {
+  int S = 0, mm = 0, nsh2 = 0;
+  std::vector<double> lo, hi, cen;
+  std::vector<int> ta, tb, tc;       // triangle list
+  std::vector<long long> nt;         // exact counts
+  std::vector<unsigned char> cc;     // centre closed
+  int nl = 0;                        // number of multipoles computed (1..3)
+  int ells[3] = {0, 2, 4};
+  std::vector<ContractItem> items;
+  int nslices = 1;
+  long long slice_len = 0;
+  // device
+  signed char* d_slut = nullptr;
+  float2* d_E = nullptr;
+  float2* d_T1 = nullptr;
+  float2* d_T2 = nullptr;
+  float* d_I = nullptr;
+  ContractItem* d_items = nullptr;
+  double* d_cpart = nullptr;
+  double* d_T = nullptr;
+  double* d_spart = nullptr;
+  int* d_spartc = nullptr;
+  double* d_shell = nullptr;
+  long long* d_shellc = nullptr;
+};
+
+__device__ __forceinline__ int wrap_mode(int n, int N) { return n < 0 ? n + N : n; }
+
+// ----------------------------------------------------------------------------
+// exact triangle counts
+// ----------------------------------------------------------------------------
+
+// ball: packed n2 vectors with |n2| < hi_max sorted by |n2|^2 (shells are
+// contiguous); shb: their shells.  reps: q1 orbit representatives
+// (nx >= ny >= nz >= 0) with shell and orbit size.  For each rep and each n2
+// in shells <= shell(q1), c = shell(|q1 + n2|); counts with c <= b add the
+// orbit size to N_T(a, b, c).
+__global__ void __launch_bounds__(256) k_counts(const int* __restrict__ ball, const signed char* __restrict__ shb,
+                                                const int* __restrict__ upto, const int4* __restrict__ reps,
+                                                const signed char* __restrict__ slut, int nsq, int S,
+                                                unsigned long long* __restrict__ NT) {
+  extern __shared__ int sh_counts[];  // [S][S]
+  signed char* sl = reinterpret_cast<signed char*>(sh_counts + S * S);
+  for (int t = threadIdx.x; t < S * S; t += blockDim.x) sh_counts[t] = 0;
+  for (int t = threadIdx.x; t < nsq; t += blockDim.x) sl[t] = slut[t];
+  __syncthreads();
+  const int4 r = reps[blockIdx.x];
+  const int a = r.w & 0xff, orbit = r.w >> 8;
+  const int lim = upto[a];
+  for (int i = threadIdx.x; i < lim; i += blockDim.x) {
+    const int p = __ldg(ball + i);
+    const int x = ((p >> 20) & 1023) - 512, y = ((p >> 10) & 1023) - 512, z = (p & 1023) - 512;
+    const int sx = r.x + x, sy = r.y + y, sz = r.z + z;
+    const int q = sx * sx + sy * sy + sz * sz;
+    if (q < nsq) {
+      const int c = sl[q];
+      const int b = __ldg(shb + i);
+      if (c >= 0 && c <= b) atomicAdd(sh_counts + b * S + c, 1);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < S * S; t += blockDim.x) {
+    const int v = sh_counts[t];
+    if (v) atomicAdd(NT + (size_t)a * S * S + t, (unsigned long long)v * (unsigned long long)orbit);
+  }
 }
 
-void bisp_plan_free(Plan* P) { (void)P; }
+// ----------------------------------------------------------------------------
+// shell-filtered inverse FFTs (eq. F_k)
+// ----------------------------------------------------------------------------
+
+constexpr int kBX = 8;      // columns per tile
+constexpr int kBR = 32;     // threads per column
+constexpr int kBRL = 16;    // points per thread (N <= 512)
+
+struct ShellParams {
+  int N, mm, S, nsh2;
+  const signed char* slut;
+};
+
+// z pass: pencils (kx, ky') of shell s, filled from E on the shell, inverse
+// transformed along z.  T1 layout [s][z][ky'][kx], ky' = ny + mm.
+__global__ void __launch_bounds__(kBX * kBR) k_shell_z(const float2* __restrict__ E, ShellParams sp, FftPlan fp,
+                                                       const float2* __restrict__ tw, float2* __restrict__ T1) {
+  extern __shared__ float2 smem[];
+  const int N = sp.N, mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1;
+  const int pst = N + 1;
+  float2* A = smem;
+  float2* B = smem + kBX * pst;
+  const int s = blockIdx.z, kyp = blockIdx.y, kx0 = blockIdx.x * kBX;
+  const int tw_ = min(kBX, m1 - kx0);
+  const int ny = kyp - mm;
+  for (int t = threadIdx.x; t < kBX * pst; t += blockDim.x) A[t] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int t = threadIdx.x; t < w2 * kBX; t += blockDim.x) {
+    const int kzp = t / kBX, cc = t - kzp * kBX;
+    if (cc < tw_) {
+      const int kx = kx0 + cc, nz = kzp - mm;
+      const int n2 = kx * kx + ny * ny + nz * nz;
+      if (n2 < sp.nsh2 && sp.slut[n2] == s)
+        A[cc * pst + wrap_mode(nz, N)] = E[((size_t)kzp * w2 + kyp) * m1 + kx];
+    }
+  }
+  __syncthreads();
+  const float2* R = fft_smem<1>(A, B, kBX, pst, fp, tw);
+  const int c = threadIdx.x % kBX, run = threadIdx.x / kBX;
+  const int rl = (N + kBR - 1) / kBR;
+  if (c < tw_) {
+#pragma unroll
+    for (int i = 0; i < kBRL; ++i) {
+      const int z = run * rl + i;
+      if (i < rl && z < N) T1[(((size_t)s * N + z) * w2 + kyp) * m1 + kx0 + c] = R[c * pst + z];
+    }
+  }
+}
+
+// y pass: pencils (z, kx) over ky'.  T2 layout [s][z][y][kx].
+__global__ void __launch_bounds__(kBX * kBR) k_shell_y(const float2* __restrict__ T1, ShellParams sp, FftPlan fp,
+                                                       const float2* __restrict__ tw, float2* __restrict__ T2) {
+  extern __shared__ float2 smem[];
+  const int N = sp.N, mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1;
+  const int pst = N + 1;
+  float2* A = smem;
+  float2* B = smem + kBX * pst;
+  const int s = blockIdx.z, z = blockIdx.y, kx0 = blockIdx.x * kBX;
+  const int tw_ = min(kBX, m1 - kx0);
+  for (int t = threadIdx.x; t < kBX * pst; t += blockDim.x) A[t] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int t = threadIdx.x; t < w2 * kBX; t += blockDim.x) {
+    const int kyp = t / kBX, cc = t - kyp * kBX;
+    if (cc < tw_) A[cc * pst + wrap_mode(kyp - mm, N)] = T1[(((size_t)s * N + z) * w2 + kyp) * m1 + kx0 + cc];
+  }
+  __syncthreads();
+  const float2* R = fft_smem<1>(A, B, kBX, pst, fp, tw);
+  const int c = threadIdx.x % kBX, run = threadIdx.x / kBX;
+  const int rl = (N + kBR - 1) / kBR;
+  if (c < tw_) {
+#pragma unroll
+    for (int i = 0; i < kBRL; ++i) {
+      const int y = run * rl + i;
+      if (i < rl && y < N) T2[(((size_t)s * N + z) * N + y) * m1 + kx0 + c] = R[c * pst + y];
+    }
+  }
+}
+
+// x pass, complex to real: two rows per complex pencil.  The half spectrum
+// k = 0..mm (zero above) is extended by Hermitian symmetry; the DC term keeps
+// its real part only.  I layout [s][z][y][x] (one multipole).
+constexpr int kXP = 8;  // pencils (row pairs) per block iteration
+
+__global__ void __launch_bounds__(256) k_shell_x(const float2* __restrict__ T2, ShellParams sp, FftPlan fp,
+                                                 const float2* __restrict__ tw, float* __restrict__ I) {
+  extern __shared__ float2 smem[];
+  const int N = sp.N, m1 = sp.mm + 1;
+  float2* A = smem;
+  float2* B = smem + kXP * N;
+  const long long rows = (long long)sp.S * N * N;
+  const long long pairs = rows / 2;
+  for (long long g0 = (long long)blockIdx.x * kXP; g0 < pairs; g0 += (long long)gridDim.x * kXP) {
+    const int np = (int)(pairs - g0 < kXP ? pairs - g0 : kXP);
+    for (int t = threadIdx.x; t < kXP * N; t += blockDim.x) {
+      const int p = t / N, k = t - p * N;
+      float2 v = make_float2(0.f, 0.f);
+      if (p < np) {
+        const long long r0 = 2 * (g0 + p);
+        const float2* h0 = T2 + r0 * m1;
+        const float2* h1 = h0 + m1;
+        float2 x1 = make_float2(0.f, 0.f), x2 = make_float2(0.f, 0.f);
+        if (k == 0) {
+          x1 = make_float2(h0[0].x, 0.f);
+          x2 = make_float2(h1[0].x, 0.f);
+        } else if (k <= sp.mm) {
+          x1 = h0[k];
+          x2 = h1[k];
+        } else if (k >= N - sp.mm) {
+          const float2 a = h0[N - k], b = h1[N - k];
+          x1 = make_float2(a.x, -a.y);
+          x2 = make_float2(b.x, -b.y);
+        }
+        v = make_float2(x1.x - x2.y, x1.y + x2.x);  // x1 + i x2
+      }
+      A[t] = v;
+    }
+    __syncthreads();
+    const float2* R = fft_smem<1>(A, B, kXP, N, fp, tw);
+    for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
+      const int p = t / N, x = t - p * N;
+      const long long r0 = 2 * (g0 + p);
+      const float2 v = R[p * N + x];
+      I[r0 * N + x] = v.x;
+      I[(r0 + 1) * N + x] = v.y;
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// triangle contraction, FP32 on CUDA cores
+// ----------------------------------------------------------------------------
+
+// blockIdx.x: item block (one item per thread), blockIdx.y: x slice.  The
+// slice's fields are staged in shared memory kCTK points at a time, layout
+// [x][field] with an odd row stride.  Each thread forms I_b I_c once per x
+// and multiplies it into up to kCA values of a.  Chunk sums are FP32 and
+// are added to compensated per-output accumulators.
+__global__ void __launch_bounds__(256) k_contract_fp32(const float* __restrict__ I, long long N3, int nf, int S,
+                                                       const ContractItem* __restrict__ items, int nitems,
+                                                       long long slice_len, double* __restrict__ part, int nout) {
+  extern __shared__ float ism[];
+  const int stride = nf | 1;
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  ContractItem item;
+  if (it < nitems) item = items[it];
+  else { item.na = 0; item.b = 0; item.c = 0; item.a0 = 0; item.ell_i = 0; }
+  const int base = item.ell_i * S + item.a0;
+  float ks[kCA], kc[kCA];
+#pragma unroll
+  for (int i = 0; i < kCA; ++i) { ks[i] = 0.f; kc[i] = 0.f; }
+  const long long x0 = (long long)blockIdx.y * slice_len;
+  const long long x1 = (N3 < x0 + slice_len) ? N3 : x0 + slice_len;
+  for (long long xc = x0; xc < x1; xc += kCTK) {
+    const int nx = (int)(x1 - xc < kCTK ? x1 - xc : kCTK);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nf * kCTK; t += blockDim.x) {
+      const int f = t / kCTK, xl = t - f * kCTK;
+      ism[xl * stride + f] = xl < nx ? __ldg(I + (size_t)f * N3 + xc + xl) : 0.f;
+    }
+    __syncthreads();
+    if (item.na > 0) {
+      float cs[kCA];
+#pragma unroll
+      for (int i = 0; i < kCA; ++i) cs[i] = 0.f;
+      for (int xl = 0; xl < kCTK; ++xl) {
+        const float* row = ism + xl * stride;
+        const float p = row[item.b] * row[item.c];
+#pragma unroll
+        for (int i = 0; i < kCA; ++i)
+          if (i < item.na) cs[i] = fmaf(row[base + i], p, cs[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < kCA; ++i) {
+        const float y = cs[i] - kc[i];
+        const float t = ks[i] + y;
+        kc[i] = (t - ks[i]) - y;
+        ks[i] = t;
+      }
+    }
+  }
+  if (it < nitems) {
+#pragma unroll
+    for (int i = 0; i < kCA; ++i)
+      if (i < item.na && item.out[i] >= 0)
+        part[(size_t)blockIdx.y * nout + item.out[i]] = (double)ks[i] - (double)kc[i];
+  }
+}
+
+__global__ void k_reduce_slices(const double* __restrict__ part, int nslices, int nout, double* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double s = 0.0;
+  for (int k = 0; k < nslices; ++k) s += part[(size_t)k * nout + o];
+  out[o] = s;
+}
+
+// ----------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------
+
+#define BCK(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return set_error(FKP_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static int pack(int x, int y, int z) { return ((x + 512) << 20) | ((y + 512) << 10) | (z + 512); }
+
+// Exact closed-triangle counts for shells lo_s <= |n| < hi_s (k_f units).
+static int compute_counts(BispState& st, cudaStream_t s, std::vector<long long>& NT) {
+  const int S = st.S;
+  const double hmax = st.hi[S - 1];
+  const int R = (int)std::ceil(hmax);
+  struct Pt { int n2, x, y, z; };
+  std::vector<Pt> ball;
+  for (int x = -R; x <= R; ++x)
+    for (int y = -R; y <= R; ++y)
+      for (int z = -R; z <= R; ++z) {
+        const int n2 = x * x + y * y + z * z;
+        if (n2 > 0 && n2 < st.nsh2) ball.push_back({n2, x, y, z});
+      }
+  std::vector<signed char> slut(st.nsh2 > 0 ? st.nsh2 : 1, -1);
+  for (int q = 1; q < st.nsh2; ++q)
+    for (int k = 0; k < S; ++k)
+      if (q >= st.lo[k] * st.lo[k] && q < st.hi[k] * st.hi[k]) { slut[q] = (signed char)k; break; }
+  std::vector<Pt> pts;
+  for (auto& p : ball) if (slut[p.n2] >= 0) pts.push_back(p);
+  std::stable_sort(pts.begin(), pts.end(), [](const Pt& a, const Pt& b) { return a.n2 < b.n2; });
+  std::vector<int> packed(pts.size());
+  std::vector<signed char> shb(pts.size());
+  std::vector<int> upto(S, 0);
+  for (size_t i = 0; i < pts.size(); ++i) {
+    packed[i] = pack(pts[i].x, pts[i].y, pts[i].z);
+    shb[i] = slut[pts[i].n2];
+  }
+  for (int k = 0; k < S; ++k) {
+    int c = 0;
+    for (size_t i = 0; i < pts.size(); ++i) if (shb[i] <= k) c = (int)i + 1;
+    upto[k] = c;
+  }
+  // orbit representatives x >= y >= z >= 0 and orbit sizes (signs x permutations)
+  std::vector<int4> reps;
+  for (int x = 0; x <= R; ++x)
+    for (int y = 0; y <= x; ++y)
+      for (int z = 0; z <= y; ++z) {
+        const int n2 = x * x + y * y + z * z;
+        if (n2 == 0 || n2 >= st.nsh2 || slut[n2] < 0) continue;
+        const int nz = (x != 0) + (y != 0) + (z != 0);
+        int perms = (x == y && y == z) ? 1 : ((x == y || y == z) ? 3 : 6);
+        const int orbit = (1 << nz) * perms;
+        reps.push_back(make_int4(x, y, z, (orbit << 8) | slut[n2]));
+      }
+  // the largest query |q1 + n2|^2 < (2 hmax)^2; entries past nsh2 are outside every shell
+  const int nsq = st.nsh2;
+  int *d_ball = nullptr, *d_upto = nullptr;
+  signed char *d_shb = nullptr, *d_sl = nullptr;
+  int4* d_reps = nullptr;
+  unsigned long long* d_NT = nullptr;
+  const size_t nt3 = (size_t)S * S * S;
+  BCK(cudaMalloc(&d_ball, sizeof(int) * std::max<size_t>(1, packed.size())));
+  BCK(cudaMalloc(&d_shb, std::max<size_t>(1, shb.size())));
+  BCK(cudaMalloc(&d_upto, sizeof(int) * S));
+  BCK(cudaMalloc(&d_reps, sizeof(int4) * std::max<size_t>(1, reps.size())));
+  BCK(cudaMalloc(&d_sl, slut.size()));
+  BCK(cudaMalloc(&d_NT, sizeof(unsigned long long) * nt3));
+  BCK(cudaMemcpyAsync(d_ball, packed.data(), sizeof(int) * packed.size(), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(d_shb, shb.data(), shb.size(), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(d_upto, upto.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(d_reps, reps.data(), sizeof(int4) * reps.size(), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemcpyAsync(d_sl, slut.data(), slut.size(), cudaMemcpyHostToDevice, s));
+  BCK(cudaMemsetAsync(d_NT, 0, sizeof(unsigned long long) * nt3, s));
+  const size_t sm = sizeof(int) * S * S + slut.size();
+  BCK(cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  if (!reps.empty()) k_counts<<<(unsigned)reps.size(), 256, sm, s>>>(d_ball, d_shb, d_upto, d_reps, d_sl, nsq, S, d_NT);
+  BCK(cudaGetLastError());
+  std::vector<unsigned long long> h(nt3);
+  BCK(cudaMemcpyAsync(h.data(), d_NT, sizeof(unsigned long long) * nt3, cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
+  cudaFree(d_ball); cudaFree(d_shb); cudaFree(d_upto); cudaFree(d_reps); cudaFree(d_sl); cudaFree(d_NT);
+  NT.assign(nt3, 0);
+  for (size_t i = 0; i < nt3; ++i) NT[i] = (long long)h[i];
+  return FKP_OK;
+}
+
+// Exact counts depend on the shells only (the grid is large enough that
+// n1 + n2 + n3 = 0 mod N means = 0), so they are cached per shell set.
+static std::mutex g_count_mu;
+static std::map<std::vector<int>, std::vector<long long>> g_count_cache;
+
+int bisp_plan_init(Plan* P) {
+  auto* st = new BispState();
+  P->bisp = st;
+  const fkp_bshells_t& bs = P->bs;
+  if (bs.step < bs.width) return set_error(FKP_EINVAL, "bispectrum shells must not overlap (step >= width)");
+  const int S = st->S = bs.nshells;
+  const int N = P->g.N;
+  for (int s = 0; s < S; ++s) {
+    const double c = bs.first + (double)s * bs.step;
+    st->cen.push_back(c);
+    st->lo.push_back(c - 0.5 * bs.width);
+    st->hi.push_back(c + 0.5 * bs.width);
+  }
+  const double hmax = st->hi[S - 1];
+  st->nsh2 = (int)std::ceil(hmax * hmax);
+  st->mm = (int)std::ceil(hmax) - 1;
+  while ((double)(st->mm + 1) * (st->mm + 1) < hmax * hmax) ++st->mm;
+  st->nl = 1;
+  if (P->want & FKP_B2) st->nl = 2;
+  if (P->want & FKP_B4) st->nl = 3;
+  if (st->nl > 1 && P->lmax < 2 * (st->nl - 1)) return set_error(FKP_EINVAL, "internal: lmax too small");
+
+  cudaStream_t s0 = nullptr;
+  std::vector<int> key = {bs.first, bs.step, bs.width, bs.nshells};
+  std::vector<long long> NT;
+  {
+    std::lock_guard<std::mutex> lk(g_count_mu);
+    auto itc = g_count_cache.find(key);
+    if (itc != g_count_cache.end()) NT = itc->second;
+  }
+  if (NT.empty()) {
+    int rc = compute_counts(*st, s0, NT);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_count_mu);
+    g_count_cache[key] = NT;
+  }
+  for (int a = 0; a < S; ++a)
+    for (int b = 0; b <= a; ++b)
+      for (int c = 0; c <= b; ++c) {
+        const long long n = NT[((size_t)a * S + b) * S + c];
+        if (n <= 0) continue;
+        st->ta.push_back(a);
+        st->tb.push_back(b);
+        st->tc.push_back(c);
+        st->nt.push_back(n);
+        st->cc.push_back(st->cen[b] + st->cen[c] >= st->cen[a] ? 1 : 0);
+      }
+  const int ntri = P->ntri = (int)st->ta.size();
+  // contraction items: for each multipole and pair (b >= c), the values of a
+  // with N_T > 0 in runs of kCA
+  std::map<long long, int> tindex;
+  for (int t = 0; t < ntri; ++t) tindex[((long long)st->ta[t] * S + st->tb[t]) * S + st->tc[t]] = t;
+  for (int li = 0; li < st->nl; ++li)
+    for (int b = 0; b < S; ++b)
+      for (int c = 0; c <= b; ++c) {
+        int amin = -1, amax = -1;
+        for (int a = b; a < S; ++a)
+          if (tindex.count(((long long)a * S + b) * S + c)) { if (amin < 0) amin = a; amax = a; }
+        if (amin < 0) continue;
+        for (int a0 = amin; a0 <= amax; a0 += kCA) {
+          ContractItem it;
+          it.ell_i = li; it.b = b; it.c = c; it.a0 = a0; it.na = std::min(kCA, amax - a0 + 1);
+          for (int i = 0; i < kCA; ++i) {
+            auto f = tindex.find(((long long)(a0 + i) * S + b) * S + c);
+            it.out[i] = (i < it.na && f != tindex.end()) ? f->second * 3 + li : -1;
+          }
+          st->items.push_back(it);
+        }
+      }
+  const long long N3 = (long long)N * N * N;
+  const int iblocks = std::max<int>(1, ((int)st->items.size() + 255) / 256);
+  st->nslices = std::max(1, (P->ctx->nsm * 8) / iblocks);
+  st->slice_len = ((N3 + st->nslices - 1) / st->nslices + kCTK - 1) / kCTK * kCTK;
+  st->nslices = (int)((N3 + st->slice_len - 1) / st->slice_len);
+
+  // shell LUT (n^2 -> shell), the same rule as the counts
+  std::vector<signed char> slut(st->nsh2, -1);
+  for (int q = 1; q < st->nsh2; ++q)
+    for (int k = 0; k < S; ++k)
+      if (q >= st->lo[k] * st->lo[k] && q < st->hi[k] * st->hi[k]) { slut[q] = (signed char)k; break; }
+
+  const int mm = st->mm, w2 = 2 * mm + 1, m1 = mm + 1;
+  bool ok = true;
+  auto A = [&](size_t bytes) { void* p = P->alloc(bytes); if (!p) ok = false; return p; };
+  st->d_slut = (signed char*)A(st->nsh2);
+  st->d_E = (float2*)A(sizeof(float2) * 3 * (size_t)w2 * w2 * m1);
+  st->d_T1 = (float2*)A(sizeof(float2) * (size_t)S * N * w2 * m1);
+  st->d_T2 = (float2*)A(sizeof(float2) * (size_t)S * N * N * m1);
+  st->d_I = (float*)A(sizeof(float) * (size_t)st->nl * S * N3);
+  st->d_items = (ContractItem*)A(sizeof(ContractItem) * std::max<size_t>(1, st->items.size()));
+  st->d_cpart = (double*)A(sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * 3);
+  st->d_T = (double*)A(sizeof(double) * std::max(1, ntri) * 3);
+  st->d_spart = (double*)A(sizeof(double) * BQ_N * S * (size_t)P->nblk_z);
+  st->d_spartc = (int*)A(sizeof(int) * S * (size_t)P->nblk_z);
+  st->d_shell = (double*)A(sizeof(double) * BQ_N * S);
+  st->d_shellc = (long long*)A(sizeof(long long) * S);
+  if (!ok) return set_error(FKP_ENOMEM, "device allocation failed for the bispectrum workspace (%.2f GB in plan)",
+                            P->bytes_total / 1e9);
+  if (P->ctx->budget && P->bytes_total > P->ctx->budget)
+    return set_error(FKP_ENOMEM, "plan needs %.2f GB, over the HBM budget", P->bytes_total / 1e9);
+  BCK(cudaMemcpy(st->d_slut, slut.data(), st->nsh2, cudaMemcpyHostToDevice));
+  if (!st->items.empty())
+    BCK(cudaMemcpy(st->d_items, st->items.data(), sizeof(ContractItem) * st->items.size(), cudaMemcpyHostToDevice));
+  BCK(cudaMemset(st->d_cpart, 0, sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * 3));
+  return FKP_OK;
+}
+
+void bisp_plan_free(Plan* P) {
+  delete static_cast<BispState*>(P->bisp);
+  P->bisp = nullptr;
+}
 
 }  // namespace fkp
 
@@ -18,6 +508,140 @@ using namespace fkp;
 
 extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_catalog_t* ran, int contraction,
                               void* stream, fkp_power_out* pout, fkp_bisp_out* bout) {
-  (void)plan; (void)gal; (void)ran; (void)contraction; (void)stream; (void)pout; (void)bout;
-  return set_error(FKP_ESTATE, "bispectrum path not built in this version");
+  auto* P = static_cast<Plan*>(plan);
+  if (!P) return set_error(FKP_EINVAL, "NULL plan");
+  if (!P->wantB || !P->bisp) return set_error(FKP_ESTATE, "plan was created without FKP_B* flags");
+  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3)
+    return set_error(FKP_EINVAL, "unknown contraction mode %d", contraction);
+  if (contraction == FKP_CONTRACT_BF16X3) return set_error(FKP_ESTATE, "BF16 hi/lo contraction not available");
+  auto* st = static_cast<BispState*>(P->bisp);
+  BCK(cudaSetDevice(P->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CatDev g, r;
+  int rc = stage_catalog(P, gal, 0, g, s);
+  if (rc) return rc;
+  rc = stage_catalog(P, ran, 1, r, s);
+  if (rc) return rc;
+  if (r.n == 0) return set_error(FKP_EINVAL, "the random catalog is empty");
+  rc = enqueue_grids(P, g, r, s);
+  if (rc) return rc;
+  const int N = P->g.N, S = st->S, mm = st->mm;
+  ZParams zp;
+  zp.nbins = P->pb.nbins;
+  zp.lmax = P->lmax;
+  zp.kf = (float)(2.0 * M_PI / P->geom.L);
+  zp.lut = P->d_lut;
+  zp.winv = P->d_winv;
+  zp.nshells = S;
+  zp.nsh2 = st->nsh2;
+  zp.slut = st->d_slut;
+  zp.E = st->d_E;
+  zp.mm = mm;
+  // F: P bins and export on the shells
+  BCK(launch_xpass(P->d_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
+  BCK(cudaEventRecord(P->ev[3], s));
+  BCK(launch_ypass(P->d_S1, P->g, P->mt, P->fp, P->d_tw, P->d_S2, s));
+  BCK(cudaEventRecord(P->ev[4], s));
+  zp.mode = 1;
+  BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, s));
+  BCK(launch_reduce_bins(P->d_zpart, P->d_zpartc, P->nblk_z, P->pb.nbins, P->d_bins, P->d_binc, s));
+  BCK(cudaEventRecord(P->ev[5], s));
+  // F^w: shell sums against the exported F_l
+  BCK(launch_xpass(P->d_gridw, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
+  BCK(launch_ypass(P->d_S1, P->g, P->mt, P->fp, P->d_tw, P->d_S2, s));
+  zp.mode = 2;
+  BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, st->d_spart, st->d_spartc, s));
+  BCK(launch_reduce_bins(st->d_spart, st->d_spartc, P->nblk_z, S, st->d_shell, st->d_shellc, s));
+  BCK(cudaEventRecord(P->ev[6], s));
+  // shell IFFTs
+  ShellParams sp{N, mm, S, st->nsh2, st->d_slut};
+  const int m1 = mm + 1, w2 = 2 * mm + 1;
+  const size_t smz = sizeof(float2) * 2 * kBX * (N + 1);
+  const size_t smx = sizeof(float2) * 2 * kXP * N;
+  BCK(cudaFuncSetAttribute(k_shell_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
+  BCK(cudaFuncSetAttribute(k_shell_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
+  BCK(cudaFuncSetAttribute(k_shell_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx));
+  const long long N3 = (long long)N * N * N;
+  const size_t es = (size_t)w2 * w2 * m1;
+  for (int li = 0; li < st->nl; ++li) {
+    k_shell_z<<<dim3((m1 + kBX - 1) / kBX, w2, S), kBX * kBR, smz, s>>>(st->d_E + li * es, sp, P->fp, P->d_tw,
+                                                                        st->d_T1);
+    BCK(cudaGetLastError());
+    k_shell_y<<<dim3((m1 + kBX - 1) / kBX, N, S), kBX * kBR, smz, s>>>(st->d_T1, sp, P->fp, P->d_tw, st->d_T2);
+    BCK(cudaGetLastError());
+    k_shell_x<<<P->ctx->nsm * 4, 256, smx, s>>>(st->d_T2, sp, P->fp, P->d_tw, st->d_I + (size_t)li * S * N3);
+    BCK(cudaGetLastError());
+  }
+  BCK(cudaEventRecord(P->ev[7], s));
+  // contraction
+  const int ntri = P->ntri, nout = std::max(1, ntri) * 3;
+  if (!st->items.empty()) {
+    const int nf = st->nl * S;
+    const size_t smc = sizeof(float) * (size_t)kCTK * (nf | 1);
+    BCK(cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+    const int iblocks = ((int)st->items.size() + 255) / 256;
+    k_contract_fp32<<<dim3(iblocks, st->nslices), 256, smc, s>>>(st->d_I, N3, nf, S, st->d_items,
+                                                                 (int)st->items.size(), st->slice_len, st->d_cpart,
+                                                                 nout);
+    BCK(cudaGetLastError());
+    k_reduce_slices<<<(nout + 255) / 256, 256, 0, s>>>(st->d_cpart, st->nslices, nout, st->d_T);
+    BCK(cudaGetLastError());
+  }
+  BCK(cudaEventRecord(P->ev[8], s));
+  std::vector<double> T(nout, 0.0), sh(BQ_N * S);
+  std::vector<long long> shc(S);
+  BCK(cudaMemcpyAsync(T.data(), st->d_T, sizeof(double) * nout, cudaMemcpyDeviceToHost, s));
+  BCK(cudaMemcpyAsync(sh.data(), st->d_shell, sizeof(double) * BQ_N * S, cudaMemcpyDeviceToHost, s));
+  BCK(cudaMemcpyAsync(shc.data(), st->d_shellc, sizeof(long long) * S, cudaMemcpyDeviceToHost, s));
+  rc = finish_power(P, s, pout, true, 0, 0);
+  if (rc) return rc;
+  float t = 0.f;
+  if (pout) {
+    if (cudaEventElapsedTime(&t, P->ev[6], P->ev[7]) == cudaSuccess) pout->timing_ms[5] = t;
+    if (cudaEventElapsedTime(&t, P->ev[7], P->ev[8]) == cudaSuccess) pout->timing_ms[6] = t;
+    if (cudaEventElapsedTime(&t, P->ev[0], P->ev[8]) == cudaSuccess) pout->timing_ms[7] = t;
+  }
+  // scalars for the finalize
+  double hds[DS_COUNT];
+  BCK(cudaMemcpy(hds, P->d_ds, sizeof(double) * DS_COUNT, cudaMemcpyDeviceToHost));
+  const double I33 = hds[DS_I33], S3 = hds[DS_S3];
+  if (!bout) return FKP_OK;
+  bout->I33 = I33;
+  bout->S3 = S3;
+  auto L = [](int l, double mu) {
+    return l == 0 ? 1.0 : (l == 2 ? 0.5 * (3 * mu * mu - 1) : (35 * mu * mu * mu * mu - 30 * mu * mu + 3) / 8.0);
+  };
+  const double N3d = (double)N3;
+  for (int t = 0; t < ntri; ++t) {
+    const int a = st->ta[t], b = st->tb[t], c = st->tc[t];
+    if (bout->tri) { bout->tri[3 * t] = (int16_t)a; bout->tri[3 * t + 1] = (int16_t)b; bout->tri[3 * t + 2] = (int16_t)c; }
+    if (bout->NT) bout->NT[t] = st->nt[t];
+    if (bout->centre_closed) bout->centre_closed[t] = st->cc[t];
+    const double ca = st->cen[a], cb = st->cen[b], cc = st->cen[c];
+    const double mu12 = std::max(-1.0, std::min(1.0, (cc * cc - ca * ca - cb * cb) / (2 * ca * cb)));
+    const double mu13 = std::max(-1.0, std::min(1.0, (cb * cb - ca * ca - cc * cc) / (2 * ca * cc)));
+    for (int li = 0; li < 3; ++li) {
+      const int l = 2 * li;
+      double* Bp = li == 0 ? bout->B0 : (li == 1 ? bout->B2 : bout->B4);
+      double* Np = li == 0 ? bout->N0 : (li == 1 ? bout->N2 : bout->N4);
+      double* Tp = li == 0 ? bout->T0 : (li == 1 ? bout->T2 : bout->T4);
+      if (li >= st->nl) {
+        if (Bp) Bp[t] = std::nan("");
+        if (Np) Np[t] = std::nan("");
+        if (Tp) Tp[t] = std::nan("");
+        continue;
+      }
+      // shell means: SQ_00 = <Re F0 Fw0*>, SQ_20/40 = <Re F_l Fw0*>, SQ_02/04 = <Re F0 Fw_l*>
+      auto mean = [&](int q, int sI) { return shc[sI] > 0 ? sh[q * S + sI] / (double)shc[sI] : 0.0; };
+      const int q1 = li == 0 ? SQ_00 : (li == 1 ? SQ_20 : SQ_40);
+      const int q2 = li == 0 ? SQ_00 : (li == 1 ? SQ_02 : SQ_04);
+      double noise = (2 * l + 1) / I33 * (mean(q1, a) + L(l, mu12) * mean(q2, b) + L(l, mu13) * mean(q2, c));
+      if (l == 0) noise -= 2.0 * S3 / I33;
+      const double Tv = T[3 * t + li];
+      if (Tp) Tp[t] = Tv;
+      if (Np) Np[t] = noise;
+      if (Bp) Bp[t] = (2 * l + 1) * Tv / (N3d * (double)st->nt[t] * I33) - noise;
+    }
+  }
+  return FKP_OK;
 }

@@ -376,6 +376,11 @@ __global__ void __launch_bounds__(kTX * kRuns) k_ypass(const float2* __restrict_
 // Per-block partials: part[(q * nbins + b) * nblk + blk], counts likewise.
 // ----------------------------------------------------------------------------
 
+// MODE 0: P bins.  MODE 1: P bins and export of F_0, F_2, F_4 on the
+// bispectrum shells into the compact cube E.  MODE 2 (the w^2-weighted field
+// F^w): per-shell sums of Re F_l F^w_0* and Re F_0 F^w_l* (thin-shell shot
+// noise of eq. SNbisp2thin) with F_l read back from E.
+template <int MODE>
 __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
                                                        FftPlan fp, const float2* __restrict__ tw, ZParams zp,
                                                        double* __restrict__ part, int* __restrict__ partc) {
@@ -384,10 +389,11 @@ __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict_
   const int pst = N + 1;
   float2* A = smem;
   float2* B = smem + kTX * pst;
-  double* sb = reinterpret_cast<double*>(B + kTX * pst);  // [BQ_N][nbins]
-  int* sc = reinterpret_cast<int*>(sb + BQ_N * zp.nbins);
-  for (int t = threadIdx.x; t < BQ_N * zp.nbins; t += blockDim.x) sb[t] = 0.0;
-  for (int t = threadIdx.x; t < zp.nbins; t += blockDim.x) sc[t] = 0;
+  const int nkey = MODE == 2 ? zp.nshells : zp.nbins;
+  double* sb = reinterpret_cast<double*>(B + kTX * pst);  // [BQ_N][nkey]
+  int* sc = reinterpret_cast<int*>(sb + BQ_N * nkey);
+  for (int t = threadIdx.x; t < BQ_N * nkey; t += blockDim.x) sb[t] = 0.0;
+  for (int t = threadIdx.x; t < nkey; t += blockDim.x) sc[t] = 0;
   const int ky = blockIdx.y;
   const int kx0 = blockIdx.x * kTX;
   const int tw_ = min(kTX, NH - kx0);
@@ -453,27 +459,45 @@ __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict_
     if (colok && rowok && i < rl && kz < N && kz != N / 2) {
       const int nzv = signed_mode(kz, N);
       const int n2 = kx * kx + nyv * nyv + nzv * nzv;
-      b = n2 > 0 ? zp.lut[n2] : -1;
-      if (b >= 0) {
+      const int sh = (MODE != 0 && n2 < zp.nsh2) ? (int)zp.slut[n2] : -1;
+      b = MODE == 2 ? sh : (n2 > 0 ? zp.lut[n2] : -1);
+      if (b >= 0 || sh >= 0) {
         const float wc = wxy * zp.winv[2 * N + kz];
         const float fn2 = (float)n2;
         const float2 F0 = make_float2(f0[i].x * wc, f0[i].y * wc);
-        vals[BQ_K] = zp.kf * sqrtf(fn2);
-        vals[BQ_F00] = F0.x * F0.x + F0.y * F0.y;
-        vals[BQ_F20] = 0.f;
-        vals[BQ_F40] = 0.f;
-        vals[BQ_F22] = 0.f;
+        float2 F2 = make_float2(0.f, 0.f), F4 = make_float2(0.f, 0.f);
         if (zp.lmax >= 2) {
           const float i2 = 1.0f / fn2;
-          const float2 F2 = make_float2(wc * (1.5f * s2[i].x * i2 - 0.5f * f0[i].x),
-                                        wc * (1.5f * s2[i].y * i2 - 0.5f * f0[i].y));
-          vals[BQ_F20] = F2.x * F0.x + F2.y * F0.y;
-          vals[BQ_F22] = F2.x * F2.x + F2.y * F2.y;
+          F2 = make_float2(wc * (1.5f * s2[i].x * i2 - 0.5f * f0[i].x), wc * (1.5f * s2[i].y * i2 - 0.5f * f0[i].y));
           if (zp.lmax >= 4) {
             const float i4 = i2 * i2;
-            const float2 F4 = make_float2(4.375f * wc * s4[i].x * i4 - 2.5f * F2.x - 0.875f * F0.x,
-                                          4.375f * wc * s4[i].y * i4 - 2.5f * F2.y - 0.875f * F0.y);
-            vals[BQ_F40] = F4.x * F0.x + F4.y * F0.y;
+            F4 = make_float2(4.375f * wc * s4[i].x * i4 - 2.5f * F2.x - 0.875f * F0.x,
+                             4.375f * wc * s4[i].y * i4 - 2.5f * F2.y - 0.875f * F0.y);
+          }
+        }
+        if (MODE != 2) {
+          vals[BQ_K] = zp.kf * sqrtf(fn2);
+          vals[BQ_F00] = F0.x * F0.x + F0.y * F0.y;
+          vals[BQ_F20] = F2.x * F0.x + F2.y * F0.y;
+          vals[BQ_F40] = F4.x * F0.x + F4.y * F0.y;
+          vals[BQ_F22] = F2.x * F2.x + F2.y * F2.y;
+        }
+        if (MODE != 0 && sh >= 0) {
+          const int w2 = 2 * zp.mm + 1;
+          const size_t e = ((size_t)(nzv + zp.mm) * w2 + (nyv + zp.mm)) * (zp.mm + 1) + kx;
+          const size_t es = (size_t)w2 * w2 * (zp.mm + 1);
+          if (MODE == 1) {
+            zp.E[e] = F0;
+            zp.E[es + e] = F2;
+            zp.E[2 * es + e] = F4;
+          } else {
+            // here F0, F2, F4 are the Legendre fields of F^w; E holds those of F
+            const float2 E0 = zp.E[e], E2 = zp.E[es + e], E4 = zp.E[2 * es + e];
+            vals[SQ_00] = E0.x * F0.x + E0.y * F0.y;
+            vals[SQ_20] = E2.x * F0.x + E2.y * F0.y;
+            vals[SQ_40] = E4.x * F0.x + E4.y * F0.y;
+            vals[SQ_02] = E0.x * F2.x + E0.y * F2.y;
+            vals[SQ_04] = E0.x * F4.x + E0.y * F4.y;
           }
         }
       }
@@ -482,7 +506,7 @@ __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict_
       if (curb >= 0) {
         atomicAdd(sc + curb, cnt);
 #pragma unroll
-        for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * zp.nbins + curb, (double)acc[q]);
+        for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, (double)acc[q]);
       }
       curb = b;
       cnt = 0;
@@ -498,13 +522,13 @@ __global__ void __launch_bounds__(kTX * kRuns) k_zpass(const float2* __restrict_
   if (curb >= 0) {
     atomicAdd(sc + curb, cnt);
 #pragma unroll
-    for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * zp.nbins + curb, (double)acc[q]);
+    for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, (double)acc[q]);
   }
   __syncthreads();
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   const int nblk = gridDim.x * gridDim.y;
-  for (int t = threadIdx.x; t < BQ_N * zp.nbins; t += blockDim.x) part[(size_t)t * nblk + blk] = sb[t];
-  for (int t = threadIdx.x; t < zp.nbins; t += blockDim.x) partc[(size_t)t * nblk + blk] = sc[t];
+  for (int t = threadIdx.x; t < BQ_N * nkey; t += blockDim.x) part[(size_t)t * nblk + blk] = sb[t];
+  for (int t = threadIdx.x; t < nkey; t += blockDim.x) partc[(size_t)t * nblk + blk] = sc[t];
 }
 
 // One block per (quantity, bin): fixed-order FP64 tree sum over the blocks.
@@ -592,10 +616,18 @@ cudaError_t launch_ypass(const float2* S1, const GeomDev& g, const MomentTable& 
 
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, const ZParams& zp, double* part, int* partc, cudaStream_t s) {
-  const size_t sm = zpass_smem(g.N, zp.nbins);
-  cudaFuncSetAttribute(k_zpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = zpass_smem(g.N, zp.mode == 2 ? zp.nshells : zp.nbins);
   dim3 grid(yz_tiles(g.N), g.N);
-  k_zpass<<<grid, kTX * kRuns, sm, s>>>(S2, g, mt, fp, tw, zp, part, partc);
+  if (zp.mode == 0) {
+    cudaFuncSetAttribute(k_zpass<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_zpass<0><<<grid, kTX * kRuns, sm, s>>>(S2, g, mt, fp, tw, zp, part, partc);
+  } else if (zp.mode == 1) {
+    cudaFuncSetAttribute(k_zpass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_zpass<1><<<grid, kTX * kRuns, sm, s>>>(S2, g, mt, fp, tw, zp, part, partc);
+  } else {
+    cudaFuncSetAttribute(k_zpass<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_zpass<2><<<grid, kTX * kRuns, sm, s>>>(S2, g, mt, fp, tw, zp, part, partc);
+  }
   return cudaGetLastError();
 }
 
