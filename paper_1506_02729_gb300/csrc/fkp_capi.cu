@@ -240,7 +240,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
 
   // device workspace
   const size_t N3 = (size_t)N * N * N;
-  const size_t half = (size_t)N * N * (N / 2 + 1);
+  const size_t half = field_elems(N);  // one tile-major half spectrum, k_x padded to tiles of 8
   P->nblk_cat = std::max(1, ctx->nsm * 8);
   P->nblk_z = yz_tiles(N) * N;
   bool ok = true;
@@ -368,7 +368,7 @@ int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream
 int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s) {
   CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
   CK(cudaEventRecord(P->ev[3], s));
-  CK(launch_ypass(P->d_S1, P->g, P->mt, P->fp, P->d_tw, P->d_S2, s));
+  CK(launch_ypass(P->d_S1, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
   CK(cudaEventRecord(P->ev[4], s));
   ZParams zp;
   zp.nbins = P->pb.nbins;
@@ -382,7 +382,7 @@ int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf,
   zp.slut = nullptr;
   zp.E = nullptr;
   zp.mm = 0;
-  CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, s));
+  CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s));
   CK(launch_reduce_bins(P->d_zpart, P->d_zpartc, P->nblk_z, P->pb.nbins, P->d_bins, P->d_binc, s));
   CK(cudaEventRecord(P->ev[5], s));
   return FKP_OK;
@@ -399,8 +399,10 @@ int fkp::finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_sca
   CK(cudaMemcpyAsync(hb, P->d_bins, sizeof(double) * BQ_N * nb, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hc, P->d_binc, sizeof(long long) * nb, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hds, P->d_ds, sizeof(double) * (DS_COUNT + LAB_NSUM), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(herr, P->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (herr[1] != 0)
+    return set_error(FKP_ETIMEOUT, "a bounded device-side wait for a tile copy gave up (flags 0x%x)", herr[1]);
   if (have_scalars && herr[0] != 0)
     return set_error(FKP_EGEOM, "an object lies within assign/2+1 cells of a box face (or is not finite); "
                                 "enlarge the box or set periodic=1 (flags 0x%x)", herr[0]);

@@ -173,3 +173,202 @@ __device__ float2* fft_smem(float2* a, float2* b, int npen, int stride, const Ff
 }
 
 }  // namespace fkp
+
+// ----------------------------------------------------------------------------
+// Compile-time-sized FFT on interleaved pencils.
+//
+// P pencils of length N are interleaved in shared memory: element i of pencil
+// p sits at buf[i * P + p], so the tile of P consecutive k_x columns that a
+// pass reads from global memory is already in FFT layout.  N, P, the block
+// size and the radix sequence are template constants, so every index
+// division is by a constant and every loop unrolls.  Twiddles come from a
+// shared-memory table.
+// ----------------------------------------------------------------------------
+
+namespace fkp {
+
+__host__ __device__ constexpr int radix_count(int n) {
+  int c = 0;
+  while (n % 8 == 0) { n /= 8; ++c; }
+  while (n % 4 == 0) { n /= 4; ++c; }
+  while (n % 2 == 0) { n /= 2; ++c; }
+  while (n % 5 == 0) { n /= 5; ++c; }
+  while (n % 3 == 0) { n /= 3; ++c; }
+  return c;
+}
+
+__host__ __device__ constexpr int radix_at(int n, int s) {
+  int i = 0;
+  while (n % 8 == 0) { if (i == s) return 8; n /= 8; ++i; }
+  while (n % 4 == 0) { if (i == s) return 4; n /= 4; ++i; }
+  while (n % 2 == 0) { if (i == s) return 2; n /= 2; ++i; }
+  while (n % 5 == 0) { if (i == s) return 5; n /= 5; ++i; }
+  while (n % 3 == 0) { if (i == s) return 3; n /= 3; ++i; }
+  return 1;
+}
+
+template <int N, int P, int NT, int DIR, int R, int NS>
+__device__ __forceinline__ void fft_ct_stage(const float2* __restrict__ src, float2* __restrict__ dst,
+                                             const float2* __restrict__ tw) {
+  constexpr int NB = N / R;
+  constexpr int TOT = NB * P;
+  constexpr int TWS = N / (NS * R);
+#pragma unroll
+  for (int t0 = 0; t0 < TOT; t0 += NT) {
+    const int t = t0 + (int)threadIdx.x;
+    if ((TOT % NT) == 0 || t < TOT) {
+      const int p = t % P;
+      const int j = t / P;
+      const int k = j % NS;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = src[(j + r * NB) * P + p];
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[r * k * TWS];
+          if (DIR > 0) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
+      }
+      dftR<R, DIR>(v);
+      const int base = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[(base + r * NS) * P + p] = v[r];
+    }
+  }
+}
+
+template <int N, int P, int NT, int DIR, int S, int NS>
+__device__ __forceinline__ float2* fft_ct_run(float2* a, float2* b, const float2* tw) {
+  if constexpr (S == radix_count(N)) {
+    return a;
+  } else {
+    constexpr int R = radix_at(N, S);
+    fft_ct_stage<N, P, NT, DIR, R, NS>(a, b, tw);
+    __syncthreads();
+    return fft_ct_run<N, P, NT, DIR, S + 1, NS * R>(b, a, tw);
+  }
+}
+
+// Transforms P interleaved pencils held in a (b is scratch of the same size).
+// Returns the buffer holding the result.  All NT threads of the block call it;
+// it ends with a __syncthreads().
+template <int N, int P, int NT, int DIR>
+__device__ __forceinline__ float2* fft_ct(float2* a, float2* b, const float2* tw) {
+  return fft_ct_run<N, P, NT, DIR, 0, 1>(a, b, tw);
+}
+
+// Runtime-N version on the same interleaved layout (sizes without a
+// compiled specialisation).
+template <int R, int DIR>
+__device__ __forceinline__ void fft_rt_stage(const float2* __restrict__ src, float2* __restrict__ dst, int n, int P,
+                                             int ns, const float2* __restrict__ tw) {
+  const int nb = n / R;
+  const int tot = nb * P;
+  const int tws = n / (ns * R);
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int p = t % P;
+    const int j = t / P;
+    const int k = j % ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * P + p];
+    if (ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[r * k * tws];
+        if (DIR > 0) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dftR<R, DIR>(v);
+    const int base = (j / ns) * ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(base + r * ns) * P + p] = v[r];
+  }
+}
+
+template <int DIR>
+__device__ float2* fft_rt(float2* a, float2* b, int P, const FftPlan& fp, const float2* tw) {
+  int ns = 1;
+  for (int s = 0; s < fp.nst; ++s) {
+    const int R = fp.radix[s];
+    switch (R) {
+      case 8: fft_rt_stage<8, DIR>(a, b, fp.n, P, ns, tw); break;
+      case 4: fft_rt_stage<4, DIR>(a, b, fp.n, P, ns, tw); break;
+      case 2: fft_rt_stage<2, DIR>(a, b, fp.n, P, ns, tw); break;
+      case 5: fft_rt_stage<5, DIR>(a, b, fp.n, P, ns, tw); break;
+      default: fft_rt_stage<3, DIR>(a, b, fp.n, P, ns, tw); break;
+    }
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+    ns *= R;
+  }
+  return a;
+}
+
+// N = 0 selects the runtime version.
+template <int N, int P, int NT, int DIR>
+__device__ __forceinline__ float2* fft_any(float2* a, float2* b, const FftPlan& fp, const float2* tw) {
+  if constexpr (N > 0) return fft_ct<N, P, NT, DIR>(a, b, tw);
+  else return fft_rt<DIR>(a, b, P, fp, tw);
+}
+
+// ----------------------------------------------------------------------------
+// Bulk (TMA) copies of contiguous tiles into shared memory, completed on an
+// mbarrier.  Waits are bounded: after kWaitLimit polls the waiter records an
+// error flag and gives up (the host then reports FKP_ETIMEOUT).
+// ----------------------------------------------------------------------------
+
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 1-D bulk copy global -> shared (addresses 16-byte aligned, size multiple of 16).
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `parity`; returns false (and sets *err |= flag) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int flag) {
+  for (unsigned it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicOr(err, flag);
+  return false;
+}
+
+}  // namespace fkp

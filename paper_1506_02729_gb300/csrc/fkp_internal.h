@@ -67,10 +67,9 @@ int bisp_plan_init(Plan* P);
 void bisp_plan_free(Plan* P);
 
 // launch wrappers (k_power.cu)
-size_t xpass_smem(int N, int nfields);
-size_t yz_smem(int N);
-size_t zpass_smem(int N, int nbins);
 int yz_tiles(int N);
+int tiles_x(int N);
+size_t field_elems(int N);
 cudaError_t launch_scalars(const CatDev& c, int is_ran, float Pfkp, double* part, int nblk, cudaStream_t s);
 cudaError_t launch_scalars_finalize(const double* part, int nbg, int nbr, long long ng, long long nr, int amode,
                                     double* ds, cudaStream_t s);
@@ -81,9 +80,9 @@ cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cu
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s);
 cudaError_t launch_ypass(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, float2* S2, cudaStream_t s);
+                         const float2* tw, float2* S2, int* err, cudaStream_t s);
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, const ZParams& zp, double* part, int* partc, cudaStream_t s);
+                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s);
 cudaError_t launch_reduce_bins(const double* part, const int* partc, int nblk, int nbins, double* out,
                                long long* outc, cudaStream_t s);
 

@@ -1,0 +1,472 @@
+// k_fftpass.cu - the three FFT passes of the power-spectrum path.
+//
+//   x-pass  per grid row: moment fields F x^_a x^_b (...) built at the nodes
+//           about the observer (eqs. Qij, Qijkl, Qab), two real fields packed
+//           per complex pencil, FFT along x, unpacked into half spectra.
+//   y-pass  per (z, k_x tile): FFT of each field along y, then the k_x^i k_y^j
+//           monomials of eqs. delta2b and delta4b and the multinomial
+//           multiplicities, summed into k_z-power groups.
+//   z-pass  per (k_y, k_x tile): FFT of each group along z, Legendre
+//           recombination F_2 = 3/2 S_2/|n|^2 - F_0/2 and
+//           F_4 = 35/8 S_4/|n|^4 - 5/2 F_2 - 7/8 F_0 (eqs. F2, delta4),
+//           window compensation and shell binning (eq. shell).
+//
+// Layouts are tile-major so that every tile a pass reads is one contiguous
+// block, fetched with a bulk (TMA) copy while the previous tile is being
+// transformed:
+//   S1[field][z][xt][y][c]   (k_x = 8 xt + c), written by the x-pass
+//   S2[group][xt][ky][z][c]  written by the y-pass, read by the z-pass
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fkp_internal.h"
+
+namespace fkp {
+
+constexpr int kT = 8;        // k_x columns per tile (64 bytes of complex64)
+constexpr int kNT = 256;     // threads per block
+constexpr int kRun = 32;     // threads per column in the accumulate/bin phase
+constexpr int kMaxRL = 16;   // points per thread along a pencil (N <= 512)
+
+__device__ __forceinline__ int smode(int k, int N) { return k <= N / 2 ? k : k - N; }
+
+__device__ __forceinline__ float powi(float v, int e) {
+  float r = 1.f;
+  for (int i = 0; i < e; ++i) r *= v;
+  return r;
+}
+
+__device__ __forceinline__ float pw5(const float* h, int e) {
+  return e == 0 ? 1.f : (e == 1 ? h[1] : (e == 2 ? h[2] : (e == 3 ? h[3] : h[4])));
+}
+
+// ----------------------------------------------------------------------------
+// x-pass
+// ----------------------------------------------------------------------------
+
+template <int N_, int NP>
+__global__ void __launch_bounds__(kNT) k_xpass2(const unsigned long long* __restrict__ gq, const float* __restrict__ gf,
+                                                GeomDev g, MomentTable mt, FftPlan fp,
+                                                const float2* __restrict__ twg, float2* __restrict__ S1) {
+  extern __shared__ float2 sm[];
+  const int N = N_ ? N_ : g.N;
+  const int NH = N / 2 + 1, NXT = (NH + kT - 1) / kT;
+  float2* tw = sm;
+  float* rowF = reinterpret_cast<float*>(sm + N);
+  float2* A = sm + N + N / 2;
+  float2* B = A + NP * N;
+  for (int i = threadIdx.x; i < N; i += kNT) tw[i] = twg[i];
+  const size_t fsz = (size_t)N * NXT * N * kT;
+  const int nf = mt.nfields;
+  for (int row = blockIdx.x; row < N * N; row += gridDim.x) {
+    const int z = row / N, y = row - z * N;
+    const size_t gbase = (size_t)row * N;
+    for (int x = threadIdx.x; x < N; x += kNT)
+      rowF[x] = gq ? (float)(long long)gq[gbase + x] * kFixInvF : gf[gbase + x];
+    __syncthreads();
+    const float Y = fmaf((float)y, g.H, g.ry), Z = fmaf((float)z, g.H, g.rz);
+    for (int x = threadIdx.x; x < N; x += kNT) {
+      float hx[5], hy[5], hz[5];
+      if (g.los_inf) {
+        hx[1] = g.lx; hy[1] = g.ly; hz[1] = g.lz;
+      } else {
+        const float X = fmaf((float)x, g.H, g.rx);
+        const float r2 = X * X + Y * Y + Z * Z;
+        const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        hx[1] = X * inv; hy[1] = Y * inv; hz[1] = Z * inv;
+      }
+      hx[2] = hx[1] * hx[1]; hx[3] = hx[2] * hx[1]; hx[4] = hx[2] * hx[2];
+      hy[2] = hy[1] * hy[1]; hy[3] = hy[2] * hy[1]; hy[4] = hy[2] * hy[2];
+      hz[2] = hz[1] * hz[1]; hz[3] = hz[2] * hz[1]; hz[4] = hz[2] * hz[2];
+      const float f = rowF[x];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const int q0 = 2 * p, q1 = 2 * p + 1;
+        const float m0 = f * pw5(hx, mt.e[q0][0]) * pw5(hy, mt.e[q0][1]) * pw5(hz, mt.e[q0][2]);
+        const float m1 = q1 < nf ? f * pw5(hx, mt.e[q1][0]) * pw5(hy, mt.e[q1][1]) * pw5(hz, mt.e[q1][2]) : 0.f;
+        A[x * NP + p] = make_float2(m0, m1);
+      }
+    }
+    __syncthreads();
+    const float2* R = fft_any<N_, NP, kNT, -1>(A, B, fp, tw);
+    const int ncol = NXT * kT;
+    for (int t = threadIdx.x; t < NP * ncol; t += kNT) {
+      const int p = t / ncol, k = t - p * ncol;
+      float2 o0 = make_float2(0.f, 0.f), o1 = o0;
+      if (k < NH) {
+        const float2 zk = R[k * NP + p];
+        const float2 zm = R[(k == 0 ? 0 : N - k) * NP + p];
+        o0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        o1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      }
+      const size_t off = (((size_t)z * NXT + (k >> 3)) * N + y) * kT + (k & 7);
+      const int q0 = 2 * p, q1 = 2 * p + 1;
+      S1[(size_t)q0 * fsz + off] = o0;
+      if (q1 < nf) S1[(size_t)q1 * fsz + off] = o1;
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// y-pass
+// ----------------------------------------------------------------------------
+
+template <int N_>
+__global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1, GeomDev g, MomentTable mt,
+                                                   FftPlan fp, const float2* __restrict__ twg,
+                                                   float2* __restrict__ S2, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int N = N_ ? N_ : g.N;
+  const int NH = N / 2 + 1, NXT = (NH + kT - 1) / kT;
+  const int tile = N * kT;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+  float2* buf0 = reinterpret_cast<float2*>(smraw + 128);
+  float2* buf1 = buf0 + tile;
+  float2* work = buf1 + tile;
+  float2* tw = work + tile;
+  const int xt = blockIdx.x, z = blockIdx.y;
+  const size_t fsz = (size_t)N * NXT * N * kT;
+  const size_t gsz = fsz;
+  const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
+  for (int i = threadIdx.x; i < N; i += kNT) tw[i] = twg[i];
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // flattened member list
+  int total = 0;
+  for (int gi = 0; gi < mt.ngroups; ++gi) total += mt.g_nmem[gi];
+  auto src_of = [&](int q) { return S1 + (size_t)q * fsz + ((size_t)z * NXT + xt) * tile; };
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar[0], bytes);
+    tma_load_1d(buf0, src_of(mt.g_field[0][0]), bytes, &bar[0]);
+  }
+  const int c = threadIdx.x % kT, run = threadIdx.x / kT;
+  const int rl = (N + kRun - 1) / kRun;
+  const float nx = (float)(xt * kT + c);
+  int it = 0;
+  for (int gi = 0; gi < mt.ngroups; ++gi) {
+    float2 acc[kMaxRL];
+#pragma unroll
+    for (int i = 0; i < kMaxRL; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int m = 0; m < mt.g_nmem[gi]; ++m, ++it) {
+      const int cur = it & 1;
+      float2* bc = cur ? buf1 : buf0;
+      if (threadIdx.x == 0 && it + 1 < total) {
+        int g2 = gi, m2 = m + 1;
+        if (m2 == mt.g_nmem[gi]) { g2 = gi + 1; m2 = 0; }
+        fence_proxy_async();
+        mbar_expect_tx(&bar[cur ^ 1], bytes);
+        tma_load_1d(cur ? buf0 : buf1, src_of(mt.g_field[g2][m2]), bytes, &bar[cur ^ 1]);
+      }
+      mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 4);
+      const float2* R = fft_any<N_, kT, kNT, -1>(bc, work, fp, tw);
+      const float coef = mt.g_coef[gi][m] * powi(nx, mt.g_ei[gi][m]);
+      const int ej = mt.g_ej[gi][m];
+#pragma unroll
+      for (int i = 0; i < kMaxRL; ++i) {
+        const int ky = run * rl + i;
+        if (i < rl && ky < N) {
+          const float s = coef * powi((float)smode(ky, N), ej);
+          const float2 v = R[ky * kT + c];
+          acc[i].x = fmaf(s, v.x, acc[i].x);
+          acc[i].y = fmaf(s, v.y, acc[i].y);
+        }
+      }
+      __syncthreads();
+    }
+    float2* dst = S2 + (size_t)gi * gsz + (size_t)xt * N * tile + (size_t)z * kT + c;
+#pragma unroll
+    for (int i = 0; i < kMaxRL; ++i) {
+      const int ky = run * rl + i;
+      if (i < rl && ky < N) dst[(size_t)ky * tile] = acc[i];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// z-pass (MODE 0: P bins; 1: P bins + export on the shells; 2: F^w shell sums)
+// ----------------------------------------------------------------------------
+
+template <int N_, int MODE>
+__global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
+                                                   FftPlan fp, const float2* __restrict__ twg, ZParams zp,
+                                                   double* __restrict__ part, int* __restrict__ partc,
+                                                   int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int N = N_ ? N_ : g.N;
+  const int NH = N / 2 + 1, NXT = (NH + kT - 1) / kT;
+  const int tile = N * kT;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+  float2* buf0 = reinterpret_cast<float2*>(smraw + 128);
+  float2* buf1 = buf0 + tile;
+  float2* work = buf1 + tile;
+  float2* tw = work + tile;
+  const int nkey = MODE == 2 ? zp.nshells : zp.nbins;
+  double* sb = reinterpret_cast<double*>(tw + N);
+  int* sc = reinterpret_cast<int*>(sb + BQ_N * nkey);
+  const int xt = blockIdx.x, ky = blockIdx.y;
+  const size_t gsz = (size_t)N * NXT * N * kT;
+  const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
+  for (int i = threadIdx.x; i < N; i += kNT) tw[i] = twg[i];
+  for (int t = threadIdx.x; t < BQ_N * nkey; t += kNT) sb[t] = 0.0;
+  for (int t = threadIdx.x; t < nkey; t += kNT) sc[t] = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto src_of = [&](int gi) { return S2 + (size_t)gi * gsz + ((size_t)xt * N + ky) * tile; };
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar[0], bytes);
+    tma_load_1d(buf0, src_of(0), bytes, &bar[0]);
+  }
+  const int c = threadIdx.x % kT, run = threadIdx.x / kT;
+  const int rl = (N + kRun - 1) / kRun;
+  const int z0 = run * rl;
+  float2 f0[kMaxRL], s2[kMaxRL], s4[kMaxRL];
+#pragma unroll
+  for (int i = 0; i < kMaxRL; ++i) {
+    f0[i] = make_float2(0.f, 0.f);
+    s2[i] = f0[i];
+    s4[i] = f0[i];
+  }
+  for (int gi = 0; gi < mt.ngroups; ++gi) {
+    const int cur = gi & 1;
+    float2* bc = cur ? buf1 : buf0;
+    if (threadIdx.x == 0 && gi + 1 < mt.ngroups) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar[cur ^ 1], bytes);
+      tma_load_1d(cur ? buf0 : buf1, src_of(gi + 1), bytes, &bar[cur ^ 1]);
+    }
+    mbar_wait(&bar[cur], (uint32_t)((gi >> 1) & 1), err, 8);
+    const float2* R = fft_any<N_, kT, kNT, -1>(bc, work, fp, tw);
+    const int ell = mt.g_ell[gi], p = mt.g_p[gi];
+#pragma unroll
+    for (int i = 0; i < kMaxRL; ++i) {
+      const int kz = z0 + i;
+      if (i < rl && kz < N) {
+        const float2 v = R[kz * kT + c];
+        if (ell == 0) {
+          f0[i] = v;
+        } else {
+          const float mz = powi((float)smode(kz, N), p);
+          if (ell == 2) {
+            s2[i].x = fmaf(mz, v.x, s2[i].x);
+            s2[i].y = fmaf(mz, v.y, s2[i].y);
+          } else {
+            s4[i].x = fmaf(mz, v.x, s4[i].x);
+            s4[i].y = fmaf(mz, v.y, s4[i].y);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // recombination and binning: each thread walks its run of k_z
+  const int kx = xt * kT + c;
+  const bool colok = kx < N / 2;
+  const int nyv = smode(ky, N);
+  const bool rowok = ky != N / 2;
+  const float wcol = kx == 0 ? 1.f : 2.f;
+  const float wxy = colok ? zp.winv[kx] * zp.winv[N + ky] : 0.f;
+  int curb = -1, cnt = 0;
+  float acc[BQ_N];
+#pragma unroll
+  for (int q = 0; q < BQ_N; ++q) acc[q] = 0.f;
+#pragma unroll
+  for (int i = 0; i < kMaxRL; ++i) {
+    const int kz = z0 + i;
+    int b = -1;
+    float vals[BQ_N];
+#pragma unroll
+    for (int q = 0; q < BQ_N; ++q) vals[q] = 0.f;
+    if (colok && rowok && i < rl && kz < N && kz != N / 2) {
+      const int nzv = smode(kz, N);
+      const int n2 = kx * kx + nyv * nyv + nzv * nzv;
+      const int sh = (MODE != 0 && n2 < zp.nsh2) ? (int)zp.slut[n2] : -1;
+      b = MODE == 2 ? sh : (n2 > 0 ? zp.lut[n2] : -1);
+      if (b >= 0 || sh >= 0) {
+        const float wc = wxy * zp.winv[2 * N + kz];
+        const float fn2 = (float)n2;
+        const float2 F0 = make_float2(f0[i].x * wc, f0[i].y * wc);
+        float2 F2 = make_float2(0.f, 0.f), F4 = make_float2(0.f, 0.f);
+        if (zp.lmax >= 2) {
+          const float i2 = 1.0f / fn2;
+          F2 = make_float2(wc * (1.5f * s2[i].x * i2 - 0.5f * f0[i].x), wc * (1.5f * s2[i].y * i2 - 0.5f * f0[i].y));
+          if (zp.lmax >= 4) {
+            const float i4 = i2 * i2;
+            F4 = make_float2(4.375f * wc * s4[i].x * i4 - 2.5f * F2.x - 0.875f * F0.x,
+                             4.375f * wc * s4[i].y * i4 - 2.5f * F2.y - 0.875f * F0.y);
+          }
+        }
+        if (MODE != 2) {
+          vals[BQ_K] = zp.kf * sqrtf(fn2);
+          vals[BQ_F00] = F0.x * F0.x + F0.y * F0.y;
+          vals[BQ_F20] = F2.x * F0.x + F2.y * F0.y;
+          vals[BQ_F40] = F4.x * F0.x + F4.y * F0.y;
+          vals[BQ_F22] = F2.x * F2.x + F2.y * F2.y;
+        }
+        if (MODE != 0 && sh >= 0) {
+          const int w2 = 2 * zp.mm + 1;
+          const size_t e = ((size_t)(nzv + zp.mm) * w2 + (nyv + zp.mm)) * (zp.mm + 1) + kx;
+          const size_t es = (size_t)w2 * w2 * (zp.mm + 1);
+          if (MODE == 1) {
+            zp.E[e] = F0;
+            zp.E[es + e] = F2;
+            zp.E[2 * es + e] = F4;
+          } else {
+            // F0, F2, F4 are the Legendre fields of F^w here; E holds those of F
+            const float2 E0 = zp.E[e], E2 = zp.E[es + e], E4 = zp.E[2 * es + e];
+            vals[SQ_00] = E0.x * F0.x + E0.y * F0.y;
+            vals[SQ_20] = E2.x * F0.x + E2.y * F0.y;
+            vals[SQ_40] = E4.x * F0.x + E4.y * F0.y;
+            vals[SQ_02] = E0.x * F2.x + E0.y * F2.y;
+            vals[SQ_04] = E0.x * F4.x + E0.y * F4.y;
+          }
+        }
+      }
+    }
+    if (b != curb) {
+      if (curb >= 0) {
+        atomicAdd(sc + curb, cnt);
+#pragma unroll
+        for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, (double)acc[q]);
+      }
+      curb = b;
+      cnt = 0;
+#pragma unroll
+      for (int q = 0; q < BQ_N; ++q) acc[q] = 0.f;
+    }
+    if (b >= 0) {
+      cnt += (int)wcol;
+#pragma unroll
+      for (int q = 0; q < BQ_N; ++q) acc[q] = fmaf(wcol, vals[q], acc[q]);
+    }
+  }
+  if (curb >= 0) {
+    atomicAdd(sc + curb, cnt);
+#pragma unroll
+    for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, (double)acc[q]);
+  }
+  __syncthreads();
+  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+  const int nblk = gridDim.x * gridDim.y;
+  for (int t = threadIdx.x; t < BQ_N * nkey; t += kNT) part[(size_t)t * nblk + blk] = sb[t];
+  for (int t = threadIdx.x; t < nkey; t += kNT) partc[(size_t)t * nblk + blk] = sc[t];
+}
+
+// ----------------------------------------------------------------------------
+// launch wrappers
+// ----------------------------------------------------------------------------
+
+int tiles_x(int N) { return (N / 2 + 1 + kT - 1) / kT; }
+size_t field_elems(int N) { return (size_t)N * tiles_x(N) * N * kT; }
+int yz_tiles(int N) { return tiles_x(N); }
+
+static size_t xsm(int N, int NP) { return sizeof(float2) * (N + N / 2 + 2 * (size_t)NP * N); }
+static size_t ysm(int N) { return 128 + sizeof(float2) * (3 * (size_t)N * kT + N); }
+static size_t zsm(int N, int nkey) { return ysm(N) + sizeof(double) * BQ_N * nkey + sizeof(int) * nkey; }
+
+template <int N_, int NP>
+static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
+                        const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s) {
+  const size_t sm = xsm(g.N, NP);
+  cudaFuncSetAttribute(k_xpass2<N_, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, NP>, kNT, sm);
+  int grid = nsm * (occ > 0 ? occ : 1) * 2;
+  if (grid > g.N * g.N) grid = g.N * g.N;
+  k_xpass2<N_, NP><<<grid, kNT, sm, s>>>(gq, gf, g, mt, fp, tw, S1);
+  return cudaGetLastError();
+}
+
+template <int NP>
+static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
+                             const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s) {
+  if (NP == 11) {
+    switch (g.N) {
+      case 512: return xrun<512, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+      case 384: return xrun<384, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+      case 360: return xrun<360, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+      case 256: return xrun<256, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+      case 128: return xrun<128, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+      case 64: return xrun<64, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+      default: break;
+    }
+  }
+  return xrun<0, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+}
+
+cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
+                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s) {
+  const int np = (mt.nfields + 1) / 2;
+  if (np == 11) return xdispatch<11>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+  if (np == 4) return xdispatch<4>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+  return xdispatch<1>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+}
+
+template <int N_>
+static cudaError_t yrun(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+                        const float2* tw, float2* S2, int* err, cudaStream_t s) {
+  const size_t sm = ysm(g.N);
+  cudaFuncSetAttribute(k_ypass2<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_ypass2<N_><<<dim3(tiles_x(g.N), g.N), kNT, sm, s>>>(S1, g, mt, fp, tw, S2, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ypass(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+                         const float2* tw, float2* S2, int* err, cudaStream_t s) {
+  switch (g.N) {
+    case 512: return yrun<512>(S1, g, mt, fp, tw, S2, err, s);
+    case 384: return yrun<384>(S1, g, mt, fp, tw, S2, err, s);
+    case 360: return yrun<360>(S1, g, mt, fp, tw, S2, err, s);
+    case 256: return yrun<256>(S1, g, mt, fp, tw, S2, err, s);
+    case 128: return yrun<128>(S1, g, mt, fp, tw, S2, err, s);
+    case 64: return yrun<64>(S1, g, mt, fp, tw, S2, err, s);
+    default: return yrun<0>(S1, g, mt, fp, tw, S2, err, s);
+  }
+}
+
+template <int N_, int MODE>
+static cudaError_t zrun(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+                        const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
+  const size_t sm = zsm(g.N, MODE == 2 ? zp.nshells : zp.nbins);
+  cudaFuncSetAttribute(k_zpass2<N_, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_zpass2<N_, MODE><<<dim3(tiles_x(g.N), g.N), kNT, sm, s>>>(S2, g, mt, fp, tw, zp, part, partc, err);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t zdispatch(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+                             const float2* tw, const ZParams& zp, double* part, int* partc, int* err,
+                             cudaStream_t s) {
+  switch (g.N) {
+    case 512: return zrun<512, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+    case 360: return zrun<360, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+    case 256: return zrun<256, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+    default: break;
+  }
+  if (MODE == 0) {
+    switch (g.N) {
+      case 384: return zrun<384, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+      case 128: return zrun<128, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+      case 64: return zrun<64, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+      default: break;
+    }
+  }
+  return zrun<0, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+}
+
+cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
+  if (zp.mode == 0) return zdispatch<0>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+  if (zp.mode == 1) return zdispatch<1>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+  return zdispatch<2>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+}
+
+}  // namespace fkp
