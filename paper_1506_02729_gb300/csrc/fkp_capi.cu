@@ -136,6 +136,8 @@ fkp::Plan::~Plan() {
   bisp_plan_free(this);
   for (void* p : buffers) cudaFree(p);
   for (void* p : staging) cudaFree(p);
+  if (d_xyzv) cudaFree(d_xyzv);
+  if (d_vw2) cudaFree(d_vw2);
   if (h_pinned) cudaFreeHost(h_pinned);
   for (auto& e : ev) if (e) cudaEventDestroy(e);
 }
@@ -256,6 +258,13 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   P->d_labpart = (double*)A(sizeof(double) * LAB_NSUM * P->nblk_cat);
   P->d_ds = (double*)A(sizeof(double) * (DS_COUNT + LAB_NSUM + 8));
   P->d_err = (int*)A(sizeof(int) * 4);
+  {
+    const int ntx = assign_tiles_per_axis(N);
+    P->ntiles = ntx * ntx * ntx;
+  }
+  P->d_tcnt = (int*)A(sizeof(int) * P->ntiles);
+  P->d_toff = (int*)A(sizeof(int) * (P->ntiles + 1));
+  P->d_tcur = (int*)A(sizeof(int) * P->ntiles);
   P->d_zpart = (double*)A(sizeof(double) * BQ_N * pb->nbins * (size_t)P->nblk_z);
   P->d_zpartc = (int*)A(sizeof(int) * pb->nbins * (size_t)P->nblk_z);
   P->d_bins = (double*)A(sizeof(double) * BQ_N * pb->nbins);
@@ -341,25 +350,46 @@ int fkp::stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, c
 // P_l
 // ----------------------------------------------------------------------------
 
-// Enqueues scalars and gridding of both catalogs into d_grid (and d_gridw).
+// Enqueues scalars and gridding of both catalogs into d_grid (and d_gridw):
+// tile counts with the scalar sums, offsets, scatter into tile order, and
+// shared-memory accumulation per tile.
 int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s) {
   const int N = P->g.N;
   const size_t N3 = (size_t)N * N * N;
+  const long long ntot = gal.n + ran.n;
+  if (ntot >= (1ll << 31)) return set_error(FKP_EINVAL, "at most 2^31-1 objects per call");
+  if ((size_t)ntot > P->sort_cap) {
+    if (P->d_xyzv) cudaFree(P->d_xyzv);
+    if (P->d_vw2) cudaFree(P->d_vw2);
+    P->d_xyzv = nullptr;
+    P->d_vw2 = nullptr;
+    P->sort_cap = 0;
+    const size_t cap = (size_t)ntot + ntot / 8 + 1024;
+    if (cudaMalloc(&P->d_xyzv, sizeof(float4) * cap) != cudaSuccess)
+      return set_error(FKP_ENOMEM, "cannot allocate the tile-sorted catalog (%lld objects)", ntot);
+    if (P->d_gridw && cudaMalloc(&P->d_vw2, sizeof(float) * cap) != cudaSuccess)
+      return set_error(FKP_ENOMEM, "cannot allocate the tile-sorted catalog (%lld objects)", ntot);
+    P->sort_cap = cap;
+  }
   const int nb = P->nblk_cat;
   auto nblocks = [&](long long n) { return (int)std::max<long long>(1, std::min<long long>(nb, (n + 255) / 256)); };
   const int nbg = nblocks(gal.n), nbr = nblocks(ran.n);
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
+  CK(cudaMemsetAsync(P->d_tcnt, 0, sizeof(int) * P->ntiles, s));
   CK(cudaEventRecord(P->ev[0], s));
-  CK(launch_scalars(gal, 0, P->g.P_fkp, P->d_scpart, nbg, s));
-  CK(launch_scalars(ran, 1, P->g.P_fkp, P->d_scpart + (size_t)nbg * SC_NSUM, nbr, s));
+  CK(launch_bin_count(gal, 0, P->g, P->d_scpart, P->d_tcnt, P->d_err, nbg, s));
+  CK(launch_bin_count(ran, 1, P->g, P->d_scpart + (size_t)nbg * SC_NSUM, P->d_tcnt, P->d_err, nbr, s));
   CK(launch_scalars_finalize(P->d_scpart, nbg, nbr, gal.n, ran.n, P->g.alpha_mode, P->d_ds, s));
+  CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, s));
   CK(cudaEventRecord(P->ev[1], s));
   CK(cudaMemsetAsync(P->d_grid, 0, N3 * 8, s));
   if (P->d_gridw) CK(cudaMemsetAsync(P->d_gridw, 0, N3 * 8, s));
   const double* obs = P->geom.observer;
-  CK(launch_assign(gal, 0, P->g, obs, P->d_ds, P->d_grid, P->d_gridw, P->d_err, nullptr, nbg, s));
-  CK(launch_assign(ran, 1, P->g, obs, P->d_ds, P->d_grid, P->d_gridw, P->d_err, P->d_labpart, nbr, s));
+  float* vw2 = P->d_gridw ? P->d_vw2 : nullptr;
+  CK(launch_bin_scatter(gal, 0, P->g, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, nullptr, nbg, s));
+  CK(launch_bin_scatter(ran, 1, P->g, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s));
   CK(launch_lab_finalize(P->d_labpart, ran.n > 0 ? nbr : 0, P->d_ds + DS_COUNT, s));
+  CK(launch_tile_accum(P->g, P->d_toff, P->d_xyzv, vw2, P->d_grid, P->d_gridw, s));
   CK(cudaEventRecord(P->ev[2], s));
   return FKP_OK;
 }

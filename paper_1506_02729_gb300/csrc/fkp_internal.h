@@ -36,6 +36,12 @@ struct Plan {
   float* d_winv = nullptr;
   double *d_scpart = nullptr, *d_labpart = nullptr, *d_ds = nullptr;
   int* d_err = nullptr;
+  // tile binning of the catalogs (gridding)
+  int ntiles = 0;
+  int *d_tcnt = nullptr, *d_toff = nullptr, *d_tcur = nullptr;
+  float4* d_xyzv = nullptr;
+  float* d_vw2 = nullptr;
+  size_t sort_cap = 0;
   double* d_zpart = nullptr;
   int* d_zpartc = nullptr;
   double* d_bins = nullptr;
@@ -70,12 +76,16 @@ void bisp_plan_free(Plan* P);
 int yz_tiles(int N);
 int tiles_x(int N);
 size_t field_elems(int N);
-cudaError_t launch_scalars(const CatDev& c, int is_ran, float Pfkp, double* part, int nblk, cudaStream_t s);
 cudaError_t launch_scalars_finalize(const double* part, int nbg, int nbr, long long ng, long long nr, int amode,
                                     double* ds, cudaStream_t s);
-cudaError_t launch_assign(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
-                          unsigned long long* grid, unsigned long long* gridw, int* err, double* labpart, int nblk,
-                          cudaStream_t s);
+int assign_tiles_per_axis(int N);
+cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, double* part, int* cnt, int* err,
+                             int nblk, cudaStream_t s);
+cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, cudaStream_t s);
+cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
+                               int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s);
+cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xyzv, const float* vw2,
+                              unsigned long long* grid, unsigned long long* gridw, cudaStream_t s);
 cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s);

@@ -81,4 +81,37 @@ struct CatDev {
   long long n;
 };
 
+// Compensated FP32 accumulator (per-thread partial sums; the block and grid
+// levels sum in FP64).
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Block-wide FP64 sum of one value per thread; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum_f64(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) r += sh[i];
+  }
+  return r;
+}
+
+// FKP weight w = 1/(1 + nbar P_FKP) unless the catalog carries weights.
+__device__ __forceinline__ float fkp_weight(const CatDev& c, long long i, float Pfkp) {
+  return c.w ? __ldg(c.w + i) : 1.0f / (1.0f + __ldg(c.nbar + i) * Pfkp);
+}
+
 }  // namespace fkp

@@ -1,0 +1,316 @@
+// k_assign.cu - scalars and gridding of galaxies and randoms (Sec. III.A).
+//
+// Interpolation of the objects to the grid nodes (eq. mapFFT) with CIC or TSC
+// weights, as a counting sort by 16^3-cell tile followed by accumulation in
+// shared memory:
+//   count    per object: FKP weight and the compensated FP32 partial sums of
+//            the scalars (W, sum w^2, sum w^3, sum nbar w^2, sum nbar^2 w^3,
+//            for alpha, I_22, I_33, N_0, S_3: eqs. I22def, N0true, Noise0),
+//            the geometry check and one count for the object's tile;
+//   scan     tile offsets (exclusive prefix sum);
+//   scatter  each object's (x, y, z, value) to its tile's segment, value =
+//            w for galaxies and -alpha w for randoms (and the w^2-weighted
+//            value for F^w, eq. SNbisp2), with the L^ab sums (eq. Lab);
+//   tiles    one block per tile: every tap is rounded once to a 2^-40
+//            fixed-point integer and added in shared memory over the tile and
+//            its one-cell halo, then the nonzero cells are added to the grid.
+// Integer sums make the grid independent of the order of the objects and of
+// the blocks (deterministic, identical alone or inside a batch).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fkp_internal.h"
+
+namespace fkp {
+
+constexpr int kTile = 16;            // cells per tile side
+constexpr int kReg = kTile + 2;      // tile plus one halo cell on each side
+constexpr int kReg3 = kReg * kReg * kReg;
+
+int assign_tiles_per_axis(int N) { return (N + kTile - 1) / kTile; }
+
+// Centre cell of an object: TSC taps c-1..c+1 around c = floor(u + 1/2);
+// CIC taps c, c+1 with c = floor(u).  Returns false when a tap would leave
+// [1, N-2] (non-periodic) or the position is not finite.
+template <int P>
+__device__ __forceinline__ bool centre_cell(const GeomDev& g, float px, float py, float pz, int& cx, int& cy,
+                                            int& cz) {
+  const float ux = (px - g.ox) * g.invH, uy = (py - g.oy) * g.invH, uz = (pz - g.oz) * g.invH;
+  const float sh = P == 3 ? 0.5f : 0.f;
+  const int N = g.N;
+  if (!g.periodic) {
+    if (!(ux >= 0.f && ux < (float)N && uy >= 0.f && uy < (float)N && uz >= 0.f && uz < (float)N)) return false;
+    cx = (int)floorf(ux + sh);
+    cy = (int)floorf(uy + sh);
+    cz = (int)floorf(uz + sh);
+    const int lo = P == 3 ? 2 : 1, hi = N - 3;
+    return cx >= lo && cy >= lo && cz >= lo && cx <= hi && cy <= hi && cz <= hi;
+  }
+  if (!(fabsf(ux) < 1e8f && fabsf(uy) < 1e8f && fabsf(uz) < 1e8f)) return false;
+  cx = (int)floorf(ux + sh);
+  cy = (int)floorf(uy + sh);
+  cz = (int)floorf(uz + sh);
+  return true;
+}
+
+__device__ __forceinline__ int wrapN(int i, int N) {
+  i %= N;
+  return i < 0 ? i + N : i;
+}
+
+__device__ __forceinline__ int tile_of(int cx, int cy, int cz, int N, int ntx) {
+  return ((wrapN(cz, N) / kTile) * ntx + wrapN(cy, N) / kTile) * ntx + wrapN(cx, N) / kTile;
+}
+
+// ---------------------------------------------------------------------------
+
+template <int P>
+__global__ void __launch_bounds__(256) k_bin_count(CatDev c, int is_ran, GeomDev g, int ntx,
+                                                   double* __restrict__ part, int* __restrict__ cnt,
+                                                   int* __restrict__ err) {
+  __shared__ double sh[32];
+  KahanF s_w, s_w2, s_w3, s_nw2, s_n2w3;
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float w = fkp_weight(c, i, g.P_fkp);
+    const float w2 = w * w;
+    s_w.add(w);
+    s_w2.add(w2);
+    s_w3.add(w2 * w);
+    if (is_ran) {
+      const float nb = __ldg(c.nbar + i);
+      s_nw2.add(nb * w2);
+      s_n2w3.add(nb * nb * w2 * w);
+    }
+    int cx, cy, cz;
+    if (centre_cell<P>(g, __ldg(c.x + i), __ldg(c.y + i), __ldg(c.z + i), cx, cy, cz))
+      atomicAdd(cnt + tile_of(cx, cy, cz, g.N, ntx), 1);
+    else
+      bad = true;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, 1);
+  double* out = part + (size_t)blockIdx.x * SC_NSUM;
+  double v;
+  if (!is_ran) {
+    v = block_sum_f64(s_w.value(), sh);  if (threadIdx.x == 0) out[SC_G_W] = v;
+    v = block_sum_f64(s_w2.value(), sh); if (threadIdx.x == 0) out[SC_G_W2] = v;
+    v = block_sum_f64(s_w3.value(), sh); if (threadIdx.x == 0) out[SC_G_W3] = v;
+  } else {
+    v = block_sum_f64(s_w.value(), sh);    if (threadIdx.x == 0) out[SC_R_W] = v;
+    v = block_sum_f64(s_w2.value(), sh);   if (threadIdx.x == 0) out[SC_R_W2] = v;
+    v = block_sum_f64(s_w3.value(), sh);   if (threadIdx.x == 0) out[SC_R_W3] = v;
+    v = block_sum_f64(s_nw2.value(), sh);  if (threadIdx.x == 0) out[SC_R_NW2] = v;
+    v = block_sum_f64(s_n2w3.value(), sh); if (threadIdx.x == 0) out[SC_R_N2W3] = v;
+  }
+}
+
+// Exclusive scan of the tile counts into offsets (off[ntiles] = total) and
+// the scatter cursors (cur = off).  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ cnt, int ntiles, int* __restrict__ off,
+                                                     int* __restrict__ cur) {
+  __shared__ int part[1024];
+  const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+  const int a = threadIdx.x * per, b = min(ntiles, a + per);
+  int s = 0;
+  for (int i = a; i < b; ++i) s += cnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int i = a; i < b; ++i) {
+    off[i] = run;
+    cur[i] = run;
+    run += cnt[i];
+  }
+  if (threadIdx.x == blockDim.x - 1) off[ntiles] = part[threadIdx.x];
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_bin_scatter(CatDev c, int is_ran, GeomDev g, int ntx, float obx, float oby,
+                                                     float obz, const double* __restrict__ ds, int* __restrict__ cur,
+                                                     float4* __restrict__ xyzv, float* __restrict__ vw2,
+                                                     double* __restrict__ labpart) {
+  __shared__ double sh[32];
+  const float alpha = (float)ds[DS_ALPHA];
+  KahanF lab[LAB_NSUM];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float w = fkp_weight(c, i, g.P_fkp);
+    const float px = __ldg(c.x + i), py = __ldg(c.y + i), pz = __ldg(c.z + i);
+    int cx, cy, cz;
+    if (centre_cell<P>(g, px, py, pz, cx, cy, cz)) {
+      const int slot = atomicAdd(cur + tile_of(cx, cy, cz, g.N, ntx), 1);
+      xyzv[slot] = make_float4(px, py, pz, is_ran ? -alpha * w : w);
+      if (vw2) vw2[slot] = is_ran ? alpha * alpha * w * w : w * w;
+    }
+    if (is_ran) {
+      float hx, hy, hz;
+      if (g.los_inf) {
+        hx = g.lx; hy = g.ly; hz = g.lz;
+      } else {
+        const float dx = px - obx, dy = py - oby, dz = pz - obz;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        hx = dx * inv; hy = dy * inv; hz = dz * inv;
+      }
+      lab[0].add(w * hx * hx);
+      lab[1].add(w * hy * hy);
+      lab[2].add(w * hz * hz);
+      lab[3].add(w * hx * hy);
+      lab[4].add(w * hy * hz);
+      lab[5].add(w * hz * hx);
+    }
+  }
+  if (is_ran) {
+#pragma unroll
+    for (int q = 0; q < LAB_NSUM; ++q) {
+      const double v = block_sum_f64(lab[q].value(), sh);
+      if (threadIdx.x == 0) labpart[(size_t)blockIdx.x * LAB_NSUM + q] = v;
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void tap_weights(float u, int& i0, float* wt) {
+  if (P == 2) {
+    const float f = floorf(u);
+    const float d = u - f;
+    i0 = (int)f;
+    wt[0] = 1.f - d;
+    wt[1] = d;
+  } else {
+    const float f = floorf(u + 0.5f);
+    const float d = u - f;
+    i0 = (int)f - 1;
+    const float a = 0.5f - d, b = 0.5f + d;
+    wt[0] = 0.5f * a * a;
+    wt[1] = 0.75f - d * d;
+    wt[2] = 0.5f * b * b;
+  }
+}
+
+// One block per tile.  The tile's region [t*16 - 1, t*16 + 17)^3 covers the
+// taps of every object whose centre cell lies in the tile.
+template <int P, bool W2>
+__global__ void __launch_bounds__(256) k_tile_accum(GeomDev g, int ntx, const int* __restrict__ off,
+                                                    const float4* __restrict__ xyzv, const float* __restrict__ vw2,
+                                                    unsigned long long* __restrict__ grid,
+                                                    unsigned long long* __restrict__ gridw) {
+  extern __shared__ unsigned long long reg[];
+  unsigned long long* regw = reg + kReg3;
+  const int t = blockIdx.x;
+  const int a = off[t], b = off[t + 1];
+  if (a == b) return;
+  const int N = g.N;
+  for (int i = threadIdx.x; i < kReg3; i += blockDim.x) {
+    reg[i] = 0ull;
+    if (W2) regw[i] = 0ull;
+  }
+  __syncthreads();
+  const int tx = t % ntx, ty = (t / ntx) % ntx, tz = t / (ntx * ntx);
+  const int lx0 = tx * kTile - 1, ly0 = ty * kTile - 1, lz0 = tz * kTile - 1;
+  for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
+    const float4 o = xyzv[i];
+    const float wv = W2 ? vw2[i] : 0.f;
+    const float ux = (o.x - g.ox) * g.invH, uy = (o.y - g.oy) * g.invH, uz = (o.z - g.oz) * g.invH;
+    int ix, iy, iz;
+    float wx[P], wy[P], wz[P];
+    tap_weights<P>(ux, ix, wx);
+    tap_weights<P>(uy, iy, wy);
+    tap_weights<P>(uz, iz, wz);
+    // taps relative to the region (periodic positions may lie one box away)
+    const int cx = ix + (P == 3 ? 1 : 0), cy = iy + (P == 3 ? 1 : 0), cz = iz + (P == 3 ? 1 : 0);
+    const int rx = ix - (cx - wrapN(cx, N)) - lx0;
+    const int ry = iy - (cy - wrapN(cy, N)) - ly0;
+    const int rz = iz - (cz - wrapN(cz, N)) - lz0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const float wzy = wz[p] * wy[q];
+        const int base = ((rz + p) * kReg + (ry + q)) * kReg + rx;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+          const float tw = wzy * wx[r];
+          atomicAdd(reg + base + r, (unsigned long long)__float2ll_rn(o.w * tw * kFixScaleF));
+          if (W2) atomicAdd(regw + base + r, (unsigned long long)__float2ll_rn(wv * tw * kFixScaleF));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kReg3; i += blockDim.x) {
+    const unsigned long long v = reg[i];
+    const unsigned long long vw = W2 ? regw[i] : 0ull;
+    if (v == 0ull && vw == 0ull) continue;
+    const int lx = i % kReg, ly = (i / kReg) % kReg, lz = i / (kReg * kReg);
+    const size_t gi = ((size_t)wrapN(lz0 + lz, N) * N + wrapN(ly0 + ly, N)) * N + wrapN(lx0 + lx, N);
+    if (v) atomicAdd(grid + gi, v);
+    if (W2 && vw) atomicAdd(gridw + gi, vw);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, double* part, int* cnt, int* err,
+                             int nblk, cudaStream_t s) {
+  if (c.n == 0) {
+    cudaMemsetAsync(part, 0, sizeof(double) * SC_NSUM * nblk, s);
+    return cudaGetLastError();
+  }
+  const int ntx = assign_tiles_per_axis(g.N);
+  if (g.assign == 2) k_bin_count<2><<<nblk, 256, 0, s>>>(c, is_ran, g, ntx, part, cnt, err);
+  else k_bin_count<3><<<nblk, 256, 0, s>>>(c, is_ran, g, ntx, part, cnt, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, cudaStream_t s) {
+  k_scan_tiles<<<1, 1024, 0, s>>>(cnt, ntiles, off, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
+                               int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s) {
+  if (c.n == 0) {
+    if (is_ran) cudaMemsetAsync(labpart, 0, sizeof(double) * LAB_NSUM * nblk, s);
+    return cudaGetLastError();
+  }
+  const int ntx = assign_tiles_per_axis(g.N);
+  if (g.assign == 2)
+    k_bin_scatter<2><<<nblk, 256, 0, s>>>(c, is_ran, g, ntx, (float)obs[0], (float)obs[1], (float)obs[2], ds, cur,
+                                          xyzv, vw2, labpart);
+  else
+    k_bin_scatter<3><<<nblk, 256, 0, s>>>(c, is_ran, g, ntx, (float)obs[0], (float)obs[1], (float)obs[2], ds, cur,
+                                          xyzv, vw2, labpart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xyzv, const float* vw2,
+                              unsigned long long* grid, unsigned long long* gridw, cudaStream_t s) {
+  const int ntx = assign_tiles_per_axis(g.N);
+  const int ntiles = ntx * ntx * ntx;
+  const bool w2 = gridw != nullptr;
+  const size_t sm = sizeof(unsigned long long) * kReg3 * (w2 ? 2 : 1);
+#define FKP_TA(PP, WW)                                                                                 \
+  do {                                                                                                 \
+    cudaFuncSetAttribute(k_tile_accum<PP, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    k_tile_accum<PP, WW><<<ntiles, 256, sm, s>>>(g, ntx, off, xyzv, vw2, grid, gridw);                 \
+  } while (0)
+  if (g.assign == 2) {
+    if (w2) FKP_TA(2, true); else FKP_TA(2, false);
+  } else {
+    if (w2) FKP_TA(3, true); else FKP_TA(3, false);
+  }
+#undef FKP_TA
+  return cudaGetLastError();
+}
+
+}  // namespace fkp
