@@ -114,6 +114,7 @@ class Clocks:
 def algorithmic_bytes(N, nfields, ngroups, n_obj):
     half = N * N * (N // 2 + 1) * 8
     return {
+        "count": 16 * n_obj,                         # catalog x,y,z,nbar read (scalars, tile counts)
         "assign": 16 * n_obj + 8 * N ** 3,          # catalog x,y,z,nbar read; fixed-point grid written once
         "xpass": 8 * N ** 3 + nfields * half,        # grid read; moment half-spectra written
         "ypass": (nfields + ngroups) * half,         # moment spectra read; k_z-power groups written
@@ -269,7 +270,7 @@ def run_gpu(args):
 
     # roofline of the dominant kernel
     st = np.mean(np.array(stage), axis=0)
-    names = {"assign": st[1], "xpass": st[2], "ypass": st[3], "zpass": st[4]}
+    names = {"count": st[0], "assign": st[1], "xpass": st[2], "ypass": st[3], "zpass": st[4]}
     mt_fields, mt_groups = 22, 9
     ab = algorithmic_bytes(sv.N, mt_fields, mt_groups, n_obj)
     dom = max(names, key=names.get)

@@ -179,6 +179,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   if (want & (FKP_P4 | FKP_B4)) lmax = 4;
   P->lmax = lmax;
   build_moments(lmax, P->mt);
+  if (!moments_match(P->mt)) { delete P; return set_error(FKP_ESTATE, "internal: moment table order mismatch"); }
   if (!radix_plan(N, P->fp)) { delete P; return set_error(FKP_EINVAL, "no radix plan for N=%d", N); }
 
   // geometry as the kernels see it
@@ -371,8 +372,10 @@ int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream
       return set_error(FKP_ENOMEM, "cannot allocate the tile-sorted catalog (%lld objects)", ntot);
     P->sort_cap = cap;
   }
-  const int nb = P->nblk_cat;
-  auto nblocks = [&](long long n) { return (int)std::max<long long>(1, std::min<long long>(nb, (n + 255) / 256)); };
+  // one 1024-thread block per SM for the binning kernels (their shared
+  // histogram spans every tile)
+  const int nb = P->ctx->nsm;
+  auto nblocks = [&](long long n) { return (int)std::max<long long>(1, std::min<long long>(nb, (n + 4095) / 4096)); };
   const int nbg = nblocks(gal.n), nbr = nblocks(ran.n);
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
   CK(cudaMemsetAsync(P->d_tcnt, 0, sizeof(int) * P->ntiles, s));

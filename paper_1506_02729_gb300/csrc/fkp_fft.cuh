@@ -207,18 +207,19 @@ __host__ __device__ constexpr int radix_at(int n, int s) {
   return 1;
 }
 
+// The block is 2-D: threadIdx.x = pencil (blockDim.x == P), threadIdx.y
+// strides over the N/R butterflies of a stage (blockDim.y == NT / P).
 template <int N, int P, int NT, int DIR, int R, int NS>
 __device__ __forceinline__ void fft_ct_stage(const float2* __restrict__ src, float2* __restrict__ dst,
                                              const float2* __restrict__ tw) {
   constexpr int NB = N / R;
-  constexpr int TOT = NB * P;
+  constexpr int JT = NT / P;
   constexpr int TWS = N / (NS * R);
+  const int p = threadIdx.x;
 #pragma unroll
-  for (int t0 = 0; t0 < TOT; t0 += NT) {
-    const int t = t0 + (int)threadIdx.x;
-    if ((TOT % NT) == 0 || t < TOT) {
-      const int p = t % P;
-      const int j = t / P;
+  for (int j0 = 0; j0 < NB; j0 += JT) {
+    const int j = j0 + (int)threadIdx.y;
+    if ((NB % JT) == 0 || j < NB) {
       const int k = j % NS;
       float2 v[R];
 #pragma unroll
@@ -252,8 +253,8 @@ __device__ __forceinline__ float2* fft_ct_run(float2* a, float2* b, const float2
 }
 
 // Transforms P interleaved pencils held in a (b is scratch of the same size).
-// Returns the buffer holding the result.  All NT threads of the block call it;
-// it ends with a __syncthreads().
+// Returns the buffer holding the result.  All NT threads of the (P, NT/P)
+// block call it; it ends with a __syncthreads().
 template <int N, int P, int NT, int DIR>
 __device__ __forceinline__ float2* fft_ct(float2* a, float2* b, const float2* tw) {
   return fft_ct_run<N, P, NT, DIR, 0, 1>(a, b, tw);
@@ -267,7 +268,8 @@ __device__ __forceinline__ void fft_rt_stage(const float2* __restrict__ src, flo
   const int nb = n / R;
   const int tot = nb * P;
   const int tws = n / (ns * R);
-  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+  const int nthr = blockDim.x * blockDim.y;
+  for (int t = threadIdx.y * blockDim.x + threadIdx.x; t < tot; t += nthr) {
     const int p = t % P;
     const int j = t / P;
     const int k = j % ns;

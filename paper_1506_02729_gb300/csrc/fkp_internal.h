@@ -75,6 +75,7 @@ void bisp_plan_free(Plan* P);
 // launch wrappers (k_power.cu)
 int yz_tiles(int N);
 int tiles_x(int N);
+bool moments_match(const MomentTable& mt);
 size_t field_elems(int N);
 cudaError_t launch_scalars_finalize(const double* part, int nbg, int nbr, long long ng, long long nr, int amode,
                                     double* ds, cudaStream_t s);

@@ -6,7 +6,8 @@
 //   count    per object: FKP weight and the compensated FP32 partial sums of
 //            the scalars (W, sum w^2, sum w^3, sum nbar w^2, sum nbar^2 w^3,
 //            for alpha, I_22, I_33, N_0, S_3: eqs. I22def, N0true, Noise0),
-//            the geometry check and one count for the object's tile;
+//            the geometry check and one count for the object's tile (block
+//            histogram in shared memory);
 //   scan     tile offsets (exclusive prefix sum);
 //   scatter  each object's (x, y, z, value) to its tile's segment, value =
 //            w for galaxies and -alpha w for randoms (and the w^2-weighted
@@ -64,11 +65,18 @@ __device__ __forceinline__ int tile_of(int cx, int cy, int cz, int N, int ntx) {
 
 // ---------------------------------------------------------------------------
 
+// Counts go to a shared-memory histogram over all tiles and are added to the
+// global counts once per block and tile.
+constexpr int kBinThreads = 1024;
+
 template <int P>
-__global__ void __launch_bounds__(256) k_bin_count(CatDev c, int is_ran, GeomDev g, int ntx,
-                                                   double* __restrict__ part, int* __restrict__ cnt,
-                                                   int* __restrict__ err) {
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran, GeomDev g, int ntx, int ntiles,
+                                                           double* __restrict__ part, int* __restrict__ cnt,
+                                                           int* __restrict__ err) {
+  extern __shared__ int hist[];
   __shared__ double sh[32];
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
+  __syncthreads();
   KahanF s_w, s_w2, s_w3, s_nw2, s_n2w3;
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
@@ -85,11 +93,13 @@ __global__ void __launch_bounds__(256) k_bin_count(CatDev c, int is_ran, GeomDev
     }
     int cx, cy, cz;
     if (centre_cell<P>(g, __ldg(c.x + i), __ldg(c.y + i), __ldg(c.z + i), cx, cy, cz))
-      atomicAdd(cnt + tile_of(cx, cy, cz, g.N, ntx), 1);
+      atomicAdd(hist + tile_of(cx, cy, cz, g.N, ntx), 1);
     else
       bad = true;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, 1);
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+    if (hist[t]) atomicAdd(cnt + t, hist[t]);
   double* out = part + (size_t)blockIdx.x * SC_NSUM;
   double v;
   if (!is_ran) {
@@ -131,21 +141,40 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ cnt
   if (threadIdx.x == blockDim.x - 1) off[ntiles] = part[threadIdx.x];
 }
 
+// Each block owns a contiguous chunk of objects.  Pass 1 counts the chunk's
+// objects per tile in shared memory; one global atomic per touched tile then
+// reserves the chunk's range inside the tile's segment; pass 2 re-reads the
+// chunk and writes each object at its reserved slot.
 template <int P>
-__global__ void __launch_bounds__(256) k_bin_scatter(CatDev c, int is_ran, GeomDev g, int ntx, float obx, float oby,
-                                                     float obz, const double* __restrict__ ds, int* __restrict__ cur,
-                                                     float4* __restrict__ xyzv, float* __restrict__ vw2,
-                                                     double* __restrict__ labpart) {
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ran, GeomDev g, int ntx, int ntiles,
+                                                             float obx, float oby, float obz,
+                                                             const double* __restrict__ ds, int* __restrict__ cur,
+                                                             float4* __restrict__ xyzv, float* __restrict__ vw2,
+                                                             double* __restrict__ labpart) {
+  extern __shared__ int hist[];
   __shared__ double sh[32];
   const float alpha = (float)ds[DS_ALPHA];
+  const long long chunk = (c.n + gridDim.x - 1) / gridDim.x;
+  const long long i0 = blockIdx.x * chunk;
+  const long long i1 = i0 + chunk < c.n ? i0 + chunk : c.n;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
+  __syncthreads();
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    int cx, cy, cz;
+    if (centre_cell<P>(g, __ldg(c.x + i), __ldg(c.y + i), __ldg(c.z + i), cx, cy, cz))
+      atomicAdd(hist + tile_of(cx, cy, cz, g.N, ntx), 1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+    if (hist[t]) hist[t] = atomicAdd(cur + t, hist[t]);
+  __syncthreads();
   KahanF lab[LAB_NSUM];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const float w = fkp_weight(c, i, g.P_fkp);
     const float px = __ldg(c.x + i), py = __ldg(c.y + i), pz = __ldg(c.z + i);
     int cx, cy, cz;
     if (centre_cell<P>(g, px, py, pz, cx, cy, cz)) {
-      const int slot = atomicAdd(cur + tile_of(cx, cy, cz, g.N, ntx), 1);
+      const int slot = atomicAdd(hist + tile_of(cx, cy, cz, g.N, ntx), 1);
       xyzv[slot] = make_float4(px, py, pz, is_ran ? -alpha * w : w);
       if (vw2) vw2[slot] = is_ran ? alpha * alpha * w * w : w * w;
     }
@@ -267,8 +296,15 @@ cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, doub
     return cudaGetLastError();
   }
   const int ntx = assign_tiles_per_axis(g.N);
-  if (g.assign == 2) k_bin_count<2><<<nblk, 256, 0, s>>>(c, is_ran, g, ntx, part, cnt, err);
-  else k_bin_count<3><<<nblk, 256, 0, s>>>(c, is_ran, g, ntx, part, cnt, err);
+  const int ntiles = ntx * ntx * ntx;
+  const size_t sm = sizeof(int) * ntiles;
+  if (g.assign == 2) {
+    cudaFuncSetAttribute(k_bin_count<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bin_count<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
+  } else {
+    cudaFuncSetAttribute(k_bin_count<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bin_count<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
+  }
   return cudaGetLastError();
 }
 
@@ -284,12 +320,17 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
     return cudaGetLastError();
   }
   const int ntx = assign_tiles_per_axis(g.N);
-  if (g.assign == 2)
-    k_bin_scatter<2><<<nblk, 256, 0, s>>>(c, is_ran, g, ntx, (float)obs[0], (float)obs[1], (float)obs[2], ds, cur,
-                                          xyzv, vw2, labpart);
-  else
-    k_bin_scatter<3><<<nblk, 256, 0, s>>>(c, is_ran, g, ntx, (float)obs[0], (float)obs[1], (float)obs[2], ds, cur,
-                                          xyzv, vw2, labpart);
+  const int ntiles = ntx * ntx * ntx;
+  const size_t sm = sizeof(int) * ntiles;
+  if (g.assign == 2) {
+    cudaFuncSetAttribute(k_bin_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bin_scatter<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, (float)obs[0], (float)obs[1],
+                                                   (float)obs[2], ds, cur, xyzv, vw2, labpart);
+  } else {
+    cudaFuncSetAttribute(k_bin_scatter<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bin_scatter<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, (float)obs[0], (float)obs[1],
+                                                   (float)obs[2], ds, cur, xyzv, vw2, labpart);
+  }
   return cudaGetLastError();
 }
 

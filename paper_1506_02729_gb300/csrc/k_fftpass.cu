@@ -44,28 +44,63 @@ __device__ __forceinline__ float pw5(const float* h, int e) {
 // x-pass
 // ----------------------------------------------------------------------------
 
-template <int N_, int NP>
-__global__ void __launch_bounds__(kNT) k_xpass2(const unsigned long long* __restrict__ gq, const float* __restrict__ gf,
-                                                GeomDev g, MomentTable mt, FftPlan fp,
-                                                const float2* __restrict__ twg, float2* __restrict__ S1) {
+// Moment-field exponents (i, j, k) of x^_x^i x^_y^j x^_z^k in the order the
+// host's moment table uses: multipole ell = 0, 2, 4, then k_z power p, then j.
+__host__ __device__ constexpr int nfields_of(int lmax) { return lmax >= 4 ? 22 : (lmax >= 2 ? 7 : 1); }
+__host__ __device__ constexpr int field_exp(int q, int a) {
+  int idx = 0;
+  for (int ell = 0; ell <= 4; ell += 2)
+    for (int p = 0; p <= ell; ++p)
+      for (int j = 0; j <= ell - p; ++j) {
+        if (idx == q) return a == 0 ? ell - p - j : (a == 1 ? j : p);
+        ++idx;
+      }
+  return 0;
+}
+
+// Moment values of pencil pairs P.., packed two real fields per complex value;
+// template recursion keeps every exponent a compile-time constant.
+template <int NP, int NF, int P>
+__device__ __forceinline__ void build_pairs(float f, const float (&hx)[5], const float (&hy)[5], const float (&hz)[5],
+                                            float2* dst) {
+  if constexpr (P < NP) {
+    constexpr int a0 = field_exp(2 * P, 0), b0 = field_exp(2 * P, 1), c0 = field_exp(2 * P, 2);
+    constexpr int a1 = field_exp(2 * P + 1, 0), b1 = field_exp(2 * P + 1, 1), c1 = field_exp(2 * P + 1, 2);
+    const float m0 = f * hx[a0] * hy[b0] * hz[c0];
+    const float m1 = (2 * P + 1 < NF) ? f * hx[a1] * hy[b1] * hz[c1] : 0.f;
+    dst[P] = make_float2(m0, m1);
+    build_pairs<NP, NF, P + 1>(f, hx, hy, hz, dst);
+  }
+}
+
+// Block (NP, 32): threadIdx.x is the packed pencil (pair of fields) in the
+// FFT; a radix-R stage's N/R butterflies per pencil are strided over
+// threadIdx.y, so no index is divided by NP.
+template <int N_, int LMAX>
+__global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
+    const unsigned long long* __restrict__ gq, const float* __restrict__ gf, GeomDev g, FftPlan fp,
+    const float2* __restrict__ twg, float2* __restrict__ S1) {
+  constexpr int NF = nfields_of(LMAX);
+  constexpr int NP = (NF + 1) / 2;
+  constexpr int NTX = 32 * NP;
   extern __shared__ float2 sm[];
   const int N = N_ ? N_ : g.N;
   const int NH = N / 2 + 1, NXT = (NH + kT - 1) / kT;
+  const int tid = threadIdx.y * NP + threadIdx.x;
   float2* tw = sm;
   float* rowF = reinterpret_cast<float*>(sm + N);
   float2* A = sm + N + N / 2;
   float2* B = A + NP * N;
-  for (int i = threadIdx.x; i < N; i += kNT) tw[i] = twg[i];
+  for (int i = tid; i < N; i += NTX) tw[i] = twg[i];
   const size_t fsz = (size_t)N * NXT * N * kT;
-  const int nf = mt.nfields;
   for (int row = blockIdx.x; row < N * N; row += gridDim.x) {
     const int z = row / N, y = row - z * N;
     const size_t gbase = (size_t)row * N;
-    for (int x = threadIdx.x; x < N; x += kNT)
+    for (int x = tid; x < N; x += NTX)
       rowF[x] = gq ? (float)(long long)gq[gbase + x] * kFixInvF : gf[gbase + x];
     __syncthreads();
     const float Y = fmaf((float)y, g.H, g.ry), Z = fmaf((float)z, g.H, g.rz);
-    for (int x = threadIdx.x; x < N; x += kNT) {
+    for (int x = tid; x < N; x += NTX) {
       float hx[5], hy[5], hz[5];
       if (g.los_inf) {
         hx[1] = g.lx; hy[1] = g.ly; hz[1] = g.lz;
@@ -75,22 +110,18 @@ __global__ void __launch_bounds__(kNT) k_xpass2(const unsigned long long* __rest
         const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
         hx[1] = X * inv; hy[1] = Y * inv; hz[1] = Z * inv;
       }
+      hx[0] = hy[0] = hz[0] = 1.f;
       hx[2] = hx[1] * hx[1]; hx[3] = hx[2] * hx[1]; hx[4] = hx[2] * hx[2];
       hy[2] = hy[1] * hy[1]; hy[3] = hy[2] * hy[1]; hy[4] = hy[2] * hy[2];
       hz[2] = hz[1] * hz[1]; hz[3] = hz[2] * hz[1]; hz[4] = hz[2] * hz[2];
-      const float f = rowF[x];
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const int q0 = 2 * p, q1 = 2 * p + 1;
-        const float m0 = f * pw5(hx, mt.e[q0][0]) * pw5(hy, mt.e[q0][1]) * pw5(hz, mt.e[q0][2]);
-        const float m1 = q1 < nf ? f * pw5(hx, mt.e[q1][0]) * pw5(hy, mt.e[q1][1]) * pw5(hz, mt.e[q1][2]) : 0.f;
-        A[x * NP + p] = make_float2(m0, m1);
-      }
+      build_pairs<NP, NF, 0>(rowF[x], hx, hy, hz, A + x * NP);
     }
     __syncthreads();
-    const float2* R = fft_any<N_, NP, kNT, -1>(A, B, fp, tw);
+    const float2* R = fft_any<N_, NP, NTX, -1>(A, B, fp, tw);
+    // unpack: consecutive threads take consecutive k_x of one field, so the
+    // stores into the tile-major layout are 64-byte contiguous runs
     const int ncol = NXT * kT;
-    for (int t = threadIdx.x; t < NP * ncol; t += kNT) {
+    for (int t = tid; t < NP * ncol; t += NTX) {
       const int p = t / ncol, k = t - p * ncol;
       float2 o0 = make_float2(0.f, 0.f), o1 = o0;
       if (k < NH) {
@@ -100,9 +131,8 @@ __global__ void __launch_bounds__(kNT) k_xpass2(const unsigned long long* __rest
         o1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
       }
       const size_t off = (((size_t)z * NXT + (k >> 3)) * N + y) * kT + (k & 7);
-      const int q0 = 2 * p, q1 = 2 * p + 1;
-      S1[(size_t)q0 * fsz + off] = o0;
-      if (q1 < nf) S1[(size_t)q1 * fsz + off] = o1;
+      S1[(size_t)(2 * p) * fsz + off] = o0;
+      if (2 * p + 1 < NF) S1[(size_t)(2 * p + 1) * fsz + off] = o1;
     }
     __syncthreads();
   }
@@ -112,6 +142,8 @@ __global__ void __launch_bounds__(kNT) k_xpass2(const unsigned long long* __rest
 // y-pass
 // ----------------------------------------------------------------------------
 
+// Block (8, 32): threadIdx.x is the k_x column of the tile (the FFT pencil),
+// threadIdx.y the run of k_y this thread accumulates.
 template <int N_>
 __global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg,
@@ -129,8 +161,9 @@ __global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1
   const size_t fsz = (size_t)N * NXT * N * kT;
   const size_t gsz = fsz;
   const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
-  for (int i = threadIdx.x; i < N; i += kNT) tw[i] = twg[i];
-  if (threadIdx.x == 0) {
+  const int tid = threadIdx.y * kT + threadIdx.x;
+  for (int i = tid; i < N; i += kNT) tw[i] = twg[i];
+  if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_fence_init();
@@ -140,11 +173,11 @@ __global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1
   int total = 0;
   for (int gi = 0; gi < mt.ngroups; ++gi) total += mt.g_nmem[gi];
   auto src_of = [&](int q) { return S1 + (size_t)q * fsz + ((size_t)z * NXT + xt) * tile; };
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     mbar_expect_tx(&bar[0], bytes);
     tma_load_1d(buf0, src_of(mt.g_field[0][0]), bytes, &bar[0]);
   }
-  const int c = threadIdx.x % kT, run = threadIdx.x / kT;
+  const int c = threadIdx.x, run = threadIdx.y;
   const int rl = (N + kRun - 1) / kRun;
   const float nx = (float)(xt * kT + c);
   int it = 0;
@@ -155,7 +188,7 @@ __global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1
     for (int m = 0; m < mt.g_nmem[gi]; ++m, ++it) {
       const int cur = it & 1;
       float2* bc = cur ? buf1 : buf0;
-      if (threadIdx.x == 0 && it + 1 < total) {
+      if (tid == 0 && it + 1 < total) {
         int g2 = gi, m2 = m + 1;
         if (m2 == mt.g_nmem[gi]) { g2 = gi + 1; m2 = 0; }
         fence_proxy_async();
@@ -191,6 +224,10 @@ __global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1
 // z-pass (MODE 0: P bins; 1: P bins + export on the shells; 2: F^w shell sums)
 // ----------------------------------------------------------------------------
 
+// Block (8, 32) as in the y-pass.  The epilogue walks each thread's run of
+// consecutive k_z (|n| is monotone along it), sums a run in FP32 and adds it
+// to the block's FP32 bins in shared memory when the bin changes; blocks'
+// bins are reduced in FP64 in a fixed order.
 template <int N_, int MODE>
 __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg, ZParams zp,
@@ -206,26 +243,27 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
   float2* work = buf1 + tile;
   float2* tw = work + tile;
   const int nkey = MODE == 2 ? zp.nshells : zp.nbins;
-  double* sb = reinterpret_cast<double*>(tw + N);
+  float* sb = reinterpret_cast<float*>(tw + N);  // [BQ_N][nkey]
   int* sc = reinterpret_cast<int*>(sb + BQ_N * nkey);
   const int xt = blockIdx.x, ky = blockIdx.y;
+  const int tid = threadIdx.y * kT + threadIdx.x;
   const size_t gsz = (size_t)N * NXT * N * kT;
   const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
-  for (int i = threadIdx.x; i < N; i += kNT) tw[i] = twg[i];
-  for (int t = threadIdx.x; t < BQ_N * nkey; t += kNT) sb[t] = 0.0;
-  for (int t = threadIdx.x; t < nkey; t += kNT) sc[t] = 0;
-  if (threadIdx.x == 0) {
+  for (int i = tid; i < N; i += kNT) tw[i] = twg[i];
+  for (int t = tid; t < BQ_N * nkey; t += kNT) sb[t] = 0.f;
+  for (int t = tid; t < nkey; t += kNT) sc[t] = 0;
+  if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
   auto src_of = [&](int gi) { return S2 + (size_t)gi * gsz + ((size_t)xt * N + ky) * tile; };
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     mbar_expect_tx(&bar[0], bytes);
     tma_load_1d(buf0, src_of(0), bytes, &bar[0]);
   }
-  const int c = threadIdx.x % kT, run = threadIdx.x / kT;
+  const int c = threadIdx.x, run = threadIdx.y;
   const int rl = (N + kRun - 1) / kRun;
   const int z0 = run * rl;
   float2 f0[kMaxRL], s2[kMaxRL], s4[kMaxRL];
@@ -238,7 +276,7 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
   for (int gi = 0; gi < mt.ngroups; ++gi) {
     const int cur = gi & 1;
     float2* bc = cur ? buf1 : buf0;
-    if (threadIdx.x == 0 && gi + 1 < mt.ngroups) {
+    if (tid == 0 && gi + 1 < mt.ngroups) {
       fence_proxy_async();
       mbar_expect_tx(&bar[cur ^ 1], bytes);
       tma_load_1d(cur ? buf0 : buf1, src_of(gi + 1), bytes, &bar[cur ^ 1]);
@@ -267,7 +305,6 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
     }
     __syncthreads();
   }
-  // recombination and binning: each thread walks its run of k_z
   const int kx = xt * kT + c;
   const bool colok = kx < N / 2;
   const int nyv = smode(ky, N);
@@ -335,7 +372,7 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
       if (curb >= 0) {
         atomicAdd(sc + curb, cnt);
 #pragma unroll
-        for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, (double)acc[q]);
+        for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, acc[q]);
       }
       curb = b;
       cnt = 0;
@@ -351,13 +388,13 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
   if (curb >= 0) {
     atomicAdd(sc + curb, cnt);
 #pragma unroll
-    for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, (double)acc[q]);
+    for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, acc[q]);
   }
   __syncthreads();
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   const int nblk = gridDim.x * gridDim.y;
-  for (int t = threadIdx.x; t < BQ_N * nkey; t += kNT) part[(size_t)t * nblk + blk] = sb[t];
-  for (int t = threadIdx.x; t < nkey; t += kNT) partc[(size_t)t * nblk + blk] = sc[t];
+  for (int t = tid; t < BQ_N * nkey; t += kNT) part[(size_t)t * nblk + blk] = (double)sb[t];
+  for (int t = tid; t < nkey; t += kNT) partc[(size_t)t * nblk + blk] = sc[t];
 }
 
 // ----------------------------------------------------------------------------
@@ -365,49 +402,58 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
 // ----------------------------------------------------------------------------
 
 int tiles_x(int N) { return (N / 2 + 1 + kT - 1) / kT; }
+
+// The x-pass builds the moment fields from compile-time exponents; the host's
+// moment table must list the fields in the same order.
+bool moments_match(const MomentTable& mt) {
+  for (int q = 0; q < mt.nfields; ++q)
+    for (int a = 0; a < 3; ++a)
+      if (mt.e[q][a] != field_exp(q, a)) return false;
+  return mt.nfields == nfields_of(4) || mt.nfields == nfields_of(2) || mt.nfields == nfields_of(0);
+}
 size_t field_elems(int N) { return (size_t)N * tiles_x(N) * N * kT; }
 int yz_tiles(int N) { return tiles_x(N); }
 
 static size_t xsm(int N, int NP) { return sizeof(float2) * (N + N / 2 + 2 * (size_t)NP * N); }
 static size_t ysm(int N) { return 128 + sizeof(float2) * (3 * (size_t)N * kT + N); }
-static size_t zsm(int N, int nkey) { return ysm(N) + sizeof(double) * BQ_N * nkey + sizeof(int) * nkey; }
+static size_t zsm(int N, int nkey) { return ysm(N) + sizeof(float) * BQ_N * nkey + sizeof(int) * nkey; }
 
-template <int N_, int NP>
-static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
-                        const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s) {
+template <int N_, int LMAX>
+static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
+                        const float2* tw, float2* S1, int nsm, cudaStream_t s) {
+  constexpr int NP = (nfields_of(LMAX) + 1) / 2;
   const size_t sm = xsm(g.N, NP);
-  cudaFuncSetAttribute(k_xpass2<N_, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_xpass2<N_, LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, NP>, kNT, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, LMAX>, 32 * NP, sm);
   int grid = nsm * (occ > 0 ? occ : 1) * 2;
   if (grid > g.N * g.N) grid = g.N * g.N;
-  k_xpass2<N_, NP><<<grid, kNT, sm, s>>>(gq, gf, g, mt, fp, tw, S1);
+  k_xpass2<N_, LMAX><<<grid, dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1);
   return cudaGetLastError();
 }
 
-template <int NP>
-static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
-                             const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s) {
-  if (NP == 11) {
+template <int LMAX>
+static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
+                             const float2* tw, float2* S1, int nsm, cudaStream_t s) {
+  if (LMAX == 4) {
     switch (g.N) {
-      case 512: return xrun<512, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
-      case 384: return xrun<384, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
-      case 360: return xrun<360, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
-      case 256: return xrun<256, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
-      case 128: return xrun<128, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
-      case 64: return xrun<64, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
+      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
+      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
+      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
+      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
+      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
       default: break;
     }
   }
-  return xrun<0, NP>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
 }
 
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s) {
-  const int np = (mt.nfields + 1) / 2;
-  if (np == 11) return xdispatch<11>(gq, gf, g, mt, fp, tw, S1, nsm, s);
-  if (np == 4) return xdispatch<4>(gq, gf, g, mt, fp, tw, S1, nsm, s);
-  return xdispatch<1>(gq, gf, g, mt, fp, tw, S1, nsm, s);
+  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s);
+  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s);
+  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s);
 }
 
 template <int N_>
@@ -415,7 +461,7 @@ static cudaError_t yrun(const float2* S1, const GeomDev& g, const MomentTable& m
                         const float2* tw, float2* S2, int* err, cudaStream_t s) {
   const size_t sm = ysm(g.N);
   cudaFuncSetAttribute(k_ypass2<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_ypass2<N_><<<dim3(tiles_x(g.N), g.N), kNT, sm, s>>>(S1, g, mt, fp, tw, S2, err);
+  k_ypass2<N_><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNT / kT), sm, s>>>(S1, g, mt, fp, tw, S2, err);
   return cudaGetLastError();
 }
 
@@ -437,7 +483,8 @@ static cudaError_t zrun(const float2* S2, const GeomDev& g, const MomentTable& m
                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
   const size_t sm = zsm(g.N, MODE == 2 ? zp.nshells : zp.nbins);
   cudaFuncSetAttribute(k_zpass2<N_, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_zpass2<N_, MODE><<<dim3(tiles_x(g.N), g.N), kNT, sm, s>>>(S2, g, mt, fp, tw, zp, part, partc, err);
+  k_zpass2<N_, MODE><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNT / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part, partc,
+                                                                             err);
   return cudaGetLastError();
 }
 

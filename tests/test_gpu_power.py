@@ -77,14 +77,14 @@ def test_ragged_grids_match_oracle(small_mock, N, assign):
 
 def test_host_catalogs_equal_device_catalogs(small_mock):
     """The host-pointer path (copies inside the call) gives the same fixed-point
-    grid, so the same P_l up to the FP64 order of the bin sums."""
+    grid, so the same P_l up to the FP32 order of the per-block bin sums."""
     fkp = _fkp()
     sv, gal, ran = small_mock
     plan = fkp.Plan(sv.geometry(), _bins_small(sv.L))
     a = plan.power(gal, ran)
     b = plan.power(to_device(gal), to_device(ran))
     for k in ("P0", "P2", "P4", "P4b", "k_eff"):
-        assert np.allclose(a[k], b[k], rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(a["P0"])), equal_nan=True), k
+        assert np.allclose(a[k], b[k], rtol=1e-6, atol=1e-6 * np.nanmax(np.abs(a["P0"])), equal_nan=True), k
     assert a["alpha"] == b["alpha"] and a["I22"] == b["I22"]
 
 
@@ -96,7 +96,7 @@ def test_repeat_runs_agree(small_mock):
     a = plan.power(g, r)
     b = plan.power(g, r)
     for k in ("P0", "P2", "P4", "P4b"):
-        assert np.allclose(a[k], b[k], rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(a["P0"])), equal_nan=True), k
+        assert np.allclose(a[k], b[k], rtol=1e-6, atol=1e-6 * np.nanmax(np.abs(a["P0"])), equal_nan=True), k
 
 
 def test_periodic_kaiser_from_grid():
