@@ -160,6 +160,28 @@ int fkp_power_from_grid(void *plan, const float *F_device, double I22, double N0
 int fkp_bispectrum(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
                    int contraction, void *cuda_stream, fkp_power_out *pout, fkp_bisp_out *bout);
 
+/* The estimator of fkp_power_from_grid for small grids without allocating
+ * any device memory: every device buffer it uses lives in one file-scope
+ * device array of about 42 MB, held by each GPU that loads the library until
+ * the process exits.  The paper has no counterpart; this is for callers that
+ * cannot call cudaMalloc while running (a process that reserved all device
+ * memory for its own pool, a real-time loop that forbids allocation after
+ * start-up, a plugin host that gives the library no allocator).
+ * Arguments: geometry and P bins as for fkp_plan_create (no plan is made),
+ * F_device the real field [z][y][x] (N^3 float32, device pointer), I22 and
+ * N0 as for fkp_power_from_grid, results in out (caller-allocated arrays of
+ * nbins entries, any may be NULL).
+ * Limits: even N <= 64 and nbins <= 64; larger requests return FKP_EINVAL
+ * with a message.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call on a device shares the array and reinitialises what
+ * must start at zero, so calls whose GPU work overlaps (two streams, or two
+ * threads) race and must be serialised by the caller.  The call
+ * synchronizes its stream before returning. */
+int fkp_power_from_grid_noalloc(const fkp_geometry_t *geom, const fkp_pbins_t *pbins, const float *F_device,
+                                double I22, double N0, void *cuda_stream, fkp_power_out *out);
+
 /* Thread-local message for the last error on this thread. */
 const char *fkp_last_error(void);
 

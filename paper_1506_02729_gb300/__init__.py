@@ -23,7 +23,8 @@ FKP_CONTRACT_FP32, FKP_CONTRACT_BF16X3 = 0, 1
 ERRORS = {-1: "FKP_EINVAL", -2: "FKP_EGEOM", -3: "FKP_ENOMEM", -4: "FKP_ETIMEOUT", -5: "FKP_ECUDA",
           -6: "FKP_ESTATE"}
 EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_plan_destroy", "fkp_plan_sizes",
-           "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version"]
+           "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version",
+           "fkp_power_from_grid_noalloc"]
 
 
 class FKPError(RuntimeError):
@@ -92,6 +93,8 @@ def lib():
         L.fkp_power_from_grid.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.POINTER(PowerOut)]
         L.fkp_bispectrum.argtypes = [vp, C.POINTER(Catalog), C.POINTER(Catalog), C.c_int, vp, C.POINTER(PowerOut),
                                      C.POINTER(BispOut)]
+        L.fkp_power_from_grid_noalloc.argtypes = [C.POINTER(Geometry), C.POINTER(PBins), vp, C.c_double,
+                                                  C.c_double, vp, C.POINTER(PowerOut)]
         L.fkp_last_error.restype = C.c_char_p
         L.fkp_version.restype = C.c_char_p
         _lib = L
@@ -261,6 +264,27 @@ class Plan:
                                     C.byref(o), C.byref(bo)))
         b["I33"], b["S3"] = bo.I33, bo.S3
         return self._scalars(o, parr), b
+
+
+def power_from_grid_noalloc(geom, pbins, F, I22=1.0, N0=0.0, stream=None):
+    """The estimator on a device field F for small grids (even N <= 64,
+    nbins <= 64) through the entry point that allocates no device memory
+    (its buffers live in a static device array shared by all calls on a
+    device; calls must not overlap on the GPU)."""
+    if not (hasattr(F, "is_cuda") and F.is_cuda and F.is_contiguous()):
+        raise TypeError("F must be a contiguous CUDA float32 tensor")
+    g = geometry(geom)
+    pb = PBins(float(pbins[0]), float(pbins[1]), int(pbins[2]))
+    nb = pb.nbins
+    arr = {k: np.full(nb, np.nan) for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw")}
+    arr["nmodes"] = np.zeros(nb, dtype=np.int64)
+    o = PowerOut()
+    for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw"):
+        setattr(o, k, arr[k].ctypes.data_as(_DP))
+    o.nmodes = arr["nmodes"].ctypes.data_as(C.POINTER(C.c_int64))
+    _check(lib().fkp_power_from_grid_noalloc(C.byref(g), C.byref(pb), F.data_ptr(), float(I22), float(N0),
+                                             _stream_handle(stream), C.byref(o)))
+    return Plan._scalars(o, arr)
 
 
 def version():
