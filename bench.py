@@ -122,6 +122,24 @@ def algorithmic_bytes(N, nfields, ngroups, n_obj):
     }
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
+    when the kernel's sources changed since the counters were taken."""
+    import hashlib
+    try:
+        srcs = [os.path.join(ROOT, "paper_1506_02729_gb300", "csrc", f) for f in ("k_fftpass.cu", "fkp_fft.cuh")]
+        sha = ",".join(hashlib.sha1(open(f, "rb").read()).hexdigest()[:12] for f in srcs)
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            if line.startswith("#") or not line.strip():
+                continue
+            kv = dict(t.split("=", 1) for t in line.split())
+            if kv.get("kernel") == kernel and kv.get("src_sha1") == sha:
+                return int(kv["bytes"])
+    except Exception:
+        return None
+    return None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -277,7 +295,8 @@ def run_gpu(args):
     pk, src = peaks()
     achieved = ab[dom] / (names[dom] * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": src,
+            "frac": achieved / pk["hbm_gbs"], "traffic": recorded_traffic(dom) if sv.N == 512 else None,
+            "algorithmic_bytes": ab[dom], "peak_source": src,
             "stage_ms": {k: float(v) for k, v in names.items()},
             "stage_GBps": {k: ab[k] / (names[k] * 1e-3) / 1e9 for k in names}}
 
