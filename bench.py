@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=512, help="grid side (512 is the benchmark workload)")
     ap.add_argument("--ran-ratio", type=float, default=50.0, help="randoms per galaxy (50 in the workload)")
+    ap.add_argument("--bisp-steps", type=int, default=3, help="timed bispectrum mocks (0 skips the B leg)")
     return ap.parse_args()
 
 
@@ -312,6 +313,8 @@ def run_gpu(args):
             "gpu_launches": 10 * args.steps,
             "roofline": roof,
             "clocks": ck}
+    if args.bisp_steps > 0:
+        line["bispectrum"] = run_bisp(args, gal, ran, dg, dr, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_mock, desc, _ = oracle_sample(gal, ran, sv, 1)
         line["cpu_baseline"] = {"value": 1.0 / t_mock, "unit": "mocks/s", "cores": cores_used(), "kind": "oracle",
@@ -321,6 +324,39 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+BSHELLS = (3, 3, 3, 37)  # centres 3(s+1) k_f, width 3 k_f, to k = 0.2 h/Mpc
+
+
+def run_bisp(args, gal, ran, dg, dr, stream):
+    """B_0,2,4 of the same catalog on a 360^3 TSC grid (37 shells to k = 0.2):
+    mocks/s of the whole P + B path and its stage times (CUDA events)."""
+    import torch
+
+    import mockgen
+    import paper_1506_02729_gb300 as fkp
+    sv = mockgen.survey_boss(N=360)
+    plan = fkp.Plan(sv.geometry(), BINS, bshells=BSHELLS, want=127)
+    plan.bispectrum(dg, dr, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st = []
+    e0.record(stream)
+    for _ in range(args.bisp_steps):
+        p, b = plan.bispectrum(dg, dr, stream=stream)
+        st.append(p["timing_ms"].copy())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.bisp_steps
+    m = np.mean(np.array(st), axis=0)
+    out = {"workload": "B_0,2,4 + P_l: BOSS-like catalog, 360^3 TSC, 37 shells of 3 k_f to k=0.2, FP32 contraction",
+           "value": 1000.0 / ms, "unit": "mocks/s", "ms_per_step": ms, "ntriangles": int(plan.ntri),
+           "stage_ms": {"grids": float(m[0] + m[1]), "F_passes": float(m[2] + m[3] + m[4]),
+                        "shell_ifft": float(m[5]), "contraction": float(m[6])}}
+    plan.close()
+    return out
 
 
 def main():

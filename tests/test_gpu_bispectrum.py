@@ -94,3 +94,31 @@ def test_aliasing_shells_are_rejected():
     with pytest.raises(fkp.FKPError) as e:
         fkp.Plan(dict(L=1000.0, N=48), (0.0, 0.01, 4), bshells=(3, 3, 3, 6), want=FKP_B0())
     assert e.value.code == -2
+
+
+@pytest.mark.slow
+def test_boss_360_bispectrum_sampled_triangles():
+    """The bispectrum workload: the BOSS-like catalog on a 360^3 TSC grid, 37
+    shells of width 3 k_f from 3 k_f (to k = 0.2): a sample of triangles
+    (equilateral, squeezed, folded, generic, largest shells) against the FP64
+    oracle, exact N_T for each."""
+    fkp = _fkp()
+    sv = mockgen.survey_boss(N=360)
+    gal, ran = mockgen.catalog(sv, 0)
+    geom = sv.geometry()
+    bs = (3, 3, 3, 37)
+    plan = fkp.Plan(geom, (0.0, 0.005, 60), bshells=bs, want=ALL)
+    p, b = plan.bispectrum(to_device(gal), to_device(ran))
+    tri = [tuple(t) for t in b["tri"].astype(int)]
+    sample = [(10, 10, 10), (36, 36, 36), (36, 35, 1), (20, 10, 10), (30, 20, 12), (25, 24, 2), (36, 18, 18)]
+    sample = [t for t in sample if t in tri]
+    assert len(sample) >= 5
+    F, Fw, sc = op.fkp_grids(gal, ran, geom, with_w2=True)
+    Fl = op.legendre(F, geom, lmax=4)
+    Fwl = op.legendre(Fw, geom, lmax=4)
+    ref = ob.bispectrum_from_fields(Fl, Fwl, sc, sv.N, bs, (0, 2, 4), tris=sample)
+    idx = [tri.index(t) for t in sample]
+    got = {k: b[k][idx] for k in ("NT", "B0", "B2", "B4", "T0")}
+    assert np.array_equal(got["NT"], ref["NT"])
+    err = b_errors(got, ref, ref["I33"], float(sv.N) ** 3)
+    assert max(err.values()) < B_TOL, err
