@@ -122,8 +122,14 @@ typedef struct {
   double I33, S3;
 } fkp_bisp_out;
 
-/* Contraction precision for the triangle sums. */
-enum { FKP_CONTRACT_FP32 = 0, FKP_CONTRACT_BF16X3 = 1 };
+/* Contraction of the triangle sums (eq. Factorize):
+ *   FP32   CUDA cores, FP32 products, compensated FP32 sums, FP64 across slices;
+ *   BF16X3 tcgen05 tensor cores, operands split v = hi + lo in BF16, products
+ *          hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory;
+ *   BF16X6 tcgen05 tensor cores, 3-way split hi + mid + lo, the six products of
+ *          order <= 2^-16: per-term error near FP32 rounding.
+ * The tensor-core modes need (number of multipoles) x (shells) <= 128. */
+enum { FKP_CONTRACT_FP32 = 0, FKP_CONTRACT_BF16X3 = 1, FKP_CONTRACT_BF16X6 = 2 };
 
 /* Context: binds a CUDA device.  hbm_budget_bytes = 0 means no limit.
  * Returns FKP_EINVAL for a bad device index, FKP_ECUDA on runtime errors. */
@@ -155,8 +161,8 @@ int fkp_power(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
 int fkp_power_from_grid(void *plan, const float *F_device, double I22, double N0,
                         void *cuda_stream, fkp_power_out *out);
 
-/* P_l and B_l of one survey (Sec. III.B).  contraction selects the plain
- * FP32 path or the BF16 hi/lo tensor-core path. */
+/* P_l and B_l of one survey (Sec. III.B).  contraction is one of
+ * FKP_CONTRACT_FP32, _BF16X3, _BF16X6. */
 int fkp_bispectrum(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
                    int contraction, void *cuda_stream, fkp_power_out *pout, fkp_bisp_out *bout);
 

@@ -56,6 +56,11 @@ struct BispState {
   int* d_spartc = nullptr;
   double* d_shell = nullptr;
   long long* d_shellc = nullptr;
+  // tensor-core contraction: columns = pairs (b >= c), outputs -> (row, column)
+  int npairs = 0, tc_slices = 0, tc_tiles = 0;
+  short2* d_pairs = nullptr;
+  int *d_om = nullptr, *d_on = nullptr;
+  float* d_tcpart = nullptr;
 };
 
 __device__ __forceinline__ int wrap_mode(int n, int N) { return n < 0 ? n + N : n; }
@@ -459,7 +464,26 @@ int bisp_plan_init(Plan* P) {
           st->items.push_back(it);
         }
       }
+  // pair columns of the tensor-core contraction and each output's (row, column)
+  std::map<long long, int> pidx;
+  std::vector<short2> pairs;
+  for (int t = 0; t < ntri; ++t) {
+    const long long key = (long long)st->tb[t] * S + st->tc[t];
+    if (!pidx.count(key)) {
+      pidx[key] = (int)pairs.size();
+      pairs.push_back(make_short2((short)st->tb[t], (short)st->tc[t]));
+    }
+  }
+  st->npairs = (int)pairs.size();
+  std::vector<int> om(std::max(1, ntri) * 3, -1), on(std::max(1, ntri) * 3, 0);
+  for (int t = 0; t < ntri; ++t)
+    for (int li = 0; li < st->nl; ++li) {
+      om[t * 3 + li] = li * S + st->ta[t];
+      on[t * 3 + li] = pidx[(long long)st->tb[t] * S + st->tc[t]];
+    }
   const long long N3 = (long long)N * N * N;
+  st->tc_slices = (int)((N3 + tc_slice_points() - 1) / tc_slice_points());
+  st->tc_tiles = (st->npairs + tc_tile_cols() - 1) / tc_tile_cols();
   const int iblocks = std::max<int>(1, ((int)st->items.size() + 255) / 256);
   st->nslices = std::max(1, (P->ctx->nsm * 8) / iblocks);
   st->slice_len = ((N3 + st->nslices - 1) / st->nslices + kCTK - 1) / kCTK * kCTK;
@@ -486,6 +510,13 @@ int bisp_plan_init(Plan* P) {
   st->d_spartc = (int*)A(sizeof(int) * S * (size_t)P->nblk_z);
   st->d_shell = (double*)A(sizeof(double) * BQ_N * S);
   st->d_shellc = (long long*)A(sizeof(long long) * S);
+  const bool tc_ok = st->nl * S <= tc_rows();
+  if (tc_ok && st->npairs > 0) {
+    st->d_pairs = (short2*)A(sizeof(short2) * st->npairs);
+    st->d_om = (int*)A(sizeof(int) * om.size());
+    st->d_on = (int*)A(sizeof(int) * on.size());
+    st->d_tcpart = (float*)A(sizeof(float) * (size_t)st->tc_slices * st->tc_tiles * tc_rows() * tc_tile_cols());
+  }
   if (!ok) return set_error(FKP_ENOMEM, "device allocation failed for the bispectrum workspace (%.2f GB in plan)",
                             P->bytes_total / 1e9);
   if (P->ctx->budget && P->bytes_total > P->ctx->budget)
@@ -494,6 +525,11 @@ int bisp_plan_init(Plan* P) {
   if (!st->items.empty())
     BCK(cudaMemcpy(st->d_items, st->items.data(), sizeof(ContractItem) * st->items.size(), cudaMemcpyHostToDevice));
   BCK(cudaMemset(st->d_cpart, 0, sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * 3));
+  if (st->d_pairs) {
+    BCK(cudaMemcpy(st->d_pairs, pairs.data(), sizeof(short2) * pairs.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(st->d_om, om.data(), sizeof(int) * om.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(st->d_on, on.data(), sizeof(int) * on.size(), cudaMemcpyHostToDevice));
+  }
   return FKP_OK;
 }
 
@@ -511,10 +547,12 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   auto* P = static_cast<Plan*>(plan);
   if (!P) return set_error(FKP_EINVAL, "NULL plan");
   if (!P->wantB || !P->bisp) return set_error(FKP_ESTATE, "plan was created without FKP_B* flags");
-  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3)
+  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3 && contraction != FKP_CONTRACT_BF16X6)
     return set_error(FKP_EINVAL, "unknown contraction mode %d", contraction);
-  if (contraction == FKP_CONTRACT_BF16X3) return set_error(FKP_ESTATE, "BF16 hi/lo contraction not available");
   auto* st = static_cast<BispState*>(P->bisp);
+  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6;
+  if (tensor && !st->d_pairs && st->npairs > 0)
+    return set_error(FKP_EINVAL, "the tensor-core contraction needs (multipoles x shells) <= %d rows", tc_rows());
   BCK(cudaSetDevice(P->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CatDev g, r;
@@ -575,7 +613,11 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   BCK(cudaEventRecord(P->ev[7], s));
   // contraction
   const int ntri = P->ntri, nout = std::max(1, ntri) * 3;
-  if (!st->items.empty()) {
+  if (tensor && st->npairs > 0) {
+    BCK(launch_contract_tc(st->d_I, N3, st->nl * S, S, st->d_pairs, st->npairs, st->d_tcpart, P->d_err + 1,
+                           st->tc_slices, contraction == FKP_CONTRACT_BF16X3 ? 2 : 3, s));
+    BCK(launch_tc_reduce(st->d_tcpart, st->tc_slices, st->tc_tiles, st->d_om, st->d_on, nout, st->d_T, s));
+  } else if (!st->items.empty()) {
     const int nf = st->nl * S;
     const size_t smc = sizeof(float) * (size_t)kCTK * (nf | 1);
     BCK(cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));

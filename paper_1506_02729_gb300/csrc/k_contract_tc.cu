@@ -1,0 +1,342 @@
+// k_contract_tc.cu - the triangle contraction of eq. Factorize on the
+// tcgen05 tensor cores.
+//
+//   T^(l)(a,b,c) = sum_x F_a^(l)(x) F_b^(0)(x) F_c^(0)(x)
+//
+// is the skinny GEMM D[(l,a), (b,c)] = sum_x A[(l,a), x] B[(b,c), x] with
+// A = the shell fields and B = the Khatri-Rao products F_b^(0) F_c^(0).  Each
+// FP32 operand v is split into BF16 v_hi = bf16(v), v_lo = bf16(v - v_hi); the
+// three products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor
+// memory (the lo*lo term, ~2^-16 relative, is dropped).  The 3-way split
+// v = v_hi + v_mid + v_lo keeps the six products whose order is at most
+// 2^-16 (hh, hm, mh, hl, lh, mm), for a per-term error near FP32 rounding:
+// the triangle sums cancel strongly (sum |t| >> |sum t|), and the 2-way
+// split's ~1e-5 per-term error was measured to reach 5e-4 - 3e-3 of the
+// bispectrum monopole scale, so the 3-way split is the accurate mode.
+//
+// One CTA per (256-column N tile, K slice of 65,536 points).  The shell
+// fields of a chunk of 32 points are fetched two chunks ahead with cp.async
+// into a 3-slot ring; operand stages are double buffered: all threads form
+// the products and the hi/lo splits into the canonical K-major
+// layout (8-row x 16-byte core matrices, no swizzle); one thread issues the
+// tcgen05.mma instructions (M = 128, N = 256, K = 16) and commits them to the
+// stage's mbarrier.  Every 32 chunks (1,024 points) the 128 x 256 FP32 tile
+// is read from tensor memory (tcgen05.ld), added to FP32 register
+// accumulators (round to nearest) and the MMA accumulation restarts: long
+// in-tensor-core accumulation runs were measured to drift linearly with their
+// length (5.6e-4 of the monopole scale over 65,536 points, under 1e-4 over
+// 1,024).  At the end of the slice the registers go to per-slice partials,
+// summed over slices in FP64 by k_tc_reduce.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fkp_internal.h"
+
+namespace fkp {
+
+constexpr int kTcM = 128;              // MMA rows (l, a)
+constexpr int kTcN = 256;              // MMA columns (pairs b >= c) per tile
+constexpr int kTcKC = 32;              // K points per chunk
+constexpr int kTcChunks = 2048;        // chunks per K slice
+constexpr int kTcThreads = 256;
+constexpr int kTcABytes = kTcM * kTcKC * 2;    // one BF16 operand tile: 8 KB
+constexpr int kTcBBytes = kTcN * kTcKC * 2;    // 16 KB
+template <int NS>
+__host__ __device__ constexpr int tc_stage_bytes() { return NS * (kTcABytes + kTcBBytes); }
+constexpr int kTcMaxF = 192;           // staged fields (l, s) per chunk
+
+constexpr int kTcDrain = 32;           // chunks per tensor-memory accumulation run
+long long tc_slice_points() { return (long long)kTcKC * kTcChunks; }
+int tc_tile_cols() { return kTcN; }
+int tc_rows() { return kTcM; }
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMEM wrappers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A * B^T, A and B K-major BF16 in shared memory, FP32 accumulate.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
+// Core matrices of 8 rows x 16 bytes; lbo = byte distance between core
+// matrices adjacent in K, sbo = between 8-row groups; descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
+  const uint64_t a = (uint64_t)((smem_u32(p) & 0x3FFFF) >> 4);
+  return a | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor for kind::f16: D FP32, A and B BF16, both K-major,
+// N = 256, M = 128.
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+// Byte offset of the 16-byte row segment (row, k-group kg) in a canonical
+// operand tile with kTcKC/8 = 4 core matrices along K per 8-row group.
+__device__ __forceinline__ int canon_off(int row, int kg) {
+  return ((row >> 3) * (kTcKC / 8) + kg) * 128 + (row & 7) * 16;
+}
+
+// BF16 split of 8 values into NS parts (each part the BF16 rounding of the
+// remainder), packed 16 bytes per part.
+template <int NS>
+__device__ __forceinline__ void split8(const float* v, uint4* out) {
+  uint32_t w[NS][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float r0 = v[2 * i], r1 = v[2 * i + 1];
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      const __nv_bfloat16 a = __float2bfloat16_rn(r0);
+      const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+      w[p][i] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+      r0 -= __bfloat162float(a);
+      r1 -= __bfloat162float(b);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NS; ++p) out[p] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+
+// ---------------------------------------------------------------------------
+
+// pairs: (b, c) of the tile's columns (b < 0 marks padding); part layout
+// [slice][tile][128][256] FP32.
+template <int NS>
+__global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
+                                                               int S, const short2* __restrict__ pairs, int npairs,
+                                                               float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  constexpr int kStage = tc_stage_bytes<NS>();
+  unsigned char* stage0 = smraw;                                  // 2 stages: A parts, then B parts
+  float* Iring = reinterpret_cast<float*>(smraw + 2 * kStage);   // 3 x [nf][32], prefetched 2 chunks ahead
+  short2* pt = reinterpret_cast<short2*>(Iring + 3 * kTcMaxF * kTcKC);  // [256]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(pt + kTcN);         // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x, slice = blockIdx.y, ntiles = gridDim.x;
+  for (int i = tid; i < kTcN; i += kTcThreads) {
+    const int n = tile * kTcN + i;
+    pt[i] = n < npairs ? pairs[n] : make_short2(-1, -1);
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, kTcN);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *tslot;
+  const long long x0 = (long long)slice * kTcKC * kTcChunks;
+  const long long xend = (x0 + (long long)kTcKC * kTcChunks < N3) ? x0 + (long long)kTcKC * kTcChunks : N3;
+  const int nch = (int)((xend - x0 + kTcKC - 1) / kTcKC);
+  const uint32_t idesc = tc_idesc();
+  bool ok = true;
+  // this thread's slice of the tile: lane quarter (warp % 4), column half (warp / 4)
+  const int q4 = warp & 3, h2 = warp >> 2;
+  float acc[128];
+#pragma unroll
+  for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+  // asynchronous copies of a chunk's field values into its ring slot (16 bytes
+  // each; points past the slice are zero-filled)
+  auto prefetch = [&](int cc) {
+    if (cc < nch) {
+      float* dst = Iring + (cc % 3) * kTcMaxF * kTcKC;
+      const long long xc = x0 + (long long)cc * kTcKC;
+      for (int i = tid; i < nf * (kTcKC / 4); i += kTcThreads) {
+        const int f = i / (kTcKC / 4), k4 = (i - f * (kTcKC / 4)) * 4;
+        const long long x = xc + k4;
+        const int bytes = x + 4 <= xend ? 16 : (x < xend ? (int)(xend - x) * 4 : 0);
+        const float* src = I + (size_t)f * N3 + (x < xend ? x : 0);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + f * kTcKC + k4)), "l"(src),
+                     "r"(bytes)
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  prefetch(0);
+  prefetch(1);
+  for (int c = 0; c < nch; ++c) {
+    const int s = c & 1;
+    unsigned char* st = stage0 + s * kStage;
+    unsigned char* Ap = st;                      // NS tiles of kTcABytes
+    unsigned char* Bp = st + NS * kTcABytes;     // NS tiles of kTcBBytes
+    prefetch(c + 2);
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+    const float* Ist = Iring + (c % 3) * kTcMaxF * kTcKC;
+    // the MMAs that read this stage two chunks ago must have finished
+    if (c >= 2 && ok) ok = mbar_wait(&bar[s], (uint32_t)(((c - 2) >> 1) & 1), err, 16);
+    __syncthreads();
+    // A: rows (l, a) = field index, zero beyond nf
+    for (int seg = tid; seg < kTcM * (kTcKC / 8); seg += kTcThreads) {
+      const int row = seg >> 2, kg = seg & 3;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = row < nf ? Ist[row * kTcKC + kg * 8 + j] : 0.f;
+      uint4 parts[NS];
+      split8<NS>(v, parts);
+#pragma unroll
+      for (int p = 0; p < NS; ++p) *reinterpret_cast<uint4*>(Ap + p * kTcABytes + canon_off(row, kg)) = parts[p];
+    }
+    // B: rows = pairs (b, c) of this tile, products of the l = 0 fields
+    for (int seg = tid; seg < kTcN * (kTcKC / 8); seg += kTcThreads) {
+      const int row = seg >> 2, kg = seg & 3;
+      const short2 bc = pt[row];
+      float v[8];
+      if (bc.x >= 0) {
+        const float* fb = Ist + bc.x * kTcKC + kg * 8;
+        const float* fc = Ist + bc.y * kTcKC + kg * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = fb[j] * fc[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = 0.f;
+      }
+      uint4 parts[NS];
+      split8<NS>(v, parts);
+#pragma unroll
+      for (int p = 0; p < NS; ++p) *reinterpret_cast<uint4*>(Bp + p * kTcBBytes + canon_off(row, kg)) = parts[p];
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      // products (i, j) of A part i and B part j whose order is at most 2^-16
+      constexpr int NP = NS == 2 ? 3 : 6;
+      constexpr int pi[6] = {0, 0, 1, 0, 2, 1};
+      constexpr int pj[6] = {0, 1, 0, 2, 0, 1};
+#pragma unroll
+      for (int ks = 0; ks < kTcKC / 16; ++ks) {
+        // K step ks covers k-groups 2 ks and 2 ks + 1 (256 bytes further in)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 256, 128, (kTcKC / 8) * 128);
+          const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 256, 128, (kTcKC / 8) * 128);
+          umma_bf16(taddr, ad, bd, idesc, ((c % kTcDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
+        }
+      }
+      umma_commit(&bar[s]);
+    }
+    __syncthreads();
+    if ((c + 1) % kTcDrain == 0 || c + 1 == nch) {
+      // drain: wait for this chunk's MMAs, add the tile to the registers
+      // (ok is made block-uniform: tcgen05.ld is a warp-collective)
+      bool w = ok && mbar_wait(&bar[s], (uint32_t)((c >> 1) & 1), err, 16);
+      ok = __syncthreads_and(w) != 0;
+      tc_fence_after();
+      if (ok) {
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) {
+          float v[32];
+          tmem_ld32(taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 128 + cg * 32), v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[cg * 32 + i] += v[i];
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  // the drain after the last chunk waited for every MMA of the slice
+  float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + lane) * kTcN + h2 * 128;
+#pragma unroll
+  for (int i = 0; i < 128; i += 4)
+    *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, kTcN);
+}
+
+// out[t * 3 + li] = sum over slices of D[m = li * S + a][n = pair(b, c)].
+__global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int ntiles, const int* __restrict__ om,
+                            const int* __restrict__ on, int nout, double* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  const int m = om[o], n = on[o];
+  if (m < 0) {
+    out[o] = 0.0;
+    return;
+  }
+  const int tile = n / kTcN, col = n - tile * kTcN;
+  double s = 0.0;
+  for (int k = 0; k < nslices; ++k) s += (double)part[(((size_t)k * ntiles + tile) * kTcM + m) * kTcN + col];
+  out[o] = s;
+}
+
+template <int NS>
+static size_t tc_smem_bytes() {
+  return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * kTcMaxF * kTcKC + sizeof(short2) * kTcN +
+         2 * sizeof(uint64_t) + 16;
+}
+
+cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, const short2* pairs, int npairs,
+                               float* part, int* err, int nslices, int nsplit, cudaStream_t s) {
+  const int ntiles = (npairs + kTcN - 1) / kTcN;
+  if (nsplit == 2) {
+    const size_t sm = tc_smem_bytes<2>();
+    cudaFuncSetAttribute(k_contract_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_contract_tc<2><<<dim3(ntiles, nslices), kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, part, err);
+  } else {
+    const size_t sm = tc_smem_bytes<3>();
+    cudaFuncSetAttribute(k_contract_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_contract_tc<3><<<dim3(ntiles, nslices), kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, part, err);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_reduce(const float* part, int nslices, int ntiles, const int* om, const int* on, int nout,
+                             double* out, cudaStream_t s) {
+  k_tc_reduce<<<(nout + 255) / 256, 256, 0, s>>>(part, nslices, ntiles, om, on, nout, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fkp

@@ -46,11 +46,12 @@ def small_b():
     return sv, gal, ran, geom, bs, ref, kf
 
 
-def test_small_bispectrum_matches_oracle(small_b):
+@pytest.mark.parametrize("contraction", [0, 1, 2], ids=["fp32", "bf16x3_tcgen05", "bf16x6_tcgen05"])
+def test_small_bispectrum_matches_oracle(small_b, contraction):
     fkp = _fkp()
     sv, gal, ran, geom, bs, ref, kf = small_b
     plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
-    p, b = plan.bispectrum(to_device(gal), to_device(ran))
+    p, b = plan.bispectrum(to_device(gal), to_device(ran), contraction=contraction)
     assert plan.ntri == len(ref["tri"])
     assert np.array_equal(b["tri"].astype(int), np.asarray(ref["tri"]))
     assert np.array_equal(b["NT"], ref["NT"])
@@ -62,6 +63,18 @@ def test_small_bispectrum_matches_oracle(small_b):
         d = np.maximum(np.abs(ref[f"N{l}"]), np.abs(ref["N0"]))
         assert np.max(np.abs(b[f"N{l}"] - ref[f"N{l}"]) / d) < SN_TOL, l
     assert abs(b["I33"] / ref["I33"] - 1) < 1e-6
+
+
+def test_bf16_hi_lo_contraction_accuracy(small_b):
+    """The 2-way split (3 products) runs on the tensor cores; its error against
+    the oracle is bounded by 1e-2 of the monopole scale (it does not meet the
+    1e-4 bar; the 3-way split does)."""
+    fkp = _fkp()
+    sv, gal, ran, geom, bs, ref, kf = small_b
+    plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
+    p, b = plan.bispectrum(to_device(gal), to_device(ran), contraction=1)
+    err = b_errors(b, ref, ref["I33"], float(sv.N) ** 3)
+    assert max(err.values()) < 1e-2, err
 
 
 def test_counts_match_oracle_convolution():
@@ -108,7 +121,9 @@ def test_boss_360_bispectrum_sampled_triangles():
     geom = sv.geometry()
     bs = (3, 3, 3, 37)
     plan = fkp.Plan(geom, (0.0, 0.005, 60), bshells=bs, want=ALL)
-    p, b = plan.bispectrum(to_device(gal), to_device(ran))
+    dg, dr = to_device(gal), to_device(ran)
+    runs = [plan.bispectrum(dg, dr, contraction=c)[1] for c in (0, 1, 2)]
+    b = runs[0]
     tri = [tuple(t) for t in b["tri"].astype(int)]
     sample = [(10, 10, 10), (36, 36, 36), (36, 35, 1), (20, 10, 10), (30, 20, 12), (25, 24, 2), (36, 18, 18)]
     sample = [t for t in sample if t in tri]
@@ -118,7 +133,8 @@ def test_boss_360_bispectrum_sampled_triangles():
     Fwl = op.legendre(Fw, geom, lmax=4)
     ref = ob.bispectrum_from_fields(Fl, Fwl, sc, sv.N, bs, (0, 2, 4), tris=sample)
     idx = [tri.index(t) for t in sample]
-    got = {k: b[k][idx] for k in ("NT", "B0", "B2", "B4", "T0")}
-    assert np.array_equal(got["NT"], ref["NT"])
-    err = b_errors(got, ref, ref["I33"], float(sv.N) ** 3)
-    assert max(err.values()) < B_TOL, err
+    for bb in runs:
+        got = {k: bb[k][idx] for k in ("NT", "B0", "B2", "B4", "T0")}
+        assert np.array_equal(got["NT"], ref["NT"])
+        err = b_errors(got, ref, ref["I33"], float(sv.N) ** 3)
+        assert max(err.values()) < B_TOL, err
