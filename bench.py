@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=512, help="grid side (512 is the benchmark workload)")
     ap.add_argument("--ran-ratio", type=float, default=50.0, help="randoms per galaxy (50 in the workload)")
     ap.add_argument("--bisp-steps", type=int, default=3, help="timed bispectrum mocks (0 skips the B leg)")
+    ap.add_argument("--bisp-grid", type=int, default=360, help="bispectrum grid (360 is the workload)")
+    ap.add_argument("--bisp-nshells", type=int, default=37, help="bispectrum shells (37 reach k = 0.2)")
     return ap.parse_args()
 
 
@@ -337,11 +339,15 @@ def run_bisp(args, gal, ran, dg, dr, stream):
 
     import mockgen
     import paper_1506_02729_gb300 as fkp
-    sv = mockgen.survey_boss(N=360)
-    plan = fkp.Plan(sv.geometry(), BINS, bshells=BSHELLS, want=127)
+    sv = mockgen.survey_boss(N=args.bisp_grid)
+    bshells = BSHELLS[:3] + (args.bisp_nshells,)
+    plan = fkp.Plan(sv.geometry(), BINS, bshells=bshells, want=127)
     modes = {"fp32": fkp.FKP_CONTRACT_FP32, "bf16x3_tcgen05": fkp.FKP_CONTRACT_BF16X3,
              "bf16x6_tcgen05": fkp.FKP_CONTRACT_BF16X6}
-    out = {"workload": "B_0,2,4 + P_l: BOSS-like catalog, 360^3 TSC, 37 shells of 3 k_f to k=0.2",
+    wl = "B_0,2,4 + P_l: BOSS-like catalog, 360^3 TSC, 37 shells of 3 k_f to k=0.2"
+    if (args.bisp_grid, args.bisp_nshells) != (360, 37):
+        wl = f"reduced case: {args.bisp_grid}^3, {args.bisp_nshells} shells (not the workload)"
+    out = {"workload": wl,
            "ntriangles": int(plan.ntri), "unit": "mocks/s", "modes": {}}
     for name, mode in modes.items():
         plan.bispectrum(dg, dr, contraction=mode, stream=stream)

@@ -44,7 +44,7 @@ constexpr int kTcABytes = kTcM * kTcKC * 2;    // one BF16 operand tile: 8 KB
 constexpr int kTcBBytes = kTcN * kTcKC * 2;    // 16 KB
 template <int NS>
 __host__ __device__ constexpr int tc_stage_bytes() { return NS * (kTcABytes + kTcBBytes); }
-constexpr int kTcMaxF = 192;           // staged fields (l, s) per chunk
+constexpr int kTcRow = kTcKC + 4;      // staged row stride (floats): 16-byte aligned, shifts banks by 4 per field
 
 constexpr int kTcDrain = 32;           // chunks per tensor-memory accumulation run
 long long tc_slice_points() { return (long long)kTcKC * kTcChunks; }
@@ -127,14 +127,16 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
   uint32_t w[NS][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float r0 = v[2 * i], r1 = v[2 * i + 1];
+    float2 r = make_float2(v[2 * i], v[2 * i + 1]);
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
-      const __nv_bfloat16 a = __float2bfloat16_rn(r0);
-      const __nv_bfloat16 b = __float2bfloat16_rn(r1);
-      w[p][i] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-      r0 -= __bfloat162float(a);
-      r1 -= __bfloat162float(b);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(r.x, r.y);  // one paired conversion
+      w[p][i] = *reinterpret_cast<const uint32_t*>(&h);
+      if (p + 1 < NS) {
+        const float2 hf = __bfloat1622float2(h);
+        r.x -= hf.x;
+        r.y -= hf.y;
+      }
     }
   }
 #pragma unroll
@@ -152,8 +154,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   extern __shared__ __align__(1024) unsigned char smraw[];
   constexpr int kStage = tc_stage_bytes<NS>();
   unsigned char* stage0 = smraw;                                  // 2 stages: A parts, then B parts
-  float* Iring = reinterpret_cast<float*>(smraw + 2 * kStage);   // 3 x [nf][32], prefetched 2 chunks ahead
-  short2* pt = reinterpret_cast<short2*>(Iring + 3 * kTcMaxF * kTcKC);  // [256]
+  float* Iring = reinterpret_cast<float*>(smraw + 2 * kStage);   // 3 x [nf][kTcRow], prefetched 2 chunks ahead
+  const int ring = nf * kTcRow;                                   // floats per ring slot
+  short2* pt = reinterpret_cast<short2*>(Iring + 3 * ring);      // [256]
   uint64_t* bar = reinterpret_cast<uint64_t*>(pt + kTcN);         // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -189,14 +192,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   // each; points past the slice are zero-filled)
   auto prefetch = [&](int cc) {
     if (cc < nch) {
-      float* dst = Iring + (cc % 3) * kTcMaxF * kTcKC;
+      float* dst = Iring + (cc % 3) * ring;
       const long long xc = x0 + (long long)cc * kTcKC;
       for (int i = tid; i < nf * (kTcKC / 4); i += kTcThreads) {
         const int f = i / (kTcKC / 4), k4 = (i - f * (kTcKC / 4)) * 4;
         const long long x = xc + k4;
         const int bytes = x + 4 <= xend ? 16 : (x < xend ? (int)(xend - x) * 4 : 0);
         const float* src = I + (size_t)f * N3 + (x < xend ? x : 0);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + f * kTcKC + k4)), "l"(src),
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + f * kTcRow + k4)), "l"(src),
                      "r"(bytes)
                      : "memory");
       }
@@ -212,16 +215,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     unsigned char* Bp = st + NS * kTcABytes;     // NS tiles of kTcBBytes
     prefetch(c + 2);
     asm volatile("cp.async.wait_group 2;" ::: "memory");
-    const float* Ist = Iring + (c % 3) * kTcMaxF * kTcKC;
+    const float* Ist = Iring + (c % 3) * ring;
     // the MMAs that read this stage two chunks ago must have finished
     if (c >= 2 && ok) ok = mbar_wait(&bar[s], (uint32_t)(((c - 2) >> 1) & 1), err, 16);
     __syncthreads();
     // A: rows (l, a) = field index, zero beyond nf
+    // consecutive threads take consecutive rows of one k-group: each
+    // quarter-warp stores one contiguous 128-byte core matrix
     for (int seg = tid; seg < kTcM * (kTcKC / 8); seg += kTcThreads) {
-      const int row = seg >> 2, kg = seg & 3;
+      const int kg = seg / kTcM, row = seg - kg * kTcM;
       float v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = row < nf ? Ist[row * kTcKC + kg * 8 + j] : 0.f;
+      for (int j = 0; j < 8; ++j) v[j] = row < nf ? Ist[row * kTcRow + kg * 8 + j] : 0.f;
       uint4 parts[NS];
       split8<NS>(v, parts);
 #pragma unroll
@@ -229,12 +234,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     }
     // B: rows = pairs (b, c) of this tile, products of the l = 0 fields
     for (int seg = tid; seg < kTcN * (kTcKC / 8); seg += kTcThreads) {
-      const int row = seg >> 2, kg = seg & 3;
+      const int kg = seg / kTcN, row = seg - kg * kTcN;
       const short2 bc = pt[row];
       float v[8];
       if (bc.x >= 0) {
-        const float* fb = Ist + bc.x * kTcKC + kg * 8;
-        const float* fc = Ist + bc.y * kTcKC + kg * 8;
+        const float* fb = Ist + bc.x * kTcRow + kg * 8;
+        const float* fc = Ist + bc.y * kTcRow + kg * 8;
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = fb[j] * fc[j];
       } else {
@@ -266,7 +271,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
       }
       umma_commit(&bar[s]);
     }
-    __syncthreads();
+    // No barrier here: the next chunk builds the other stage, which the MMAs
+    // of chunk c - 1 have released (mbarrier wait), and reads a ring slot the
+    // copies of chunk c + 1 filled; stage s is rebuilt only after this commit.
     if ((c + 1) % kTcDrain == 0 || c + 1 == nch) {
       // drain: wait for this chunk's MMAs, add the tile to the registers
       // (ok is made block-uniform: tcgen05.ld is a warp-collective)
@@ -313,8 +320,8 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int nti
 }
 
 template <int NS>
-static size_t tc_smem_bytes() {
-  return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * kTcMaxF * kTcKC + sizeof(short2) * kTcN +
+static size_t tc_smem_bytes(int nf) {
+  return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * (size_t)nf * kTcRow + sizeof(short2) * kTcN +
          2 * sizeof(uint64_t) + 16;
 }
 
@@ -322,11 +329,11 @@ cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, cons
                                float* part, int* err, int nslices, int nsplit, cudaStream_t s) {
   const int ntiles = (npairs + kTcN - 1) / kTcN;
   if (nsplit == 2) {
-    const size_t sm = tc_smem_bytes<2>();
+    const size_t sm = tc_smem_bytes<2>(nf);
     cudaFuncSetAttribute(k_contract_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_contract_tc<2><<<dim3(ntiles, nslices), kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, part, err);
   } else {
-    const size_t sm = tc_smem_bytes<3>();
+    const size_t sm = tc_smem_bytes<3>(nf);
     cudaFuncSetAttribute(k_contract_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_contract_tc<3><<<dim3(ntiles, nslices), kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, part, err);
   }
