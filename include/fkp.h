@@ -188,6 +188,56 @@ int fkp_bispectrum(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ra
 int fkp_power_from_grid_noalloc(const fkp_geometry_t *geom, const fkp_pbins_t *pbins, const float *F_device,
                                 double I22, double N0, void *cuda_stream, fkp_power_out *out);
 
+/* ---------------------------------------------------------------------------
+ * Request server (continuous batching).  The paper's use of the estimators is
+ * covariance estimation from many realisations of a survey (Sec. III.C, the
+ * ~10^4 mocks of its performance section); the server runs such requests as
+ * they arrive.  It keeps nslots worker threads, each with its own CUDA stream
+ * and a cached plan, and admits a request when its estimated device
+ * footprint fits next to the running requests and cached plans within
+ * hbm_budget_bytes (0 = 90 % of the free device memory at creation); the
+ * queue is first-in first-out with skip-ahead.  Requests on different slots
+ * run concurrently on the device.  Every result equals the one the same
+ * request gives alone (gridding is order independent; bin sums agree to FP32
+ * rounding of per-block partial sums).
+ * ------------------------------------------------------------------------- */
+
+/* One request: the arguments of fkp_plan_create plus catalogs and outputs.
+ * The catalog arrays and the output arrays must stay valid until the ticket
+ * has completed (fkp_server_wait returned). */
+typedef struct {
+  fkp_geometry_t geom;
+  fkp_pbins_t pbins;
+  fkp_bshells_t bshells;   /* read when want has an FKP_B* flag */
+  uint32_t want;
+  int contraction;         /* FKP_CONTRACT_* for bispectrum requests */
+  fkp_catalog_t gal, ran;
+  fkp_power_out *pout;     /* may be NULL */
+  fkp_bisp_out *bout;      /* may be NULL */
+} fkp_request_t;
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected, queued;
+  int running, peak_running;
+  size_t bytes_in_use, peak_bytes, budget_bytes;
+} fkp_server_stats_t;
+
+/* Creates the server on a device.  FKP_EINVAL unless 1 <= nslots <= 64. */
+int fkp_server_create(int device, int nslots, size_t hbm_budget_bytes, void **server);
+/* Queues a request; *ticket identifies it.  FKP_ENOMEM when the request alone
+ * exceeds the budget (it is not queued), FKP_EINVAL for malformed requests. */
+int fkp_server_submit(void *server, const fkp_request_t *req, uint64_t *ticket);
+/* *done = 1 when the request has finished (successfully or not). */
+int fkp_server_poll(void *server, uint64_t ticket, int *done);
+/* Waits up to timeout_ms (< 0: no limit) for the ticket; FKP_ETIMEOUT if it is
+ * still running (the ticket stays valid).  On completion *status is the
+ * request's own return code and *latency_ms the time from submission to
+ * completion, and the ticket is retired. */
+int fkp_server_wait(void *server, uint64_t ticket, int timeout_ms, int *status, double *latency_ms);
+int fkp_server_stats(void *server, fkp_server_stats_t *stats);
+/* Lets queued and running requests finish, then frees everything. */
+void fkp_server_destroy(void *server);
+
 /* Thread-local message for the last error on this thread. */
 const char *fkp_last_error(void);
 

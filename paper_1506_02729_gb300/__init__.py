@@ -24,7 +24,8 @@ ERRORS = {-1: "FKP_EINVAL", -2: "FKP_EGEOM", -3: "FKP_ENOMEM", -4: "FKP_ETIMEOUT
           -6: "FKP_ESTATE"}
 EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_plan_destroy", "fkp_plan_sizes",
            "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version",
-           "fkp_power_from_grid_noalloc"]
+           "fkp_power_from_grid_noalloc", "fkp_server_create", "fkp_server_submit", "fkp_server_poll",
+           "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy"]
 
 
 class FKPError(RuntimeError):
@@ -69,6 +70,18 @@ class BispOut(C.Structure):
                 ("T0", _DP), ("T2", _DP), ("T4", _DP), ("I33", C.c_double), ("S3", C.c_double)]
 
 
+class Request(C.Structure):
+    _fields_ = [("geom", Geometry), ("pbins", PBins), ("bshells", BShells), ("want", C.c_uint32),
+                ("contraction", C.c_int), ("gal", Catalog), ("ran", Catalog), ("pout", C.POINTER(PowerOut)),
+                ("bout", C.POINTER(BispOut))]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("rejected", C.c_int64),
+                ("queued", C.c_int64), ("running", C.c_int), ("peak_running", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t), ("budget_bytes", C.c_size_t)]
+
+
 _lib = None
 
 
@@ -95,6 +108,13 @@ def lib():
                                      C.POINTER(BispOut)]
         L.fkp_power_from_grid_noalloc.argtypes = [C.POINTER(Geometry), C.POINTER(PBins), vp, C.c_double,
                                                   C.c_double, vp, C.POINTER(PowerOut)]
+        L.fkp_server_create.argtypes = [C.c_int, C.c_int, C.c_size_t, C.POINTER(vp)]
+        L.fkp_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
+        L.fkp_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int)]
+        L.fkp_server_wait.argtypes = [vp, C.c_uint64, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.fkp_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.fkp_server_destroy.argtypes = [vp]
+        L.fkp_server_destroy.restype = None
         L.fkp_last_error.restype = C.c_char_p
         L.fkp_version.restype = C.c_char_p
         _lib = L
@@ -285,6 +305,94 @@ def power_from_grid_noalloc(geom, pbins, F, I22=1.0, N0=0.0, stream=None):
     _check(lib().fkp_power_from_grid_noalloc(C.byref(g), C.byref(pb), F.data_ptr(), float(I22), float(N0),
                                              _stream_handle(stream), C.byref(o)))
     return Plan._scalars(o, arr)
+
+
+def _bout(nt):
+    b = {"tri": np.zeros((nt, 3), dtype=np.int16), "NT": np.zeros(nt, dtype=np.int64),
+         "centre_closed": np.zeros(nt, dtype=np.uint8)}
+    for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
+        b[k] = np.full(nt, np.nan)
+    bo = BispOut()
+    bo.tri = b["tri"].ctypes.data_as(C.POINTER(C.c_int16))
+    bo.NT = b["NT"].ctypes.data_as(C.POINTER(C.c_int64))
+    bo.centre_closed = b["centre_closed"].ctypes.data_as(C.POINTER(C.c_uint8))
+    for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
+        setattr(bo, k, b[k].ctypes.data_as(_DP))
+    return bo, b
+
+
+def max_triangles(bshells):
+    """Upper bound on the triangle count of a shell set (all a >= b >= c)."""
+    S = int(bshells[3])
+    return S * (S + 1) * (S + 2) // 6
+
+
+class Server:
+    """Continuous-batching server: requests (catalogs + geometry + outputs)
+    are admitted by device footprint and run concurrently on `nslots`
+    streams.  The catalogs passed to submit() are kept referenced until
+    their ticket is waited for."""
+
+    def __init__(self, nslots=3, budget=0, device=0):
+        self._h = C.c_void_p()
+        _check(lib().fkp_server_create(device, nslots, budget, C.byref(self._h)))
+        self._live = {}
+
+    def submit(self, geom, pbins, gal, ran, want=FKP_P0 | FKP_P2 | FKP_P4 | FKP_P4B, bshells=None,
+               contraction=FKP_CONTRACT_BF16X3):
+        cg, k1 = make_catalog(gal)
+        cr, k2 = make_catalog(ran)
+        pb = PBins(float(pbins[0]), float(pbins[1]), int(pbins[2]))
+        bs = BShells(*[int(v) for v in bshells]) if bshells is not None else BShells(1, 1, 1, 1)
+        tmp = Plan.__new__(Plan)
+        tmp.nbins = pb.nbins
+        o, parr = tmp._pout()
+        bo, barr = (None, None)
+        if bshells is not None:
+            bo, barr = _bout(max_triangles(bshells))
+        req = Request(geometry(geom), pb, bs, int(want), int(contraction), cg, cr, C.pointer(o),
+                      C.pointer(bo) if bo is not None else None)
+        t = C.c_uint64()
+        _check(lib().fkp_server_submit(self._h, C.byref(req), C.byref(t)))
+        self._live[t.value] = (req, o, parr, bo, barr, k1, k2, gal, ran)
+        return t.value
+
+    def poll(self, ticket):
+        d = C.c_int()
+        _check(lib().fkp_server_poll(self._h, ticket, C.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_ms=-1):
+        """(power dict, bispectrum dict or None, latency in ms); raises the
+        request's own error if it failed."""
+        st, lat = C.c_int(), C.c_double()
+        _check(lib().fkp_server_wait(self._h, ticket, int(timeout_ms), C.byref(st), C.byref(lat)))
+        req, o, parr, bo, barr, *_ = self._live.pop(ticket)
+        _check(st.value)
+        p = Plan._scalars(o, parr)
+        if barr is not None:
+            n = int(np.count_nonzero(barr["NT"]))
+            barr = {k: (v[:n] if hasattr(v, "shape") and v.shape[:1] == (len(barr["NT"]),) else v)
+                    for k, v in barr.items()}
+            barr["I33"], barr["S3"] = bo.I33, bo.S3
+        return p, barr, lat.value
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().fkp_server_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().fkp_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version():
