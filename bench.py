@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--bisp-steps", type=int, default=3, help="timed bispectrum mocks (0 skips the B leg)")
     ap.add_argument("--bisp-grid", type=int, default=360, help="bispectrum grid (360 is the workload)")
     ap.add_argument("--bisp-nshells", type=int, default=37, help="bispectrum shells (37 reach k = 0.2)")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving leg (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving leg (req/s)")
+    ap.add_argument("--serve-slots", type=int, default=3)
     return ap.parse_args()
 
 
@@ -317,6 +320,10 @@ def run_gpu(args):
             "clocks": ck}
     if args.bisp_steps > 0:
         line["bispectrum"] = run_bisp(args, gal, ran, dg, dr, stream)
+    if args.serve_requests > 0 and world == 1:
+        del dg, dr
+        torch.cuda.empty_cache()
+        line["serving"] = run_serve(args, gal, ran)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_mock, desc, _ = oracle_sample(gal, ran, sv, 1)
         line["cpu_baseline"] = {"value": 1.0 / t_mock, "unit": "mocks/s", "cores": cores_used(), "kind": "oracle",
@@ -370,6 +377,96 @@ def run_bisp(args, gal, ran, dg, dr, stream):
     out["value"], out["best_mode"] = out["modes"][best]["value"], best
     plan.close()
     return out
+
+
+def run_serve(args, gal, ran):
+    """A stream of uneven requests shaped like the batched-mock workload:
+    grid drawn from {256, 384, 512}, galaxies a random 50-100 % subsample of
+    the 7e5-galaxy catalog, randoms 30x the galaxies, host (pinned) catalogs
+    copied in by each request; half ask for P_0,2,4 + P_4b only, half also
+    for B_0 to k = 0.15 (27 shells, hi/lo tensor-core contraction).  Reports
+    p50/p99 latency (submission to result on the host) under Poisson arrivals,
+    saturated mocks/s (all requests submitted at once) and the plain
+    sequential GPU path (one request at a time on one stream)."""
+    import torch
+
+    import mockgen
+    import paper_1506_02729_gb300 as fkp
+    g = np.random.default_rng(args.seed + 77)
+    reqs = []
+    for i in range(args.serve_requests):
+        N = int(g.choice([256, 384, 512]))
+        ng = int(gal["x"].size * g.uniform(0.5, 1.0))
+        nr = min(ran["x"].size, 30 * ng)
+        gi = np.sort(g.choice(gal["x"].size, ng, replace=False))
+        ri = np.sort(g.choice(ran["x"].size, nr, replace=False))
+        hg = {k: torch.from_numpy(np.ascontiguousarray(v[gi])).pin_memory() for k, v in gal.items()}
+        hr = {k: torch.from_numpy(np.ascontiguousarray(v[ri])).pin_memory() for k, v in ran.items()}
+        B = bool(i % 2)
+        reqs.append(dict(geom=mockgen.survey_boss(N=N).geometry(), gal=hg, ran=hr, B=B, n_obj=ng + nr))
+    pb = BINS
+
+    def submit(srv, r):
+        if r["B"]:
+            return srv.submit(r["geom"], pb, r["gal"], r["ran"], want=15 | fkp.FKP_B0, bshells=(3, 3, 3, 27),
+                              contraction=fkp.FKP_CONTRACT_BF16X3)
+        return srv.submit(r["geom"], pb, r["gal"], r["ran"])
+
+    srv = fkp.Server(nslots=args.serve_slots)
+    for t in [submit(srv, r) for r in reqs]:  # warm the plan pool and the kernels
+        srv.wait(t)
+    # Poisson arrivals
+    arr = np.cumsum(g.exponential(1.0 / args.serve_rate, size=len(reqs)))
+    t0 = time.perf_counter()
+    tickets = []
+    for a, r in zip(arr, reqs):
+        dt = t0 + a - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(submit(srv, r))
+    lat = [srv.wait(t)[2] for t in tickets]
+    wall_poisson = time.perf_counter() - t0
+    # saturated: everything at once
+    t1 = time.perf_counter()
+    ts = [submit(srv, r) for r in reqs]
+    lat_sat = [srv.wait(t)[2] for t in ts]
+    wall_sat = time.perf_counter() - t1
+    st = srv.stats()
+    srv.close()
+    # plain sequential GPU path: one request at a time on one stream, plans
+    # cached by geometry (made before the timed loop, as the server's pool is
+    # warm before its timed stream)
+    plans = {}
+
+    def plan_for(r):
+        key = (r["geom"]["N"], r["B"])
+        if key not in plans:
+            plans[key] = (fkp.Plan(r["geom"], pb, bshells=(3, 3, 3, 27), want=15 | fkp.FKP_B0) if r["B"]
+                          else fkp.Plan(r["geom"], pb))
+        return plans[key]
+
+    for r in reqs:
+        plan_for(r)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for r in reqs:
+        plan = plan_for(r)
+        if r["B"]:
+            plan.bispectrum(r["gal"], r["ran"], contraction=fkp.FKP_CONTRACT_BF16X3)
+        else:
+            plan.power(r["gal"], r["ran"])
+    wall_seq = time.perf_counter() - t2
+    for p in plans.values():
+        p.close()
+    n = len(reqs)
+    return {"workload": f"{n} requests, grids {{256,384,512}}, 3.5e5-7e5 galaxies + 30x randoms (host catalogs), "
+                        "half P_0,2,4+P_4b, half also B_0 (27 shells, bf16x3 tcgen05)",
+            "arrival_rate_per_s": args.serve_rate, "slots": args.serve_slots,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "poisson_wall_s": wall_poisson,
+            "saturated_mocks_per_s": n / wall_sat, "saturated_p50_ms": float(np.percentile(lat_sat, 50)),
+            "plain_sequential_mocks_per_s": n / wall_seq,
+            "peak_running": st["peak_running"], "peak_bytes": int(st["peak_bytes"])}
 
 
 def main():

@@ -145,7 +145,8 @@ int fkp_plan_create(void *ctx, const fkp_geometry_t *geom, const fkp_pbins_t *pb
                     const fkp_bshells_t *bshells, uint32_t want, void **plan);
 void fkp_plan_destroy(void *plan);
 
-/* Sizes the caller needs for its outputs and the plan's device footprint. */
+/* Sizes the caller needs for its outputs and the plan's device footprint
+ * (workspace plus the catalog buffers it keeps between calls). */
 int fkp_plan_sizes(const void *plan, int *nbins, int *ntriangles, size_t *workspace_bytes);
 
 /* P_l of one survey (Sec. III.A).  Enqueues every step on cuda_stream (a
@@ -192,11 +193,14 @@ int fkp_power_from_grid_noalloc(const fkp_geometry_t *geom, const fkp_pbins_t *p
  * Request server (continuous batching).  The paper's use of the estimators is
  * covariance estimation from many realisations of a survey (Sec. III.C, the
  * ~10^4 mocks of its performance section); the server runs such requests as
- * they arrive.  It keeps nslots worker threads, each with its own CUDA stream
- * and a cached plan, and admits a request when its estimated device
- * footprint fits next to the running requests and cached plans within
- * hbm_budget_bytes (0 = 90 % of the free device memory at creation); the
- * queue is first-in first-out with skip-ahead.  Requests on different slots
+ * they arrive.  It keeps nslots worker threads, each with its own CUDA
+ * stream, and a pool of plans shared by the slots (a request reuses an idle
+ * plan of its geometry, so workspaces stay on the device between requests).
+ * A request is admitted when its estimated device footprint fits next to the
+ * pooled plans and running requests within hbm_budget_bytes (0 = 90 % of the
+ * free device memory at creation), evicting idle plans of other geometries
+ * (least recently used first) when that makes room; the queue is first-in
+ * first-out with skip-ahead.  Requests on different slots
  * run concurrently on the device.  Every result equals the one the same
  * request gives alone (gridding is order independent; bin sums agree to FP32
  * rounding of per-block partial sums).
@@ -232,7 +236,8 @@ int fkp_server_poll(void *server, uint64_t ticket, int *done);
 /* Waits up to timeout_ms (< 0: no limit) for the ticket; FKP_ETIMEOUT if it is
  * still running (the ticket stays valid).  On completion *status is the
  * request's own return code and *latency_ms the time from submission to
- * completion, and the ticket is retired. */
+ * completion, and the ticket is retired.  When the request failed, its
+ * worker's error message becomes this thread's fkp_last_error(). */
 int fkp_server_wait(void *server, uint64_t ticket, int timeout_ms, int *status, double *latency_ms);
 int fkp_server_stats(void *server, fkp_server_stats_t *stats);
 /* Lets queued and running requests finish, then frees everything. */

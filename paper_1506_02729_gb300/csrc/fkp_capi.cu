@@ -12,6 +12,10 @@
 #include <vector>
 
 #include "../../include/fkp.h"
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "fkp_internal.h"
 
 using namespace fkp;
@@ -30,6 +34,20 @@ int fkp::set_error(int code, const char* fmt, ...) {
   va_end(ap);
   g_last_error = buf;
   return code;
+}
+
+cudaError_t fkp::raise_smem_limit(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[{func, dev}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 extern "C" const char* fkp_last_error(void) { return g_last_error.c_str(); }
@@ -306,7 +324,9 @@ extern "C" int fkp_plan_sizes(const void* plan, int* nbins, int* ntri, size_t* w
   if (!P) return set_error(FKP_EINVAL, "NULL plan");
   if (nbins) *nbins = P->pb.nbins;
   if (ntri) *ntri = P->ntri;
-  if (ws) *ws = P->bytes_total;
+  // workspace plus the per-call buffers the plan keeps (tile-sorted and staged catalogs)
+  if (ws) *ws = P->bytes_total + P->sort_cap * (sizeof(float4) + (P->d_vw2 ? sizeof(float) : 0)) +
+                P->staging_bytes[0] + P->staging_bytes[1];
   return FKP_OK;
 }
 

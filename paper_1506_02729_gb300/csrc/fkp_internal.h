@@ -64,6 +64,10 @@ struct Plan {
 };
 
 int set_error(int code, const char* fmt, ...);
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The limit is process-wide per kernel and is never lowered
+// here, so a launch with a smaller need on another thread stays valid.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
 void build_moments(int lmax, MomentTable& mt);
 int stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, cudaStream_t s);
 int enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s);

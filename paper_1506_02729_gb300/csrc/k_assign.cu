@@ -299,10 +299,10 @@ cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, doub
   const int ntiles = ntx * ntx * ntx;
   const size_t sm = sizeof(int) * ntiles;
   if (g.assign == 2) {
-    cudaFuncSetAttribute(k_bin_count<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_bin_count<2>, sm);
     k_bin_count<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
   } else {
-    cudaFuncSetAttribute(k_bin_count<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_bin_count<3>, sm);
     k_bin_count<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
   }
   return cudaGetLastError();
@@ -323,11 +323,11 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
   const int ntiles = ntx * ntx * ntx;
   const size_t sm = sizeof(int) * ntiles;
   if (g.assign == 2) {
-    cudaFuncSetAttribute(k_bin_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_bin_scatter<2>, sm);
     k_bin_scatter<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, (float)obs[0], (float)obs[1],
                                                    (float)obs[2], ds, cur, xyzv, vw2, labpart);
   } else {
-    cudaFuncSetAttribute(k_bin_scatter<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_bin_scatter<3>, sm);
     k_bin_scatter<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, (float)obs[0], (float)obs[1],
                                                    (float)obs[2], ds, cur, xyzv, vw2, labpart);
   }
@@ -342,7 +342,7 @@ cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xy
   const size_t sm = sizeof(unsigned long long) * kReg3 * (w2 ? 2 : 1);
 #define FKP_TA(PP, WW)                                                                                 \
   do {                                                                                                 \
-    cudaFuncSetAttribute(k_tile_accum<PP, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    raise_smem_limit((const void*)k_tile_accum<PP, WW>, sm); \
     k_tile_accum<PP, WW><<<ntiles, 256, sm, s>>>(g, ntx, off, xyzv, vw2, grid, gridw);                 \
   } while (0)
   if (g.assign == 2) {

@@ -378,7 +378,7 @@ static int compute_counts(BispState& st, cudaStream_t s, std::vector<long long>&
   BCK(cudaMemcpyAsync(d_sl, slut.data(), slut.size(), cudaMemcpyHostToDevice, s));
   BCK(cudaMemsetAsync(d_NT, 0, sizeof(unsigned long long) * nt3, s));
   const size_t sm = sizeof(int) * S * S + slut.size();
-  BCK(cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  BCK(raise_smem_limit((const void*)k_counts, sm));
   if (!reps.empty()) k_counts<<<(unsigned)reps.size(), 256, sm, s>>>(d_ball, d_shb, d_upto, d_reps, d_sl, nsq, S, d_NT);
   BCK(cudaGetLastError());
   std::vector<unsigned long long> h(nt3);
@@ -596,9 +596,9 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   const int m1 = mm + 1, w2 = 2 * mm + 1;
   const size_t smz = sizeof(float2) * 2 * kBX * (N + 1);
   const size_t smx = sizeof(float2) * 2 * kXP * N;
-  BCK(cudaFuncSetAttribute(k_shell_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
-  BCK(cudaFuncSetAttribute(k_shell_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz));
-  BCK(cudaFuncSetAttribute(k_shell_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx));
+  BCK(raise_smem_limit((const void*)k_shell_z, smz));
+  BCK(raise_smem_limit((const void*)k_shell_y, smz));
+  BCK(raise_smem_limit((const void*)k_shell_x, smx));
   const long long N3 = (long long)N * N * N;
   const size_t es = (size_t)w2 * w2 * m1;
   for (int li = 0; li < st->nl; ++li) {
@@ -620,7 +620,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   } else if (!st->items.empty()) {
     const int nf = st->nl * S;
     const size_t smc = sizeof(float) * (size_t)kCTK * (nf | 1);
-    BCK(cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+    BCK(raise_smem_limit((const void*)k_contract_fp32, smc));
     const int iblocks = ((int)st->items.size() + 255) / 256;
     k_contract_fp32<<<dim3(iblocks, st->nslices), 256, smc, s>>>(st->d_I, N3, nf, S, st->d_items,
                                                                  (int)st->items.size(), st->slice_len, st->d_cpart,

@@ -330,11 +330,11 @@ cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, cons
   const int ntiles = (npairs + kTcN - 1) / kTcN;
   if (nsplit == 2) {
     const size_t sm = tc_smem_bytes<2>(nf);
-    cudaFuncSetAttribute(k_contract_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_contract_tc<2>, sm);
     k_contract_tc<2><<<dim3(ntiles, nslices), kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, part, err);
   } else {
     const size_t sm = tc_smem_bytes<3>(nf);
-    cudaFuncSetAttribute(k_contract_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)k_contract_tc<3>, sm);
     k_contract_tc<3><<<dim3(ntiles, nslices), kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, part, err);
   }
   return cudaGetLastError();

@@ -423,7 +423,7 @@ static cudaError_t xrun(const unsigned long long* gq, const float* gf, const Geo
                         const float2* tw, float2* S1, int nsm, cudaStream_t s) {
   constexpr int NP = (nfields_of(LMAX) + 1) / 2;
   const size_t sm = xsm(g.N, NP);
-  cudaFuncSetAttribute(k_xpass2<N_, LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_xpass2<N_, LMAX>, sm);
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, LMAX>, 32 * NP, sm);
   int grid = nsm * (occ > 0 ? occ : 1) * 2;
@@ -460,7 +460,7 @@ template <int N_>
 static cudaError_t yrun(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                         const float2* tw, float2* S2, int* err, cudaStream_t s) {
   const size_t sm = ysm(g.N);
-  cudaFuncSetAttribute(k_ypass2<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_ypass2<N_>, sm);
   k_ypass2<N_><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNT / kT), sm, s>>>(S1, g, mt, fp, tw, S2, err);
   return cudaGetLastError();
 }
@@ -482,7 +482,7 @@ template <int N_, int MODE>
 static cudaError_t zrun(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
   const size_t sm = zsm(g.N, MODE == 2 ? zp.nshells : zp.nbins);
-  cudaFuncSetAttribute(k_zpass2<N_, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)k_zpass2<N_, MODE>, sm);
   k_zpass2<N_, MODE><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNT / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part, partc,
                                                                              err);
   return cudaGetLastError();
