@@ -296,7 +296,7 @@ def run_gpu(args):
     # roofline of the dominant kernel
     st = np.mean(np.array(stage), axis=0)
     names = {"count": st[0], "assign": st[1], "xpass": st[2], "ypass": st[3], "zpass": st[4]}
-    mt_fields, mt_groups = 22, 9
+    mt_fields, mt_groups = 16, 9  # trace-reduced moment fields, k_z-power groups
     ab = algorithmic_bytes(sv.N, mt_fields, mt_groups, n_obj)
     dom = max(names, key=names.get)
     pk, src = peaks()
@@ -374,8 +374,13 @@ def run_bisp(args, gal, ran, dg, dr, stream):
         out["modes"][name] = {"value": 1000.0 / ms, "ms_per_step": ms,
                               "stage_ms": {"grids": float(m[0] + m[1]), "F_passes": float(m[2] + m[3] + m[4]),
                                            "shell_ifft": float(m[5]), "contraction": float(m[6])}}
-    best = max(out["modes"], key=lambda k: out["modes"][k]["value"])
-    out["value"], out["best_mode"] = out["modes"][best]["value"], best
+    # the headline is the accurate tensor-core mode (3-way split, within the
+    # 1e-4 bar like the FP32 contraction); the hi/lo split is the fast mode,
+    # with a random per-product error of ~2^-18
+    out["value"], out["mode"] = out["modes"]["bf16x6_tcgen05"]["value"], "bf16x6_tcgen05"
+    out["accuracy"] = {"fp32": "within 1e-4 of the FP64 oracle", "bf16x6_tcgen05": "within 1e-4 of the FP64 oracle",
+                       "bf16x3_tcgen05": "random per-product error ~2^-18 (triangle sums within 6 x 2^-17 "
+                                         "sqrt(sum_x t^2) of the 3-way split)"}
     plan.close()
     return out
 
@@ -387,8 +392,8 @@ def run_serve(args, gal, ran):
     copied in by each request; half ask for P_0,2,4 + P_4b only, half also
     for B_0,2,4 to k = 0.2 (37 shells of 3 k_f) where the grid allows it
     (3 n_max < N), else to k = 0.15 (27 shells).  The served form runs the
-    hi/lo tensor-core contraction; the plain form is the sequential GPU path
-    (one request at a time on one stream) with the FP32 CUDA-core
+    3-way split tensor-core contraction; the plain form is the sequential GPU
+    path (one request at a time on one stream) with the FP32 CUDA-core
     contraction, both within the 1e-4 bar.  Reports p50/p99 latency
     (submission to result on the host) under Poisson arrivals and saturated
     mocks/s (all requests submitted at once) against the plain form."""
@@ -414,7 +419,7 @@ def run_serve(args, gal, ran):
     def submit(srv, r):
         if r["B"]:
             return srv.submit(r["geom"], pb, r["gal"], r["ran"], want=BALL, bshells=(3, 3, 3, r["S"]),
-                              contraction=fkp.FKP_CONTRACT_BF16X3)
+                              contraction=fkp.FKP_CONTRACT_BF16X6)
         return srv.submit(r["geom"], pb, r["gal"], r["ran"])
 
     srv = fkp.Server(nslots=args.serve_slots)
@@ -466,7 +471,7 @@ def run_serve(args, gal, ran):
     n = len(reqs)
     return {"workload": f"{n} requests, grids {{256,384,512}}, 3.5e5-7e5 galaxies + 30x randoms (host catalogs), "
                         "half P_0,2,4+P_4b, half also B_0,2,4 (37 shells to k=0.2, 27 at 256^3); served: "
-                        "bf16 hi/lo tcgen05 contraction, plain: sequential FP32 contraction",
+                        "3-way split bf16 tcgen05 contraction, plain: sequential FP32 contraction",
             "arrival_rate_per_s": args.serve_rate, "slots": args.serve_slots,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "poisson_wall_s": wall_poisson,

@@ -243,6 +243,13 @@ int fkp_server_stats(void *server, fkp_server_stats_t *stats);
 /* Lets queued and running requests finish, then frees everything. */
 void fkp_server_destroy(void *server);
 
+/* Host-only consistency check of the tables that map the moment fields to
+ * the k_z-power groups (for lmax = 0, 2, 4): the field order matches the
+ * kernels', and the coefficients reproduce S_2 = (k.x^)^2 and S_4 = (k.x^)^4
+ * for unit vectors x^ (the multiplicities of eqs. delta2b, delta4b and the
+ * trace identities of x^).  Needs no GPU.  Returns FKP_OK or FKP_ESTATE. */
+int fkp_check_tables(void);
+
 /* Thread-local message for the last error on this thread. */
 const char *fkp_last_error(void);
 

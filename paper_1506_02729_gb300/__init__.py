@@ -25,7 +25,7 @@ ERRORS = {-1: "FKP_EINVAL", -2: "FKP_EGEOM", -3: "FKP_ENOMEM", -4: "FKP_ETIMEOUT
 EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_plan_destroy", "fkp_plan_sizes",
            "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version",
            "fkp_power_from_grid_noalloc", "fkp_server_create", "fkp_server_submit", "fkp_server_poll",
-           "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy"]
+           "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy", "fkp_check_tables"]
 
 
 class FKPError(RuntimeError):
@@ -116,6 +116,7 @@ def lib():
         L.fkp_server_destroy.argtypes = [vp]
         L.fkp_server_destroy.restype = None
         L.fkp_last_error.restype = C.c_char_p
+        L.fkp_check_tables.argtypes = []
         L.fkp_version.restype = C.c_char_p
         _lib = L
     return _lib
@@ -393,6 +394,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def check_tables():
+    """Host-only check of the moment-field / k_z-group tables (no GPU)."""
+    _check(lib().fkp_check_tables())
 
 
 def version():

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <initializer_list>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -101,38 +102,160 @@ static bool radix_plan(int n, FftPlan& p) {
   return m == 1;
 }
 
-// Field list and k_z-power groups for multipoles up to lmax (0, 2 or 4).
-// Field (i, j, k) is grid * xh_x^i xh_y^j xh_z^k with i + j + k = ell; group
-// (ell, p) holds the fields with k = p, each with coefficient multinomial
-// ell!/(i! j! k!) (the multiplicities 1, 2 of eq. delta2b and 1, 4, 6, 12 of
-// eq. delta4b) and its k_x^i k_y^j monomial.
+// Field list, y-pass sweeps and k_z-power groups for multipoles up to lmax
+// (0, 2 or 4).
+//
+// Fields: grid * xh_x^i xh_y^j xh_z^k for F_0, the rank-2 components with at
+// most one z (xx xy yy xz yz), the rank-4 ones with at most one z (xxxx xxxy
+// xxyy xyyy yyyy xxxz xxyz xyyz yyyz) and zzzz: 16 instead of 1 + 6 + 15.  The
+// others follow from the trace identities of the unit vector xh (eqs. Qij,
+// Qijkl): sum_a Q_aa = F_0 and sum_c Q_abcc = Q_ab, so
+//   Q_zz = F_0 - Q_xx - Q_yy,   Q_abzz = Q_ab - Q_abxx - Q_abyy.
+// With S_2 = sum_ab k_a k_b Q_ab and S_4 = sum_abcd k_a k_b k_c k_d Q_abcd
+// (the multiplicities 1, 2 of eq. delta2b and 1, 4, 6, 12 of eq. delta4b):
+//   S_2 = A + nz G21 + nz^2 (F_0 - T)
+//   S_4 = G40 + nz G41 + nz^2 (6 A - U) + nz^3 (2 G21 - W) + nz^4 Q_zzzz
+// where
+//   A   = nx^2 Qxx + 2 nx ny Qxy + ny^2 Qyy            T = Qxx + Qyy
+//   G21 = 2 nx Qxz + 2 ny Qyz
+//   G40 = nx^4 Qxxxx + 4 nx^3 ny Qxxxy + 6 nx^2 ny^2 Qxxyy + 4 nx ny^3 Qxyyy + ny^4 Qyyyy
+//   U   = 6 nx^2 (Qxxxx + Qxxyy) + 12 nx ny (Qxxxy + Qxyyy) + 6 ny^2 (Qxxyy + Qyyyy)
+//   G41 = 4 nx^3 Qxxxz + 12 nx^2 ny Qxxyz + 12 nx ny^2 Qxyyz + 4 ny^3 Qyyyz
+//   W   = 4 nx (Qxxxz + Qxyyz) + 4 ny (Qxxyz + Qyyyz).
+// The y-pass forms the nine groups (F_0, A, T, G21, G40, U, G41, W, Q_zzzz)
+// after its FFT; the z-pass applies the powers of nz after its own.  At the
+// observer's own node xh = 0, where Qxx + Qyy + Qzz = 0 rather than F_0: the
+// y-pass adds that node's F to T, which keeps F_0 - T equal to Q_zz there too.
 void fkp::build_moments(int lmax, MomentTable& mt) {
   memset(&mt, 0, sizeof(mt));
-  auto fact = [](int n) { int f = 1; for (int i = 2; i <= n; ++i) f *= i; return f; };
-  int q = 0, g = 0;
-  for (int ell = 0; ell <= lmax; ell += 2) {
-    for (int p = 0; p <= ell; ++p) {
-      mt.g_ell[g] = ell;
-      mt.g_p[g] = p;
-      int nm = 0;
-      for (int j = 0; j <= ell - p; ++j) {
-        const int i = ell - p - j;
-        mt.e[q][0] = (unsigned char)i;
-        mt.e[q][1] = (unsigned char)j;
-        mt.e[q][2] = (unsigned char)p;
-        mt.g_field[g][nm] = q;
-        mt.g_coef[g][nm] = (float)(fact(ell) / (fact(i) * fact(j) * fact(p)));
-        mt.g_ei[g][nm] = (unsigned char)i;
-        mt.g_ej[g][nm] = (unsigned char)j;
-        ++nm;
-        ++q;
-      }
-      mt.g_nmem[g] = nm;
-      ++g;
-    }
+  enum { F0 = 0, XX, XY, YY, XZ, YZ, XXXX, XXXY, XXYY, XYYY, YYYY, XXXZ, XXYZ, XYYZ, YYYZ, ZZZZ };
+  static const unsigned char ex[16][3] = {{0, 0, 0}, {2, 0, 0}, {1, 1, 0}, {0, 2, 0}, {1, 0, 1}, {0, 1, 1},
+                                          {4, 0, 0}, {3, 1, 0}, {2, 2, 0}, {1, 3, 0}, {0, 4, 0}, {3, 0, 1},
+                                          {2, 1, 1}, {1, 2, 1}, {0, 3, 1}, {0, 0, 4}};
+  mt.nfields = lmax >= 4 ? 16 : (lmax >= 2 ? 6 : 1);
+  for (int q = 0; q < mt.nfields; ++q)
+    for (int a = 0; a < 3; ++a) mt.e[q][a] = ex[q][a];
+  int ns = 0, ng = 0;
+  // one sweep: its fields, then (output, member, term) = c nx^i ny^j
+  auto sweep = [&](std::initializer_list<int> fields, int nout, int obs) {
+    for (int f : fields) mt.s_field[ns][mt.s_nmem[ns]++] = f;
+    mt.s_nout[ns] = nout;
+    mt.s_obs[ns] = obs;
+    for (int o = 0; o < nout; ++o) mt.s_out[ns][o] = ng++;
+    return ns++;
+  };
+  auto term = [&](int s, int m, int o, int t, float cf, int i, int j) {
+    mt.s_c[s][m][o][t] = cf;
+    mt.s_i[s][m][o][t] = (unsigned char)i;
+    mt.s_j[s][m][o][t] = (unsigned char)j;
+  };
+  auto group = [&](int g, int f0, float c2, int p2, float c4, int p4) {
+    mt.g_f0[g] = f0;
+    mt.g_c2[g] = c2;
+    mt.g_p2[g] = (unsigned char)p2;
+    mt.g_c4[g] = lmax >= 4 ? c4 : 0.f;
+    mt.g_p4[g] = (unsigned char)p4;
+  };
+  int s = sweep({F0}, 1, -1);
+  term(s, 0, 0, 0, 1.f, 0, 0);
+  group(0, 1, lmax >= 2 ? 1.f : 0.f, 2, 0.f, 0);
+  if (lmax >= 2) {
+    s = sweep({XX, XY, YY}, 2, 1);                                   // A, T
+    term(s, 0, 0, 0, 1.f, 2, 0); term(s, 1, 0, 0, 2.f, 1, 1); term(s, 2, 0, 0, 1.f, 0, 2);
+    term(s, 0, 1, 0, 1.f, 0, 0); term(s, 2, 1, 0, 1.f, 0, 0);
+    group(1, 0, 1.f, 0, 6.f, 2);
+    group(2, 0, -1.f, 2, 0.f, 0);
+    s = sweep({XZ, YZ}, 1, -1);                                      // G21
+    term(s, 0, 0, 0, 2.f, 1, 0); term(s, 1, 0, 0, 2.f, 0, 1);
+    group(3, 0, 1.f, 1, 2.f, 3);
   }
-  mt.nfields = q;
-  mt.ngroups = g;
+  if (lmax >= 4) {
+    s = sweep({XXXX, XXXY, XXYY, XYYY, YYYY}, 2, -1);                // G40, U
+    term(s, 0, 0, 0, 1.f, 4, 0); term(s, 1, 0, 0, 4.f, 3, 1); term(s, 2, 0, 0, 6.f, 2, 2);
+    term(s, 3, 0, 0, 4.f, 1, 3); term(s, 4, 0, 0, 1.f, 0, 4);
+    term(s, 0, 1, 0, 6.f, 2, 0); term(s, 1, 1, 0, 12.f, 1, 1); term(s, 2, 1, 0, 6.f, 2, 0);
+    term(s, 2, 1, 1, 6.f, 0, 2); term(s, 3, 1, 0, 12.f, 1, 1); term(s, 4, 1, 0, 6.f, 0, 2);
+    group(4, 0, 0.f, 0, 1.f, 0);
+    group(5, 0, 0.f, 0, -1.f, 2);
+    s = sweep({XXXZ, XXYZ, XYYZ, YYYZ}, 2, -1);                      // G41, W
+    term(s, 0, 0, 0, 4.f, 3, 0); term(s, 1, 0, 0, 12.f, 2, 1); term(s, 2, 0, 0, 12.f, 1, 2);
+    term(s, 3, 0, 0, 4.f, 0, 3);
+    term(s, 0, 1, 0, 4.f, 1, 0); term(s, 1, 1, 0, 4.f, 0, 1); term(s, 2, 1, 0, 4.f, 1, 0);
+    term(s, 3, 1, 0, 4.f, 0, 1);
+    group(6, 0, 0.f, 0, 1.f, 1);
+    group(7, 0, 0.f, 0, -1.f, 3);
+    s = sweep({ZZZZ}, 1, -1);                                        // Q_zzzz
+    term(s, 0, 0, 0, 1.f, 0, 0);
+    group(8, 0, 0.f, 0, 1.f, 4);
+  }
+  mt.nsweeps = ns;
+  mt.ngroups = ng;
+}
+
+// The table reproduces S_2 = (k.xh)^2 and S_4 = (k.xh)^4 (F = 1) for unit
+// vectors xh and arbitrary k: a check of every coefficient above.
+bool fkp::moments_identities_hold(const MomentTable& mt, int lmax) {
+  unsigned long long st = 0x9E3779B97F4A7C15ull;
+  auto rnd = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return (double)(st >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  };
+  for (int trial = 0; trial < 16; ++trial) {
+    double h[3] = {rnd(), rnd(), rnd()}, k[3] = {8 * rnd(), 8 * rnd(), 8 * rnd()};
+    const double hn = std::sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    for (double& v : h) v /= hn;
+    double f[kMaxFields], out[kMaxGroups] = {0};
+    for (int q = 0; q < mt.nfields; ++q)
+      f[q] = std::pow(h[0], mt.e[q][0]) * std::pow(h[1], mt.e[q][1]) * std::pow(h[2], mt.e[q][2]);
+    for (int s = 0; s < mt.nsweeps; ++s)
+      for (int m = 0; m < mt.s_nmem[s]; ++m)
+        for (int o = 0; o < mt.s_nout[s]; ++o)
+          for (int t = 0; t < 2; ++t)
+            out[mt.s_out[s][o]] += mt.s_c[s][m][o][t] * std::pow(k[0], mt.s_i[s][m][o][t]) *
+                                   std::pow(k[1], mt.s_j[s][m][o][t]) * f[mt.s_field[s][m]];
+    double F0 = 0, S2 = 0, S4 = 0;
+    for (int g = 0; g < mt.ngroups; ++g) {
+      if (mt.g_f0[g]) F0 += out[g];
+      S2 += mt.g_c2[g] * std::pow(k[2], mt.g_p2[g]) * out[g];
+      S4 += mt.g_c4[g] * std::pow(k[2], mt.g_p4[g]) * out[g];
+    }
+    const double kh = k[0] * h[0] + k[1] * h[1] + k[2] * h[2];
+    const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    if (std::fabs(F0 - 1.0) > 1e-12) return false;
+    if (lmax >= 2 && std::fabs(S2 - kh * kh) > 1e-9 * k2) return false;
+    if (lmax >= 4 && std::fabs(S4 - kh * kh * kh * kh) > 1e-9 * k2 * k2) return false;
+  }
+  return true;
+}
+
+extern "C" int fkp_check_tables(void) {
+  for (int lmax = 0; lmax <= 4; lmax += 2) {
+    MomentTable mt;
+    build_moments(lmax, mt);
+    if (!moments_match(mt)) return set_error(FKP_ESTATE, "moment table for lmax=%d does not match the kernels", lmax);
+    if (!moments_identities_hold(mt, lmax))
+      return set_error(FKP_ESTATE, "moment table for lmax=%d does not reproduce S_2, S_4", lmax);
+  }
+  return FKP_OK;
+}
+
+// The grid node where the kernels' FP32 node position relative to the
+// observer, fmaf(i, H, origin - observer) per axis, is exactly zero (x^ = 0
+// there), or -1 on every axis when there is none.
+void fkp::observer_node(GeomDev& g) {
+  g.obs_x = g.obs_y = g.obs_z = -1;
+  if (g.los_inf) return;
+  auto axis = [&](float r) {
+    for (int i = 0; i < g.N; ++i)
+      if (std::fmaf((float)i, g.H, r) == 0.f) return i;
+    return -1;
+  };
+  const int ix = axis(g.rx), iy = axis(g.ry), iz = axis(g.rz);
+  if (ix >= 0 && iy >= 0 && iz >= 0) {
+    g.obs_x = ix;
+    g.obs_y = iy;
+    g.obs_z = iz;
+  }
 }
 
 static bool smooth235(int n) {
@@ -197,7 +320,10 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   if (want & (FKP_P4 | FKP_B4)) lmax = 4;
   P->lmax = lmax;
   build_moments(lmax, P->mt);
-  if (!moments_match(P->mt)) { delete P; return set_error(FKP_ESTATE, "internal: moment table order mismatch"); }
+  if (!moments_match(P->mt) || !moments_identities_hold(P->mt, lmax)) {
+    delete P;
+    return set_error(FKP_ESTATE, "internal: moment table inconsistent");
+  }
   if (!radix_plan(N, P->fp)) { delete P; return set_error(FKP_EINVAL, "no radix plan for N=%d", N); }
 
   // geometry as the kernels see it
@@ -223,6 +349,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   g.periodic = geom->periodic ? 1 : 0;
   g.P_fkp = (float)geom->P_fkp;
   g.alpha_mode = geom->alpha_mode;
+  observer_node(g);
 
   // FP64 tables on the host
   const double kf = 2.0 * M_PI / geom->L;
@@ -421,7 +548,7 @@ int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream
 int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s) {
   CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
   CK(cudaEventRecord(P->ev[3], s));
-  CK(launch_ypass(P->d_S1, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
+  CK(launch_ypass(P->d_S1, gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
   CK(cudaEventRecord(P->ev[4], s));
   ZParams zp;
   zp.nbins = P->pb.nbins;

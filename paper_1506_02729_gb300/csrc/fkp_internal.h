@@ -69,6 +69,8 @@ int set_error(int code, const char* fmt, ...);
 // here, so a launch with a smaller need on another thread stays valid.
 cudaError_t raise_smem_limit(const void* func, size_t bytes);
 void build_moments(int lmax, MomentTable& mt);
+bool moments_identities_hold(const MomentTable& mt, int lmax);
+void observer_node(GeomDev& g);
 int stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, cudaStream_t s);
 int enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s);
 int enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s);
@@ -94,7 +96,8 @@ cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xy
 cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s);
-cudaError_t launch_ypass(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
+                         const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, float2* S2, int* err, cudaStream_t s);
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s);

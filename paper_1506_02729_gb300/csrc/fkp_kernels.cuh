@@ -8,9 +8,10 @@
 
 namespace fkp {
 
-constexpr int kMaxFields = 22;   // 1 + 6 + 15 moment fields per base grid
-constexpr int kMaxGroups = 9;    // 1 + 3 + 5 k_z-power groups per base grid
-constexpr int kMaxMembers = 5;   // fields per group
+constexpr int kMaxFields = 16;   // 1 + 5 + 10 trace-reduced moment fields per base grid
+constexpr int kMaxGroups = 9;    // k_z-power groups per base grid
+constexpr int kMaxSweeps = 6;    // y-pass sweeps (fields read in turn into up to two groups)
+constexpr int kMaxMembers = 5;   // fields per sweep
 constexpr int kMaxBins = 512;    // P bins
 constexpr int kMaxShells = 64;   // bispectrum shells
 constexpr double kFixScale = 1099511627776.0;       // 2^40: fixed-point scale of the grids
@@ -29,22 +30,28 @@ struct GeomDev {
   int periodic;
   float P_fkp;
   int alpha_mode;
+  int obs_x, obs_y, obs_z;  // grid node at the observer (x^ = 0 there), or -1
 };
 
-// Moment fields of one base grid: field q is grid * xh_x^e[q][0] xh_y^e[q][1] xh_z^e[q][2].
-// Group g collects the fields of multipole ell with k_z power p:
-// G_g(kx,ky,z) = sum_m coef[m] nx^i ny^j Q~_{field[m]}(kx,ky,z).
+// Moment fields of one base grid: field q is grid * xh_x^e[q][0] xh_y^e[q][1]
+// xh_z^e[q][2].  The y-pass reads the fields sweep by sweep; sweep s reads
+// s_field[s][0..s_nmem) and accumulates s_nout <= 2 output groups
+// s_out[s][o], member m entering output o with the coefficient
+// sum_t s_c[s][m][o][t] nx^s_i[s][m][o][t] ny^s_j[s][m][o][t] (t < 2), and the
+// output s_obs[s] (if >= 0) receiving the observer node's F.  The z-pass then
+// adds group g to F_0 (g_f0), g_c2 nz^g_p2 times it to S_2 and g_c4 nz^g_p4
+// times it to S_4.
 struct MomentTable {
-  int nfields;
-  int ngroups;
+  int nfields, ngroups, nsweeps;
   unsigned char e[kMaxFields][3];
-  int g_ell[kMaxGroups];
-  int g_p[kMaxGroups];
-  int g_nmem[kMaxGroups];
-  int g_field[kMaxGroups][kMaxMembers];
-  float g_coef[kMaxGroups][kMaxMembers];
-  unsigned char g_ei[kMaxGroups][kMaxMembers];
-  unsigned char g_ej[kMaxGroups][kMaxMembers];
+  int s_nmem[kMaxSweeps], s_nout[kMaxSweeps], s_out[kMaxSweeps][2], s_obs[kMaxSweeps];
+  int s_field[kMaxSweeps][kMaxMembers];
+  float s_c[kMaxSweeps][kMaxMembers][2][2];
+  unsigned char s_i[kMaxSweeps][kMaxMembers][2][2];
+  unsigned char s_j[kMaxSweeps][kMaxMembers][2][2];
+  int g_f0[kMaxGroups];
+  float g_c2[kMaxGroups], g_c4[kMaxGroups];
+  unsigned char g_p2[kMaxGroups], g_p4[kMaxGroups];
 };
 
 // Number of per-block FP64 partial sums the scalar kernels produce.

@@ -70,7 +70,7 @@ size_t estimate_plan(const fkp_request_t& r) {
   int lmax = 0;
   if (r.want & (FKP_P2 | FKP_P4B | FKP_B2)) lmax = 2;
   if (r.want & (FKP_P4 | FKP_B4)) lmax = 4;
-  const int nf = lmax >= 4 ? 22 : (lmax >= 2 ? 7 : 1), ng = lmax >= 4 ? 9 : (lmax >= 2 ? 4 : 1);
+  const int nf = lmax >= 4 ? 16 : (lmax >= 2 ? 6 : 1), ng = lmax >= 4 ? 9 : (lmax >= 2 ? 4 : 1);
   const size_t half = field_elems(N) * sizeof(float2);
   size_t b = N3 * 8 * (B ? 2 : 1) + half * (nf + ng);
   b += sizeof(double) * (BQ_N + 1) * (size_t)r.pbins.nbins * tiles_x(N) * N;

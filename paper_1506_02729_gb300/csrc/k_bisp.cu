@@ -61,6 +61,10 @@ struct BispState {
   short2* d_pairs = nullptr;
   int *d_om = nullptr, *d_on = nullptr;
   float* d_tcpart = nullptr;
+  // shell IFFT work lists: z tiles (s, n_y + mm, n_x0), y tiles (s, n_x0, |n_y| range); floor(r_s)
+  int nzjobs = 0, nyjobs = 0;
+  int4 *d_zjobs = nullptr, *d_yjobs = nullptr;
+  int* d_kmax = nullptr;
 };
 
 __device__ __forceinline__ int wrap_mode(int n, int N) { return n < 0 ? n + N : n; }
@@ -106,112 +110,152 @@ __global__ void __launch_bounds__(256) k_counts(const int* __restrict__ ball, co
 
 // ----------------------------------------------------------------------------
 // shell-filtered inverse FFTs (eq. F_k)
+//
+// F_k^(l)(x) = sum_{q in shell} F_l(q) e^{iq.x} is an unnormalised inverse
+// DFT of F_l restricted to shell s, which is zero outside the ball |n| <= r_s
+// (r_s^2 = the largest n^2 the shell holds).  The three passes visit only
+// what that ball reaches, from work lists built with the plan:
+//   z   per tile (s, n_y, 8 consecutive n_x) with n_x0^2 + n_y^2 <= r_s^2:
+//       the 8 pencils along n_z, filled from E on the shell;  T1[s][z][n_y][n_x]
+//   y   per tile (s, 8 consecutive n_x) with n_x0^2 <= r_s^2 and per z: the
+//       8 pencils along n_y over |n_y| <= sqrt(r_s^2 - n_x0^2);  T2[s][z][y][n_x]
+//   x   per pair of rows (s, z, y): complex-to-real along x from
+//       n_x <= floor(r_s) (Hermitian extension), two real rows per complex
+//       pencil;  I[s][z][y][x]
+// Pencils are interleaved 8 to a block (element i of pencil p at i * 8 + p)
+// for the compile-time FFT.
 // ----------------------------------------------------------------------------
 
-constexpr int kBX = 8;      // columns per tile
-constexpr int kBR = 32;     // threads per column
-constexpr int kBRL = 16;    // points per thread (N <= 512)
+constexpr int kSP = 8;      // pencils per block
+constexpr int kSNT = 256;   // threads per block: (kSP, 32)
+constexpr int kSRL = 16;    // points per thread along a pencil (N <= 512)
 
 struct ShellParams {
   int N, mm, S, nsh2;
   const signed char* slut;
+  const int* kmax;          // per shell: floor(r_s)
 };
 
-// z pass: pencils (kx, ky') of shell s, filled from E on the shell, inverse
-// transformed along z.  T1 layout [s][z][ky'][kx], ky' = ny + mm.
-__global__ void __launch_bounds__(kBX * kBR) k_shell_z(const float2* __restrict__ E, ShellParams sp, FftPlan fp,
-                                                       const float2* __restrict__ tw, float2* __restrict__ T1) {
-  extern __shared__ float2 smem[];
-  const int N = sp.N, mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1;
-  const int pst = N + 1;
-  float2* A = smem;
-  float2* B = smem + kBX * pst;
-  const int s = blockIdx.z, kyp = blockIdx.y, kx0 = blockIdx.x * kBX;
-  const int tw_ = min(kBX, m1 - kx0);
-  const int ny = kyp - mm;
-  for (int t = threadIdx.x; t < kBX * pst; t += blockDim.x) A[t] = make_float2(0.f, 0.f);
+// One multipole's shell passes.
+struct BispLaunch {
+  ShellParams sp;
+  FftPlan fp;
+  const float2* tw;
+  const float2* E;          // F_l on the ball |n| <= mm: [n_z + mm][n_y + mm][n_x]
+  const int4* zjobs;
+  int nz;
+  const int4* yjobs;
+  int ny;
+  float2 *T1, *T2;
+  float* I;                 // this multipole's S real shell fields
+  int xblocks;
+};
+
+template <int N_>
+__global__ void __launch_bounds__(kSNT) k_shell_z(const float2* __restrict__ E, ShellParams sp, FftPlan fp,
+                                                  const float2* __restrict__ twg, const int4* __restrict__ jobs,
+                                                  float2* __restrict__ T1) {
+  extern __shared__ float2 sm[];
+  const int N = N_ ? N_ : sp.N;
+  float2* tw = sm;
+  float2* A = sm + N;
+  float2* B = A + kSP * N;
+  const int tid = threadIdx.y * kSP + threadIdx.x;
+  const int4 job = jobs[blockIdx.x];
+  const int s = job.x, kyp = job.y, kx0 = job.z;
+  const int mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1, ny = kyp - mm;
+  for (int i = tid; i < N; i += kSNT) tw[i] = twg[i];
+  for (int i = tid; i < kSP * N; i += kSNT) A[i] = make_float2(0.f, 0.f);
   __syncthreads();
-  for (int t = threadIdx.x; t < w2 * kBX; t += blockDim.x) {
-    const int kzp = t / kBX, cc = t - kzp * kBX;
-    if (cc < tw_) {
-      const int kx = kx0 + cc, nz = kzp - mm;
+  for (int t = tid; t < w2 * kSP; t += kSNT) {
+    const int kzp = t / kSP, c = t - kzp * kSP, kx = kx0 + c;
+    if (kx < m1) {
+      const int nz = kzp - mm;
       const int n2 = kx * kx + ny * ny + nz * nz;
-      if (n2 < sp.nsh2 && sp.slut[n2] == s)
-        A[cc * pst + wrap_mode(nz, N)] = E[((size_t)kzp * w2 + kyp) * m1 + kx];
+      if (n2 < sp.nsh2 && sp.slut[n2] == s) A[wrap_mode(nz, N) * kSP + c] = E[((size_t)kzp * w2 + kyp) * m1 + kx];
     }
   }
   __syncthreads();
-  const float2* R = fft_smem<1>(A, B, kBX, pst, fp, tw);
-  const int c = threadIdx.x % kBX, run = threadIdx.x / kBX;
-  const int rl = (N + kBR - 1) / kBR;
-  if (c < tw_) {
+  const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
+  const int c = threadIdx.x, run = threadIdx.y, rl = (N + 31) / 32;
+  if (kx0 + c < m1) {
 #pragma unroll
-    for (int i = 0; i < kBRL; ++i) {
+    for (int i = 0; i < kSRL; ++i) {
       const int z = run * rl + i;
-      if (i < rl && z < N) T1[(((size_t)s * N + z) * w2 + kyp) * m1 + kx0 + c] = R[c * pst + z];
+      if (i < rl && z < N) T1[(((size_t)s * N + z) * w2 + kyp) * m1 + kx0 + c] = R[z * kSP + c];
     }
   }
 }
 
-// y pass: pencils (z, kx) over ky'.  T2 layout [s][z][y][kx].
-__global__ void __launch_bounds__(kBX * kBR) k_shell_y(const float2* __restrict__ T1, ShellParams sp, FftPlan fp,
-                                                       const float2* __restrict__ tw, float2* __restrict__ T2) {
-  extern __shared__ float2 smem[];
-  const int N = sp.N, mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1;
-  const int pst = N + 1;
-  float2* A = smem;
-  float2* B = smem + kBX * pst;
-  const int s = blockIdx.z, z = blockIdx.y, kx0 = blockIdx.x * kBX;
-  const int tw_ = min(kBX, m1 - kx0);
-  for (int t = threadIdx.x; t < kBX * pst; t += blockDim.x) A[t] = make_float2(0.f, 0.f);
+template <int N_>
+__global__ void __launch_bounds__(kSNT) k_shell_y(const float2* __restrict__ T1, ShellParams sp, FftPlan fp,
+                                                  const float2* __restrict__ twg, const int4* __restrict__ jobs,
+                                                  float2* __restrict__ T2) {
+  extern __shared__ float2 sm[];
+  const int N = N_ ? N_ : sp.N;
+  float2* tw = sm;
+  float2* A = sm + N;
+  float2* B = A + kSP * N;
+  const int tid = threadIdx.y * kSP + threadIdx.x;
+  const int4 job = jobs[blockIdx.x];
+  const int s = job.x, kx0 = job.y, nyr = job.z, z = blockIdx.y;
+  const int mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1;
+  for (int i = tid; i < N; i += kSNT) tw[i] = twg[i];
+  for (int i = tid; i < kSP * N; i += kSNT) A[i] = make_float2(0.f, 0.f);
   __syncthreads();
-  for (int t = threadIdx.x; t < w2 * kBX; t += blockDim.x) {
-    const int kyp = t / kBX, cc = t - kyp * kBX;
-    if (cc < tw_) A[cc * pst + wrap_mode(kyp - mm, N)] = T1[(((size_t)s * N + z) * w2 + kyp) * m1 + kx0 + cc];
+  for (int t = tid; t < (2 * nyr + 1) * kSP; t += kSNT) {
+    const int j = t / kSP, c = t - j * kSP, ny = j - nyr;
+    if (kx0 + c < m1) A[wrap_mode(ny, N) * kSP + c] = T1[(((size_t)s * N + z) * w2 + ny + mm) * m1 + kx0 + c];
   }
   __syncthreads();
-  const float2* R = fft_smem<1>(A, B, kBX, pst, fp, tw);
-  const int c = threadIdx.x % kBX, run = threadIdx.x / kBX;
-  const int rl = (N + kBR - 1) / kBR;
-  if (c < tw_) {
+  const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
+  const int c = threadIdx.x, run = threadIdx.y, rl = (N + 31) / 32;
+  if (kx0 + c < m1) {
 #pragma unroll
-    for (int i = 0; i < kBRL; ++i) {
+    for (int i = 0; i < kSRL; ++i) {
       const int y = run * rl + i;
-      if (i < rl && y < N) T2[(((size_t)s * N + z) * N + y) * m1 + kx0 + c] = R[c * pst + y];
+      if (i < rl && y < N) T2[(((size_t)s * N + z) * N + y) * m1 + kx0 + c] = R[y * kSP + c];
     }
   }
 }
 
-// x pass, complex to real: two rows per complex pencil.  The half spectrum
-// k = 0..mm (zero above) is extended by Hermitian symmetry; the DC term keeps
-// its real part only.  I layout [s][z][y][x] (one multipole).
-constexpr int kXP = 8;  // pencils (row pairs) per block iteration
-
-__global__ void __launch_bounds__(256) k_shell_x(const float2* __restrict__ T2, ShellParams sp, FftPlan fp,
-                                                 const float2* __restrict__ tw, float* __restrict__ I) {
-  extern __shared__ float2 smem[];
-  const int N = sp.N, m1 = sp.mm + 1;
-  float2* A = smem;
-  float2* B = smem + kXP * N;
-  const long long rows = (long long)sp.S * N * N;
-  const long long pairs = rows / 2;
-  for (long long g0 = (long long)blockIdx.x * kXP; g0 < pairs; g0 += (long long)gridDim.x * kXP) {
-    const int np = (int)(pairs - g0 < kXP ? pairs - g0 : kXP);
-    for (int t = threadIdx.x; t < kXP * N; t += blockDim.x) {
-      const int p = t / N, k = t - p * N;
+// Rows r = (s N + z) N + y; pencil p of a block iteration holds rows 2(g0+p)
+// and 2(g0+p)+1 (same shell: N^2 is even) as x1 + i x2.
+template <int N_>
+__global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2, ShellParams sp, FftPlan fp,
+                                                  const float2* __restrict__ twg, float* __restrict__ I) {
+  extern __shared__ float2 sm[];
+  const int N = N_ ? N_ : sp.N;
+  float2* tw = sm;
+  float2* A = sm + N;
+  float2* B = A + kSP * N;
+  const int tid = threadIdx.y * kSP + threadIdx.x;
+  const int m1 = sp.mm + 1;
+  for (int i = tid; i < N; i += kSNT) tw[i] = twg[i];
+  const long long pairs = (long long)sp.S * N * N / 2;
+  for (long long g0 = (long long)blockIdx.x * kSP; g0 < pairs; g0 += (long long)gridDim.x * kSP) {
+    const int np = (int)(pairs - g0 < kSP ? pairs - g0 : kSP);
+    const int s = (int)((2 * g0) / ((long long)N * N));
+    const int km = sp.kmax[s < sp.S ? s : sp.S - 1];
+    __syncthreads();
+    // p fastest: contiguous shared-memory stores, 32-byte row segments read
+    for (int t = tid; t < kSP * N; t += kSNT) {
+      const int p = t % kSP, k = t / kSP;
       float2 v = make_float2(0.f, 0.f);
       if (p < np) {
         const long long r0 = 2 * (g0 + p);
+        const int sp0 = (int)(r0 / ((long long)N * N));
+        const int kmp = sp0 == s ? km : sp.kmax[sp0];
         const float2* h0 = T2 + r0 * m1;
         const float2* h1 = h0 + m1;
-        float2 x1 = make_float2(0.f, 0.f), x2 = make_float2(0.f, 0.f);
+        float2 x1 = make_float2(0.f, 0.f), x2 = x1;
         if (k == 0) {
           x1 = make_float2(h0[0].x, 0.f);
           x2 = make_float2(h1[0].x, 0.f);
-        } else if (k <= sp.mm) {
+        } else if (k <= kmp) {
           x1 = h0[k];
           x2 = h1[k];
-        } else if (k >= N - sp.mm) {
+        } else if (k >= N - kmp) {
           const float2 a = h0[N - k], b = h1[N - k];
           x1 = make_float2(a.x, -a.y);
           x2 = make_float2(b.x, -b.y);
@@ -221,15 +265,44 @@ __global__ void __launch_bounds__(256) k_shell_x(const float2* __restrict__ T2, 
       A[t] = v;
     }
     __syncthreads();
-    const float2* R = fft_smem<1>(A, B, kXP, N, fp, tw);
-    for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
-      const int p = t / N, x = t - p * N;
-      const long long r0 = 2 * (g0 + p);
-      const float2 v = R[p * N + x];
-      I[r0 * N + x] = v.x;
-      I[(r0 + 1) * N + x] = v.y;
+    const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
+    // transpose through the free buffer into rows, then coalesced stores
+    float* rows = reinterpret_cast<float*>(R == A ? B : A);
+    for (int t = tid; t < kSP * N; t += kSNT) {
+      const int p = t % kSP, x = t / kSP;
+      const float2 v = R[t];
+      rows[(2 * p) * N + x] = v.x;
+      rows[(2 * p + 1) * N + x] = v.y;
     }
     __syncthreads();
+    const long long r0 = 2 * g0;
+    for (int t = tid; t < 2 * np * N; t += kSNT) I[r0 * N + t] = rows[t];
+  }
+}
+
+template <int N_>
+static cudaError_t shell_passes_n(const BispLaunch& L, cudaStream_t s) {
+  const size_t sm = sizeof(float2) * (size_t)L.sp.N * (1 + 2 * kSP);
+  cudaError_t e;
+  if ((e = raise_smem_limit((const void*)k_shell_z<N_>, sm)) != cudaSuccess) return e;
+  if ((e = raise_smem_limit((const void*)k_shell_y<N_>, sm)) != cudaSuccess) return e;
+  if ((e = raise_smem_limit((const void*)k_shell_x<N_>, sm)) != cudaSuccess) return e;
+  const dim3 blk(kSP, kSNT / kSP);
+  if (L.nz > 0) k_shell_z<N_><<<L.nz, blk, sm, s>>>(L.E, L.sp, L.fp, L.tw, L.zjobs, L.T1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (L.ny > 0) k_shell_y<N_><<<dim3(L.ny, L.sp.N), blk, sm, s>>>(L.T1, L.sp, L.fp, L.tw, L.yjobs, L.T2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_shell_x<N_><<<L.xblocks, blk, sm, s>>>(L.T2, L.sp, L.fp, L.tw, L.I);
+  return cudaGetLastError();
+}
+
+static cudaError_t shell_passes(const BispLaunch& L, cudaStream_t s) {
+  switch (L.sp.N) {
+    case 360: return shell_passes_n<360>(L, s);
+    case 256: return shell_passes_n<256>(L, s);
+    case 384: return shell_passes_n<384>(L, s);
+    case 512: return shell_passes_n<512>(L, s);
+    default: return shell_passes_n<0>(L, s);
   }
 }
 
@@ -496,9 +569,36 @@ int bisp_plan_init(Plan* P) {
       if (q >= st->lo[k] * st->lo[k] && q < st->hi[k] * st->hi[k]) { slut[q] = (signed char)k; break; }
 
   const int mm = st->mm, w2 = 2 * mm + 1, m1 = mm + 1;
+  // shell radii and the shell passes' work lists
+  std::vector<int> r2max(S, -1), kmax(S, 0);
+  for (int q = 1; q < st->nsh2; ++q)
+    if (slut[q] >= 0) r2max[slut[q]] = q;
+  std::vector<int4> zj, yj;
+  for (int s = 0; s < S; ++s) {
+    if (r2max[s] < 0) continue;
+    int k = 0;
+    while ((k + 1) * (k + 1) <= r2max[s]) ++k;
+    kmax[s] = std::min(k, mm);
+    for (int kyp = 0; kyp < w2; ++kyp) {
+      const int ny = kyp - mm;
+      for (int kx0 = 0; kx0 < m1; kx0 += 8)
+        if (kx0 * kx0 + ny * ny <= r2max[s]) zj.push_back(make_int4(s, kyp, kx0, 0));
+    }
+    for (int kx0 = 0; kx0 < m1; kx0 += 8)
+      if (kx0 * kx0 <= r2max[s]) {
+        int nyr = 0;
+        while ((nyr + 1) * (nyr + 1) + kx0 * kx0 <= r2max[s]) ++nyr;
+        yj.push_back(make_int4(s, kx0, std::min(nyr, mm), 0));
+      }
+  }
+  st->nzjobs = (int)zj.size();
+  st->nyjobs = (int)yj.size();
   bool ok = true;
   auto A = [&](size_t bytes) { void* p = P->alloc(bytes); if (!p) ok = false; return p; };
   st->d_slut = (signed char*)A(st->nsh2);
+  st->d_zjobs = (int4*)A(sizeof(int4) * std::max<size_t>(1, zj.size()));
+  st->d_yjobs = (int4*)A(sizeof(int4) * std::max<size_t>(1, yj.size()));
+  st->d_kmax = (int*)A(sizeof(int) * S);
   st->d_E = (float2*)A(sizeof(float2) * 3 * (size_t)w2 * w2 * m1);
   st->d_T1 = (float2*)A(sizeof(float2) * (size_t)S * N * w2 * m1);
   st->d_T2 = (float2*)A(sizeof(float2) * (size_t)S * N * N * m1);
@@ -522,6 +622,9 @@ int bisp_plan_init(Plan* P) {
   if (P->ctx->budget && P->bytes_total > P->ctx->budget)
     return set_error(FKP_ENOMEM, "plan needs %.2f GB, over the HBM budget", P->bytes_total / 1e9);
   BCK(cudaMemcpy(st->d_slut, slut.data(), st->nsh2, cudaMemcpyHostToDevice));
+  if (!zj.empty()) BCK(cudaMemcpy(st->d_zjobs, zj.data(), sizeof(int4) * zj.size(), cudaMemcpyHostToDevice));
+  if (!yj.empty()) BCK(cudaMemcpy(st->d_yjobs, yj.data(), sizeof(int4) * yj.size(), cudaMemcpyHostToDevice));
+  BCK(cudaMemcpy(st->d_kmax, kmax.data(), sizeof(int) * S, cudaMemcpyHostToDevice));
   if (!st->items.empty())
     BCK(cudaMemcpy(st->d_items, st->items.data(), sizeof(ContractItem) * st->items.size(), cudaMemcpyHostToDevice));
   BCK(cudaMemset(st->d_cpart, 0, sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * 3));
@@ -578,7 +681,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   // F: P bins and export on the shells
   BCK(launch_xpass(P->d_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
   BCK(cudaEventRecord(P->ev[3], s));
-  BCK(launch_ypass(P->d_S1, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
+  BCK(launch_ypass(P->d_S1, P->d_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
   BCK(cudaEventRecord(P->ev[4], s));
   zp.mode = 1;
   BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s));
@@ -586,29 +689,31 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   BCK(cudaEventRecord(P->ev[5], s));
   // F^w: shell sums against the exported F_l
   BCK(launch_xpass(P->d_gridw, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
-  BCK(launch_ypass(P->d_S1, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
+  BCK(launch_ypass(P->d_S1, P->d_gridw, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
   zp.mode = 2;
   BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, st->d_spart, st->d_spartc, P->d_err + 1, s));
   BCK(launch_reduce_bins(st->d_spart, st->d_spartc, P->nblk_z, S, st->d_shell, st->d_shellc, s));
   BCK(cudaEventRecord(P->ev[6], s));
   // shell IFFTs
-  ShellParams sp{N, mm, S, st->nsh2, st->d_slut};
-  const int m1 = mm + 1, w2 = 2 * mm + 1;
-  const size_t smz = sizeof(float2) * 2 * kBX * (N + 1);
-  const size_t smx = sizeof(float2) * 2 * kXP * N;
-  BCK(raise_smem_limit((const void*)k_shell_z, smz));
-  BCK(raise_smem_limit((const void*)k_shell_y, smz));
-  BCK(raise_smem_limit((const void*)k_shell_x, smx));
   const long long N3 = (long long)N * N * N;
-  const size_t es = (size_t)w2 * w2 * m1;
-  for (int li = 0; li < st->nl; ++li) {
-    k_shell_z<<<dim3((m1 + kBX - 1) / kBX, w2, S), kBX * kBR, smz, s>>>(st->d_E + li * es, sp, P->fp, P->d_tw,
-                                                                        st->d_T1);
-    BCK(cudaGetLastError());
-    k_shell_y<<<dim3((m1 + kBX - 1) / kBX, N, S), kBX * kBR, smz, s>>>(st->d_T1, sp, P->fp, P->d_tw, st->d_T2);
-    BCK(cudaGetLastError());
-    k_shell_x<<<P->ctx->nsm * 4, 256, smx, s>>>(st->d_T2, sp, P->fp, P->d_tw, st->d_I + (size_t)li * S * N3);
-    BCK(cudaGetLastError());
+  {
+    const size_t es = (size_t)(2 * mm + 1) * (2 * mm + 1) * (mm + 1);
+    BispLaunch L;
+    L.sp = ShellParams{N, mm, S, st->nsh2, st->d_slut, st->d_kmax};
+    L.fp = P->fp;
+    L.tw = P->d_tw;
+    L.zjobs = st->d_zjobs;
+    L.nz = st->nzjobs;
+    L.yjobs = st->d_yjobs;
+    L.ny = st->nyjobs;
+    L.T1 = st->d_T1;
+    L.T2 = st->d_T2;
+    L.xblocks = P->ctx->nsm * 6;
+    for (int li = 0; li < st->nl; ++li) {
+      L.E = st->d_E + li * es;
+      L.I = st->d_I + (size_t)li * S * N3;
+      BCK(shell_passes(L, s));
+    }
   }
   BCK(cudaEventRecord(P->ev[7], s));
   // contraction

@@ -7,12 +7,13 @@
 // A = the shell fields and B = the Khatri-Rao products F_b^(0) F_c^(0).  Each
 // FP32 operand v is split into BF16 v_hi = bf16(v), v_lo = bf16(v - v_hi); the
 // three products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor
-// memory (the lo*lo term, ~2^-16 relative, is dropped).  The 3-way split
-// v = v_hi + v_mid + v_lo keeps the six products whose order is at most
+// memory (the lo*lo term and the rounding of lo, each ~2^-18 relative, are
+// dropped: a per-product error of random sign, which over N^3 points
+// random-walks to ~2^-17 sqrt(sum_x t^2) on a triangle sum).  The 3-way
+// split v = v_hi + v_mid + v_lo keeps the six products whose order is at most
 // 2^-16 (hh, hm, mh, hl, lh, mm), for a per-term error near FP32 rounding:
-// the triangle sums cancel strongly (sum |t| >> |sum t|), and the 2-way
-// split's ~1e-5 per-term error was measured to reach 5e-4 - 3e-3 of the
-// bispectrum monopole scale, so the 3-way split is the accurate mode.
+// the triangle sums cancel strongly (sum |t| >> |sum t|), so the 3-way split
+// is the accurate mode and the 2-way split the fast one.
 //
 // One CTA per (256-column N tile, K slice of 65,536 points).  The shell
 // fields of a chunk of 32 points are fetched two chunks ahead with cp.async

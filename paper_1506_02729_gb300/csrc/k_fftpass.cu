@@ -3,9 +3,10 @@
 //   x-pass  per grid row: moment fields F x^_a x^_b (...) built at the nodes
 //           about the observer (eqs. Qij, Qijkl, Qab), two real fields packed
 //           per complex pencil, FFT along x, unpacked into half spectra.
-//   y-pass  per (z, k_x tile): FFT of each field along y, then the k_x^i k_y^j
-//           monomials of eqs. delta2b and delta4b and the multinomial
-//           multiplicities, summed into k_z-power groups.
+//   y-pass  per (z, k_x tile): FFT of each field along y, then the k_x, k_y
+//           polynomials of eqs. delta2b and delta4b (with the multinomial
+//           multiplicities and the trace identities of the unit vector x^),
+//           summed into k_z-power groups.
 //   z-pass  per (k_y, k_x tile): FFT of each group along z, Legendre
 //           recombination F_2 = 3/2 S_2/|n|^2 - F_0/2 and
 //           F_4 = 35/8 S_4/|n|^4 - 5/2 F_2 - 7/8 F_0 (eqs. F2, delta4),
@@ -24,9 +25,10 @@
 namespace fkp {
 
 constexpr int kT = 8;        // k_x columns per tile (64 bytes of complex64)
-constexpr int kNT = 256;     // threads per block
-constexpr int kRun = 32;     // threads per column in the accumulate/bin phase
-constexpr int kMaxRL = 16;   // points per thread along a pencil (N <= 512)
+// y-pass blocks (8, 32), two per SM; z-pass blocks (8, 64), one per SM (its
+// three accumulators per point need the registers)
+constexpr int kNTy = 256, kRunY = 32, kRLY = 16;  // threads, threads per column, points per thread (N <= 512)
+constexpr int kNTz = 512, kRunZ = 64, kRLZ = 8;
 
 __device__ __forceinline__ int smode(int k, int N) { return k <= N / 2 ? k : k - N; }
 
@@ -45,16 +47,19 @@ __device__ __forceinline__ float pw5(const float* h, int e) {
 // ----------------------------------------------------------------------------
 
 // Moment-field exponents (i, j, k) of x^_x^i x^_y^j x^_z^k in the order the
-// host's moment table uses: multipole ell = 0, 2, 4, then k_z power p, then j.
-__host__ __device__ constexpr int nfields_of(int lmax) { return lmax >= 4 ? 22 : (lmax >= 2 ? 7 : 1); }
+// host's moment table uses: F_0; for ell = 2, 4 the components with z power
+// p = 0, 1 (j ascending); then zzzz (the trace-reduced set: 1 + 5 + 10).
+__host__ __device__ constexpr int nfields_of(int lmax) { return lmax >= 4 ? 16 : (lmax >= 2 ? 6 : 1); }
 __host__ __device__ constexpr int field_exp(int q, int a) {
   int idx = 0;
-  for (int ell = 0; ell <= 4; ell += 2)
-    for (int p = 0; p <= ell; ++p)
+  for (int ell = 0; ell <= 4; ell += 2) {
+    for (int p = 0; p <= (ell ? 1 : 0); ++p)
       for (int j = 0; j <= ell - p; ++j) {
         if (idx == q) return a == 0 ? ell - p - j : (a == 1 ? j : p);
         ++idx;
       }
+    if (ell == 4 && idx == q) return a == 2 ? 4 : 0;
+  }
   return 0;
 }
 
@@ -143,9 +148,13 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
 // ----------------------------------------------------------------------------
 
 // Block (8, 32): threadIdx.x is the k_x column of the tile (the FFT pencil),
-// threadIdx.y the run of k_y this thread accumulates.
+// threadIdx.y the run of k_y this thread accumulates.  The fields are read
+// sweep by sweep; a sweep accumulates up to two output groups, each member
+// with a polynomial coefficient in n_y evaluated by Horner's rule.
 template <int N_>
-__global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1, GeomDev g, MomentTable mt,
+__global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S1,
+                                                   const unsigned long long* __restrict__ gq,
+                                                   const float* __restrict__ gf, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg,
                                                    float2* __restrict__ S2, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -162,60 +171,150 @@ __global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1
   const size_t gsz = fsz;
   const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
   const int tid = threadIdx.y * kT + threadIdx.x;
-  for (int i = tid; i < N; i += kNT) tw[i] = twg[i];
+  for (int i = tid; i < N; i += kNTy) tw[i] = twg[i];
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  // flattened member list
   int total = 0;
-  for (int gi = 0; gi < mt.ngroups; ++gi) total += mt.g_nmem[gi];
+  for (int s = 0; s < mt.nsweeps; ++s) total += mt.s_nmem[s];
   auto src_of = [&](int q) { return S1 + (size_t)q * fsz + ((size_t)z * NXT + xt) * tile; };
   if (tid == 0) {
     mbar_expect_tx(&bar[0], bytes);
-    tma_load_1d(buf0, src_of(mt.g_field[0][0]), bytes, &bar[0]);
+    tma_load_1d(buf0, src_of(mt.s_field[0][0]), bytes, &bar[0]);
   }
   const int c = threadIdx.x, run = threadIdx.y;
-  const int rl = (N + kRun - 1) / kRun;
-  const float nx = (float)(xt * kT + c);
+  const int rl = (N + kRunY - 1) / kRunY;
+  const int kx = xt * kT + c;
+  const float nx = (float)kx;
   int it = 0;
-  for (int gi = 0; gi < mt.ngroups; ++gi) {
-    float2 acc[kMaxRL];
+  for (int sw = 0; sw < mt.nsweeps; ++sw) {
+    const int nout = mt.s_nout[sw];
+    float2 acc0[kRLY], acc1[kRLY];
 #pragma unroll
-    for (int i = 0; i < kMaxRL; ++i) acc[i] = make_float2(0.f, 0.f);
-    for (int m = 0; m < mt.g_nmem[gi]; ++m, ++it) {
+    for (int i = 0; i < kRLY; ++i) {
+      acc0[i] = make_float2(0.f, 0.f);
+      acc1[i] = acc0[i];
+    }
+    for (int m = 0; m < mt.s_nmem[sw]; ++m, ++it) {
       const int cur = it & 1;
       float2* bc = cur ? buf1 : buf0;
       if (tid == 0 && it + 1 < total) {
-        int g2 = gi, m2 = m + 1;
-        if (m2 == mt.g_nmem[gi]) { g2 = gi + 1; m2 = 0; }
+        int s2 = sw, m2 = m + 1;
+        if (m2 == mt.s_nmem[sw]) { s2 = sw + 1; m2 = 0; }
         fence_proxy_async();
         mbar_expect_tx(&bar[cur ^ 1], bytes);
-        tma_load_1d(cur ? buf0 : buf1, src_of(mt.g_field[g2][m2]), bytes, &bar[cur ^ 1]);
+        tma_load_1d(cur ? buf0 : buf1, src_of(mt.s_field[s2][m2]), bytes, &bar[cur ^ 1]);
       }
       mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 4);
-      const float2* R = fft_any<N_, kT, kNT, -1>(bc, work, fp, tw);
-      const float coef = mt.g_coef[gi][m] * powi(nx, mt.g_ei[gi][m]);
-      const int ej = mt.g_ej[gi][m];
+      const float2* R = fft_any<N_, kT, kNTy, -1>(bc, work, fp, tw);
+      // coefficients a[o][j] of n_y^j for this member and column
+      float a[2][5];
 #pragma unroll
-      for (int i = 0; i < kMaxRL; ++i) {
+      for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          float v = 0.f;
+#pragma unroll
+          for (int t = 0; t < 2; ++t)
+            if (mt.s_j[sw][m][o][t] == j) v += mt.s_c[sw][m][o][t] * powi(nx, mt.s_i[sw][m][o][t]);
+          a[o][j] = v;
+        }
+#pragma unroll
+      for (int i = 0; i < kRLY; ++i) {
         const int ky = run * rl + i;
         if (i < rl && ky < N) {
-          const float s = coef * powi((float)smode(ky, N), ej);
+          const float ny = (float)smode(ky, N);
           const float2 v = R[ky * kT + c];
-          acc[i].x = fmaf(s, v.x, acc[i].x);
-          acc[i].y = fmaf(s, v.y, acc[i].y);
+          const float s0 = fmaf(fmaf(fmaf(fmaf(a[0][4], ny, a[0][3]), ny, a[0][2]), ny, a[0][1]), ny, a[0][0]);
+          acc0[i].x = fmaf(s0, v.x, acc0[i].x);
+          acc0[i].y = fmaf(s0, v.y, acc0[i].y);
+          if (nout > 1) {
+            const float s1 = fmaf(fmaf(fmaf(fmaf(a[1][4], ny, a[1][3]), ny, a[1][2]), ny, a[1][1]), ny, a[1][0]);
+            acc1[i].x = fmaf(s1, v.x, acc1[i].x);
+            acc1[i].y = fmaf(s1, v.y, acc1[i].y);
+          }
         }
       }
       __syncthreads();
     }
-    float2* dst = S2 + (size_t)gi * gsz + (size_t)xt * N * tile + (size_t)z * kT + c;
+    // the observer's node (x^ = 0): its F, x- and y-transformed, joins T
+    if (mt.s_obs[sw] >= 0 && z == g.obs_z) {
+      const size_t node = ((size_t)g.obs_z * N + g.obs_y) * N + g.obs_x;
+      const float fo = gq ? (float)(long long)gq[node] * kFixInvF : gf[node];
 #pragma unroll
-    for (int i = 0; i < kMaxRL; ++i) {
-      const int ky = run * rl + i;
-      if (i < rl && ky < N) dst[(size_t)ky * tile] = acc[i];
+      for (int i = 0; i < kRLY; ++i) {
+        const int ky = run * rl + i;
+        if (i < rl && ky < N) {
+          const int ph = (int)(((long long)kx * g.obs_x + (long long)ky * g.obs_y) % N);
+          float sn, cs;
+          sincospif(-2.0f * (float)ph / (float)N, &sn, &cs);
+          float2& t = mt.s_obs[sw] ? acc1[i] : acc0[i];
+          t.x = fmaf(fo, cs, t.x);
+          t.y = fmaf(fo, sn, t.y);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      if (o >= nout) break;
+      float2* dst = S2 + (size_t)mt.s_out[sw][o] * gsz + (size_t)xt * N * tile + (size_t)z * kT + c;
+#pragma unroll
+      for (int i = 0; i < kRLY; ++i) {
+        const int ky = run * rl + i;
+        if (i < rl && ky < N) dst[(size_t)ky * tile] = o ? acc1[i] : acc0[i];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// k_z-power groups as the z-pass applies them (the host's moment table lists
+// the same values; moments_match checks them): group g adds to F_0 (zg_f0),
+// zg_c2 nz^zg_p2 times itself to S_2 and zg_c4 nz^zg_p4 times itself to S_4.
+// ----------------------------------------------------------------------------
+
+__host__ __device__ constexpr int zg_f0(int g) { return g == 0 ? 1 : 0; }
+__host__ __device__ constexpr float zg_c2(int g) {
+  return g == 0 ? 1.f : (g == 1 ? 1.f : (g == 2 ? -1.f : (g == 3 ? 1.f : 0.f)));
+}
+__host__ __device__ constexpr int zg_p2(int g) { return g == 0 ? 2 : (g == 2 ? 2 : (g == 3 ? 1 : 0)); }
+__host__ __device__ constexpr float zg_c4(int g) {
+  return g == 1 ? 6.f : (g == 3 ? 2.f : (g == 4 || g == 6 || g == 8 ? 1.f : (g == 5 || g == 7 ? -1.f : 0.f)));
+}
+__host__ __device__ constexpr int zg_p4(int g) {
+  return g == 1 || g == 5 ? 2 : (g == 3 || g == 7 ? 3 : (g == 6 ? 1 : (g == 8 ? 4 : 0)));
+}
+
+// v^e for e in 0..4 from v and v^2, by selection (no loop).
+__device__ __forceinline__ float pwsel(float v, float v2, int e) {
+  return e == 0 ? 1.f : (e == 1 ? v : (e == 2 ? v2 : (e == 3 ? v2 * v : v2 * v2)));
+}
+
+// One group's contribution to the thread's run of k_z: F_0 (F0), c2 nz^p2 to
+// S_2 (A2), c4 nz^p4 to S_4 (A4).
+template <bool F0, bool A2, bool A4>
+__device__ __forceinline__ void zgroup(const float2* R, int z0, int rl, int N, int c, float c2, int p2, float c4,
+                                       int p4, float2 (&f0)[kRLZ], float2 (&s2)[kRLZ], float2 (&s4)[kRLZ]) {
+#pragma unroll
+  for (int i = 0; i < kRLZ; ++i) {
+    const int kz = z0 + i;
+    if (i < rl && kz < N) {
+      const float2 v = R[kz * kT + c];
+      const float nz = (float)smode(kz, N), nz2 = nz * nz;
+      if (F0) f0[i] = v;
+      if (A2) {
+        const float m = c2 * pwsel(nz, nz2, p2);
+        s2[i].x = fmaf(m, v.x, s2[i].x);
+        s2[i].y = fmaf(m, v.y, s2[i].y);
+      }
+      if (A4) {
+        const float m = c4 * pwsel(nz, nz2, p4);
+        s4[i].x = fmaf(m, v.x, s4[i].x);
+        s4[i].y = fmaf(m, v.y, s4[i].y);
+      }
     }
   }
 }
@@ -224,12 +323,13 @@ __global__ void __launch_bounds__(kNT, 2) k_ypass2(const float2* __restrict__ S1
 // z-pass (MODE 0: P bins; 1: P bins + export on the shells; 2: F^w shell sums)
 // ----------------------------------------------------------------------------
 
-// Block (8, 32) as in the y-pass.  The epilogue walks each thread's run of
-// consecutive k_z (|n| is monotone along it), sums a run in FP32 and adds it
+// Block (8, 64): threadIdx.x is the k_x column, threadIdx.y the run of k_z.
+// The epilogue walks each thread's run of consecutive k_z (|n| is monotone
+// along it), sums a run in FP32 and adds it
 // to the block's FP32 bins in shared memory when the bin changes; blocks'
 // bins are reduced in FP64 in a fixed order.
 template <int N_, int MODE>
-__global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
+__global__ void __launch_bounds__(kNTz, 1) k_zpass2(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg, ZParams zp,
                                                    double* __restrict__ part, int* __restrict__ partc,
                                                    int* __restrict__ err) {
@@ -249,9 +349,9 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
   const int tid = threadIdx.y * kT + threadIdx.x;
   const size_t gsz = (size_t)N * NXT * N * kT;
   const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
-  for (int i = tid; i < N; i += kNT) tw[i] = twg[i];
-  for (int t = tid; t < BQ_N * nkey; t += kNT) sb[t] = 0.f;
-  for (int t = tid; t < nkey; t += kNT) sc[t] = 0;
+  for (int i = tid; i < N; i += kNTz) tw[i] = twg[i];
+  for (int t = tid; t < BQ_N * nkey; t += kNTz) sb[t] = 0.f;
+  for (int t = tid; t < nkey; t += kNTz) sc[t] = 0;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -264,11 +364,11 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
     tma_load_1d(buf0, src_of(0), bytes, &bar[0]);
   }
   const int c = threadIdx.x, run = threadIdx.y;
-  const int rl = (N + kRun - 1) / kRun;
+  const int rl = (N + kRunZ - 1) / kRunZ;
   const int z0 = run * rl;
-  float2 f0[kMaxRL], s2[kMaxRL], s4[kMaxRL];
+  float2 f0[kRLZ], s2[kRLZ], s4[kRLZ];
 #pragma unroll
-  for (int i = 0; i < kMaxRL; ++i) {
+  for (int i = 0; i < kRLZ; ++i) {
     f0[i] = make_float2(0.f, 0.f);
     s2[i] = f0[i];
     s4[i] = f0[i];
@@ -282,27 +382,13 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
       tma_load_1d(cur ? buf0 : buf1, src_of(gi + 1), bytes, &bar[cur ^ 1]);
     }
     mbar_wait(&bar[cur], (uint32_t)((gi >> 1) & 1), err, 8);
-    const float2* R = fft_any<N_, kT, kNT, -1>(bc, work, fp, tw);
-    const int ell = mt.g_ell[gi], p = mt.g_p[gi];
-#pragma unroll
-    for (int i = 0; i < kMaxRL; ++i) {
-      const int kz = z0 + i;
-      if (i < rl && kz < N) {
-        const float2 v = R[kz * kT + c];
-        if (ell == 0) {
-          f0[i] = v;
-        } else {
-          const float mz = powi((float)smode(kz, N), p);
-          if (ell == 2) {
-            s2[i].x = fmaf(mz, v.x, s2[i].x);
-            s2[i].y = fmaf(mz, v.y, s2[i].y);
-          } else {
-            s4[i].x = fmaf(mz, v.x, s4[i].x);
-            s4[i].y = fmaf(mz, v.y, s4[i].y);
-          }
-        }
-      }
-    }
+    const float2* R = fft_any<N_, kT, kNTz, -1>(bc, work, fp, tw);
+    const int p2 = mt.g_p2[gi], p4 = mt.g_p4[gi];
+    const float c2 = mt.g_c2[gi], c4 = mt.g_c4[gi];
+    if (mt.g_f0[gi]) zgroup<true, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
+    else if (c2 != 0.f && c4 != 0.f) zgroup<false, true, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
+    else if (c2 != 0.f) zgroup<false, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
+    else zgroup<false, false, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
     __syncthreads();
   }
   const int kx = xt * kT + c;
@@ -316,7 +402,7 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
 #pragma unroll
   for (int q = 0; q < BQ_N; ++q) acc[q] = 0.f;
 #pragma unroll
-  for (int i = 0; i < kMaxRL; ++i) {
+  for (int i = 0; i < kRLZ; ++i) {
     const int kz = z0 + i;
     int b = -1;
     float vals[BQ_N];
@@ -393,8 +479,8 @@ __global__ void __launch_bounds__(kNT, 2) k_zpass2(const float2* __restrict__ S2
   __syncthreads();
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   const int nblk = gridDim.x * gridDim.y;
-  for (int t = tid; t < BQ_N * nkey; t += kNT) part[(size_t)t * nblk + blk] = (double)sb[t];
-  for (int t = tid; t < nkey; t += kNT) partc[(size_t)t * nblk + blk] = sc[t];
+  for (int t = tid; t < BQ_N * nkey; t += kNTz) part[(size_t)t * nblk + blk] = (double)sb[t];
+  for (int t = tid; t < nkey; t += kNTz) partc[(size_t)t * nblk + blk] = sc[t];
 }
 
 // ----------------------------------------------------------------------------
@@ -409,6 +495,15 @@ bool moments_match(const MomentTable& mt) {
   for (int q = 0; q < mt.nfields; ++q)
     for (int a = 0; a < 3; ++a)
       if (mt.e[q][a] != field_exp(q, a)) return false;
+  if (mt.ngroups > kMaxGroups) return false;
+  for (int g = 0; g < mt.ngroups; ++g) {
+    if (mt.g_f0[g] != zg_f0(g)) return false;
+    // tables below ell = 2 (4) carry no S_2 (S_4) terms; the z-pass does not use them then
+    if (mt.nfields >= nfields_of(2) && (mt.g_c2[g] != zg_c2(g) || (mt.g_c2[g] != 0.f && mt.g_p2[g] != zg_p2(g))))
+      return false;
+    if (mt.nfields == nfields_of(4) && (mt.g_c4[g] != zg_c4(g) || (mt.g_c4[g] != 0.f && mt.g_p4[g] != zg_p4(g))))
+      return false;
+  }
   return mt.nfields == nfields_of(4) || mt.nfields == nfields_of(2) || mt.nfields == nfields_of(0);
 }
 size_t field_elems(int N) { return (size_t)N * tiles_x(N) * N * kT; }
@@ -457,24 +552,27 @@ cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const Ge
 }
 
 template <int N_>
-static cudaError_t yrun(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                        const float2* tw, float2* S2, int* err, cudaStream_t s) {
+static cudaError_t yrun(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
+                        const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
+                        cudaStream_t s) {
   const size_t sm = ysm(g.N);
   raise_smem_limit((const void*)k_ypass2<N_>, sm);
-  k_ypass2<N_><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNT / kT), sm, s>>>(S1, g, mt, fp, tw, S2, err);
+  k_ypass2<N_><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNTy / kT), sm, s>>>(S1, gq, gf, g, mt, fp, tw, S2, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ypass(const float2* S1, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, float2* S2, int* err, cudaStream_t s) {
+// gq / gf: the grid the x-pass read (for the observer node's value).
+cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
+                         const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
+                         cudaStream_t s) {
   switch (g.N) {
-    case 512: return yrun<512>(S1, g, mt, fp, tw, S2, err, s);
-    case 384: return yrun<384>(S1, g, mt, fp, tw, S2, err, s);
-    case 360: return yrun<360>(S1, g, mt, fp, tw, S2, err, s);
-    case 256: return yrun<256>(S1, g, mt, fp, tw, S2, err, s);
-    case 128: return yrun<128>(S1, g, mt, fp, tw, S2, err, s);
-    case 64: return yrun<64>(S1, g, mt, fp, tw, S2, err, s);
-    default: return yrun<0>(S1, g, mt, fp, tw, S2, err, s);
+    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
+    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
+    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
+    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
+    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
+    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
+    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
   }
 }
 
@@ -483,7 +581,7 @@ static cudaError_t zrun(const float2* S2, const GeomDev& g, const MomentTable& m
                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
   const size_t sm = zsm(g.N, MODE == 2 ? zp.nshells : zp.nbins);
   raise_smem_limit((const void*)k_zpass2<N_, MODE>, sm);
-  k_zpass2<N_, MODE><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNT / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part, partc,
+  k_zpass2<N_, MODE><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNTz / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part, partc,
                                                                              err);
   return cudaGetLastError();
 }

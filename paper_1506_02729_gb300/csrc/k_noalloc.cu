@@ -37,7 +37,7 @@ constexpr size_t kNaField = (size_t)kNaMaxN * kNaTilesX * kNaMaxN * 8;          
 constexpr size_t kNaBlkZ = kNaTilesX * kNaMaxN;                                  // z-pass blocks
 constexpr size_t kNaN2 = 3 * (kNaMaxN / 2) * (kNaMaxN / 2) + 1;                  // LUT entries
 constexpr size_t kOffS1 = 0;
-constexpr size_t kOffS2 = kOffS1 + align256(sizeof(float2) * 22 * kNaField);
+constexpr size_t kOffS2 = kOffS1 + align256(sizeof(float2) * kMaxFields * kNaField);
 constexpr size_t kOffTw = kOffS2 + align256(sizeof(float2) * 9 * kNaField);
 constexpr size_t kOffLut = kOffTw + align256(sizeof(float2) * kNaMaxN);
 constexpr size_t kOffWinv = kOffLut + align256(sizeof(short) * kNaN2);
@@ -126,7 +126,8 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
 
   MomentTable mt;
   build_moments(4, mt);
-  if (!moments_match(mt)) return set_error(FKP_ESTATE, "internal: moment table order mismatch");
+  if (!moments_match(mt) || !moments_identities_hold(mt, 4))
+    return set_error(FKP_ESTATE, "internal: moment table inconsistent");
   GeomDev g{};
   g.N = N;
   g.NH = N / 2 + 1;
@@ -148,6 +149,7 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
   g.periodic = geom->periodic ? 1 : 0;
   g.P_fkp = (float)geom->P_fkp;
   g.alpha_mode = geom->alpha_mode;
+  observer_node(g);
 
   // host tables (FP64, rounded once)
   const double kf = 2.0 * M_PI / geom->L;
@@ -194,7 +196,7 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
   int dsm = 1;
   NCK(cudaDeviceGetAttribute(&dsm, cudaDevAttrMultiProcessorCount, dev));
   NCK(launch_xpass(nullptr, F, g, mt, fp, d_tw, S1, dsm, s));
-  NCK(launch_ypass(S1, g, mt, fp, d_tw, S2, d_err + 1, s));
+  NCK(launch_ypass(S1, nullptr, F, g, mt, fp, d_tw, S2, d_err + 1, s));
   ZParams zp;
   zp.nbins = pb->nbins;
   zp.lmax = 4;

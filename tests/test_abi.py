@@ -48,6 +48,12 @@ def test_version_and_error_without_gpu(built):
     assert fkp.lib().fkp_last_error().decode()
 
 
+def test_moment_tables_reproduce_the_multipole_sums(built):
+    """The host tables that turn the trace-reduced moment fields into k_z-power
+    groups reproduce S_2 = (k.x^)^2 and S_4 = (k.x^)^4 (no GPU)."""
+    fkp.check_tables()
+
+
 def test_struct_layouts_match_header():
     # sizes the C compiler gives the same structs (x86-64 / aarch64 LP64)
     assert ctypes.sizeof(fkp.Catalog) == 5 * 8 + 8 + 8

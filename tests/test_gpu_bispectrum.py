@@ -46,7 +46,7 @@ def small_b():
     return sv, gal, ran, geom, bs, ref, kf
 
 
-@pytest.mark.parametrize("contraction", [0, 1, 2], ids=["fp32", "bf16x3_tcgen05", "bf16x6_tcgen05"])
+@pytest.mark.parametrize("contraction", [0, 2], ids=["fp32", "bf16x6_tcgen05"])
 def test_small_bispectrum_matches_oracle(small_b, contraction):
     fkp = _fkp()
     sv, gal, ran, geom, bs, ref, kf = small_b
@@ -65,20 +65,50 @@ def test_small_bispectrum_matches_oracle(small_b, contraction):
     assert abs(b["I33"] / ref["I33"] - 1) < 1e-6
 
 
-def test_split_contractions_match_fp32_contraction(small_b):
-    """The tensor-core contractions (BF16 hi/lo, 3 products; hi/mid/lo, 6
-    products) against the FP32 CUDA-core contraction on the same device shell
-    fields: this isolates the split's own error from the FFTs'.  Same
-    denominators and triangle set (N_T >= 100) as the oracle comparison."""
+def test_3way_split_matches_fp32_contraction(small_b):
+    """The 3-way split (6 products) on the tensor cores against the FP32
+    CUDA-core contraction on the same device shell fields: this isolates the
+    contraction's error from the FFTs'.  Same denominators and triangle set
+    (N_T >= 100) as the oracle comparison."""
     fkp = _fkp()
     sv, gal, ran, geom, bs, ref, kf = small_b
     plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
     dg, dr = to_device(gal), to_device(ran)
     b32 = plan.bispectrum(dg, dr, contraction=0)[1]
-    for c in (1, 2):
-        b = plan.bispectrum(dg, dr, contraction=c)[1]
-        err = b_errors(b, b32, float(b32["I33"]), float(sv.N) ** 3)
-        assert max(err.values()) < B_TOL, (c, err)
+    b6 = plan.bispectrum(dg, dr, contraction=2)[1]
+    err = b_errors(b6, b32, float(b32["I33"]), float(sv.N) ** 3)
+    assert max(err.values()) < B_TOL, err
+
+
+def test_hi_lo_split_follows_its_error_model(small_b):
+    """The 2-way split (3 products) drops lo*lo and the rounding of lo, each
+    ~2^-18 of a product, with random sign: over the N^3 points the error of a
+    triangle sum random-walks to ~2^-17 sqrt(sum_x t^2), t = F_a^(l) F_b^(0)
+    F_c^(0) (measured spread: median 0.4-0.7, max 3.6 of those units with
+    256-point tensor-memory runs).  The FP32 rounding of the tensor-memory
+    accumulation over 1,024-point runs (192 accumulating MMAs per run for the
+    2-way split, 384 for the 3-way one) adds to the difference of the two
+    splits (max 6.3 units on this case).  Against the 3-way split on the same
+    fields, every triangle sum (N_T >= 100, l = 0, 2, 4) stays within 8 units;
+    the shell fields for sum_x t^2 come from the oracle."""
+    fkp = _fkp()
+    sv, gal, ran, geom, bs, ref, kf = small_b
+    plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
+    dg, dr = to_device(gal), to_device(ran)
+    b3 = plan.bispectrum(dg, dr, contraction=1)[1]
+    b6 = plan.bispectrum(dg, dr, contraction=2)[1]
+    F = op.fkp_grids(gal, ran, geom)[0]
+    Fl = op.legendre(F, geom, lmax=4)
+    sidx, _ = ob.shell_index(sv.N, bs)
+    I = {(l, s): ob.shell_field(Fl[l], sidx, s, sv.N) for l in (0, 2, 4) for s in range(bs[3])}
+    worst = 0.0
+    for t, (a, b, c) in enumerate(ref["tri"]):
+        if ref["NT"][t] < 100:
+            continue
+        for l in (0, 2, 4):
+            q = math.sqrt(float(np.sum((I[(l, a)] * I[(0, b)] * I[(0, c)]) ** 2)))
+            worst = max(worst, abs(b3[f"T{l}"][t] - b6[f"T{l}"][t]) / (2.0 ** -17 * q))
+    assert worst < 8.0, worst
 
 
 def test_counts_match_oracle_convolution():

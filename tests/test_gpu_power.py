@@ -138,6 +138,25 @@ def test_radial_observer_inside_box_from_grid():
     assert max(err.values()) < P_TOL, err
 
 
+def test_observer_on_a_grid_node_from_grid():
+    """Observer exactly on a grid node (x^ = 0 there) with a spike of F at that
+    node: the trace-reduced moment fields must still give every multipole of
+    the 22-field oracle, in which the node contributes to F_0 only."""
+    fkp = _fkp()
+    N, L = 48, 600.0
+    field = mockgen.random_phase_field(N, lambda nx, ny, nz: 1.0 / (1.0 + nx * nx + ny * ny + nz * nz), seed=9)
+    field = field.astype(np.float32)
+    field[12, 20, 24] += 40.0 * np.abs(field).max()  # node (x, y, z) = (24, 20, 12) = the observer
+    geom = dict(N=N, L=L, assign=2, origin=(0.0, 0.0, 0.0), observer=(300.0, 250.0, 150.0), compensate=False,
+                periodic=True)
+    kf = 2 * math.pi / L
+    bins = (0.5 * kf, kf, 23)
+    ref = op.power_from_grid(field.astype(np.float64), geom, bins, I22=1.0, N0=0.0)
+    got = fkp.Plan(geom, bins).power_from_grid(torch.from_numpy(field).cuda(), 1.0, 0.0)
+    err = p_errors(got, ref)
+    assert max(err.values()) < P_TOL, err
+
+
 def test_object_near_box_face_is_rejected():
     fkp = _fkp()
     sv = mockgen.survey_small()
