@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving leg (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving leg (req/s)")
     ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--small-steps", type=int, default=200, help="timed 64^3 mocks per mode (0 skips that leg)")
     return ap.parse_args()
 
 
@@ -319,6 +320,8 @@ def run_gpu(args):
             "gpu_launches": 10 * args.steps,
             "roofline": roof,
             "clocks": ck}
+    if args.small_steps > 0:
+        line["small_grid"] = run_small(args, stream)
     if args.bisp_steps > 0:
         line["bispectrum"] = run_bisp(args, gal, ran, dg, dr, stream)
     if args.serve_requests > 0 and world == 1:
@@ -337,6 +340,37 @@ def run_gpu(args):
 
 
 BSHELLS = (3, 3, 3, 37)  # centres 3(s+1) k_f, width 3 k_f, to k = 0.2 h/Mpc
+
+
+def run_small(args, stream):
+    """The small survey (L = 1000 Mpc/h, 64^3 CIC, 2e4 galaxies + 2e5 randoms,
+    P_0,2,4 + P_4b in 32 bins): launch-bound, so it is where CUDA-graph replay
+    of the power path shows; mocks/s with the graph and with plain launches
+    (each call synchronizes and finishes the bins on the host)."""
+    import torch
+
+    import mockgen
+    import paper_1506_02729_gb300 as fkp
+    sv = mockgen.survey_small()
+    gal, ran = mockgen.catalog(sv, args.seed)
+    dg = {k: torch.from_numpy(v).cuda() for k, v in gal.items()}
+    dr = {k: torch.from_numpy(v).cuda() for k, v in ran.items()}
+    kf = 2 * np.pi / sv.L
+    plan = fkp.Plan(sv.geometry(), (0.5 * kf, kf, 32))
+    out = {"workload": "small survey: L=1000 Mpc/h, 64^3 CIC, 2e4 galaxies + 2e5 randoms, 32 bins", "unit": "mocks/s"}
+    for name, on in (("graph", True), ("plain", False)):
+        plan.set_graphs(on)
+        for _ in range(3):
+            plan.power(dg, dr, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.small_steps):
+            p = plan.power(dg, dr, stream=stream)
+        dt = time.perf_counter() - t0
+        assert p["graph"] == (1 if on else 0)
+        out[name] = {"value": args.small_steps / dt, "ms_per_step": 1000.0 * dt / args.small_steps}
+    plan.close()
+    return out
 
 
 def run_bisp(args, gal, ran, dg, dr, stream):

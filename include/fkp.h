@@ -107,6 +107,7 @@ typedef struct {
   double Lab[6];        /* eq. Lab at k = 0, order xx yy zz xy yz zx */
   int64_t n_gal, n_ran;
   float timing_ms[8];   /* scalars, assign, xpass, ypass, zpass, bisp ifft, contraction, total */
+  int graph;            /* 1 when the call replayed the plan's CUDA graph (see fkp_plan_set_graphs) */
 } fkp_power_out;
 
 /* Bispectrum results, ntri entries each (caller-allocated host arrays, any
@@ -148,6 +149,15 @@ void fkp_plan_destroy(void *plan);
 /* Sizes the caller needs for its outputs and the plan's device footprint
  * (workspace plus the catalog buffers it keeps between calls). */
 int fkp_plan_sizes(const void *plan, int *nbins, int *ntriangles, size_t *workspace_bytes);
+
+/* CUDA graphs of the power path (default on).  With device catalogs, the
+ * second fkp_power call on a plan with the same catalog pointers and sizes
+ * captures the gridding, FFT passes and binning into a graph; later calls
+ * with those catalogs replay it (one launch instead of about twenty).  A
+ * different catalog runs the plain launches; host catalogs never use the
+ * graph.  enable = 0 frees the graph and keeps plain launches.  Results
+ * are the same either way. */
+int fkp_plan_set_graphs(void *plan, int enable);
 
 /* P_l of one survey (Sec. III.A).  Enqueues every step on cuda_stream (a
  * cudaStream_t, NULL = legacy default stream), then synchronizes it and

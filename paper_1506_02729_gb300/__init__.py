@@ -25,7 +25,8 @@ ERRORS = {-1: "FKP_EINVAL", -2: "FKP_EGEOM", -3: "FKP_ENOMEM", -4: "FKP_ETIMEOUT
 EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_plan_destroy", "fkp_plan_sizes",
            "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version",
            "fkp_power_from_grid_noalloc", "fkp_server_create", "fkp_server_submit", "fkp_server_poll",
-           "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy", "fkp_check_tables"]
+           "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy", "fkp_check_tables",
+           "fkp_plan_set_graphs"]
 
 
 class FKPError(RuntimeError):
@@ -61,7 +62,7 @@ class PowerOut(C.Structure):
                 ("nmodes", C.POINTER(C.c_int64)), ("alpha", C.c_double), ("I22", C.c_double), ("I33", C.c_double),
                 ("N0", C.c_double), ("N0_fkp", C.c_double), ("S3", C.c_double), ("W_g", C.c_double),
                 ("W_r", C.c_double), ("Lab", C.c_double * 6), ("n_gal", C.c_int64), ("n_ran", C.c_int64),
-                ("timing_ms", C.c_float * 8)]
+                ("timing_ms", C.c_float * 8), ("graph", C.c_int)]
 
 
 class BispOut(C.Structure):
@@ -117,6 +118,7 @@ def lib():
         L.fkp_server_destroy.restype = None
         L.fkp_last_error.restype = C.c_char_p
         L.fkp_check_tables.argtypes = []
+        L.fkp_plan_set_graphs.argtypes = [vp, C.c_int]
         L.fkp_version.restype = C.c_char_p
         _lib = L
     return _lib
@@ -245,7 +247,12 @@ class Plan:
             arr[k] = getattr(o, k)
         arr["Lab"] = np.array(list(o.Lab))
         arr["timing_ms"] = np.array(list(o.timing_ms))
+        arr["graph"] = int(o.graph)
         return arr
+
+    def set_graphs(self, enable):
+        """CUDA-graph replay of the device-catalog power path (default on)."""
+        _check(lib().fkp_plan_set_graphs(self._h, 1 if enable else 0))
 
     def power(self, gal, ran, stream=None):
         """P_0, P_2, P_4, P_4b and the scalars for one survey."""

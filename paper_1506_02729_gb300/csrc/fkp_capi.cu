@@ -274,6 +274,8 @@ void* fkp::Plan::alloc(size_t bytes) {
 }
 
 fkp::Plan::~Plan() {
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
   bisp_plan_free(this);
   for (void* p : buffers) cudaFree(p);
   for (void* p : staging) cudaFree(p);
@@ -498,6 +500,17 @@ int fkp::stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, c
 // P_l
 // ----------------------------------------------------------------------------
 
+// Records a stage event on s.  Inside a stream capture it is recorded as an
+// external event, so that the graph keeps it as a timed event node (a plain
+// record only orders the captured work).
+static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(s, &st);
+  if (e != cudaSuccess) return e;
+  return st == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, s);
+}
+
 // Enqueues scalars and gridding of both catalogs into d_grid (and d_gridw):
 // tile counts with the scalar sums, offsets, scatter into tile order, and
 // shared-memory accumulation per tile.
@@ -507,6 +520,9 @@ int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream
   const long long ntot = gal.n + ran.n;
   if (ntot >= (1ll << 31)) return set_error(FKP_EINVAL, "at most 2^31-1 objects per call");
   if ((size_t)ntot > P->sort_cap) {
+    // a captured graph refers to the old buffers
+    if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+    P->graph_exec = nullptr;
     if (P->d_xyzv) cudaFree(P->d_xyzv);
     if (P->d_vw2) cudaFree(P->d_vw2);
     P->d_xyzv = nullptr;
@@ -526,12 +542,12 @@ int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream
   const int nbg = nblocks(gal.n), nbr = nblocks(ran.n);
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
   CK(cudaMemsetAsync(P->d_tcnt, 0, sizeof(int) * P->ntiles, s));
-  CK(cudaEventRecord(P->ev[0], s));
+  CK(record_stage(P->ev[0], s));
   CK(launch_bin_count(gal, 0, P->g, P->d_scpart, P->d_tcnt, P->d_err, nbg, s));
   CK(launch_bin_count(ran, 1, P->g, P->d_scpart + (size_t)nbg * SC_NSUM, P->d_tcnt, P->d_err, nbr, s));
   CK(launch_scalars_finalize(P->d_scpart, nbg, nbr, gal.n, ran.n, P->g.alpha_mode, P->d_ds, s));
   CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, s));
-  CK(cudaEventRecord(P->ev[1], s));
+  CK(record_stage(P->ev[1], s));
   CK(cudaMemsetAsync(P->d_grid, 0, N3 * 8, s));
   if (P->d_gridw) CK(cudaMemsetAsync(P->d_gridw, 0, N3 * 8, s));
   const double* obs = P->geom.observer;
@@ -540,16 +556,16 @@ int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream
   CK(launch_bin_scatter(ran, 1, P->g, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s));
   CK(launch_lab_finalize(P->d_labpart, ran.n > 0 ? nbr : 0, P->d_ds + DS_COUNT, s));
   CK(launch_tile_accum(P->g, P->d_toff, P->d_xyzv, vw2, P->d_grid, P->d_gridw, s));
-  CK(cudaEventRecord(P->ev[2], s));
+  CK(record_stage(P->ev[2], s));
   return FKP_OK;
 }
 
 // Enqueues the three FFT passes, recombination and binning of one base grid.
 int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s) {
   CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
-  CK(cudaEventRecord(P->ev[3], s));
+  CK(record_stage(P->ev[3], s));
   CK(launch_ypass(P->d_S1, gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
-  CK(cudaEventRecord(P->ev[4], s));
+  CK(record_stage(P->ev[4], s));
   ZParams zp;
   zp.nbins = P->pb.nbins;
   zp.lmax = P->lmax;
@@ -564,7 +580,7 @@ int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf,
   zp.mm = 0;
   CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s));
   CK(launch_reduce_bins(P->d_zpart, P->d_zpartc, P->nblk_z, P->pb.nbins, P->d_bins, P->d_binc, s));
-  CK(cudaEventRecord(P->ev[5], s));
+  CK(record_stage(P->ev[5], s));
   return FKP_OK;
 }
 
@@ -620,6 +636,7 @@ int fkp::finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_sca
   }
   float t = 0.f;
   for (int i = 0; i < 8; ++i) out->timing_ms[i] = 0.f;
+  out->graph = 0;
   if (cudaEventElapsedTime(&t, P->ev[0], P->ev[1]) == cudaSuccess) out->timing_ms[0] = t;
   if (cudaEventElapsedTime(&t, P->ev[1], P->ev[2]) == cudaSuccess) out->timing_ms[1] = t;
   if (cudaEventElapsedTime(&t, P->ev[2], P->ev[3]) == cudaSuccess) out->timing_ms[2] = t;
@@ -627,6 +644,75 @@ int fkp::finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_sca
   if (cudaEventElapsedTime(&t, P->ev[4], P->ev[5]) == cudaSuccess) out->timing_ms[4] = t;
   if (cudaEventElapsedTime(&t, P->ev[0], P->ev[5]) == cudaSuccess) out->timing_ms[7] = t;
   cudaGetLastError();  // events not recorded on this path leave a benign error
+  return FKP_OK;
+}
+
+static bool same_cat(const CatDev& a, const CatDev& b) { return std::memcmp(&a, &b, sizeof(CatDev)) == 0; }
+
+// Captures gridding + FFT passes + binning of these catalogs into the plan's
+// graph, on the plan's own stream (the legacy default stream cannot capture).
+static int capture_power(Plan* P, const CatDev& g, const CatDev& r) {
+  if (!P->cap_stream) CK(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+  P->graph_exec = nullptr;
+  CK(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_grids(P, g, r, P->cap_stream);
+  if (!rc) rc = enqueue_fft_bin(P, P->d_grid, nullptr, P->cap_stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(P->cap_stream, &graph);
+  if (rc || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc ? rc : set_error(FKP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&P->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    P->graph_exec = nullptr;
+    return set_error(FKP_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+  }
+  P->graph_key[0] = g;
+  P->graph_key[1] = r;
+  return FKP_OK;
+}
+
+// Enqueues the device part of one power call: the plan's graph when the
+// catalogs are those it was captured with; a new capture on the second
+// identical call in a row; plain launches otherwise.  *replayed tells which.
+static int enqueue_power(Plan* P, const CatDev& g, const CatDev& r, bool device_cats, cudaStream_t s,
+                         int* replayed) {
+  *replayed = 0;
+  if (P->graphs && device_cats) {
+    const bool cached = P->graph_exec && same_cat(g, P->graph_key[0]) && same_cat(r, P->graph_key[1]);
+    if (!cached && P->last_valid && same_cat(g, P->last_key[0]) && same_cat(r, P->last_key[1])) {
+      if (capture_power(P, g, r) != FKP_OK) {
+        cudaGetLastError();
+        P->graphs = false;  // plain launches from now on
+      }
+    }
+    if (P->graphs && P->graph_exec && same_cat(g, P->graph_key[0]) && same_cat(r, P->graph_key[1])) {
+      CK(cudaGraphLaunch(P->graph_exec, s));
+      ++P->graph_launches;
+      *replayed = 1;
+      return FKP_OK;
+    }
+    P->last_key[0] = g;
+    P->last_key[1] = r;
+    P->last_valid = true;
+  }
+  int rc = enqueue_grids(P, g, r, s);
+  if (rc) return rc;
+  return enqueue_fft_bin(P, P->d_grid, nullptr, s);
+}
+
+extern "C" int fkp_plan_set_graphs(void* plan, int enable) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P) return set_error(FKP_EINVAL, "NULL plan");
+  P->graphs = enable != 0;
+  if (!P->graphs && P->graph_exec) {
+    cudaGraphExecDestroy(P->graph_exec);
+    P->graph_exec = nullptr;
+  }
+  P->last_valid = false;
   return FKP_OK;
 }
 
@@ -642,11 +728,13 @@ extern "C" int fkp_power(void* plan, const fkp_catalog_t* gal, const fkp_catalog
   rc = stage_catalog(P, ran, 1, r, s);
   if (rc) return rc;
   if (r.n == 0) return set_error(FKP_EINVAL, "the random catalog is empty");
-  rc = enqueue_grids(P, g, r, s);
+  const bool device_cats = (gal->on_device || gal->n == 0) && (ran->on_device || ran->n == 0);
+  int replayed = 0;
+  rc = enqueue_power(P, g, r, device_cats, s, &replayed);
   if (rc) return rc;
-  rc = enqueue_fft_bin(P, P->d_grid, nullptr, s);
-  if (rc) return rc;
-  return finish_power(P, s, out, true, 0, 0);
+  rc = finish_power(P, s, out, true, 0, 0);
+  if (out) out->graph = replayed;
+  return rc;
 }
 
 extern "C" int fkp_power_from_grid(void* plan, const float* F, double I22, double N0, void* stream,

@@ -57,6 +57,16 @@ struct Plan {
   void* h_pinned = nullptr;
   cudaEvent_t ev[12] = {};
 
+  // CUDA graph of the device-catalog power path (gridding, FFT passes,
+  // binning), keyed by the catalogs it was captured with
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  CatDev graph_key[2] = {};
+  CatDev last_key[2] = {};
+  bool last_valid = false;
+  int graph_launches = 0;
+
   std::vector<void*> buffers;
   size_t bytes_total = 0;
   void* alloc(size_t bytes);

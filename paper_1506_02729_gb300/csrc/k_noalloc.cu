@@ -228,6 +228,7 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
   out->W_g = out->W_r = 0; out->n_gal = out->n_ran = 0;
   for (int a = 0; a < 6; ++a) out->Lab[a] = 0;
   for (int i = 0; i < 8; ++i) out->timing_ms[i] = 0.f;
+  out->graph = 0;
   for (int b = 0; b < nb; ++b) {
     const double n = (double)hc[b];
     const double s00 = hb[BQ_F00 * nb + b], s20 = hb[BQ_F20 * nb + b], s40 = hb[BQ_F40 * nb + b],

@@ -54,8 +54,20 @@ def test_moment_tables_reproduce_the_multipole_sums(built):
     fkp.check_tables()
 
 
-def test_struct_layouts_match_header():
-    # sizes the C compiler gives the same structs (x86-64 / aarch64 LP64)
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structs have the sizes the C compiler gives the
+    header's structs on this machine."""
     assert ctypes.sizeof(fkp.Catalog) == 5 * 8 + 8 + 8
     assert ctypes.sizeof(fkp.PBins) == 24
     assert ctypes.sizeof(fkp.BShells) == 16
+    names = {"fkp_catalog_t": fkp.Catalog, "fkp_geometry_t": fkp.Geometry, "fkp_pbins_t": fkp.PBins,
+             "fkp_bshells_t": fkp.BShells, "fkp_power_out": fkp.PowerOut, "fkp_bisp_out": fkp.BispOut,
+             "fkp_request_t": fkp.Request, "fkp_server_stats_t": fkp.ServerStats}
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "fkp.h"\nint main(void) {\n' +
+                   "".join(f'  printf("%zu\\n", sizeof({n}));\n' for n in names) + "  return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    sizes = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    for (n, cls), size in zip(names.items(), sizes):
+        assert ctypes.sizeof(cls) == size, n

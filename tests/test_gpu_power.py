@@ -99,6 +99,33 @@ def test_repeat_runs_agree(small_mock):
         assert np.allclose(a[k], b[k], rtol=1e-6, atol=1e-6 * np.nanmax(np.abs(a["P0"])), equal_nan=True), k
 
 
+def test_graph_replay_equals_plain_launches(small_mock):
+    """The second call with the same device catalogs captures a CUDA graph and
+    later calls replay it; another catalog runs plain launches and the graph
+    still serves the first one.  Replayed results equal plain ones (to the
+    FP32 order of the per-block bin sums)."""
+    fkp = _fkp()
+    sv, gal, ran = small_mock
+    plan = fkp.Plan(sv.geometry(), _bins_small(sv.L))
+    g, r = to_device(gal), to_device(ran)
+    half = {k: v[: v.shape[0] // 2] for k, v in g.items()}
+    flags, res = [], []
+    for gg in (g, g, g, half, g):
+        out = plan.power(gg, r)
+        flags.append(out["graph"])
+        res.append(out)
+    assert flags == [0, 1, 1, 0, 1]
+    assert all(out["timing_ms"][7] > 0 for out in res)
+    plan.set_graphs(False)
+    plain = plan.power(g, r)
+    assert plain["graph"] == 0
+    for out in (res[1], res[2], res[4]):
+        for k in ("P0", "P2", "P4", "P4b"):
+            assert np.allclose(out[k], plain[k], rtol=1e-6, atol=1e-6 * np.nanmax(np.abs(plain["P0"])),
+                               equal_nan=True), k
+    assert not np.allclose(res[3]["P0"], plain["P0"], equal_nan=True)
+
+
 def test_periodic_kaiser_from_grid():
     """Plane-parallel field with |F_0|^2 = A(|n|)(1+f mu^2)^2 through
     fkp_power_from_grid against the oracle on the same float32 field."""
