@@ -207,9 +207,23 @@ __host__ __device__ constexpr int radix_at(int n, int s) {
   return 1;
 }
 
+// Shared-memory index of element i of pencil p among P interleaved pencils.
+// With SWZ (P a power of two) the pencil slot is XOR-swizzled by i >> 1:
+// one pencil read or written at consecutive i, and all pencils at one i,
+// then both fall in distinct banks (per half-warp).
+template <int P, bool SWZ>
+__device__ __forceinline__ int ilv(int i, int p) {
+  if constexpr (SWZ) {
+    static_assert((P & (P - 1)) == 0, "swizzled interleave needs a power-of-two pencil count");
+    return i * P + (p ^ ((i >> 1) & (P - 1)));
+  } else {
+    return i * P + p;
+  }
+}
+
 // The block is 2-D: threadIdx.x = pencil (blockDim.x == P), threadIdx.y
 // strides over the N/R butterflies of a stage (blockDim.y == NT / P).
-template <int N, int P, int NT, int DIR, int R, int NS>
+template <int N, int P, int NT, int DIR, int R, int NS, bool SWZ>
 __device__ __forceinline__ void fft_ct_stage(const float2* __restrict__ src, float2* __restrict__ dst,
                                              const float2* __restrict__ tw) {
   constexpr int NB = N / R;
@@ -223,7 +237,7 @@ __device__ __forceinline__ void fft_ct_stage(const float2* __restrict__ src, flo
       const int k = j % NS;
       float2 v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = src[(j + r * NB) * P + p];
+      for (int r = 0; r < R; ++r) v[r] = src[ilv<P, SWZ>(j + r * NB, p)];
       if (NS > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -235,34 +249,34 @@ __device__ __forceinline__ void fft_ct_stage(const float2* __restrict__ src, flo
       dftR<R, DIR>(v);
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[(base + r * NS) * P + p] = v[r];
+      for (int r = 0; r < R; ++r) dst[ilv<P, SWZ>(base + r * NS, p)] = v[r];
     }
   }
 }
 
-template <int N, int P, int NT, int DIR, int S, int NS>
+template <int N, int P, int NT, int DIR, int S, int NS, bool SWZ>
 __device__ __forceinline__ float2* fft_ct_run(float2* a, float2* b, const float2* tw) {
   if constexpr (S == radix_count(N)) {
     return a;
   } else {
     constexpr int R = radix_at(N, S);
-    fft_ct_stage<N, P, NT, DIR, R, NS>(a, b, tw);
+    fft_ct_stage<N, P, NT, DIR, R, NS, SWZ>(a, b, tw);
     __syncthreads();
-    return fft_ct_run<N, P, NT, DIR, S + 1, NS * R>(b, a, tw);
+    return fft_ct_run<N, P, NT, DIR, S + 1, NS * R, SWZ>(b, a, tw);
   }
 }
 
 // Transforms P interleaved pencils held in a (b is scratch of the same size).
 // Returns the buffer holding the result.  All NT threads of the (P, NT/P)
 // block call it; it ends with a __syncthreads().
-template <int N, int P, int NT, int DIR>
+template <int N, int P, int NT, int DIR, bool SWZ = false>
 __device__ __forceinline__ float2* fft_ct(float2* a, float2* b, const float2* tw) {
-  return fft_ct_run<N, P, NT, DIR, 0, 1>(a, b, tw);
+  return fft_ct_run<N, P, NT, DIR, 0, 1, SWZ>(a, b, tw);
 }
 
 // Runtime-N version on the same interleaved layout (sizes without a
 // compiled specialisation).
-template <int R, int DIR>
+template <int R, int DIR, bool SWZ>
 __device__ __forceinline__ void fft_rt_stage(const float2* __restrict__ src, float2* __restrict__ dst, int n, int P,
                                              int ns, const float2* __restrict__ tw) {
   const int nb = n / R;
@@ -275,7 +289,7 @@ __device__ __forceinline__ void fft_rt_stage(const float2* __restrict__ src, flo
     const int k = j % ns;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * P + p];
+    for (int r = 0; r < R; ++r) v[r] = src[SWZ ? (j + r * nb) * P + (p ^ (((j + r * nb) >> 1) & (P - 1))) : (j + r * nb) * P + p];
     if (ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -287,21 +301,24 @@ __device__ __forceinline__ void fft_rt_stage(const float2* __restrict__ src, flo
     dftR<R, DIR>(v);
     const int base = (j / ns) * ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[(base + r * ns) * P + p] = v[r];
+    for (int r = 0; r < R; ++r) {
+      const int i = base + r * ns;
+      dst[SWZ ? i * P + (p ^ ((i >> 1) & (P - 1))) : i * P + p] = v[r];
+    }
   }
 }
 
-template <int DIR>
+template <int DIR, bool SWZ = false>
 __device__ float2* fft_rt(float2* a, float2* b, int P, const FftPlan& fp, const float2* tw) {
   int ns = 1;
   for (int s = 0; s < fp.nst; ++s) {
     const int R = fp.radix[s];
     switch (R) {
-      case 8: fft_rt_stage<8, DIR>(a, b, fp.n, P, ns, tw); break;
-      case 4: fft_rt_stage<4, DIR>(a, b, fp.n, P, ns, tw); break;
-      case 2: fft_rt_stage<2, DIR>(a, b, fp.n, P, ns, tw); break;
-      case 5: fft_rt_stage<5, DIR>(a, b, fp.n, P, ns, tw); break;
-      default: fft_rt_stage<3, DIR>(a, b, fp.n, P, ns, tw); break;
+      case 8: fft_rt_stage<8, DIR, SWZ>(a, b, fp.n, P, ns, tw); break;
+      case 4: fft_rt_stage<4, DIR, SWZ>(a, b, fp.n, P, ns, tw); break;
+      case 2: fft_rt_stage<2, DIR, SWZ>(a, b, fp.n, P, ns, tw); break;
+      case 5: fft_rt_stage<5, DIR, SWZ>(a, b, fp.n, P, ns, tw); break;
+      default: fft_rt_stage<3, DIR, SWZ>(a, b, fp.n, P, ns, tw); break;
     }
     __syncthreads();
     float2* t = a;
@@ -312,11 +329,11 @@ __device__ float2* fft_rt(float2* a, float2* b, int P, const FftPlan& fp, const 
   return a;
 }
 
-// N = 0 selects the runtime version.
-template <int N, int P, int NT, int DIR>
+// N = 0 selects the runtime version.  SWZ: swizzled interleave (see ilv).
+template <int N, int P, int NT, int DIR, bool SWZ = false>
 __device__ __forceinline__ float2* fft_any(float2* a, float2* b, const FftPlan& fp, const float2* tw) {
-  if constexpr (N > 0) return fft_ct<N, P, NT, DIR>(a, b, tw);
-  else return fft_rt<DIR>(a, b, P, fp, tw);
+  if constexpr (N > 0) return fft_ct<N, P, NT, DIR, SWZ>(a, b, tw);
+  else return fft_rt<DIR, SWZ>(a, b, P, fp, tw);
 }
 
 // ----------------------------------------------------------------------------

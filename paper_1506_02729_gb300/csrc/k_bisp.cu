@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kSNT) k_shell_z(const float2* __restrict__ E, 
   if (kx0 + c < m1) {
 #pragma unroll
     for (int i = 0; i < kSRL; ++i) {
-      const int z = run * rl + i;
+      const int z = i * 32 + run;
       if (i < rl && z < N) T1[(((size_t)s * N + z) * w2 + kyp) * m1 + kx0 + c] = R[z * kSP + c];
     }
   }
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kSNT) k_shell_y(const float2* __restrict__ T1,
   if (kx0 + c < m1) {
 #pragma unroll
     for (int i = 0; i < kSRL; ++i) {
-      const int y = run * rl + i;
+      const int y = i * 32 + run;
       if (i < rl && y < N) T2[(((size_t)s * N + z) * N + y) * m1 + kx0 + c] = R[y * kSP + c];
     }
   }

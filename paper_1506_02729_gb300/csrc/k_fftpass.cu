@@ -65,16 +65,16 @@ __host__ __device__ constexpr int field_exp(int q, int a) {
 
 // Moment values of pencil pairs P.., packed two real fields per complex value;
 // template recursion keeps every exponent a compile-time constant.
-template <int NP, int NF, int P>
+template <int NP, int NF, int P, bool SWZ>
 __device__ __forceinline__ void build_pairs(float f, const float (&hx)[5], const float (&hy)[5], const float (&hz)[5],
-                                            float2* dst) {
+                                            float2* A, int x) {
   if constexpr (P < NP) {
     constexpr int a0 = field_exp(2 * P, 0), b0 = field_exp(2 * P, 1), c0 = field_exp(2 * P, 2);
     constexpr int a1 = field_exp(2 * P + 1, 0), b1 = field_exp(2 * P + 1, 1), c1 = field_exp(2 * P + 1, 2);
     const float m0 = f * hx[a0] * hy[b0] * hz[c0];
     const float m1 = (2 * P + 1 < NF) ? f * hx[a1] * hy[b1] * hz[c1] : 0.f;
-    dst[P] = make_float2(m0, m1);
-    build_pairs<NP, NF, P + 1>(f, hx, hy, hz, dst);
+    A[ilv<NP, SWZ>(x, P)] = make_float2(m0, m1);
+    build_pairs<NP, NF, P + 1, SWZ>(f, hx, hy, hz, A, x);
   }
 }
 
@@ -88,6 +88,10 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
   constexpr int NF = nfields_of(LMAX);
   constexpr int NP = (NF + 1) / 2;
   constexpr int NTX = 32 * NP;
+  // swizzled interleave when NP is a power of two: the moment stores (one
+  // pencil slot, consecutive x) and the unpack loads (consecutive k) are then
+  // free of bank conflicts
+  constexpr bool SWZ = NP > 1 && (NP & (NP - 1)) == 0;
   extern __shared__ float2 sm[];
   const int N = N_ ? N_ : g.N;
   const int NH = N / 2 + 1, NXT = (NH + kT - 1) / kT;
@@ -119,10 +123,10 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
       hx[2] = hx[1] * hx[1]; hx[3] = hx[2] * hx[1]; hx[4] = hx[2] * hx[2];
       hy[2] = hy[1] * hy[1]; hy[3] = hy[2] * hy[1]; hy[4] = hy[2] * hy[2];
       hz[2] = hz[1] * hz[1]; hz[3] = hz[2] * hz[1]; hz[4] = hz[2] * hz[2];
-      build_pairs<NP, NF, 0>(rowF[x], hx, hy, hz, A + x * NP);
+      build_pairs<NP, NF, 0, SWZ>(rowF[x], hx, hy, hz, A, x);
     }
     __syncthreads();
-    const float2* R = fft_any<N_, NP, NTX, -1>(A, B, fp, tw);
+    const float2* R = fft_any<N_, NP, NTX, -1, SWZ>(A, B, fp, tw);
     // unpack: consecutive threads take consecutive k_x of one field, so the
     // stores into the tile-major layout are 64-byte contiguous runs
     const int ncol = NXT * kT;
@@ -130,8 +134,8 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
       const int p = t / ncol, k = t - p * ncol;
       float2 o0 = make_float2(0.f, 0.f), o1 = o0;
       if (k < NH) {
-        const float2 zk = R[k * NP + p];
-        const float2 zm = R[(k == 0 ? 0 : N - k) * NP + p];
+        const float2 zk = R[ilv<NP, SWZ>(k, p)];
+        const float2 zm = R[ilv<NP, SWZ>(k == 0 ? 0 : N - k, p)];
         o0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         o1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
       }
@@ -147,8 +151,9 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
 // y-pass
 // ----------------------------------------------------------------------------
 
-// Block (8, 32): threadIdx.x is the k_x column of the tile (the FFT pencil),
-// threadIdx.y the run of k_y this thread accumulates.  The fields are read
+// Block (8, 32): threadIdx.x is the k_x column of the tile (the FFT pencil);
+// thread (c, r) accumulates k_y = r, r + 32, r + 64, ... (a warp's four r
+// read 32 consecutive values: no bank conflicts).  The fields are read
 // sweep by sweep; a sweep accumulates up to two output groups, each member
 // with a polynomial coefficient in n_y evaluated by Horner's rule.
 template <int N_>
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
         }
 #pragma unroll
       for (int i = 0; i < kRLY; ++i) {
-        const int ky = run * rl + i;
+        const int ky = i * kRunY + run;
         if (i < rl && ky < N) {
           const float ny = (float)smode(ky, N);
           const float2 v = R[ky * kT + c];
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
       const float fo = gq ? (float)(long long)gq[node] * kFixInvF : gf[node];
 #pragma unroll
       for (int i = 0; i < kRLY; ++i) {
-        const int ky = run * rl + i;
+        const int ky = i * kRunY + run;
         if (i < rl && ky < N) {
           const int ph = (int)(((long long)kx * g.obs_x + (long long)ky * g.obs_y) % N);
           float sn, cs;
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
       float2* dst = S2 + (size_t)mt.s_out[sw][o] * gsz + (size_t)xt * N * tile + (size_t)z * kT + c;
 #pragma unroll
       for (int i = 0; i < kRLY; ++i) {
-        const int ky = run * rl + i;
+        const int ky = i * kRunY + run;
         if (i < rl && ky < N) dst[(size_t)ky * tile] = o ? acc1[i] : acc0[i];
       }
     }
