@@ -319,6 +319,7 @@ def run_gpu(args):
             "e2e": {"value": world / e2e_s, "unit": "mocks/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 10 * args.steps,
             "roofline": roof,
+            "fft_schedule": plan.schedule(),
             "clocks": ck}
     if args.small_steps > 0:
         line["small_grid"] = run_small(args, stream)

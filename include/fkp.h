@@ -150,6 +150,18 @@ void fkp_plan_destroy(void *plan);
  * (workspace plus the catalog buffers it keeps between calls). */
 int fkp_plan_sizes(const void *plan, int *nbins, int *ntriangles, size_t *workspace_bytes);
 
+/* Launch schedule of the three FFT passes of a plan: x_mult (x-pass blocks
+ * per SM = resident blocks x x_mult: 1, 2 or 4), and the threads per block
+ * of the y- and z-passes (256 or 512).  The first plan of a given grid and
+ * multipole order in a context times every candidate on its own workspace
+ * (about 12 launches of each pass) and keeps the fastest of each; later
+ * plans of that kind reuse the choice.  tuned_ms (3 floats, may be NULL)
+ * receives the chosen passes' times.  fkp_plan_set_schedule overrides the
+ * choice for one plan (FKP_EINVAL outside those values).  Results do not
+ * depend on the schedule. */
+int fkp_plan_schedule(const void *plan, int *x_mult, int *y_threads, int *z_threads, float *tuned_ms);
+int fkp_plan_set_schedule(void *plan, int x_mult, int y_threads, int z_threads);
+
 /* CUDA graphs of the power path (default on).  With device catalogs, the
  * second fkp_power call on a plan with the same catalog pointers and sizes
  * captures the gridding, FFT passes and binning into a graph; later calls

@@ -26,7 +26,7 @@ EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_
            "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version",
            "fkp_power_from_grid_noalloc", "fkp_server_create", "fkp_server_submit", "fkp_server_poll",
            "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy", "fkp_check_tables",
-           "fkp_plan_set_graphs"]
+           "fkp_plan_set_graphs", "fkp_plan_schedule", "fkp_plan_set_schedule"]
 
 
 class FKPError(RuntimeError):
@@ -119,6 +119,9 @@ def lib():
         L.fkp_last_error.restype = C.c_char_p
         L.fkp_check_tables.argtypes = []
         L.fkp_plan_set_graphs.argtypes = [vp, C.c_int]
+        L.fkp_plan_schedule.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_float)]
+        L.fkp_plan_set_schedule.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.fkp_version.restype = C.c_char_p
         _lib = L
     return _lib
@@ -249,6 +252,17 @@ class Plan:
         arr["timing_ms"] = np.array(list(o.timing_ms))
         arr["graph"] = int(o.graph)
         return arr
+
+    def schedule(self):
+        """The FFT passes' launch schedule (tuned when the plan was made)."""
+        xm, yt, zt = C.c_int(), C.c_int(), C.c_int()
+        ms = (C.c_float * 3)()
+        _check(lib().fkp_plan_schedule(self._h, C.byref(xm), C.byref(yt), C.byref(zt), ms))
+        return {"x_mult": xm.value, "y_threads": yt.value, "z_threads": zt.value, "tuned_ms": list(ms)}
+
+    def set_schedule(self, x_mult, y_threads, z_threads):
+        """Overrides the tuned schedule for this plan."""
+        _check(lib().fkp_plan_set_schedule(self._h, int(x_mult), int(y_threads), int(z_threads)))
 
     def set_graphs(self, enable):
         """CUDA-graph replay of the device-catalog power path (default on)."""

@@ -285,6 +285,110 @@ fkp::Plan::~Plan() {
   for (auto& e : ev) if (e) cudaEventDestroy(e);
 }
 
+// Times the candidate launch schedules of the three FFT passes on the plan's
+// own workspace (zeroed: the passes' cost does not depend on the values) and
+// keeps the fastest of each; the choice is shared by later plans of the same
+// grid and multipole order in this context.  About 12 launches of each pass,
+// once per (N, lmax).
+static int tune_schedule(Plan* P) {
+  const std::pair<int, int> key{P->g.N, P->lmax};
+  std::lock_guard<std::mutex> lk(P->ctx->tune_mu);
+  auto it = P->ctx->schedules.find(key);
+  if (it != P->ctx->schedules.end()) {
+    P->sched = it->second;
+    return FKP_OK;
+  }
+  const int N = P->g.N;
+  const size_t N3 = (size_t)N * N * N, half = field_elems(N) * sizeof(float2);
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  int rc = FKP_OK;
+  auto fail = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == FKP_OK) rc = set_error(FKP_ECUDA, "schedule tuning (%s): %s", what, cudaGetErrorString(e));
+    return e != cudaSuccess;
+  };
+  if (!fail(cudaEventCreate(&e0), "event") && !fail(cudaEventCreate(&e1), "event")) {
+    fail(cudaMemsetAsync(P->d_grid, 0, N3 * 8, s), "memset");
+    fail(cudaMemsetAsync(P->d_S1, 0, half * P->mt.nfields, s), "memset");
+    fail(cudaMemsetAsync(P->d_S2, 0, half * P->mt.ngroups, s), "memset");
+    fail(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s), "memset");
+    ZParams zp{};
+    zp.nbins = P->pb.nbins;
+    zp.lmax = P->lmax;
+    zp.kf = (float)(2.0 * M_PI / P->geom.L);
+    zp.lut = P->d_lut;
+    zp.winv = P->d_winv;
+    zp.mode = 0;
+    // mean time of 3 launches after one warm-up launch
+    auto timed = [&](auto&& launch, const char* what) -> float {
+      if (rc || fail(launch(), what)) return 1e30f;
+      fail(cudaEventRecord(e0, s), "event");
+      for (int r = 0; r < 3; ++r) fail(launch(), what);
+      fail(cudaEventRecord(e1, s), "event");
+      float ms = 1e30f;
+      if (!fail(cudaEventSynchronize(e1), what)) fail(cudaEventElapsedTime(&ms, e0, e1), "event");
+      return ms / 3.f;
+    };
+    PassSchedule best;
+    float bx = 1e30f, by = 1e30f, bz = 1e30f;
+    for (int xm : {1, 2, 4}) {
+      const float t = timed([&] { return launch_xpass(P->d_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1,
+                                                      P->ctx->nsm, s, xm); }, "x-pass");
+      if (t < bx) { bx = t; best.x_mult = xm; }
+    }
+    for (int nt : {256, 512}) {
+      const float t = timed([&] { return launch_ypass(P->d_S1, P->d_grid, nullptr, P->g, P->mt, P->fp, P->d_tw,
+                                                      P->d_S2, P->d_err + 1, s, nt); }, "y-pass");
+      if (t < by) { by = t; best.y_threads = nt; }
+    }
+    for (int nt : {256, 512}) {
+      const float t = timed([&] { return launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart,
+                                                      P->d_zpartc, P->d_err + 1, s, nt); }, "z-pass");
+      if (t < bz) { bz = t; best.z_threads = nt; }
+    }
+    best.ms[0] = bx;
+    best.ms[1] = by;
+    best.ms[2] = bz;
+    best.tuned = true;
+    if (rc == FKP_OK) {
+      P->sched = best;
+      P->ctx->schedules[key] = best;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  return rc;
+}
+
+extern "C" int fkp_plan_schedule(const void* plan, int* x_mult, int* y_threads, int* z_threads, float* tuned_ms) {
+  const auto* P = static_cast<const Plan*>(plan);
+  if (!P) return set_error(FKP_EINVAL, "NULL plan");
+  if (x_mult) *x_mult = P->sched.x_mult;
+  if (y_threads) *y_threads = P->sched.y_threads;
+  if (z_threads) *z_threads = P->sched.z_threads;
+  if (tuned_ms)
+    for (int i = 0; i < 3; ++i) tuned_ms[i] = P->sched.tuned ? P->sched.ms[i] : 0.f;
+  return FKP_OK;
+}
+
+extern "C" int fkp_plan_set_schedule(void* plan, int x_mult, int y_threads, int z_threads) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P) return set_error(FKP_EINVAL, "NULL plan");
+  if ((x_mult != 1 && x_mult != 2 && x_mult != 4) || (y_threads != 256 && y_threads != 512) ||
+      (z_threads != 256 && z_threads != 512))
+    return set_error(FKP_EINVAL, "schedule: x_mult in {1, 2, 4}, y_threads and z_threads in {256, 512}");
+  P->sched.x_mult = x_mult;
+  P->sched.y_threads = y_threads;
+  P->sched.z_threads = z_threads;
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);  // captured with the old launches
+  P->graph_exec = nullptr;
+  P->last_valid = false;
+  return FKP_OK;
+}
+
 extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp_pbins_t* pb,
                                const fkp_bshells_t* bs, uint32_t want, void** out) {
   auto* ctx = static_cast<Context*>(vctx);
@@ -437,6 +541,10 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   const size_t hbytes = sizeof(double) * (BQ_N * pb->nbins + pb->nbins + DS_COUNT + LAB_NSUM + 8) + 64;
   CK(cudaMallocHost(&P->h_pinned, hbytes));
   for (auto& e : P->ev) CK(cudaEventCreate(&e));
+  {
+    const int rc = tune_schedule(P);
+    if (rc) { delete P; return rc; }
+  }
   *out = P;
   return FKP_OK;
 }
@@ -562,9 +670,9 @@ int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream
 
 // Enqueues the three FFT passes, recombination and binning of one base grid.
 int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s) {
-  CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s));
+  CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult));
   CK(record_stage(P->ev[3], s));
-  CK(launch_ypass(P->d_S1, gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s));
+  CK(launch_ypass(P->d_S1, gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s, P->sched.y_threads));
   CK(record_stage(P->ev[4], s));
   ZParams zp;
   zp.nbins = P->pb.nbins;
@@ -578,7 +686,8 @@ int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf,
   zp.slut = nullptr;
   zp.E = nullptr;
   zp.mm = 0;
-  CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s));
+  CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s,
+                  P->sched.z_threads));
   CK(launch_reduce_bins(P->d_zpart, P->d_zpartc, P->nblk_z, P->pb.nbins, P->d_bins, P->d_binc, s));
   CK(record_stage(P->ev[5], s));
   return FKP_OK;

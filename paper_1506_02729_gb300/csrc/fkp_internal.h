@@ -2,6 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/fkp.h"
@@ -9,10 +12,22 @@
 
 namespace fkp {
 
+// Launch schedule of the FFT passes, chosen per (grid, multipole order) by
+// timing the candidates when the first plan of that kind is made.
+struct PassSchedule {
+  int x_mult = 2;       // x-pass blocks per SM = resident blocks x x_mult (1, 2 or 4)
+  int y_threads = 256;  // y-pass block: 256 (two per SM) or 512
+  int z_threads = 512;  // z-pass block: 256 or 512
+  float ms[3] = {0, 0, 0};  // the chosen x, y, z times when tuned (ms)
+  bool tuned = false;
+};
+
 struct Context {
   int device = 0;
   size_t budget = 0;
   int nsm = 1;
+  std::mutex tune_mu;
+  std::map<std::pair<int, int>, PassSchedule> schedules;  // (N, lmax) -> schedule
 };
 
 struct Plan {
@@ -24,6 +39,7 @@ struct Plan {
   bool wantB = false;
   int lmax = 0;
   MomentTable mt{};
+  PassSchedule sched{};
   FftPlan fp{};
   GeomDev g{};
   double min_edge_gap = 0;
@@ -104,13 +120,16 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
 cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xyzv, const float* vw2,
                               unsigned long long* grid, unsigned long long* gridw, cudaStream_t s);
 cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
+// xm: x-pass blocks = SMs x resident blocks x xm; nt: threads per y- or
+// z-pass block (256 or 512).  The defaults are the 512^3 choices.
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
-                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s);
+                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm = 2);
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, float2* S2, int* err, cudaStream_t s);
+                         const float2* tw, float2* S2, int* err, cudaStream_t s, int nt = 256);
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s);
+                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
+                         int nt = 512);
 cudaError_t launch_reduce_bins(const double* part, const int* partc, int nblk, int nbins, double* out,
                                long long* outc, cudaStream_t s);
 

@@ -27,8 +27,15 @@ namespace fkp {
 constexpr int kT = 8;        // k_x columns per tile (64 bytes of complex64)
 // y-pass blocks (8, 32), two per SM; z-pass blocks (8, 64), one per SM (its
 // three accumulators per point need the registers)
-constexpr int kNTy = 256, kRunY = 32, kRLY = 16;  // threads, threads per column, points per thread (N <= 512)
-constexpr int kNTz = 512, kRunZ = 64, kRLZ = 8;
+// The y- and z-pass blocks are (8, NT / 8): NT / 8 threads per column, each
+// holding RL = 512 / (NT / 8) points (N <= 512).  NT is 256 or 512, chosen per
+// grid by timing when a plan is made (PassSchedule).
+template <int NT>
+struct PassShape {
+  static constexpr int kRun = NT / kT;
+  static constexpr int kRL = (512 + kRun - 1) / kRun;
+  static constexpr int kMinBlocks = NT <= 256 ? 2 : 1;
+};
 
 __device__ __forceinline__ int smode(int k, int N) { return k <= N / 2 ? k : k - N; }
 
@@ -82,7 +89,7 @@ __device__ __forceinline__ void build_pairs(float f, const float (&hx)[5], const
 // FFT; a radix-R stage's N/R butterflies per pencil are strided over
 // threadIdx.y, so no index is divided by NP.
 template <int N_, int LMAX>
-__global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
+__global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX >= 4 ? 3 : 1) k_xpass2(
     const unsigned long long* __restrict__ gq, const float* __restrict__ gf, GeomDev g, FftPlan fp,
     const float2* __restrict__ twg, float2* __restrict__ S1) {
   constexpr int NF = nfields_of(LMAX);
@@ -102,11 +109,31 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
   float2* B = A + NP * N;
   for (int i = tid; i < N; i += NTX) tw[i] = twg[i];
   const size_t fsz = (size_t)N * NXT * N * kT;
+  // the next row's grid values are loaded into registers while this row is
+  // transformed (N <= 512)
+  constexpr int NPRE = (512 + NTX - 1) / NTX;
+  float pre[NPRE];
+  auto load_row = [&](int row) {
+#pragma unroll
+    for (int j = 0; j < NPRE; ++j) {
+      const int x = tid + j * NTX;
+      float v = 0.f;
+      if (row < N * N && x < N) {
+        const size_t gi = (size_t)row * N + x;
+        v = gq ? (float)(long long)__ldg(gq + gi) * kFixInvF : __ldg(gf + gi);
+      }
+      pre[j] = v;
+    }
+  };
+  load_row(blockIdx.x);
   for (int row = blockIdx.x; row < N * N; row += gridDim.x) {
     const int z = row / N, y = row - z * N;
-    const size_t gbase = (size_t)row * N;
-    for (int x = tid; x < N; x += NTX)
-      rowF[x] = gq ? (float)(long long)gq[gbase + x] * kFixInvF : gf[gbase + x];
+#pragma unroll
+    for (int j = 0; j < NPRE; ++j) {
+      const int x = tid + j * NTX;
+      if (x < N) rowF[x] = pre[j];
+    }
+    load_row(row + gridDim.x);
     __syncthreads();
     const float Y = fmaf((float)y, g.H, g.ry), Z = fmaf((float)z, g.H, g.rz);
     for (int x = tid; x < N; x += NTX) {
@@ -156,8 +183,8 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2)) k_xpass2(
 // read 32 consecutive values: no bank conflicts).  The fields are read
 // sweep by sweep; a sweep accumulates up to two output groups, each member
 // with a polynomial coefficient in n_y evaluated by Horner's rule.
-template <int N_>
-__global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S1,
+template <int N_, int NT>
+__global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const float2* __restrict__ S1,
                                                    const unsigned long long* __restrict__ gq,
                                                    const float* __restrict__ gf, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg,
@@ -176,7 +203,7 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
   const size_t gsz = fsz;
   const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
   const int tid = threadIdx.y * kT + threadIdx.x;
-  for (int i = tid; i < N; i += kNTy) tw[i] = twg[i];
+  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -191,15 +218,15 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
     tma_load_1d(buf0, src_of(mt.s_field[0][0]), bytes, &bar[0]);
   }
   const int c = threadIdx.x, run = threadIdx.y;
-  const int rl = (N + kRunY - 1) / kRunY;
+  const int rl = (N + PassShape<NT>::kRun - 1) / PassShape<NT>::kRun;
   const int kx = xt * kT + c;
   const float nx = (float)kx;
   int it = 0;
   for (int sw = 0; sw < mt.nsweeps; ++sw) {
     const int nout = mt.s_nout[sw];
-    float2 acc0[kRLY], acc1[kRLY];
+    float2 acc0[PassShape<NT>::kRL], acc1[PassShape<NT>::kRL];
 #pragma unroll
-    for (int i = 0; i < kRLY; ++i) {
+    for (int i = 0; i < PassShape<NT>::kRL; ++i) {
       acc0[i] = make_float2(0.f, 0.f);
       acc1[i] = acc0[i];
     }
@@ -214,7 +241,7 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
         tma_load_1d(cur ? buf0 : buf1, src_of(mt.s_field[s2][m2]), bytes, &bar[cur ^ 1]);
       }
       mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 4);
-      const float2* R = fft_any<N_, kT, kNTy, -1>(bc, work, fp, tw);
+      const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
       // coefficients a[o][j] of n_y^j for this member and column
       float a[2][5];
 #pragma unroll
@@ -228,8 +255,8 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
           a[o][j] = v;
         }
 #pragma unroll
-      for (int i = 0; i < kRLY; ++i) {
-        const int ky = i * kRunY + run;
+      for (int i = 0; i < PassShape<NT>::kRL; ++i) {
+        const int ky = i * PassShape<NT>::kRun + run;
         if (i < rl && ky < N) {
           const float ny = (float)smode(ky, N);
           const float2 v = R[ky * kT + c];
@@ -250,8 +277,8 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
       const size_t node = ((size_t)g.obs_z * N + g.obs_y) * N + g.obs_x;
       const float fo = gq ? (float)(long long)gq[node] * kFixInvF : gf[node];
 #pragma unroll
-      for (int i = 0; i < kRLY; ++i) {
-        const int ky = i * kRunY + run;
+      for (int i = 0; i < PassShape<NT>::kRL; ++i) {
+        const int ky = i * PassShape<NT>::kRun + run;
         if (i < rl && ky < N) {
           const int ph = (int)(((long long)kx * g.obs_x + (long long)ky * g.obs_y) % N);
           float sn, cs;
@@ -267,8 +294,8 @@ __global__ void __launch_bounds__(kNTy, 2) k_ypass2(const float2* __restrict__ S
       if (o >= nout) break;
       float2* dst = S2 + (size_t)mt.s_out[sw][o] * gsz + (size_t)xt * N * tile + (size_t)z * kT + c;
 #pragma unroll
-      for (int i = 0; i < kRLY; ++i) {
-        const int ky = i * kRunY + run;
+      for (int i = 0; i < PassShape<NT>::kRL; ++i) {
+        const int ky = i * PassShape<NT>::kRun + run;
         if (i < rl && ky < N) dst[(size_t)ky * tile] = o ? acc1[i] : acc0[i];
       }
     }
@@ -300,11 +327,11 @@ __device__ __forceinline__ float pwsel(float v, float v2, int e) {
 
 // One group's contribution to the thread's run of k_z: F_0 (F0), c2 nz^p2 to
 // S_2 (A2), c4 nz^p4 to S_4 (A4).
-template <bool F0, bool A2, bool A4>
+template <int RL, bool F0, bool A2, bool A4>
 __device__ __forceinline__ void zgroup(const float2* R, int z0, int rl, int N, int c, float c2, int p2, float c4,
-                                       int p4, float2 (&f0)[kRLZ], float2 (&s2)[kRLZ], float2 (&s4)[kRLZ]) {
+                                       int p4, float2 (&f0)[RL], float2 (&s2)[RL], float2 (&s4)[RL]) {
 #pragma unroll
-  for (int i = 0; i < kRLZ; ++i) {
+  for (int i = 0; i < RL; ++i) {
     const int kz = z0 + i;
     if (i < rl && kz < N) {
       const float2 v = R[kz * kT + c];
@@ -333,8 +360,8 @@ __device__ __forceinline__ void zgroup(const float2* R, int z0, int rl, int N, i
 // along it), sums a run in FP32 and adds it
 // to the block's FP32 bins in shared memory when the bin changes; blocks'
 // bins are reduced in FP64 in a fixed order.
-template <int N_, int MODE>
-__global__ void __launch_bounds__(kNTz, 1) k_zpass2(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
+template <int N_, int MODE, int NT>
+__global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg, ZParams zp,
                                                    double* __restrict__ part, int* __restrict__ partc,
                                                    int* __restrict__ err) {
@@ -354,9 +381,9 @@ __global__ void __launch_bounds__(kNTz, 1) k_zpass2(const float2* __restrict__ S
   const int tid = threadIdx.y * kT + threadIdx.x;
   const size_t gsz = (size_t)N * NXT * N * kT;
   const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
-  for (int i = tid; i < N; i += kNTz) tw[i] = twg[i];
-  for (int t = tid; t < BQ_N * nkey; t += kNTz) sb[t] = 0.f;
-  for (int t = tid; t < nkey; t += kNTz) sc[t] = 0;
+  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  for (int t = tid; t < BQ_N * nkey; t += NT) sb[t] = 0.f;
+  for (int t = tid; t < nkey; t += NT) sc[t] = 0;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -369,11 +396,11 @@ __global__ void __launch_bounds__(kNTz, 1) k_zpass2(const float2* __restrict__ S
     tma_load_1d(buf0, src_of(0), bytes, &bar[0]);
   }
   const int c = threadIdx.x, run = threadIdx.y;
-  const int rl = (N + kRunZ - 1) / kRunZ;
+  const int rl = (N + PassShape<NT>::kRun - 1) / PassShape<NT>::kRun;
   const int z0 = run * rl;
-  float2 f0[kRLZ], s2[kRLZ], s4[kRLZ];
+  float2 f0[PassShape<NT>::kRL], s2[PassShape<NT>::kRL], s4[PassShape<NT>::kRL];
 #pragma unroll
-  for (int i = 0; i < kRLZ; ++i) {
+  for (int i = 0; i < PassShape<NT>::kRL; ++i) {
     f0[i] = make_float2(0.f, 0.f);
     s2[i] = f0[i];
     s4[i] = f0[i];
@@ -387,13 +414,13 @@ __global__ void __launch_bounds__(kNTz, 1) k_zpass2(const float2* __restrict__ S
       tma_load_1d(cur ? buf0 : buf1, src_of(gi + 1), bytes, &bar[cur ^ 1]);
     }
     mbar_wait(&bar[cur], (uint32_t)((gi >> 1) & 1), err, 8);
-    const float2* R = fft_any<N_, kT, kNTz, -1>(bc, work, fp, tw);
+    const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
     const int p2 = mt.g_p2[gi], p4 = mt.g_p4[gi];
     const float c2 = mt.g_c2[gi], c4 = mt.g_c4[gi];
-    if (mt.g_f0[gi]) zgroup<true, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
-    else if (c2 != 0.f && c4 != 0.f) zgroup<false, true, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
-    else if (c2 != 0.f) zgroup<false, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
-    else zgroup<false, false, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
+    if (mt.g_f0[gi]) zgroup<PassShape<NT>::kRL, true, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
+    else if (c2 != 0.f && c4 != 0.f) zgroup<PassShape<NT>::kRL, false, true, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
+    else if (c2 != 0.f) zgroup<PassShape<NT>::kRL, false, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
+    else zgroup<PassShape<NT>::kRL, false, false, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
     __syncthreads();
   }
   const int kx = xt * kT + c;
@@ -407,7 +434,7 @@ __global__ void __launch_bounds__(kNTz, 1) k_zpass2(const float2* __restrict__ S
 #pragma unroll
   for (int q = 0; q < BQ_N; ++q) acc[q] = 0.f;
 #pragma unroll
-  for (int i = 0; i < kRLZ; ++i) {
+  for (int i = 0; i < PassShape<NT>::kRL; ++i) {
     const int kz = z0 + i;
     int b = -1;
     float vals[BQ_N];
@@ -484,8 +511,8 @@ __global__ void __launch_bounds__(kNTz, 1) k_zpass2(const float2* __restrict__ S
   __syncthreads();
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   const int nblk = gridDim.x * gridDim.y;
-  for (int t = tid; t < BQ_N * nkey; t += kNTz) part[(size_t)t * nblk + blk] = (double)sb[t];
-  for (int t = tid; t < nkey; t += kNTz) partc[(size_t)t * nblk + blk] = sc[t];
+  for (int t = tid; t < BQ_N * nkey; t += NT) part[(size_t)t * nblk + blk] = (double)sb[t];
+  for (int t = tid; t < nkey; t += NT) partc[(size_t)t * nblk + blk] = sc[t];
 }
 
 // ----------------------------------------------------------------------------
@@ -520,13 +547,13 @@ static size_t zsm(int N, int nkey) { return ysm(N) + sizeof(float) * BQ_N * nkey
 
 template <int N_, int LMAX>
 static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                        const float2* tw, float2* S1, int nsm, cudaStream_t s) {
+                        const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm) {
   constexpr int NP = (nfields_of(LMAX) + 1) / 2;
   const size_t sm = xsm(g.N, NP);
   raise_smem_limit((const void*)k_xpass2<N_, LMAX>, sm);
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, LMAX>, 32 * NP, sm);
-  int grid = nsm * (occ > 0 ? occ : 1) * 2;
+  int grid = nsm * (occ > 0 ? occ : 1) * (xm > 0 ? xm : 2);
   if (grid > g.N * g.N) grid = g.N * g.N;
   k_xpass2<N_, LMAX><<<grid, dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1);
   return cudaGetLastError();
@@ -534,89 +561,106 @@ static cudaError_t xrun(const unsigned long long* gq, const float* gf, const Geo
 
 template <int LMAX>
 static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                             const float2* tw, float2* S1, int nsm, cudaStream_t s) {
+                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm) {
   if (LMAX == 4) {
     switch (g.N) {
-      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
-      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
-      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
-      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
-      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
-      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
+      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
       default: break;
     }
   }
-  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s);
+  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
 }
 
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
-                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s) {
-  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s);
-  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s);
-  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s);
+                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm) {
+  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+}
+
+template <int N_, int NT>
+static cudaError_t yrun_nt(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
+                           const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
+                           cudaStream_t s) {
+  const size_t sm = ysm(g.N);
+  raise_smem_limit((const void*)k_ypass2<N_, NT>, sm);
+  k_ypass2<N_, NT><<<dim3(tiles_x(g.N), g.N), dim3(kT, NT / kT), sm, s>>>(S1, gq, gf, g, mt, fp, tw, S2, err);
+  return cudaGetLastError();
 }
 
 template <int N_>
 static cudaError_t yrun(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                         const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                        cudaStream_t s) {
-  const size_t sm = ysm(g.N);
-  raise_smem_limit((const void*)k_ypass2<N_>, sm);
-  k_ypass2<N_><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNTy / kT), sm, s>>>(S1, gq, gf, g, mt, fp, tw, S2, err);
-  return cudaGetLastError();
+                        cudaStream_t s, int nt) {
+  return nt == 512 ? yrun_nt<N_, 512>(S1, gq, gf, g, mt, fp, tw, S2, err, s)
+                   : yrun_nt<N_, 256>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
 }
 
 // gq / gf: the grid the x-pass read (for the observer node's value).
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                         cudaStream_t s) {
+                         cudaStream_t s, int nt) {
   switch (g.N) {
-    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
-    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
-    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
-    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
-    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
-    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
-    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
+    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
+    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
+    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
+    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
+    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
+    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
+    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
   }
+}
+
+template <int N_, int MODE, int NT>
+static cudaError_t zrun_nt(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
+                           const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
+  const size_t sm = zsm(g.N, MODE == 2 ? zp.nshells : zp.nbins);
+  raise_smem_limit((const void*)k_zpass2<N_, MODE, NT>, sm);
+  k_zpass2<N_, MODE, NT><<<dim3(tiles_x(g.N), g.N), dim3(kT, NT / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part,
+                                                                                partc, err);
+  return cudaGetLastError();
 }
 
 template <int N_, int MODE>
 static cudaError_t zrun(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                        const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
-  const size_t sm = zsm(g.N, MODE == 2 ? zp.nshells : zp.nbins);
-  raise_smem_limit((const void*)k_zpass2<N_, MODE>, sm);
-  k_zpass2<N_, MODE><<<dim3(tiles_x(g.N), g.N), dim3(kT, kNTz / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part, partc,
-                                                                             err);
-  return cudaGetLastError();
+                        const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
+                        int nt) {
+  return nt == 256 ? zrun_nt<N_, MODE, 256>(S2, g, mt, fp, tw, zp, part, partc, err, s)
+                   : zrun_nt<N_, MODE, 512>(S2, g, mt, fp, tw, zp, part, partc, err, s);
 }
 
 template <int MODE>
 static cudaError_t zdispatch(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                              const float2* tw, const ZParams& zp, double* part, int* partc, int* err,
-                             cudaStream_t s) {
+                             cudaStream_t s, int nt) {
   switch (g.N) {
-    case 512: return zrun<512, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
-    case 360: return zrun<360, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
-    case 256: return zrun<256, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+    case 512: return zrun<512, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+    case 360: return zrun<360, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+    case 256: return zrun<256, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
     default: break;
   }
   if (MODE == 0) {
     switch (g.N) {
-      case 384: return zrun<384, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
-      case 128: return zrun<128, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
-      case 64: return zrun<64, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+      case 384: return zrun<384, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+      case 128: return zrun<128, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+      case 64: return zrun<64, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
       default: break;
     }
   }
-  return zrun<0, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+  return zrun<0, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
 }
 
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
-  if (zp.mode == 0) return zdispatch<0>(S2, g, mt, fp, tw, zp, part, partc, err, s);
-  if (zp.mode == 1) return zdispatch<1>(S2, g, mt, fp, tw, zp, part, partc, err, s);
-  return zdispatch<2>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
+                         int nt) {
+  if (zp.mode == 0) return zdispatch<0>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+  if (zp.mode == 1) return zdispatch<1>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+  return zdispatch<2>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
 }
 
 }  // namespace fkp

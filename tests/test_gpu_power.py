@@ -99,6 +99,32 @@ def test_repeat_runs_agree(small_mock):
         assert np.allclose(a[k], b[k], rtol=1e-6, atol=1e-6 * np.nanmax(np.abs(a["P0"])), equal_nan=True), k
 
 
+@pytest.mark.parametrize("N", [64, 60])
+def test_every_pass_schedule_matches_oracle(small_mock, N):
+    """The tuner picks among x-pass grid sizes and y/z-pass block shapes; every
+    candidate gives P_l within the tolerance of the oracle (compile-time FFT at
+    64, runtime FFT at 60), and the tuned choice is one of them."""
+    fkp = _fkp()
+    sv0, gal, ran = small_mock
+    sv = mockgen.survey_small(N=N, assign=2)
+    geom = dict(sv.geometry(), periodic=True)
+    kf = 2 * math.pi / sv.L
+    bins = (0.0, 1.7 * kf, 14)
+    ref = _oracle_power(gal, ran, geom, bins)
+    plan = fkp.Plan(geom, bins)
+    sch = plan.schedule()
+    assert sch["x_mult"] in (1, 2, 4) and sch["y_threads"] in (256, 512) and sch["z_threads"] in (256, 512)
+    assert all(t > 0 for t in sch["tuned_ms"])
+    g, r = to_device(gal), to_device(ran)
+    for xm, yt, zt in [(1, 256, 256), (4, 512, 512), (2, 256, 512), (2, 512, 256)]:
+        plan.set_schedule(xm, yt, zt)
+        got = plan.power(g, r)
+        err = p_errors(got, ref)
+        assert max(err.values()) < P_TOL, (xm, yt, zt, err)
+    with pytest.raises(fkp.FKPError):
+        plan.set_schedule(3, 256, 512)
+
+
 def test_graph_replay_equals_plain_launches(small_mock):
     """The second call with the same device catalogs captures a CUDA graph and
     later calls replay it; another catalog runs plain launches and the graph
