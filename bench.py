@@ -317,7 +317,7 @@ def run_gpu(args):
                        "n_ran": int(ran["x"].size), "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": world / e2e_s, "unit": "mocks/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 10 * args.steps,
+            "gpu_launches": 12 * args.steps,  # per step: 2 counts, totals, scan, 2 scatters, L^ab, tiles, x, y, z, bins
             "roofline": roof,
             "fft_schedule": plan.schedule(),
             "clocks": ck}
