@@ -87,9 +87,12 @@ __device__ __forceinline__ void build_pairs(float f, const float (&hx)[5], const
 
 // Block (NP, 32): threadIdx.x is the packed pencil (pair of fields) in the
 // FFT; a radix-R stage's N/R butterflies per pencil are strided over
-// threadIdx.y, so no index is divided by NP.
+// threadIdx.y, so no index is divided by NP.  The register cap keeps as many
+// blocks per SM as shared memory allows for the full moment set (4 up to
+// N = 256, 3 above).
 template <int N_, int LMAX>
-__global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX >= 4 ? 3 : 1) k_xpass2(
+__global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 1 : (N_ > 0 && N_ <= 256 ? 4 : 3))
+    k_xpass2(
     const unsigned long long* __restrict__ gq, const float* __restrict__ gf, GeomDev g, FftPlan fp,
     const float2* __restrict__ twg, float2* __restrict__ S1) {
   constexpr int NF = nfields_of(LMAX);
