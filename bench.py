@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving leg (req/s)")
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--small-steps", type=int, default=200, help="timed 64^3 mocks per mode (0 skips that leg)")
+    ap.add_argument("--batch-mocks", type=int, default=32, help="mocks in the batched leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -329,6 +330,9 @@ def run_gpu(args):
         del dg, dr
         torch.cuda.empty_cache()
         line["serving"] = run_serve(args, gal, ran)
+    if args.batch_mocks > 0 and world == 1:
+        torch.cuda.empty_cache()
+        line["batch"] = run_batch(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_mock, desc, _ = oracle_sample(gal, ran, sv, 1)
         line["cpu_baseline"] = {"value": 1.0 / t_mock, "unit": "mocks/s", "cores": cores_used(), "kind": "oracle",
@@ -418,6 +422,97 @@ def run_bisp(args, gal, ran, dg, dr, stream):
                                          "sqrt(sum_x t^2) of the 3-way split)"}
     plan.close()
     return out
+
+
+def _rel_diff(a, b, keys, den):
+    """max |a - b| / max(|b|, den) over the entries where den is finite."""
+    out = 0.0
+    m = np.isfinite(den) & (den > 0)
+    for k in keys:
+        d = np.maximum(np.abs(b[k][m]), den[m])
+        out = max(out, float(np.max(np.abs(a[k][m] - b[k][m]) / d)))
+    return out
+
+
+def run_batch(args):
+    """The batched-mock workload: mocks drawn from a device-resident master
+    catalog (1.2e6 galaxies and 30x randoms, the BOSS-like footprint with nbar
+    scaled up): grid from {256, 384, 512}, N_g uniform in [5e5, 1.2e6] (a
+    random subsample), randoms 30 N_g; each mock P_0,2,4 plus B_0 to k = 0.15
+    (27 shells).  Batched: all mocks submitted to the request server at once
+    (3 slots, plans pooled per grid, 3-way split tensor-core contraction).
+    Plain: the per-mock path, one at a time on one stream, FP32 contraction.
+    Reports mocks/s for both and, per mock, the largest difference between
+    them (P_l graded by the raw monopole, B_0 by |T_0|/(N^3 N_T I_33) over
+    triangles with N_T >= 100); the FP64 parity of each path is what
+    tests/test_gpu_power.py and tests/test_gpu_bispectrum.py check."""
+    import dataclasses
+
+    import torch
+
+    import mockgen
+    import paper_1506_02729_gb300 as fkp
+    base = mockgen.survey_boss(N=256)
+    sv = dataclasses.replace(base, nbar_peak=base.nbar_peak * 1.2e6 / 7.0e5, random_ratio=30.0)
+    gal, ran = mockgen.catalog(sv, args.seed + 500)
+    dgal = {k: torch.from_numpy(v).cuda() for k, v in gal.items()}
+    dran = {k: torch.from_numpy(v).cuda() for k, v in ran.items()}
+    ngal, nran = gal["x"].size, ran["x"].size
+    del gal, ran
+    g = np.random.default_rng(args.seed + 300)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(args.seed + 301)
+    want = fkp.FKP_P0 | fkp.FKP_P2 | fkp.FKP_P4 | fkp.FKP_B0
+    bshells = (3, 3, 3, 27)
+    mocks = []
+    for _ in range(args.batch_mocks):
+        N = int(g.choice([256, 384, 512]))
+        ng = int(min(ngal, g.uniform(5e5, 1.2e6)))
+        nr = min(nran, 30 * ng)
+        gi = torch.sort(torch.randperm(ngal, device="cuda", generator=gen)[:ng]).values
+        ri = torch.sort(torch.randperm(nran, device="cuda", generator=gen)[:nr]).values
+        mocks.append(dict(geom=mockgen.survey_boss(N=N).geometry(),
+                          gal={k: v[gi].contiguous() for k, v in dgal.items()},
+                          ran={k: v[ri].contiguous() for k, v in dran.items()}, n_obj=ng + nr))
+    del dgal, dran
+    torch.cuda.synchronize()
+    srv = fkp.Server(nslots=3)
+
+    def submit_all():
+        return [srv.submit(m["geom"], BINS, m["gal"], m["ran"], want=want, bshells=bshells,
+                           contraction=fkp.FKP_CONTRACT_BF16X6) for m in mocks]
+
+    for t in submit_all():  # plans and schedules for every grid
+        srv.wait(t)
+    t0 = time.perf_counter()
+    served = [srv.wait(t) for t in submit_all()]
+    wall_b = time.perf_counter() - t0
+    srv.close()
+    plans = {}
+    for m in mocks:
+        N = m["geom"]["N"]
+        if N not in plans:
+            plans[N] = fkp.Plan(m["geom"], BINS, bshells=bshells, want=want)
+            plans[N].bispectrum(m["gal"], m["ran"], contraction=fkp.FKP_CONTRACT_FP32)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    plain = [plans[m["geom"]["N"]].bispectrum(m["gal"], m["ran"], contraction=fkp.FKP_CONTRACT_FP32) for m in mocks]
+    wall_p = time.perf_counter() - t1
+    for p in plans.values():
+        p.close()
+    dp, db = [], []
+    for m, (ps, bs, _), (pp, bp) in zip(mocks, served, plain):
+        dp.append(_rel_diff(ps, pp, ("P0", "P2", "P4"), np.abs(pp["mono_raw"])))
+        N3 = float(m["geom"]["N"]) ** 3
+        den = np.where(bp["NT"] >= 100, np.abs(bp["T0"]) / (N3 * np.maximum(bp["NT"], 1) * bp["I33"]), np.nan)
+        db.append(_rel_diff(bs, bp, ("B0",), den))
+    return {"workload": f"{len(mocks)} mocks: grids {{256,384,512}}, N_g in [5e5, 1.2e6] + 30x randoms (device "
+                        "catalogs), P_0,2,4 + B_0 to k=0.15 (27 shells)",
+            "unit": "mocks/s", "batched_mocks_per_s": len(mocks) / wall_b,
+            "plain_mocks_per_s": len(mocks) / wall_p,
+            "objects_per_mock_mean": float(np.mean([m["n_obj"] for m in mocks])),
+            "batched_vs_plain_max_rel_diff": {"P": max(dp), "B0": max(db)},
+            "per_mock_rel_diff_P": dp, "per_mock_rel_diff_B0": db}
 
 
 def run_serve(args, gal, ran):
