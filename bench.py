@@ -63,6 +63,31 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+# Replicas: mocks are independent, so N GPUs run N replicas, each on its own
+# seed, with no collective on the data path; only the timing is combined.
+
+def replica_seed(seed, rank):
+    """Each rank's mock seed (the seed range is partitioned by rank)."""
+    return seed + rank
+
+
+def max_over_ranks(x, world):
+    """The largest of each rank's x (a time), over the process group."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, seconds_per_mock_max):
+    """Whole-job mocks/s: every rank finished one mock per step, the step
+    lasting as long as the slowest rank's."""
+    return world / seconds_per_mock_max
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -237,7 +262,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     fbuild.build()
     sv = mockgen.survey_boss(N=args.grid, random_ratio=args.ran_ratio)
-    gal, ran = mockgen.catalog(sv, args.seed + rank)
+    gal, ran = mockgen.catalog(sv, replica_seed(args.seed, rank))
     n_obj = gal["x"].size + ran["x"].size
     dg = {k: torch.from_numpy(v).cuda() for k, v in gal.items()}
     dr = {k: torch.from_numpy(v).cuda() for k, v in ran.items()}
@@ -268,13 +293,8 @@ def run_gpu(args):
     barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_all = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * 1000.0 / ms_all
+    ms_all = max_over_ranks(ms, world)
+    value = job_rate(world, ms_all / 1000.0)
 
     # end to end through the C ABI with host (pinned) catalogs
     hg = {k: torch.from_numpy(v).pin_memory() for k, v in gal.items()}
@@ -286,12 +306,7 @@ def run_gpu(args):
     for _ in range(args.e2e_steps):
         plan.power(hg, hr, stream=stream)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world)
     h2d = 16 * n_obj
     d2h = 8 * (6 * 60 + 60) + 8 * 24
 
@@ -317,7 +332,8 @@ def run_gpu(args):
             "config": {"workload": workload, "grid": sv.N, "n_gal": int(gal["x"].size),
                        "n_ran": int(ran["x"].size), "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "e2e": {"value": world / e2e_s, "unit": "mocks/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": job_rate(world, e2e_s), "unit": "mocks/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
             "gpu_launches": 12 * args.steps,  # per step: 2 counts, totals, scan, 2 scatters, L^ab, tiles, x, y, z, bins
             "roofline": roof,
             "fft_schedule": plan.schedule(),
