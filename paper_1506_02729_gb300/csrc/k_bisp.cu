@@ -229,14 +229,30 @@ __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2,
   float2* tw = sm;
   float2* A = sm + N;
   float2* B = A + kSP * N;
+  // the next iteration's rows of T2: its 2 kSP rows are one contiguous span
+  // (row 2 g0 with g0 a multiple of kSP = 8, so 16-byte aligned) fetched with
+  // cp.async while this iteration transforms and stores
+  float2* stg = B + kSP * N;
   const int tid = threadIdx.y * kSP + threadIdx.x;
   const int m1 = sp.mm + 1;
   for (int i = tid; i < N; i += kSNT) tw[i] = twg[i];
   const long long pairs = (long long)sp.S * N * N / 2;
+  auto stage = [&](long long gn) {
+    if (gn < pairs) {
+      const int npn = (int)(pairs - gn < kSP ? pairs - gn : kSP);
+      const float2* src = T2 + 2 * gn * m1;
+      for (int t = tid; t < npn * m1; t += kSNT)  // 16-byte chunks
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(stg + 2 * t)), "l"(src + 2 * t)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  stage((long long)blockIdx.x * kSP);
   for (long long g0 = (long long)blockIdx.x * kSP; g0 < pairs; g0 += (long long)gridDim.x * kSP) {
     const int np = (int)(pairs - g0 < kSP ? pairs - g0 : kSP);
     const int s = (int)((2 * g0) / ((long long)N * N));
     const int km = sp.kmax[s < sp.S ? s : sp.S - 1];
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     // p fastest: contiguous shared-memory stores, 32-byte row segments read
     for (int t = tid; t < kSP * N; t += kSNT) {
@@ -246,7 +262,7 @@ __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2,
         const long long r0 = 2 * (g0 + p);
         const int sp0 = (int)(r0 / ((long long)N * N));
         const int kmp = sp0 == s ? km : sp.kmax[sp0];
-        const float2* h0 = T2 + r0 * m1;
+        const float2* h0 = stg + (size_t)(2 * p) * m1;
         const float2* h1 = h0 + m1;
         float2 x1 = make_float2(0.f, 0.f), x2 = x1;
         if (k == 0) {
@@ -265,6 +281,7 @@ __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2,
       A[t] = v;
     }
     __syncthreads();
+    stage(g0 + (long long)gridDim.x * kSP);
     const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
     // transpose through the free buffer into rows, then coalesced stores
     float* rows = reinterpret_cast<float*>(R == A ? B : A);
@@ -292,7 +309,9 @@ static cudaError_t shell_passes_n(const BispLaunch& L, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (L.ny > 0) k_shell_y<N_><<<dim3(L.ny, L.sp.N), blk, sm, s>>>(L.T1, L.sp, L.fp, L.tw, L.yjobs, L.T2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_shell_x<N_><<<L.xblocks, blk, sm, s>>>(L.T2, L.sp, L.fp, L.tw, L.I);
+  const size_t smx = sm + sizeof(float2) * 2 * kSP * (size_t)(L.sp.mm + 1);  // + the row staging
+  if ((e = raise_smem_limit((const void*)k_shell_x<N_>, smx)) != cudaSuccess) return e;
+  k_shell_x<N_><<<L.xblocks, blk, smx, s>>>(L.T2, L.sp, L.fp, L.tw, L.I);
   return cudaGetLastError();
 }
 
