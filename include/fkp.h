@@ -151,7 +151,7 @@ void fkp_plan_destroy(void *plan);
 int fkp_plan_sizes(const void *plan, int *nbins, int *ntriangles, size_t *workspace_bytes);
 
 /* Launch schedule of the three FFT passes of a plan: x_mult (x-pass blocks
- * per SM = resident blocks x x_mult: 1, 2 or 4), and the threads per block
+ * per SM = resident blocks x x_mult: 1, 2, 4 or 8), and the threads per block
  * of the y- and z-passes (256 or 512).  The first plan of a given grid and
  * multipole order in a context times every candidate on its own workspace
  * (about 12 launches of each pass) and keeps the fastest of each; later

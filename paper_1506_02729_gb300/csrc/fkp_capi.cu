@@ -332,7 +332,7 @@ static int tune_schedule(Plan* P) {
     };
     PassSchedule best;
     float bx = 1e30f, by = 1e30f, bz = 1e30f;
-    for (int xm : {1, 2, 4}) {
+    for (int xm : {1, 2, 4, 8}) {
       const float t = timed([&] { return launch_xpass(P->d_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1,
                                                       P->ctx->nsm, s, xm); }, "x-pass");
       if (t < bx) { bx = t; best.x_mult = xm; }
@@ -377,9 +377,9 @@ extern "C" int fkp_plan_schedule(const void* plan, int* x_mult, int* y_threads, 
 extern "C" int fkp_plan_set_schedule(void* plan, int x_mult, int y_threads, int z_threads) {
   auto* P = static_cast<Plan*>(plan);
   if (!P) return set_error(FKP_EINVAL, "NULL plan");
-  if ((x_mult != 1 && x_mult != 2 && x_mult != 4) || (y_threads != 256 && y_threads != 512) ||
+  if ((x_mult != 1 && x_mult != 2 && x_mult != 4 && x_mult != 8) || (y_threads != 256 && y_threads != 512) ||
       (z_threads != 256 && z_threads != 512))
-    return set_error(FKP_EINVAL, "schedule: x_mult in {1, 2, 4}, y_threads and z_threads in {256, 512}");
+    return set_error(FKP_EINVAL, "schedule: x_mult in {1, 2, 4, 8}, y_threads and z_threads in {256, 512}");
   P->sched.x_mult = x_mult;
   P->sched.y_threads = y_threads;
   P->sched.z_threads = z_threads;

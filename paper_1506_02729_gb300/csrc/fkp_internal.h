@@ -15,7 +15,7 @@ namespace fkp {
 // Launch schedule of the FFT passes, chosen per (grid, multipole order) by
 // timing the candidates when the first plan of that kind is made.
 struct PassSchedule {
-  int x_mult = 2;       // x-pass blocks per SM = resident blocks x x_mult (1, 2 or 4)
+  int x_mult = 2;       // x-pass blocks per SM = resident blocks x x_mult (1, 2, 4 or 8)
   int y_threads = 256;  // y-pass block: 256 (two per SM) or 512
   int z_threads = 512;  // z-pass block: 256 or 512
   float ms[3] = {0, 0, 0};  // the chosen x, y, z times when tuned (ms)

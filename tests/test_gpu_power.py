@@ -113,10 +113,10 @@ def test_every_pass_schedule_matches_oracle(small_mock, N):
     ref = _oracle_power(gal, ran, geom, bins)
     plan = fkp.Plan(geom, bins)
     sch = plan.schedule()
-    assert sch["x_mult"] in (1, 2, 4) and sch["y_threads"] in (256, 512) and sch["z_threads"] in (256, 512)
+    assert sch["x_mult"] in (1, 2, 4, 8) and sch["y_threads"] in (256, 512) and sch["z_threads"] in (256, 512)
     assert all(t > 0 for t in sch["tuned_ms"])
     g, r = to_device(gal), to_device(ran)
-    for xm, yt, zt in [(1, 256, 256), (4, 512, 512), (2, 256, 512), (2, 512, 256)]:
+    for xm, yt, zt in [(1, 256, 256), (8, 512, 512), (2, 256, 512), (4, 512, 256)]:
         plan.set_schedule(xm, yt, zt)
         got = plan.power(g, r)
         err = p_errors(got, ref)
