@@ -344,7 +344,7 @@ static int tune_schedule(Plan* P) {
     }
     for (int nt : {256, 512}) {
       const float t = timed([&] { return launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart,
-                                                      P->d_zpartc, P->d_err + 1, s, nt); }, "z-pass");
+                                                      P->d_zpartc, P->d_err + 1, s, P->ctx->nsm, nt); }, "z-pass");
       if (t < bz) { bz = t; best.z_threads = nt; }
     }
     best.ms[0] = bx;
@@ -687,8 +687,9 @@ int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf,
   zp.E = nullptr;
   zp.mm = 0;
   CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s,
-                  P->sched.z_threads));
-  CK(launch_reduce_bins(P->d_zpart, P->d_zpartc, P->nblk_z, P->pb.nbins, P->d_bins, P->d_binc, s));
+                  P->ctx->nsm, P->sched.z_threads));
+  CK(launch_reduce_bins(P->d_zpart, P->d_zpartc, zpass_blocks(P->g.N, P->sched.z_threads, P->ctx->nsm),
+                        P->pb.nbins, P->d_bins, P->d_binc, s));
   CK(record_stage(P->ev[5], s));
   return FKP_OK;
 }

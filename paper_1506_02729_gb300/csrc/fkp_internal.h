@@ -127,9 +127,12 @@ cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const Ge
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, float2* S2, int* err, cudaStream_t s, int nt = 256);
+// The z-pass is persistent: zpass_blocks(N, nt, nsm) blocks, each writing
+// one column of the partial bins (part[key][block]); reduce over that count.
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
-                         int nt = 512);
+                         int nsm, int nt = 512);
+int zpass_blocks(int N, int nt, int nsm);
 cudaError_t launch_reduce_bins(const double* part, const int* partc, int nblk, int nbins, double* out,
                                long long* outc, cudaStream_t s);
 

@@ -704,9 +704,10 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
                    P->sched.y_threads));
   BCK(cudaEventRecord(P->ev[4], s));
   zp.mode = 1;
+  const int nbz = zpass_blocks(N, P->sched.z_threads, P->ctx->nsm);
   BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s,
-                   P->sched.z_threads));
-  BCK(launch_reduce_bins(P->d_zpart, P->d_zpartc, P->nblk_z, P->pb.nbins, P->d_bins, P->d_binc, s));
+                   P->ctx->nsm, P->sched.z_threads));
+  BCK(launch_reduce_bins(P->d_zpart, P->d_zpartc, nbz, P->pb.nbins, P->d_bins, P->d_binc, s));
   BCK(cudaEventRecord(P->ev[5], s));
   // F^w: shell sums against the exported F_l
   BCK(launch_xpass(P->d_gridw, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult));
@@ -714,8 +715,8 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
                    P->sched.y_threads));
   zp.mode = 2;
   BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, st->d_spart, st->d_spartc, P->d_err + 1, s,
-                   P->sched.z_threads));
-  BCK(launch_reduce_bins(st->d_spart, st->d_spartc, P->nblk_z, S, st->d_shell, st->d_shellc, s));
+                   P->ctx->nsm, P->sched.z_threads));
+  BCK(launch_reduce_bins(st->d_spart, st->d_spartc, nbz, S, st->d_shell, st->d_shellc, s));
   BCK(cudaEventRecord(P->ev[6], s));
   // shell IFFTs
   const long long N3 = (long long)N * N * N;

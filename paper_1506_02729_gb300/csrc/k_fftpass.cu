@@ -378,14 +378,18 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   float2* work = buf1 + tile;
   float2* tw = work + tile;
   const int nkey = MODE == 2 ? zp.nshells : zp.nbins;
-  float* sb = reinterpret_cast<float*>(tw + N);  // [BQ_N][nkey]
+  double* sbd = reinterpret_cast<double*>(tw + N);        // [BQ_N][nkey] the block's FP64 sums over its tiles
+  float* sb = reinterpret_cast<float*>(sbd + BQ_N * nkey);  // [BQ_N][nkey] one tile's FP32 sums
   int* sc = reinterpret_cast<int*>(sb + BQ_N * nkey);
-  const int xt = blockIdx.x, ky = blockIdx.y;
   const int tid = threadIdx.y * kT + threadIdx.x;
+  const int ntiles = NXT * N;
   const size_t gsz = (size_t)N * NXT * N * kT;
   const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
   for (int i = tid; i < N; i += NT) tw[i] = twg[i];
-  for (int t = tid; t < BQ_N * nkey; t += NT) sb[t] = 0.f;
+  for (int t = tid; t < BQ_N * nkey; t += NT) {
+    sb[t] = 0.f;
+    sbd[t] = 0.0;
+  }
   for (int t = tid; t < nkey; t += NT) sc[t] = 0;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -393,14 +397,23 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
     mbar_fence_init();
   }
   __syncthreads();
-  auto src_of = [&](int gi) { return S2 + (size_t)gi * gsz + ((size_t)xt * N + ky) * tile; };
-  if (tid == 0) {
+  // tile t = (xt, ky) = (t % NXT, t / NXT); group gi of tile t
+  auto src_of = [&](int t, int gi) {
+    return S2 + (size_t)gi * gsz + ((size_t)(t % NXT) * N + t / NXT) * tile;
+  };
+  if (tid == 0 && (int)blockIdx.x < ntiles) {
     mbar_expect_tx(&bar[0], bytes);
-    tma_load_1d(buf0, src_of(0), bytes, &bar[0]);
+    tma_load_1d(buf0, src_of(blockIdx.x, 0), bytes, &bar[0]);
   }
   const int c = threadIdx.x, run = threadIdx.y;
   const int rl = (N + PassShape<NT>::kRun - 1) / PassShape<NT>::kRun;
   const int z0 = run * rl;
+  // persistent: the block walks its tiles; the copy of the next (tile, group)
+  // is always in flight, across tile boundaries too (it counts them: buffer
+  // it & 1, phase (it >> 1) & 1)
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  const int xt = t % NXT, ky = t / NXT;
   float2 f0[PassShape<NT>::kRL], s2[PassShape<NT>::kRL], s4[PassShape<NT>::kRL];
 #pragma unroll
   for (int i = 0; i < PassShape<NT>::kRL; ++i) {
@@ -408,15 +421,19 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
     s2[i] = f0[i];
     s4[i] = f0[i];
   }
-  for (int gi = 0; gi < mt.ngroups; ++gi) {
-    const int cur = gi & 1;
+  for (int gi = 0; gi < mt.ngroups; ++gi, ++it) {
+    const int cur = it & 1;
     float2* bc = cur ? buf1 : buf0;
-    if (tid == 0 && gi + 1 < mt.ngroups) {
-      fence_proxy_async();
-      mbar_expect_tx(&bar[cur ^ 1], bytes);
-      tma_load_1d(cur ? buf0 : buf1, src_of(gi + 1), bytes, &bar[cur ^ 1]);
+    if (tid == 0) {
+      const int tn = gi + 1 < mt.ngroups ? t : t + (int)gridDim.x;
+      const int gn = gi + 1 < mt.ngroups ? gi + 1 : 0;
+      if (tn < ntiles) {
+        fence_proxy_async();
+        mbar_expect_tx(&bar[cur ^ 1], bytes);
+        tma_load_1d(cur ? buf0 : buf1, src_of(tn, gn), bytes, &bar[cur ^ 1]);
+      }
     }
-    mbar_wait(&bar[cur], (uint32_t)((gi >> 1) & 1), err, 8);
+    mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 8);
     const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
     const int p2 = mt.g_p2[gi], p4 = mt.g_p4[gi];
     const float c2 = mt.g_c2[gi], c4 = mt.g_c4[gi];
@@ -512,10 +529,16 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
     for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, acc[q]);
   }
   __syncthreads();
-  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-  const int nblk = gridDim.x * gridDim.y;
-  for (int t = tid; t < BQ_N * nkey; t += NT) part[(size_t)t * nblk + blk] = (double)sb[t];
-  for (int t = tid; t < nkey; t += NT) partc[(size_t)t * nblk + blk] = sc[t];
+  // the tile's FP32 bin sums join the block's FP64 sums (each slot by one thread)
+  for (int q = tid; q < BQ_N * nkey; q += NT) {
+    sbd[q] += (double)sb[q];
+    sb[q] = 0.f;
+  }
+  __syncthreads();
+  }
+  const int blk = blockIdx.x, nblk = gridDim.x;
+  for (int q = tid; q < BQ_N * nkey; q += NT) part[(size_t)q * nblk + blk] = sbd[q];
+  for (int q = tid; q < nkey; q += NT) partc[(size_t)q * nblk + blk] = sc[q];
 }
 
 // ----------------------------------------------------------------------------
@@ -546,7 +569,17 @@ int yz_tiles(int N) { return tiles_x(N); }
 
 static size_t xsm(int N, int NP) { return sizeof(float2) * (N + N / 2 + 2 * (size_t)NP * N); }
 static size_t ysm(int N) { return 128 + sizeof(float2) * (3 * (size_t)N * kT + N); }
-static size_t zsm(int N, int nkey) { return ysm(N) + sizeof(float) * BQ_N * nkey + sizeof(int) * nkey; }
+static size_t zsm(int N, int nkey) {
+  return ysm(N) + (sizeof(double) + sizeof(float)) * BQ_N * nkey + sizeof(int) * nkey;
+}
+
+// Persistent z-pass grid: one block per resident slot (two 256-thread or one
+// 512-thread block per SM), at most one per tile.
+int zpass_blocks(int N, int nt, int nsm) {
+  const int ntiles = tiles_x(N) * N;
+  const int nb = nsm * (nt == 256 ? 2 : 1);
+  return nb < ntiles ? nb : ntiles;
+}
 
 template <int N_, int LMAX>
 static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
@@ -621,49 +654,49 @@ cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const f
 
 template <int N_, int MODE, int NT>
 static cudaError_t zrun_nt(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                           const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s) {
+                           const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s, int nsm) {
   const size_t sm = zsm(g.N, MODE == 2 ? zp.nshells : zp.nbins);
   raise_smem_limit((const void*)k_zpass2<N_, MODE, NT>, sm);
-  k_zpass2<N_, MODE, NT><<<dim3(tiles_x(g.N), g.N), dim3(kT, NT / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part,
-                                                                                partc, err);
+  k_zpass2<N_, MODE, NT><<<zpass_blocks(g.N, NT, nsm), dim3(kT, NT / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part,
+                                                                                    partc, err);
   return cudaGetLastError();
 }
 
 template <int N_, int MODE>
 static cudaError_t zrun(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
-                        int nt) {
-  return nt == 256 ? zrun_nt<N_, MODE, 256>(S2, g, mt, fp, tw, zp, part, partc, err, s)
-                   : zrun_nt<N_, MODE, 512>(S2, g, mt, fp, tw, zp, part, partc, err, s);
+                        int nsm, int nt) {
+  return nt == 256 ? zrun_nt<N_, MODE, 256>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm)
+                   : zrun_nt<N_, MODE, 512>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm);
 }
 
 template <int MODE>
 static cudaError_t zdispatch(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                              const float2* tw, const ZParams& zp, double* part, int* partc, int* err,
-                             cudaStream_t s, int nt) {
+                             cudaStream_t s, int nsm, int nt) {
   switch (g.N) {
-    case 512: return zrun<512, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
-    case 360: return zrun<360, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
-    case 256: return zrun<256, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+    case 512: return zrun<512, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+    case 360: return zrun<360, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+    case 256: return zrun<256, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
     default: break;
   }
   if (MODE == 0) {
     switch (g.N) {
-      case 384: return zrun<384, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
-      case 128: return zrun<128, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
-      case 64: return zrun<64, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+      case 384: return zrun<384, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+      case 128: return zrun<128, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+      case 64: return zrun<64, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
       default: break;
     }
   }
-  return zrun<0, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+  return zrun<0, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
 }
 
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
-                         int nt) {
-  if (zp.mode == 0) return zdispatch<0>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
-  if (zp.mode == 1) return zdispatch<1>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
-  return zdispatch<2>(S2, g, mt, fp, tw, zp, part, partc, err, s, nt);
+                         int nsm, int nt) {
+  if (zp.mode == 0) return zdispatch<0>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+  if (zp.mode == 1) return zdispatch<1>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+  return zdispatch<2>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
 }
 
 }  // namespace fkp

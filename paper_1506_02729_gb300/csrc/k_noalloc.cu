@@ -209,9 +209,8 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
   zp.slut = nullptr;
   zp.E = nullptr;
   zp.mm = 0;
-  const int nblk = yz_tiles(N) * N;
-  NCK(launch_zpass(S2, g, mt, fp, d_tw, zp, d_part, d_partc, d_err + 1, s));
-  NCK(launch_reduce_bins(d_part, d_partc, nblk, pb->nbins, d_bins, d_binc, s));
+  NCK(launch_zpass(S2, g, mt, fp, d_tw, zp, d_part, d_partc, d_err + 1, s, dsm));
+  NCK(launch_reduce_bins(d_part, d_partc, zpass_blocks(N, 512, dsm), pb->nbins, d_bins, d_binc, s));
 
   const int nb = pb->nbins;
   std::vector<double> hb(BQ_N * nb);
