@@ -157,13 +157,27 @@ def algorithmic_bytes(N, nfields, ngroups, n_obj):
     }
 
 
+def source_sha():
+    """First 12 hex of sha1 of the FFT-pass sources (k_fftpass.cu, fkp_fft.cuh)
+    with comments and blank lines removed, so that only code changes disown a
+    recorded capture."""
+    import hashlib
+    import re
+    out = []
+    for f in ("k_fftpass.cu", "fkp_fft.cuh"):
+        src = open(os.path.join(ROOT, "paper_1506_02729_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        lines = [re.sub(r"//.*", "", ln).rstrip() for ln in src.splitlines()]
+        code = "\n".join(ln for ln in lines if ln.strip())
+        out.append(hashlib.sha1(code.encode()).hexdigest()[:12])
+    return ",".join(out)
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
     when the kernel's sources changed since the counters were taken."""
-    import hashlib
     try:
-        srcs = [os.path.join(ROOT, "paper_1506_02729_gb300", "csrc", f) for f in ("k_fftpass.cu", "fkp_fft.cuh")]
-        sha = ",".join(hashlib.sha1(open(f, "rb").read()).hexdigest()[:12] for f in srcs)
+        sha = source_sha()
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             if line.startswith("#") or not line.strip():
                 continue

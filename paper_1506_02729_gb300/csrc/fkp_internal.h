@@ -43,7 +43,9 @@ struct Plan {
   FftPlan fp{};
   GeomDev g{};
   double min_edge_gap = 0;
-  int nblk_cat = 0, nblk_z = 0;
+  int nblk_cat = 0;
+  int nblk_z = 0;  // capacity (in blocks) of the z-pass partial bins: one per tile; the
+                   // persistent z-pass writes zpass_blocks(...) <= nblk_z of them
 
   // power workspace
   unsigned long long *d_grid = nullptr, *d_gridw = nullptr;

@@ -1,20 +1,24 @@
 // k_fftpass.cu - the three FFT passes of the power-spectrum path.
 //
-//   x-pass  per grid row: moment fields F x^_a x^_b (...) built at the nodes
-//           about the observer (eqs. Qij, Qijkl, Qab), two real fields packed
-//           per complex pencil, FFT along x, unpacked into half spectra.
+//   x-pass  per grid row (blocks walk rows, the next row's values loaded
+//           while this one is transformed): moment fields F x^_a x^_b (...)
+//           built at the nodes about the observer (eqs. Qij, Qijkl, Qab), two
+//           real fields packed per complex pencil (XOR-swizzled interleave),
+//           FFT along x, unpacked into half spectra.
 //   y-pass  per (z, k_x tile): FFT of each field along y, then the k_x, k_y
 //           polynomials of eqs. delta2b and delta4b (with the multinomial
 //           multiplicities and the trace identities of the unit vector x^),
 //           summed into k_z-power groups.
-//   z-pass  per (k_y, k_x tile): FFT of each group along z, Legendre
+//   z-pass  per (k_y, k_x tile), persistent blocks walking their tiles with
+//           the next tile's first copy in flight: FFT of each group along z, Legendre
 //           recombination F_2 = 3/2 S_2/|n|^2 - F_0/2 and
 //           F_4 = 35/8 S_4/|n|^4 - 5/2 F_2 - 7/8 F_0 (eqs. F2, delta4),
 //           window compensation and shell binning (eq. shell).
 //
-// Layouts are tile-major so that every tile a pass reads is one contiguous
-// block, fetched with a bulk (TMA) copy while the previous tile is being
-// transformed:
+// Block shapes and the x-pass grid are chosen per grid by timing when a plan
+// is made (PassSchedule).  Layouts are tile-major so that every tile a pass
+// reads is one contiguous block, fetched with a bulk (TMA) copy while the
+// previous one is being transformed:
 //   S1[field][z][xt][y][c]   (k_x = 8 xt + c), written by the x-pass
 //   S2[group][xt][ky][z][c]  written by the y-pass, read by the z-pass
 #include <cuda_runtime.h>
