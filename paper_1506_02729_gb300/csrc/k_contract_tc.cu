@@ -101,12 +101,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
-// Core matrices of 8 rows x 16 bytes; lbo = byte distance between core
-// matrices adjacent in K, sbo = between 8-row groups; descriptor version 1.
+// Shared-memory matrix descriptor: K-major operand with the 64-byte swizzle.
+// Each row holds the chunk's 32 K values (64 bytes); 8 rows form a 512-byte
+// swizzle atom (sbo = 512 between atoms); the K steps of 16 advance the start
+// address by 32 bytes within the rows.  Descriptor version 1, layout type
+// SWIZZLE_64B (4) in bits 61-63.
 __device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
   const uint64_t a = (uint64_t)((smem_u32(p) & 0x3FFFF) >> 4);
-  return a | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+  return a | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
 // Instruction descriptor for kind::f16: D FP32, A and B BF16, both K-major,
@@ -115,10 +117,13 @@ __host__ __device__ constexpr uint32_t tc_idesc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
 
-// Byte offset of the 16-byte row segment (row, k-group kg) in a canonical
-// operand tile with kTcKC/8 = 4 core matrices along K per 8-row group.
+// Byte offset of the 16-byte segment (row, k-group kg) of an operand tile in
+// the 64-byte-swizzled K-major layout: row r at 64 r, its 16-byte chunk kg
+// stored at chunk kg ^ ((r >> 1) & 3) (address bits 4-5 XOR bits 7-8).  A
+// quarter-warp storing 8 consecutive rows of one kg hits 8 distinct 16-byte
+// bank groups.
 __device__ __forceinline__ int canon_off(int row, int kg) {
-  return ((row >> 3) * (kTcKC / 8) + kg) * 128 + (row & 7) * 16;
+  return row * 64 + ((kg ^ ((row >> 1) & 3)) << 4);
 }
 
 // BF16 split of 8 values into NS parts (each part the BF16 rounding of the
@@ -262,11 +267,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
       constexpr int pj[6] = {0, 1, 0, 2, 0, 1};
 #pragma unroll
       for (int ks = 0; ks < kTcKC / 16; ++ks) {
-        // K step ks covers k-groups 2 ks and 2 ks + 1 (256 bytes further in)
+        // K step ks covers k-groups 2 ks and 2 ks + 1 (32 bytes further along the rows)
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-          const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 256, 128, (kTcKC / 8) * 128);
-          const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 256, 128, (kTcKC / 8) * 128);
+          const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 32, 16, 512);
+          const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 32, 16, 512);
           umma_bf16(taddr, ad, bd, idesc, ((c % kTcDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
         }
       }
