@@ -15,19 +15,20 @@
 // the triangle sums cancel strongly (sum |t| >> |sum t|), so the 3-way split
 // is the accurate mode and the 2-way split the fast one.
 //
-// One CTA per (256-column N tile, K slice of 65,536 points).  The shell
-// fields of a chunk of 32 points are fetched two chunks ahead with cp.async
-// into a 3-slot ring; operand stages are double buffered: all threads form
-// the products and the hi/lo splits into the canonical K-major
-// layout (8-row x 16-byte core matrices, no swizzle); one thread issues the
-// tcgen05.mma instructions (M = 128, N = 256, K = 16) and commits them to the
-// stage's mbarrier.  Every 32 chunks (1,024 points) the 128 x 256 FP32 tile
-// is read from tensor memory (tcgen05.ld), added to FP32 register
-// accumulators (round to nearest) and the MMA accumulation restarts: long
-// in-tensor-core accumulation runs were measured to drift linearly with their
-// length (5.6e-4 of the monopole scale over 65,536 points, under 1e-4 over
-// 1,024).  At the end of the slice the registers go to per-slice partials,
-// summed over slices in FP64 by k_tc_reduce.
+// One CTA of 16 warps per (256-column N tile, K slice of 65,536 points).
+// The shell fields of a chunk of 32 points are fetched two chunks ahead with
+// cp.async into a 3-slot ring; operand stages are double buffered: all
+// threads form the products and the BF16 splits into K-major tiles with the
+// 64-byte swizzle (one 64-byte row of K per operand row); one thread issues
+// the tcgen05.mma instructions (M = 128, N = 256, K = 16) and commits them to
+// the stage's mbarrier.  Every 32 chunks (1,024 points) the 128 x 256 FP32
+// tile is read from tensor memory (tcgen05.ld; each warp its lane quarter and
+// 64 columns), added to FP32 register accumulators (64 per thread, round to
+// nearest) and the MMA accumulation restarts: long in-tensor-core
+// accumulation runs were measured to drift linearly with their length
+// (5.6e-4 of the monopole scale over 65,536 points, under 1e-4 over 1,024).
+// At the end of the slice the registers go to per-slice partials, summed over
+// slices in FP64 by k_tc_reduce.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,7 +41,7 @@ constexpr int kTcM = 128;              // MMA rows (l, a)
 constexpr int kTcN = 256;              // MMA columns (pairs b >= c) per tile
 constexpr int kTcKC = 32;              // K points per chunk
 constexpr int kTcChunks = 2048;        // chunks per K slice
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kTcABytes = kTcM * kTcKC * 2;    // one BF16 operand tile: 8 KB
 constexpr int kTcBBytes = kTcN * kTcKC * 2;    // 16 KB
 template <int NS>
@@ -189,11 +190,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   const int nch = (int)((xend - x0 + kTcKC - 1) / kTcKC);
   const uint32_t idesc = tc_idesc();
   bool ok = true;
-  // this thread's slice of the tile: lane quarter (warp % 4), column half (warp / 4)
+  // this thread's slice of the tile: TMEM lane quarter (warp % 4) and 64 of
+  // the 256 columns (warp / 4)
   const int q4 = warp & 3, h2 = warp >> 2;
-  float acc[128];
+  float acc[64];
 #pragma unroll
-  for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+  for (int i = 0; i < 64; ++i) acc[i] = 0.f;
   // asynchronous copies of a chunk's field values into its ring slot (16 bytes
   // each; points past the slice are zero-filled)
   auto prefetch = [&](int cc) {
@@ -288,9 +290,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
       tc_fence_after();
       if (ok) {
 #pragma unroll
-        for (int cg = 0; cg < 4; ++cg) {
+        for (int cg = 0; cg < 2; ++cg) {
           float v[32];
-          tmem_ld32(taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 128 + cg * 32), v);
+          tmem_ld32(taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 64 + cg * 32), v);
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[cg * 32 + i] += v[i];
         }
@@ -300,9 +302,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     }
   }
   // the drain after the last chunk waited for every MMA of the slice
-  float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + lane) * kTcN + h2 * 128;
+  float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + lane) * kTcN + h2 * 64;
 #pragma unroll
-  for (int i = 0; i < 128; i += 4)
+  for (int i = 0; i < 64; i += 4)
     *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
   tc_fence_before();
   __syncthreads();
