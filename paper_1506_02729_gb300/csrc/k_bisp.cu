@@ -303,7 +303,6 @@ static cudaError_t shell_passes_n(const BispLaunch& L, cudaStream_t s) {
   cudaError_t e;
   if ((e = raise_smem_limit((const void*)k_shell_z<N_>, sm)) != cudaSuccess) return e;
   if ((e = raise_smem_limit((const void*)k_shell_y<N_>, sm)) != cudaSuccess) return e;
-  if ((e = raise_smem_limit((const void*)k_shell_x<N_>, sm)) != cudaSuccess) return e;
   const dim3 blk(kSP, kSNT / kSP);
   if (L.nz > 0) k_shell_z<N_><<<L.nz, blk, sm, s>>>(L.E, L.sp, L.fp, L.tw, L.zjobs, L.T1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
