@@ -5,10 +5,12 @@
 //   export     F_0, F_2, F_4 on the shells (z-pass MODE 1, k_power.cu),
 //   shot noise shell means of Re F_l F^w_0* and Re F_0 F^w_l* (z-pass MODE 2)
 //              for the thin-shell form of eq. SNbisp2thin,
-//   shell IFFT F_k^(l)(x) = sum_{q in shell} F_l(q) e^{+iq.x} (eq. F_k): pruned
-//              z and y passes over |n_a| <= mm, then a complex-to-real x pass,
-//   contract   T^(l)(a,b,c) = sum_x F_a^(l) F_b^(0) F_c^(0) (eq. Factorize) in
-//              FP32 with compensated accumulation, FP64 across x slices,
+//   shell IFFT F_k^(l)(x) = sum_{q in shell} F_l(q) e^{+iq.x} (eq. F_k): z and
+//              y passes over each shell's ball only (host-built work lists),
+//              then a complex-to-real x pass,
+//   contract   T^(l)(a,b,c) = sum_x F_a^(l) F_b^(0) F_c^(0) (eq. Factorize):
+//              here the FP32 CUDA-core form with compensated accumulation, FP64
+//              across x slices (the tensor-core form is in k_contract_tc.cu),
 //   finalize   B^(l) = (2l+1) T^(l) / (N^3 N_T I_33) - N^(l) (eqs. BispMono,
 //              BispQuad) on the host in FP64.
 #include <cuda_runtime.h>
