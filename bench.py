@@ -459,7 +459,7 @@ def run_bisp(args, gal, ran, dg, dr, stream):
         m = np.mean(np.array(st), axis=0)
         out["modes"][name] = {"value": 1000.0 / ms, "ms_per_step": ms,
                               "stage_ms": {"grids": float(m[0] + m[1]), "F_passes": float(m[2] + m[3] + m[4]),
-                                           "shell_ifft": float(m[5]), "contraction": float(m[6])}}
+                                           "Fw_passes_and_shell_ifft": float(m[5]), "contraction": float(m[6])}}
     # the headline is the accurate tensor-core mode (3-way split, within the
     # 1e-4 bar like the FP32 contraction); the hi/lo split is the fast mode,
     # with a random per-product error of ~2^-18

@@ -106,7 +106,8 @@ typedef struct {
   double alpha, I22, I33, N0, N0_fkp, S3, W_g, W_r;
   double Lab[6];        /* eq. Lab at k = 0, order xx yy zz xy yz zx */
   int64_t n_gal, n_ran;
-  float timing_ms[8];   /* scalars, assign, xpass, ypass, zpass, bisp ifft, contraction, total */
+  float timing_ms[8];   /* scalars, assign, xpass, ypass, zpass, bisp ifft (the F^w passes and the shell
+                         * IFFTs), contraction, total */
   int graph;            /* 1 when the call replayed the plan's CUDA graph (see fkp_plan_set_graphs) */
 } fkp_power_out;
 

@@ -769,7 +769,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   if (rc) return rc;
   float t = 0.f;
   if (pout) {
-    if (cudaEventElapsedTime(&t, P->ev[6], P->ev[7]) == cudaSuccess) pout->timing_ms[5] = t;
+    if (cudaEventElapsedTime(&t, P->ev[5], P->ev[7]) == cudaSuccess) pout->timing_ms[5] = t;  // F^w + shell IFFTs
     if (cudaEventElapsedTime(&t, P->ev[7], P->ev[8]) == cudaSuccess) pout->timing_ms[6] = t;
     if (cudaEventElapsedTime(&t, P->ev[0], P->ev[8]) == cudaSuccess) pout->timing_ms[7] = t;
   }

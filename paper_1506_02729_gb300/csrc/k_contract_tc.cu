@@ -23,12 +23,12 @@
 // the tcgen05.mma instructions (M = 128, N = 256, K = 16) and commits them to
 // the stage's mbarrier.  Every 32 chunks (1,024 points) the 128 x 256 FP32
 // tile is read from tensor memory (tcgen05.ld; each warp its lane quarter and
-// 64 columns), added to FP32 register accumulators (64 per thread, round to
-// nearest) and the MMA accumulation restarts: long in-tensor-core
-// accumulation runs were measured to drift linearly with their length
-// (5.6e-4 of the monopole scale over 65,536 points, under 1e-4 over 1,024).
-// At the end of the slice the registers go to per-slice partials, summed over
-// slices in FP64 by k_tc_reduce.
+// 64 columns), added with round-to-nearest to a running FP32 sum held in the
+// other 256 tensor-memory columns (tcgen05.ld, add, tcgen05.st) and the MMA
+// accumulation restarts: long in-tensor-core accumulation runs were measured
+// to drift linearly with their length (5.6e-4 of the monopole scale over
+// 65,536 points, under 1e-4 over 1,024).  At the end of the slice the sums go
+// to per-slice partials, summed over slices in FP64 by k_tc_reduce.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -102,6 +102,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes, stored.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+      ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+        "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+        "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+        "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+        "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+        "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand with the 64-byte swizzle.
 // Each row holds the chunk's 32 K values (64 bytes); 8 rows form a 512-byte
 // swizzle atom (sbo = 512 between atoms); the K steps of 16 advance the start
@@ -154,6 +174,15 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
 
 // pairs: (b, c) of the tile's columns (b < 0 marks padding); part layout
 // [slice][tile][128][256] FP32.
+//
+// Every thread has a fixed share of each chunk: A row t % 128, k-group t / 128
+// (8 points); B row t % 256, k-groups 2 (t / 256) and 2 (t / 256) + 1 (16
+// points); its field copies are f = i / 8, points 4 (i % 8) of i = t, t + 512.
+// Offsets and pair indices are therefore computed once.  Rows of A beyond nf
+// and padding columns of B are zeroed once in both stages and never
+// rewritten.  The running FP32 sum of the drained tiles sits in tensor memory
+// columns 256-511 (each drain: tcgen05.ld tile and sum, add, tcgen05.st), so
+// no accumulator occupies registers through the chunk loop.
 template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
                                                                int S, const short2* __restrict__ pairs, int npairs,
@@ -163,17 +192,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   unsigned char* stage0 = smraw;                                  // 2 stages: A parts, then B parts
   float* Iring = reinterpret_cast<float*>(smraw + 2 * kStage);   // 3 x [nf][kTcRow], prefetched 2 chunks ahead
   const int ring = nf * kTcRow;                                   // floats per ring slot
-  short2* pt = reinterpret_cast<short2*>(Iring + 3 * ring);      // [256]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(pt + kTcN);         // [2]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Iring + 3 * ring);  // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int tile = blockIdx.x, slice = blockIdx.y, ntiles = gridDim.x;
-  for (int i = tid; i < kTcN; i += kTcThreads) {
-    const int n = tile * kTcN + i;
-    pt[i] = n < npairs ? pairs[n] : make_short2(-1, -1);
-  }
+  // zero both stages once: rows that are never written stay zero
+  for (int i = tid; i < 2 * kStage / 16; i += kTcThreads) reinterpret_cast<uint4*>(stage0)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) {
-    tmem_alloc(tslot, kTcN);
+    tmem_alloc(tslot, 2 * kTcN);
     tmem_relinquish();
   }
   if (tid == 0) {
@@ -185,32 +211,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *tslot;
+  // this thread's slice of the tile: TMEM lane quarter (warp % 4) and 64 of
+  // the 256 columns (warp / 4); its running sum 256 columns further on
+  const int q4 = warp & 3, h2 = warp >> 2;
+  const uint32_t tcol = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 64);
+  {
+    float z[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z[i] = 0.f;
+    tmem_st32(tcol + kTcN, z);
+    tmem_st32(tcol + kTcN + 32, z);
+  }
   const long long x0 = (long long)slice * kTcKC * kTcChunks;
   const long long xend = (x0 + (long long)kTcKC * kTcChunks < N3) ? x0 + (long long)kTcKC * kTcChunks : N3;
   const int nch = (int)((xend - x0 + kTcKC - 1) / kTcKC);
   const uint32_t idesc = tc_idesc();
+  // fixed roles
+  const int rowA = tid & (kTcM - 1), kgA = tid / kTcM;
+  const bool actA = rowA < nf;
+  const int srcA = rowA * kTcRow + kgA * 8, dstA = canon_off(rowA, kgA);
+  const int rowB = tid & (kTcN - 1), khB = tid / kTcN;
+  short2 bc = make_short2(-1, -1);
+  if (tile * kTcN + rowB < npairs) bc = pairs[tile * kTcN + rowB];
+  const bool actB = bc.x >= 0;
+  const int srcB1 = (actB ? bc.x : 0) * kTcRow + khB * 16, srcB2 = (actB ? bc.y : 0) * kTcRow + khB * 16;
+  const int dstB0 = canon_off(rowB, 2 * khB), dstB1 = canon_off(rowB, 2 * khB + 1);
+  const int cf0 = tid >> 3, cf1 = (tid + kTcThreads) >> 3, ck4 = (tid & 7) * 4;
+  const bool cp0 = cf0 < nf, cp1 = cf1 < nf;
+  const float* csrc0 = I + (size_t)(cp0 ? cf0 : 0) * N3;
+  const float* csrc1 = I + (size_t)(cp1 ? cf1 : 0) * N3;
+  const uint32_t cdst0 = smem_u32(Iring + cf0 * kTcRow + ck4), cdst1 = smem_u32(Iring + cf1 * kTcRow + ck4);
   bool ok = true;
-  // this thread's slice of the tile: TMEM lane quarter (warp % 4) and 64 of
-  // the 256 columns (warp / 4)
-  const int q4 = warp & 3, h2 = warp >> 2;
-  float acc[64];
-#pragma unroll
-  for (int i = 0; i < 64; ++i) acc[i] = 0.f;
   // asynchronous copies of a chunk's field values into its ring slot (16 bytes
   // each; points past the slice are zero-filled)
   auto prefetch = [&](int cc) {
     if (cc < nch) {
-      float* dst = Iring + (cc % 3) * ring;
-      const long long xc = x0 + (long long)cc * kTcKC;
-      for (int i = tid; i < nf * (kTcKC / 4); i += kTcThreads) {
-        const int f = i / (kTcKC / 4), k4 = (i - f * (kTcKC / 4)) * 4;
-        const long long x = xc + k4;
-        const int bytes = x + 4 <= xend ? 16 : (x < xend ? (int)(xend - x) * 4 : 0);
-        const float* src = I + (size_t)f * N3 + (x < xend ? x : 0);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + f * kTcRow + k4)), "l"(src),
-                     "r"(bytes)
+      const long long x = x0 + (long long)cc * kTcKC + ck4;
+      const int bytes = x + 4 <= xend ? 16 : (x < xend ? (int)(xend - x) * 4 : 0);
+      const long long xs = x < xend ? x : 0;
+      const uint32_t so = (uint32_t)((cc % 3) * ring * 4);
+      if (cp0)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(cdst0 + so), "l"(csrc0 + xs), "r"(bytes)
                      : "memory");
-      }
+      if (cp1)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(cdst1 + so), "l"(csrc1 + xs), "r"(bytes)
+                     : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -226,42 +271,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     const float* Ist = Iring + (c % 3) * ring;
     // the MMAs that read this stage two chunks ago must have finished
     if (c >= 2 && ok) ok = mbar_wait(&bar[s], (uint32_t)(((c - 2) >> 1) & 1), err, 16);
-    __syncthreads();
-    // A: rows (l, a) = field index, zero beyond nf
-    // consecutive threads take consecutive rows of one k-group: each
-    // quarter-warp stores one contiguous 128-byte core matrix
-    for (int seg = tid; seg < kTcM * (kTcKC / 8); seg += kTcThreads) {
-      const int kg = seg / kTcM, row = seg - kg * kTcM;
-      float v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = row < nf ? Ist[row * kTcRow + kg * 8 + j] : 0.f;
+    ok = __syncthreads_and(ok) != 0;
+    // A: rows (l, a) = field index; a quarter-warp stores 8 consecutive rows
+    // of one k-group (one contiguous, conflict-free 128-byte span)
+    if (actA) {
+      const float4 p = *reinterpret_cast<const float4*>(Ist + srcA);
+      const float4 q = *reinterpret_cast<const float4*>(Ist + srcA + 4);
+      const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
       uint4 parts[NS];
       split8<NS>(v, parts);
 #pragma unroll
-      for (int p = 0; p < NS; ++p) *reinterpret_cast<uint4*>(Ap + p * kTcABytes + canon_off(row, kg)) = parts[p];
+      for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Ap + k * kTcABytes + dstA) = parts[k];
     }
     // B: rows = pairs (b, c) of this tile, products of the l = 0 fields
-    for (int seg = tid; seg < kTcN * (kTcKC / 8); seg += kTcThreads) {
-      const int kg = seg / kTcN, row = seg - kg * kTcN;
-      const short2 bc = pt[row];
-      float v[8];
-      if (bc.x >= 0) {
-        const float* fb = Ist + bc.x * kTcRow + kg * 8;
-        const float* fc = Ist + bc.y * kTcRow + kg * 8;
+    if (actB) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = fb[j] * fc[j];
-      } else {
+      for (int h = 0; h < 2; ++h) {
+        const float4 b0 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h);
+        const float4 b1 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h + 4);
+        const float4 c0 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h);
+        const float4 c1 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h + 4);
+        const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
+                            b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
+        uint4 parts[NS];
+        split8<NS>(v, parts);
+        const int d = h ? dstB1 : dstB0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Bp + k * kTcBBytes + d) = parts[k];
       }
-      uint4 parts[NS];
-      split8<NS>(v, parts);
-#pragma unroll
-      for (int p = 0; p < NS; ++p) *reinterpret_cast<uint4*>(Bp + p * kTcBBytes + canon_off(row, kg)) = parts[p];
     }
     fence_proxy_async();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && ok) {
       tc_fence_after();
       // products (i, j) of A part i and B part j whose order is at most 2^-16
       constexpr int NP = NS == 2 ? 3 : 6;
@@ -283,7 +324,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     // of chunk c - 1 have released (mbarrier wait), and reads a ring slot the
     // copies of chunk c + 1 filled; stage s is rebuilt only after this commit.
     if ((c + 1) % kTcDrain == 0 || c + 1 == nch) {
-      // drain: wait for this chunk's MMAs, add the tile to the registers
+      // drain: wait for this chunk's MMAs, add the tile to the running sum
       // (ok is made block-uniform: tcgen05.ld is a warp-collective)
       bool w = ok && mbar_wait(&bar[s], (uint32_t)((c >> 1) & 1), err, 16);
       ok = __syncthreads_and(w) != 0;
@@ -291,24 +332,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
       if (ok) {
 #pragma unroll
         for (int cg = 0; cg < 2; ++cg) {
-          float v[32];
-          tmem_ld32(taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 64 + cg * 32), v);
+          float v[32], u[32];
+          tmem_ld32(tcol + cg * 32, v);
+          tmem_ld32(tcol + kTcN + cg * 32, u);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[cg * 32 + i] += v[i];
+          for (int i = 0; i < 32; ++i) u[i] += v[i];
+          tmem_st32(tcol + kTcN + cg * 32, u);
         }
       }
       tc_fence_before();
       __syncthreads();
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   // the drain after the last chunk waited for every MMA of the slice
-  float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + lane) * kTcN + h2 * 64;
+  float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + (tid & 31)) * kTcN + h2 * 64;
 #pragma unroll
-  for (int i = 0; i < 64; i += 4)
-    *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+  for (int cg = 0; cg < 2; ++cg) {
+    float u[32];
+    tmem_ld32(tcol + kTcN + cg * 32, u);
+#pragma unroll
+    for (int i = 0; i < 32; i += 4)
+      *reinterpret_cast<float4*>(dst + cg * 32 + i) = make_float4(u[i], u[i + 1], u[i + 2], u[i + 3]);
+  }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(taddr, kTcN);
+  if (warp == 0) tmem_dealloc(taddr, 2 * kTcN);
 }
 
 // out[t * 3 + li] = sum over slices of D[m = li * S + a][n = pair(b, c)].
@@ -329,8 +378,7 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int nti
 
 template <int NS>
 static size_t tc_smem_bytes(int nf) {
-  return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * (size_t)nf * kTcRow + sizeof(short2) * kTcN +
-         2 * sizeof(uint64_t) + 16;
+  return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * (size_t)nf * kTcRow + 2 * sizeof(uint64_t) + 16;
 }
 
 cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, const short2* pairs, int npairs,
