@@ -59,7 +59,7 @@ struct BispState {
   double* d_shell = nullptr;
   long long* d_shellc = nullptr;
   // tensor-core contraction: columns = pairs (b >= c), outputs -> (row, column)
-  int npairs = 0, tc_slices = 0, tc_tiles = 0;
+  int npairs = 0, tc_slices = 0, tc_tiles = 0, tc_chunks = 0;
   short2* d_pairs = nullptr;
   int *d_om = nullptr, *d_on = nullptr;
   float* d_tcpart = nullptr;
@@ -575,8 +575,8 @@ int bisp_plan_init(Plan* P) {
       on[t * 3 + li] = pidx[(long long)st->tb[t] * S + st->tc[t]];
     }
   const long long N3 = (long long)N * N * N;
-  st->tc_slices = (int)((N3 + tc_slice_points() - 1) / tc_slice_points());
   st->tc_tiles = (st->npairs + tc_tile_cols() - 1) / tc_tile_cols();
+  tc_slicing(N3, std::max(1, st->tc_tiles), P->ctx->nsm, &st->tc_slices, &st->tc_chunks);
   const int iblocks = std::max<int>(1, ((int)st->items.size() + 255) / 256);
   st->nslices = std::max(1, (P->ctx->nsm * 8) / iblocks);
   st->slice_len = ((N3 + st->nslices - 1) / st->nslices + kCTK - 1) / kCTK * kCTK;
@@ -745,7 +745,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   const int ntri = P->ntri, nout = std::max(1, ntri) * 3;
   if (tensor && st->npairs > 0) {
     BCK(launch_contract_tc(st->d_I, N3, st->nl * S, S, st->d_pairs, st->npairs, st->d_tcpart, P->d_err + 1,
-                           st->tc_slices, contraction == FKP_CONTRACT_BF16X3 ? 2 : 3, s));
+                           st->tc_slices, st->tc_chunks, contraction == FKP_CONTRACT_BF16X3 ? 2 : 3, s));
     BCK(launch_tc_reduce(st->d_tcpart, st->tc_slices, st->tc_tiles, st->d_om, st->d_on, nout, st->d_T, s));
   } else if (!st->items.empty()) {
     const int nf = st->nl * S;

@@ -15,20 +15,29 @@
 // the triangle sums cancel strongly (sum |t| >> |sum t|), so the 3-way split
 // is the accurate mode and the 2-way split the fast one.
 //
-// One CTA of 16 warps per (256-column N tile, K slice of 65,536 points).
+// One CTA of 16 warps per (256-column N tile, K slice).  The slices (up to
+// about 4,096 chunks of 32 points) are sized at plan time so that tiles x
+// slices CTAs fill whole waves of the SMs.
 // The shell fields of a chunk of 32 points are fetched two chunks ahead with
 // cp.async into a 3-slot ring; operand stages are double buffered: all
 // threads form the products and the BF16 splits into K-major tiles with the
 // 64-byte swizzle (one 64-byte row of K per operand row); one thread issues
 // the tcgen05.mma instructions (M = 128, N = 256, K = 16) and commits them to
-// the stage's mbarrier.  Every 32 chunks (1,024 points) the 128 x 256 FP32
-// tile is read from tensor memory (tcgen05.ld; each warp its lane quarter and
-// 64 columns), added with round-to-nearest to a running FP32 sum held in the
-// other 256 tensor-memory columns (tcgen05.ld, add, tcgen05.st) and the MMA
-// accumulation restarts: long in-tensor-core accumulation runs were measured
-// to drift linearly with their length (5.6e-4 of the monopole scale over
-// 65,536 points, under 1e-4 over 1,024).  At the end of the slice the sums go
+// the stage's mbarrier.  After every run of 96 accumulating MMAs (16 chunks,
+// 8 for the 3-way split) the 128 x 256 FP32 tile is read from tensor memory
+// (tcgen05.ld; each warp its lane quarter and 64 columns), added with
+// round-to-nearest to a running FP32 sum held in the other 256 tensor-memory
+// columns (tcgen05.ld, add, tcgen05.st) and the MMA accumulation restarts.
+// In-tensor-core accumulation runs were measured to drift linearly with their
+// length (5.6e-4 of the monopole scale over 65,536 points, under 1e-4 over
+// 1,024).  With 1,024-point runs that rounding, not the operand split, set
+// the 3-way split's error (B_4 8.4e-5 of the FP32 contraction on a 64^3
+// case, above the 2-way split's 5.1e-5); with runs of 96 MMAs it is 6.7e-6.
+// The drain of a run waits until the next chunk's operands are built, so the
+// tensor pipe idles only for the drain.  At the end of the slice the sums go
 // to per-slice partials, summed over slices in FP64 by k_tc_reduce.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,7 +49,7 @@ namespace fkp {
 constexpr int kTcM = 128;              // MMA rows (l, a)
 constexpr int kTcN = 256;              // MMA columns (pairs b >= c) per tile
 constexpr int kTcKC = 32;              // K points per chunk
-constexpr int kTcChunks = 2048;        // chunks per K slice
+constexpr int kTcSliceTarget = 4096;   // chunks per K slice, at most (about)
 constexpr int kTcThreads = 512;
 constexpr int kTcABytes = kTcM * kTcKC * 2;    // one BF16 operand tile: 8 KB
 constexpr int kTcBBytes = kTcN * kTcKC * 2;    // 16 KB
@@ -48,8 +57,23 @@ template <int NS>
 __host__ __device__ constexpr int tc_stage_bytes() { return NS * (kTcABytes + kTcBBytes); }
 constexpr int kTcRow = kTcKC + 4;      // staged row stride (floats): 16-byte aligned, shifts banks by 4 per field
 
-constexpr int kTcDrain = 32;           // chunks per tensor-memory accumulation run
-long long tc_slice_points() { return (long long)kTcKC * kTcChunks; }
+// chunks per tensor-memory accumulation run: 96 accumulating MMAs per run for
+// every split (3 products x 2 K steps x 16 chunks; 6 x 2 x 8)
+template <int NS>
+__host__ __device__ constexpr int tc_drain() { return NS == 3 ? 8 : 16; }
+// K slicing: the fewest whole waves of the SMs (tiles x slices CTAs, one per
+// SM at a time) whose slices hold at most about kTcSliceTarget chunks; slices
+// of equal length (the last one shorter), none empty.
+void tc_slicing(long long N3, int ntiles, int nsm, int* nslices, int* chunks) {
+  const long long total = (N3 + kTcKC - 1) / kTcKC;
+  const long long per_wave = (long long)nsm * kTcSliceTarget;
+  const long long waves = std::max<long long>(1, (total * ntiles + per_wave - 1) / per_wave);
+  long long ns = std::max<long long>(1, waves * nsm / std::max(1, ntiles));
+  ns = std::min(ns, std::max<long long>(1, total));
+  const long long ch = (total + ns - 1) / ns;
+  *chunks = (int)ch;
+  *nslices = (int)((total + ch - 1) / ch);
+}
 int tc_tile_cols() { return kTcN; }
 int tc_rows() { return kTcM; }
 
@@ -122,6 +146,42 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// tcgen05.ld of 32 columns without the wait, and the wait that completes
+// every load in flight; the wait names the destination registers as in-out
+// operands so that no use of them is moved ahead of it.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+// tcgen05.st of 32 columns without the wait (tcgen05.wait::st completes it)
+__device__ __forceinline__ void tmem_st32_async(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+      ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+        "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+        "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand with the 64-byte swizzle.
 // Each row holds the chunk's 32 K values (64 bytes); 8 rows form a 512-byte
 // swizzle atom (sbo = 512 between atoms); the K steps of 16 advance the start
@@ -186,7 +246,8 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
 template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
                                                                int S, const short2* __restrict__ pairs, int npairs,
-                                                               float* __restrict__ part, int* __restrict__ err) {
+                                                               int chunks, float* __restrict__ part,
+                                                               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   constexpr int kStage = tc_stage_bytes<NS>();
   unsigned char* stage0 = smraw;                                  // 2 stages: A parts, then B parts
@@ -222,9 +283,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     tmem_st32(tcol + kTcN, z);
     tmem_st32(tcol + kTcN + 32, z);
   }
-  const long long x0 = (long long)slice * kTcKC * kTcChunks;
-  const long long xend = (x0 + (long long)kTcKC * kTcChunks < N3) ? x0 + (long long)kTcKC * kTcChunks : N3;
-  const int nch = (int)((xend - x0 + kTcKC - 1) / kTcKC);
+  const long long x0 = (long long)slice * kTcKC * chunks;
+  const long long xend = (x0 + (long long)kTcKC * chunks < N3) ? x0 + (long long)kTcKC * chunks : N3;
+  const int nch = x0 < xend ? (int)((xend - x0 + kTcKC - 1) / kTcKC) : 0;
   const uint32_t idesc = tc_idesc();
   // fixed roles
   const int rowA = tid & (kTcM - 1), kgA = tid / kTcM;
@@ -258,6 +319,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
                      : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // drain of the run ending with chunk cl: wait for that chunk's MMAs, add
+  // the tile to the running sum (ok is made block-uniform: tcgen05.ld is a
+  // warp-collective)
+  constexpr int kDrain = tc_drain<NS>();
+  auto drain = [&](int cl) {
+    const bool w = ok && mbar_wait(&bar[cl & 1], (uint32_t)((cl >> 1) & 1), err, 16);
+    ok = __syncthreads_and(w) != 0;
+    tc_fence_after();
+    if (ok) {
+      // per 32 columns: both loads, one wait, add, store; one store wait
+#pragma unroll
+      for (int cg = 0; cg < 2; ++cg) {
+        uint32_t v[32], u[32];
+        tmem_ld32_async(tcol + cg * 32, v);
+        tmem_ld32_async(tcol + kTcN + cg * 32, u);
+        tmem_wait_ld(v);
+        tmem_wait_ld(u);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) u[i] = __float_as_uint(__uint_as_float(u[i]) + __uint_as_float(v[i]));
+        tmem_st32_async(tcol + kTcN + cg * 32, u);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
   };
   prefetch(0);
   prefetch(1);
@@ -302,6 +389,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     }
     fence_proxy_async();
     __syncthreads();
+    // a run ended with chunk c - 1: its MMAs ran while this chunk was built,
+    // so the tensor pipe waits only for the drain, not for a build
+    if (c > 0 && c % kDrain == 0) drain(c - 1);
     if (tid == 0 && ok) {
       tc_fence_after();
       // products (i, j) of A part i and B part j whose order is at most 2^-16
@@ -315,7 +405,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
         for (int q = 0; q < NP; ++q) {
           const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 32, 16, 512);
           const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 32, 16, 512);
-          umma_bf16(taddr, ad, bd, idesc, ((c % kTcDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
+          umma_bf16(taddr, ad, bd, idesc, ((c % kDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
         }
       }
       umma_commit(&bar[s]);
@@ -323,29 +413,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     // No barrier here: the next chunk builds the other stage, which the MMAs
     // of chunk c - 1 have released (mbarrier wait), and reads a ring slot the
     // copies of chunk c + 1 filled; stage s is rebuilt only after this commit.
-    if ((c + 1) % kTcDrain == 0 || c + 1 == nch) {
-      // drain: wait for this chunk's MMAs, add the tile to the running sum
-      // (ok is made block-uniform: tcgen05.ld is a warp-collective)
-      bool w = ok && mbar_wait(&bar[s], (uint32_t)((c >> 1) & 1), err, 16);
-      ok = __syncthreads_and(w) != 0;
-      tc_fence_after();
-      if (ok) {
-#pragma unroll
-        for (int cg = 0; cg < 2; ++cg) {
-          float v[32], u[32];
-          tmem_ld32(tcol + cg * 32, v);
-          tmem_ld32(tcol + kTcN + cg * 32, u);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) u[i] += v[i];
-          tmem_st32(tcol + kTcN + cg * 32, u);
-        }
-      }
-      tc_fence_before();
-      __syncthreads();
-    }
   }
+  if (nch > 0) drain(nch - 1);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
-  // the drain after the last chunk waited for every MMA of the slice
+  // the last drain waited for every MMA of the slice
   float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + (tid & 31)) * kTcN + h2 * 64;
 #pragma unroll
   for (int cg = 0; cg < 2; ++cg) {
@@ -382,16 +453,17 @@ static size_t tc_smem_bytes(int nf) {
 }
 
 cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, const short2* pairs, int npairs,
-                               float* part, int* err, int nslices, int nsplit, cudaStream_t s) {
+                               float* part, int* err, int nslices, int chunks, int nsplit, cudaStream_t s) {
   const int ntiles = (npairs + kTcN - 1) / kTcN;
+  const dim3 grid(ntiles, nslices);
   if (nsplit == 2) {
     const size_t sm = tc_smem_bytes<2>(nf);
     raise_smem_limit((const void*)k_contract_tc<2>, sm);
-    k_contract_tc<2><<<dim3(ntiles, nslices), kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, part, err);
+    k_contract_tc<2><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   } else {
     const size_t sm = tc_smem_bytes<3>(nf);
     raise_smem_limit((const void*)k_contract_tc<3>, sm);
-    k_contract_tc<3><<<dim3(ntiles, nslices), kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, part, err);
+    k_contract_tc<3><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   }
   return cudaGetLastError();
 }

@@ -86,9 +86,10 @@ def test_hi_lo_split_follows_its_error_model(small_b):
     triangle sum random-walks to ~2^-17 sqrt(sum_x t^2), t = F_a^(l) F_b^(0)
     F_c^(0) (measured spread: median 0.4-0.7, max 3.6 of those units with
     256-point tensor-memory runs).  The FP32 rounding of the tensor-memory
-    accumulation over 1,024-point runs (192 accumulating MMAs per run for the
-    2-way split, 384 for the 3-way one) adds to the difference of the two
-    splits (max 6.3 units on this case).  Against the 3-way split on the same
+    accumulation (runs of 96 accumulating MMAs: 512 points for the 2-way
+    split, 256 for the 3-way one) adds to the difference of the two splits
+    (max 6.3 units on this case with 1,024-point runs, 1.6 with these runs).
+    Against the 3-way split on the same
     fields, every triangle sum (N_T >= 100, l = 0, 2, 4) stays within 8 units;
     the shell fields for sum_x t^2 come from the oracle."""
     fkp = _fkp()
