@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--small-steps", type=int, default=200, help="timed 64^3 mocks per mode (0 skips that leg)")
     ap.add_argument("--batch-mocks", type=int, default=32, help="mocks in the batched leg (0 skips it)")
+    ap.add_argument("--fused-mocks", type=int, default=64,
+                    help="64^3 mocks per fused call in the fused leg (0 skips it; 256^3: a quarter)")
     return ap.parse_args()
 
 
@@ -380,6 +382,9 @@ def run_gpu(args):
     if args.batch_mocks > 0 and world == 1:
         torch.cuda.empty_cache()
         line["batch"] = run_batch(args)
+    if args.fused_mocks > 0 and world == 1:
+        torch.cuda.empty_cache()
+        line["fused"] = run_fused(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_mock, desc, _ = oracle_sample(gal, ran, sv, 1)
         line["cpu_baseline"] = {"value": 1.0 / t_mock, "unit": "mocks/s", "cores": cores_used(), "kind": "oracle",
@@ -468,6 +473,83 @@ def run_bisp(args, gal, ran, dg, dr, stream):
                        "bf16x3_tcgen05": "random per-product error ~2^-18 (triangle sums within 6 x 2^-17 "
                                          "sqrt(sum_x t^2) of the 3-way split)"}
     plan.close()
+    return out
+
+
+def _fused_vs_single(plan, mocks, reps):
+    """mocks/s of plan.power_batch over all mocks against one plan.power call
+    per mock (device catalogs), and their largest P_l difference."""
+    import torch
+    gals, rans = [m[0] for m in mocks], [m[1] for m in mocks]
+    plan.power_batch(gals, rans)  # the batch workspace
+    for g, r in mocks:
+        plan.power(g, r)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fused = plan.power_batch(gals, rans)
+    tf = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        single = [plan.power(g, r) for g, r in mocks]
+    ts = (time.perf_counter() - t0) / reps
+    diff = max(_rel_diff(a, b, ("P0", "P2", "P4"), np.abs(b["mono_raw"])) for a, b in zip(fused, single))
+    st = fused[0]["timing_ms"]
+    plan.close()
+    return {"mocks": len(mocks), "fused_mocks_per_s": len(mocks) / tf, "single_mocks_per_s": len(mocks) / ts,
+            "fused_stage_ms": {"gridding_all": float(st[1]), "xpass": float(st[2]), "ypass": float(st[3]),
+                               "zpass_and_bins": float(st[4]), "total": float(st[7])},
+            "fused_vs_single_max_rel_diff_P": diff}
+
+
+def run_fused(args):
+    """Several mocks per call (fkp_power_batch: each mock gridded with launches
+    shaped by its own catalogs, then one launch per FFT pass and one bin
+    reduction for all of them) against one fkp_power call per mock, on two
+    ensembles of uneven mocks: the small survey (64^3 CIC; each mock a random
+    50-100 % subsample of 2e4 galaxies and of 2e5 randoms), where launches and
+    the per-call synchronisation dominate, and BOSS-like mocks on a 256^3 grid
+    (N_g uniform in [5e5, 1.2e6], a random subsample of a 1.2e6-galaxy master
+    catalog, and 30 N_g randoms).  Device catalogs on both paths; P_0,2,4."""
+    import dataclasses
+
+    import torch
+
+    import mockgen
+    import paper_1506_02729_gb300 as fkp
+    g = np.random.default_rng(args.seed + 700)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(args.seed + 701)
+
+    def subsample(cat, n_keep):
+        idx = torch.sort(torch.randperm(cat["x"].numel(), device="cuda", generator=gen)[:n_keep]).values
+        return {k: v[idx].contiguous() for k, v in cat.items()}
+
+    want = fkp.FKP_P0 | fkp.FKP_P2 | fkp.FKP_P4
+    out = {"unit": "mocks/s", "path": "fkp_power_batch vs fkp_power per mock"}
+    sv = mockgen.survey_small()
+    gal, ran = mockgen.catalog(sv, args.seed + 702)
+    dg = {k: torch.from_numpy(v).cuda() for k, v in gal.items()}
+    dr = {k: torch.from_numpy(v).cuda() for k, v in ran.items()}
+    ms = [(subsample(dg, int(g.uniform(0.5, 1.0) * gal["x"].size)), subsample(dr, int(g.uniform(0.5, 1.0) *
+                                                                                        ran["x"].size)))
+          for _ in range(args.fused_mocks)]
+    kf = 2 * np.pi / sv.L
+    out["small"] = dict(workload=f"{len(ms)} small-survey mocks, 64^3 CIC, 1e4-2e4 galaxies + 1e5-2e5 randoms",
+                        **_fused_vs_single(fkp.Plan(sv.geometry(), (0.5 * kf, kf, 32), want=want), ms, 5))
+    del ms, dg, dr
+    base = mockgen.survey_boss(N=256)
+    svb = dataclasses.replace(base, nbar_peak=base.nbar_peak * 1.2e6 / 7.0e5, random_ratio=30.0)
+    gal, ran = mockgen.catalog(svb, args.seed + 703)
+    dg = {k: torch.from_numpy(v).cuda() for k, v in gal.items()}
+    dr = {k: torch.from_numpy(v).cuda() for k, v in ran.items()}
+    ms = []
+    for _ in range(max(1, args.fused_mocks // 4)):
+        ng = int(min(gal["x"].size, g.uniform(5e5, 1.2e6)))
+        ms.append((subsample(dg, ng), subsample(dr, min(ran["x"].size, 30 * ng))))
+    del dg, dr
+    out["boss_256"] = dict(workload=f"{len(ms)} BOSS-like mocks, 256^3 TSC, N_g in [5e5, 1.2e6] + 30x randoms",
+                           **_fused_vs_single(fkp.Plan(svb.geometry(), BINS, want=want), ms, 3))
     return out
 
 

@@ -179,6 +179,23 @@ int fkp_plan_set_graphs(void *plan, int enable);
 int fkp_power(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
               void *cuda_stream, fkp_power_out *out);
 
+/* P_l of nmock independent surveys (mocks) on one plan's grid, for the
+ * ensembles that covariance estimates need (abstract; Sec. III.C, Performance): gals[k] and
+ * rans[k] (host or device, any sizes, randoms non-empty) give mock k, whose
+ * results go to outs[k] (NULL: none).  Each mock is gridded with launches
+ * shaped by its own catalogs; then the three FFT passes and the bin
+ * reduction run once for all mocks (one launch each, the mock index in the
+ * grid).  Every mock's results are those of fkp_power on the same catalogs:
+ * the same grid and scalars, bins equal up to the run-to-run order of the
+ * FP32 per-block sums (~1e-7).  The plan keeps a batch workspace (grid, pass buffers and bins
+ * per mock: about 15 GB per mock at 512^3, 1.9 GB at 256^3) sized for the
+ * largest nmock seen; FKP_ENOMEM when that exceeds the context's HBM budget
+ * or the device.  Stage times in outs[k].timing_ms are those of the whole
+ * batch: [1] gridding of all mocks, [2..4] the fused x, y, z passes (z with
+ * the bin reduction), [7] the whole batch.  nmock: 1 .. 65535. */
+int fkp_power_batch(void *plan, int nmock, const fkp_catalog_t *gals, const fkp_catalog_t *rans,
+                    void *cuda_stream, fkp_power_out *outs);
+
 /* The same estimator applied to a given real field F(x) (device pointer to
  * N^3 float32, layout [z][y][x]), with caller-supplied I_22 and N_0.  Test
  * hook for periodic-box checks. */

@@ -26,7 +26,7 @@ EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_
            "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version",
            "fkp_power_from_grid_noalloc", "fkp_server_create", "fkp_server_submit", "fkp_server_poll",
            "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy", "fkp_check_tables",
-           "fkp_plan_set_graphs", "fkp_plan_schedule", "fkp_plan_set_schedule"]
+           "fkp_plan_set_graphs", "fkp_plan_schedule", "fkp_plan_set_schedule", "fkp_power_batch"]
 
 
 class FKPError(RuntimeError):
@@ -105,6 +105,7 @@ def lib():
         L.fkp_plan_sizes.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.fkp_power.argtypes = [vp, C.POINTER(Catalog), C.POINTER(Catalog), vp, C.POINTER(PowerOut)]
         L.fkp_power_from_grid.argtypes = [vp, vp, C.c_double, C.c_double, vp, C.POINTER(PowerOut)]
+        L.fkp_power_batch.argtypes = [vp, C.c_int, C.POINTER(Catalog), C.POINTER(Catalog), vp, C.POINTER(PowerOut)]
         L.fkp_bispectrum.argtypes = [vp, C.POINTER(Catalog), C.POINTER(Catalog), C.c_int, vp, C.POINTER(PowerOut),
                                      C.POINTER(BispOut)]
         L.fkp_power_from_grid_noalloc.argtypes = [C.POINTER(Geometry), C.POINTER(PBins), vp, C.c_double,
@@ -275,6 +276,27 @@ class Plan:
         o, arr = self._pout()
         _check(lib().fkp_power(self._h, C.byref(cg), C.byref(cr), _stream_handle(stream), C.byref(o)))
         return self._scalars(o, arr)
+
+    def power_batch(self, gals, rans, stream=None):
+        """P_0, P_2, P_4, P_4b and the scalars of several mocks on this plan's
+        grid: each mock gridded on its own, then one launch per FFT pass for
+        all of them.  Returns one result dict per mock."""
+        if len(gals) != len(rans) or not gals:
+            raise ValueError("need equal, non-zero numbers of galaxy and random catalogs")
+        n = len(gals)
+        cg, cr, keep = (Catalog * n)(), (Catalog * n)(), []
+        for k in range(n):
+            cg[k], k1 = make_catalog(gals[k])
+            cr[k], k2 = make_catalog(rans[k])
+            keep += [k1, k2]
+        outs = (PowerOut * n)()
+        arrs = []
+        for k in range(n):
+            o, arr = self._pout()
+            outs[k] = o
+            arrs.append(arr)
+        _check(lib().fkp_power_batch(self._h, n, cg, cr, _stream_handle(stream), outs))
+        return [self._scalars(outs[k], arrs[k]) for k in range(n)]
 
     def power_from_grid(self, F, I22=1.0, N0=0.0, stream=None):
         """The estimator on a given device field F (torch float32 CUDA tensor

@@ -282,6 +282,7 @@ fkp::Plan::~Plan() {
   if (d_xyzv) cudaFree(d_xyzv);
   if (d_vw2) cudaFree(d_vw2);
   if (h_pinned) cudaFreeHost(h_pinned);
+  if (batch_mem) cudaFree(batch_mem);
   for (auto& e : ev) if (e) cudaEventDestroy(e);
 }
 
@@ -845,6 +846,162 @@ extern "C" int fkp_power(void* plan, const fkp_catalog_t* gal, const fkp_catalog
   rc = finish_power(P, s, out, true, 0, 0);
   if (out) out->graph = replayed;
   return rc;
+}
+
+// Per-mock element counts of the fused batch workspace.
+namespace {
+struct BatchSizes {
+  size_t grid, s1, s2, zpart, zpartc, bins, binc, ds, err;
+};
+BatchSizes batch_sizes(const fkp::Plan* P) {
+  const size_t N = (size_t)P->g.N, half = fkp::field_elems(P->g.N);
+  BatchSizes z;
+  z.grid = N * N * N;
+  z.s1 = half * P->mt.nfields;
+  z.s2 = half * P->mt.ngroups;
+  z.zpart = (size_t)BQ_N * P->pb.nbins * P->nblk_z;
+  z.zpartc = (size_t)P->pb.nbins * P->nblk_z;
+  z.bins = (size_t)BQ_N * P->pb.nbins;
+  z.binc = (size_t)P->pb.nbins;
+  z.ds = DS_COUNT + LAB_NSUM + 8;
+  z.err = 4;
+  return z;
+}
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+// Sizes (and on request allocates) the fused batch workspace for nmock mocks.
+static int reserve_batch(fkp::Plan* P, int nmock) {
+  using namespace fkp;
+  if (P->batch_cap >= nmock) return FKP_OK;
+  const BatchSizes z = batch_sizes(P);
+  const size_t K = (size_t)nmock;
+  const size_t parts[9] = {align256(K * z.grid * 8),  align256(K * z.s1 * 8),     align256(K * z.s2 * 8),
+                           align256(K * z.zpart * 8), align256(K * z.zpartc * 4), align256(K * z.bins * 8),
+                           align256(K * z.binc * 8),  align256(K * z.ds * 8),     align256(K * z.err * 4)};
+  size_t tot = 0;
+  for (size_t b : parts) tot += b;
+  if (P->ctx->budget && P->bytes_total + tot > P->ctx->budget)
+    return set_error(FKP_ENOMEM, "a batch of %d mocks needs %.2f GB beyond the plan's %.2f GB, over the HBM budget",
+                     nmock, tot / 1e9, P->bytes_total / 1e9);
+  if (P->batch_mem) cudaFree(P->batch_mem);
+  P->batch_mem = nullptr;
+  P->batch_cap = 0;
+  P->batch_bytes = 0;
+  if (cudaMalloc(&P->batch_mem, tot) != cudaSuccess) {
+    cudaGetLastError();
+    P->batch_mem = nullptr;
+    return set_error(FKP_ENOMEM, "cannot allocate %.2f GB for a batch of %d mocks", tot / 1e9, nmock);
+  }
+  char* m = static_cast<char*>(P->batch_mem);
+  P->b_grid = reinterpret_cast<unsigned long long*>(m);  m += parts[0];
+  P->b_S1 = reinterpret_cast<float2*>(m);                m += parts[1];
+  P->b_S2 = reinterpret_cast<float2*>(m);                m += parts[2];
+  P->b_zpart = reinterpret_cast<double*>(m);             m += parts[3];
+  P->b_zpartc = reinterpret_cast<int*>(m);               m += parts[4];
+  P->b_bins = reinterpret_cast<double*>(m);              m += parts[5];
+  P->b_binc = reinterpret_cast<long long*>(m);           m += parts[6];
+  P->b_ds = reinterpret_cast<double*>(m);                m += parts[7];
+  P->b_err = reinterpret_cast<int*>(m);
+  P->batch_cap = nmock;
+  P->batch_bytes = tot;
+  return FKP_OK;
+}
+
+extern "C" int fkp_power_batch(void* plan, int nmock, const fkp_catalog_t* gals, const fkp_catalog_t* rans,
+                               void* stream, fkp_power_out* outs) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P) return set_error(FKP_EINVAL, "NULL plan");
+  if (nmock < 1 || nmock > 65535) return set_error(FKP_EINVAL, "nmock = %d (1 .. 65535)", nmock);
+  if (!gals || !rans) return set_error(FKP_EINVAL, "NULL catalog array");
+  CK(cudaSetDevice(P->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = reserve_batch(P, nmock);
+  if (rc) return rc;
+  const BatchSizes z = batch_sizes(P);
+  // gridding, mock by mock (each launch shaped by its own catalogs), into the
+  // mock's grid, scalars and flags
+  unsigned long long* const grid0 = P->d_grid;
+  double* const ds0 = P->d_ds;
+  int* const err0 = P->d_err;
+  CK(cudaEventRecord(P->ev[9], s));
+  for (int k = 0; k < nmock; ++k) {
+    CatDev g, r;
+    rc = stage_catalog(P, &gals[k], 0, g, s);
+    if (!rc) rc = stage_catalog(P, &rans[k], 1, r, s);
+    if (!rc && r.n == 0) rc = set_error(FKP_EINVAL, "mock %d: the random catalog is empty", k);
+    if (rc) return rc;
+    P->d_grid = P->b_grid + k * z.grid;
+    P->d_ds = P->b_ds + k * z.ds;
+    P->d_err = P->b_err + k * z.err;
+    rc = enqueue_grids(P, g, r, s);
+    P->d_grid = grid0;
+    P->d_ds = ds0;
+    P->d_err = err0;
+    if (rc) return rc;
+  }
+  // the three FFT passes and the bin reduction: one launch each for all mocks
+  // (blockIdx.z / blockIdx.y = mock); bounded-wait flags go to mock 0's word
+  int* perr = P->b_err + 1;
+  MockBatch mx;
+  mx.n = nmock; mx.in = (long long)z.grid; mx.out = (long long)z.s1;
+  CK(launch_xpass(P->b_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->b_S1, P->ctx->nsm, s, P->sched.x_mult, mx));
+  CK(cudaEventRecord(P->ev[3], s));
+  MockBatch my;
+  my.n = nmock; my.in = (long long)z.s1; my.in2 = (long long)z.grid; my.out = (long long)z.s2;
+  CK(launch_ypass(P->b_S1, P->b_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->b_S2, perr, s, P->sched.y_threads,
+                  my));
+  CK(cudaEventRecord(P->ev[4], s));
+  ZParams zp;
+  zp.nbins = P->pb.nbins;
+  zp.lmax = P->lmax;
+  zp.kf = (float)(2.0 * M_PI / P->geom.L);
+  zp.lut = P->d_lut;
+  zp.winv = P->d_winv;
+  zp.mode = 0;
+  zp.nshells = 0;
+  zp.nsh2 = 0;
+  zp.slut = nullptr;
+  zp.E = nullptr;
+  zp.mm = 0;
+  MockBatch mz;
+  mz.n = nmock; mz.in = (long long)z.s2; mz.out = (long long)z.zpart; mz.out2 = (long long)z.zpartc;
+  CK(launch_zpass(P->b_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->b_zpart, P->b_zpartc, perr, s, P->ctx->nsm,
+                  P->sched.z_threads, mz));
+  CK(launch_reduce_bins(P->b_zpart, P->b_zpartc, zpass_blocks(P->g.N, P->sched.z_threads, P->ctx->nsm), P->pb.nbins,
+                        P->b_bins, P->b_binc, s, nmock, (long long)z.zpart, (long long)z.zpartc));
+  CK(cudaEventRecord(P->ev[5], s));
+  // bins and scalars back, mock by mock
+  double* const bins0 = P->d_bins;
+  long long* const binc0 = P->d_binc;
+  float tg = 0.f, tx = 0.f, ty = 0.f, tz = 0.f, tt = 0.f;
+  for (int k = 0; k < nmock; ++k) {
+    P->d_bins = P->b_bins + k * z.bins;
+    P->d_binc = P->b_binc + k * z.binc;
+    P->d_ds = P->b_ds + k * z.ds;
+    P->d_err = P->b_err + k * z.err;
+    rc = finish_power(P, s, outs ? &outs[k] : nullptr, true, 0, 0);
+    P->d_bins = bins0;
+    P->d_binc = binc0;
+    P->d_ds = ds0;
+    P->d_err = err0;
+    if (rc) return rc;
+    if (k == 0) {
+      cudaEventElapsedTime(&tg, P->ev[9], P->ev[2]);
+      cudaEventElapsedTime(&tx, P->ev[2], P->ev[3]);
+      cudaEventElapsedTime(&ty, P->ev[3], P->ev[4]);
+      cudaEventElapsedTime(&tz, P->ev[4], P->ev[5]);
+      cudaEventElapsedTime(&tt, P->ev[9], P->ev[5]);
+      cudaGetLastError();
+    }
+    if (outs) {
+      // stage times of the whole batch
+      float* t = outs[k].timing_ms;
+      t[0] = 0.f; t[1] = tg; t[2] = tx; t[3] = ty; t[4] = tz; t[5] = t[6] = 0.f; t[7] = tt;
+      outs[k].graph = 0;
+    }
+  }
+  return FKP_OK;
 }
 
 extern "C" int fkp_power_from_grid(void* plan, const float* F, double I22, double N0, void* stream,

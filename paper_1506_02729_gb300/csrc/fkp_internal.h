@@ -85,6 +85,18 @@ struct Plan {
   bool last_valid = false;
   int graph_launches = 0;
 
+  // fused multi-mock power (fkp_power_batch): one allocation holding, for up
+  // to batch_cap mocks, the grids, pass buffers, partial and final bins,
+  // scalars and flags, each mock's at a fixed stride from the first's
+  int batch_cap = 0;
+  void* batch_mem = nullptr;
+  size_t batch_bytes = 0;
+  unsigned long long* b_grid = nullptr;
+  float2 *b_S1 = nullptr, *b_S2 = nullptr;
+  double *b_zpart = nullptr, *b_bins = nullptr, *b_ds = nullptr;
+  int *b_zpartc = nullptr, *b_err = nullptr;
+  long long* b_binc = nullptr;
+
   std::vector<void*> buffers;
   size_t bytes_total = 0;
   void* alloc(size_t bytes);
@@ -123,20 +135,24 @@ cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xy
                               unsigned long long* grid, unsigned long long* gridw, cudaStream_t s);
 cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
 // xm: x-pass blocks = SMs x resident blocks x xm; nt: threads per y- or
-// z-pass block (256 or 512).  The defaults are the 512^3 choices.
+// z-pass block (256 or 512).  The defaults are the 512^3 choices.  mb: the
+// mocks of one fused launch (blockIdx.z) and their buffer strides.
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
-                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm = 2);
+                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm = 2,
+                         MockBatch mb = MockBatch());
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp,
-                         const float2* tw, float2* S2, int* err, cudaStream_t s, int nt = 256);
+                         const float2* tw, float2* S2, int* err, cudaStream_t s, int nt = 256,
+                         MockBatch mb = MockBatch());
 // The z-pass is persistent: zpass_blocks(N, nt, nsm) blocks, each writing
 // one column of the partial bins (part[key][block]); reduce over that count.
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
-                         int nsm, int nt = 512);
+                         int nsm, int nt = 512, MockBatch mb = MockBatch());
 int zpass_blocks(int N, int nt, int nsm);
 cudaError_t launch_reduce_bins(const double* part, const int* partc, int nblk, int nbins, double* out,
-                               long long* outc, cudaStream_t s);
+                               long long* outc, cudaStream_t s, int nmock = 1, long long pstride = 0,
+                               long long pcstride = 0);
 
 // tensor-core triangle contraction (k_contract_tc.cu)
 void tc_slicing(long long N3, int ntiles, int nsm, int* nslices, int* chunks);

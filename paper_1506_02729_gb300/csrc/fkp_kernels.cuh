@@ -68,6 +68,17 @@ enum { BQ_K = 0, BQ_F00, BQ_F20, BQ_F40, BQ_F22, BQ_N };
 enum { SQ_00 = 0, SQ_20, SQ_40, SQ_02, SQ_04 };
 
 // z-pass parameters.
+// Several mocks of one plan in one launch of an FFT pass: blockIdx.z picks the
+// mock, whose buffers lie at fixed element strides from the first mock's.
+// n = 1 (strides unused) is the single-mock launch.
+struct MockBatch {
+  int n = 1;
+  long long in = 0;    // stride of the pass's input (x: grid; y: S1; z: S2)
+  long long in2 = 0;   // y: stride of the grid (observer-node value)
+  long long out = 0;   // stride of the output (x: S1; y: S2; z: partial bin sums)
+  long long out2 = 0;  // z: stride of the partial bin counts
+};
+
 struct ZParams {
   int nbins;
   int lmax;          // 0, 2 or 4

@@ -98,7 +98,10 @@ template <int N_, int LMAX>
 __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 1 : (N_ > 0 && N_ <= 256 ? 4 : 3))
     k_xpass2(
     const unsigned long long* __restrict__ gq, const float* __restrict__ gf, GeomDev g, FftPlan fp,
-    const float2* __restrict__ twg, float2* __restrict__ S1) {
+    const float2* __restrict__ twg, float2* __restrict__ S1, MockBatch mb) {
+  if (gq) gq += (long long)blockIdx.z * mb.in;
+  if (gf) gf += (long long)blockIdx.z * mb.in;
+  S1 += (long long)blockIdx.z * mb.out;
   constexpr int NF = nfields_of(LMAX);
   constexpr int NP = (NF + 1) / 2;
   constexpr int NTX = 32 * NP;
@@ -195,7 +198,11 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
                                                    const unsigned long long* __restrict__ gq,
                                                    const float* __restrict__ gf, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg,
-                                                   float2* __restrict__ S2, int* __restrict__ err) {
+                                                   float2* __restrict__ S2, int* __restrict__ err, MockBatch mb) {
+  S1 += (long long)blockIdx.z * mb.in;
+  if (gq) gq += (long long)blockIdx.z * mb.in2;
+  if (gf) gf += (long long)blockIdx.z * mb.in2;
+  S2 += (long long)blockIdx.z * mb.out;
   extern __shared__ __align__(128) unsigned char smraw[];
   const int N = N_ ? N_ : g.N;
   const int NH = N / 2 + 1, NXT = (NH + kT - 1) / kT;
@@ -371,7 +378,10 @@ template <int N_, int MODE, int NT>
 __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg, ZParams zp,
                                                    double* __restrict__ part, int* __restrict__ partc,
-                                                   int* __restrict__ err) {
+                                                   int* __restrict__ err, MockBatch mb) {
+  S2 += (long long)blockIdx.z * mb.in;
+  part += (long long)blockIdx.z * mb.out;
+  partc += (long long)blockIdx.z * mb.out2;
   extern __shared__ __align__(128) unsigned char smraw[];
   const int N = N_ ? N_ : g.N;
   const int NH = N / 2 + 1, NXT = (NH + kT - 1) / kT;
@@ -587,7 +597,7 @@ int zpass_blocks(int N, int nt, int nsm) {
 
 template <int N_, int LMAX>
 static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                        const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm) {
+                        const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb) {
   constexpr int NP = (nfields_of(LMAX) + 1) / 2;
   const size_t sm = xsm(g.N, NP);
   raise_smem_limit((const void*)k_xpass2<N_, LMAX>, sm);
@@ -595,112 +605,115 @@ static cudaError_t xrun(const unsigned long long* gq, const float* gf, const Geo
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, LMAX>, 32 * NP, sm);
   int grid = nsm * (occ > 0 ? occ : 1) * (xm > 0 ? xm : 2);
   if (grid > g.N * g.N) grid = g.N * g.N;
-  k_xpass2<N_, LMAX><<<grid, dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1);
+  k_xpass2<N_, LMAX><<<dim3(grid, 1, mb.n), dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1, mb);
   return cudaGetLastError();
 }
 
 template <int LMAX>
 static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm) {
+                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb) {
   if (LMAX == 4) {
     switch (g.N) {
-      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
-      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
-      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
-      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
-      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
-      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
       default: break;
     }
   }
-  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
 }
 
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
-                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm) {
-  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm);
-  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm);
-  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm);
+                         const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm,
+                         MockBatch mb) {
+  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
 }
 
 template <int N_, int NT>
 static cudaError_t yrun_nt(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                            const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                           cudaStream_t s) {
+                           cudaStream_t s, const MockBatch& mb) {
   const size_t sm = ysm(g.N);
   raise_smem_limit((const void*)k_ypass2<N_, NT>, sm);
-  k_ypass2<N_, NT><<<dim3(tiles_x(g.N), g.N), dim3(kT, NT / kT), sm, s>>>(S1, gq, gf, g, mt, fp, tw, S2, err);
+  k_ypass2<N_, NT><<<dim3(tiles_x(g.N), g.N, mb.n), dim3(kT, NT / kT), sm, s>>>(S1, gq, gf, g, mt, fp, tw, S2, err,
+                                                                                    mb);
   return cudaGetLastError();
 }
 
 template <int N_>
 static cudaError_t yrun(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                         const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                        cudaStream_t s, int nt) {
-  return nt == 512 ? yrun_nt<N_, 512>(S1, gq, gf, g, mt, fp, tw, S2, err, s)
-                   : yrun_nt<N_, 256>(S1, gq, gf, g, mt, fp, tw, S2, err, s);
+                        cudaStream_t s, int nt, const MockBatch& mb) {
+  return nt == 512 ? yrun_nt<N_, 512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb)
+                   : yrun_nt<N_, 256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb);
 }
 
 // gq / gf: the grid the x-pass read (for the observer node's value).
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                         cudaStream_t s, int nt) {
+                         cudaStream_t s, int nt, MockBatch mb) {
   switch (g.N) {
-    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
-    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
-    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
-    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
-    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
-    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
-    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt);
+    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
   }
 }
 
 template <int N_, int MODE, int NT>
 static cudaError_t zrun_nt(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
-                           const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s, int nsm) {
+                           const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
+                           int nsm, const MockBatch& mb) {
   const size_t sm = zsm(g.N, MODE == 2 ? zp.nshells : zp.nbins);
   raise_smem_limit((const void*)k_zpass2<N_, MODE, NT>, sm);
-  k_zpass2<N_, MODE, NT><<<zpass_blocks(g.N, NT, nsm), dim3(kT, NT / kT), sm, s>>>(S2, g, mt, fp, tw, zp, part,
-                                                                                    partc, err);
+  k_zpass2<N_, MODE, NT><<<dim3(zpass_blocks(g.N, NT, nsm), 1, mb.n), dim3(kT, NT / kT), sm, s>>>(
+      S2, g, mt, fp, tw, zp, part, partc, err, mb);
   return cudaGetLastError();
 }
 
 template <int N_, int MODE>
 static cudaError_t zrun(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                         const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
-                        int nsm, int nt) {
-  return nt == 256 ? zrun_nt<N_, MODE, 256>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm)
-                   : zrun_nt<N_, MODE, 512>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm);
+                        int nsm, int nt, const MockBatch& mb) {
+  return nt == 256 ? zrun_nt<N_, MODE, 256>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, mb)
+                   : zrun_nt<N_, MODE, 512>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, mb);
 }
 
 template <int MODE>
 static cudaError_t zdispatch(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                              const float2* tw, const ZParams& zp, double* part, int* partc, int* err,
-                             cudaStream_t s, int nsm, int nt) {
+                             cudaStream_t s, int nsm, int nt, const MockBatch& mb) {
   switch (g.N) {
-    case 512: return zrun<512, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
-    case 360: return zrun<360, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
-    case 256: return zrun<256, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+    case 512: return zrun<512, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
+    case 360: return zrun<360, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
+    case 256: return zrun<256, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
     default: break;
   }
   if (MODE == 0) {
     switch (g.N) {
-      case 384: return zrun<384, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
-      case 128: return zrun<128, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
-      case 64: return zrun<64, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+      case 384: return zrun<384, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
+      case 128: return zrun<128, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
+      case 64: return zrun<64, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
       default: break;
     }
   }
-  return zrun<0, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+  return zrun<0, MODE>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
 }
 
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, const ZParams& zp, double* part, int* partc, int* err, cudaStream_t s,
-                         int nsm, int nt) {
-  if (zp.mode == 0) return zdispatch<0>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
-  if (zp.mode == 1) return zdispatch<1>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
-  return zdispatch<2>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt);
+                         int nsm, int nt, MockBatch mb) {
+  if (zp.mode == 0) return zdispatch<0>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
+  if (zp.mode == 1) return zdispatch<1>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
+  return zdispatch<2>(S2, g, mt, fp, tw, zp, part, partc, err, s, nsm, nt, mb);
 }
 
 }  // namespace fkp

@@ -57,9 +57,16 @@ __global__ void k_lab_finalize(const double* __restrict__ labpart, int nblk, dou
 }
 
 // One block per (quantity, bin): fixed-order FP64 tree sum over the blocks.
+// blockIdx.y picks the mock of a fused launch (partials at pstride / pcstride,
+// bins contiguous per mock).
 __global__ void __launch_bounds__(256) k_reduce_bins(const double* __restrict__ part, const int* __restrict__ partc,
                                                      int nblk, int nbins, double* __restrict__ out,
-                                                     long long* __restrict__ outc) {
+                                                     long long* __restrict__ outc, long long pstride,
+                                                     long long pcstride) {
+  part += (long long)blockIdx.y * pstride;
+  partc += (long long)blockIdx.y * pcstride;
+  out += (long long)blockIdx.y * BQ_N * nbins;
+  outc += (long long)blockIdx.y * nbins;
   __shared__ double sh[32];
   const int row = blockIdx.x;  // 0 .. BQ_N*nbins (float rows) then nbins (count rows)
   double s = 0.0;
@@ -92,8 +99,9 @@ cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cu
 }
 
 cudaError_t launch_reduce_bins(const double* part, const int* partc, int nblk, int nbins, double* out, long long* outc,
-                               cudaStream_t s) {
-  k_reduce_bins<<<(BQ_N + 1) * nbins, 256, 0, s>>>(part, partc, nblk, nbins, out, outc);
+                               cudaStream_t s, int nmock, long long pstride, long long pcstride) {
+  k_reduce_bins<<<dim3((BQ_N + 1) * nbins, nmock), 256, 0, s>>>(part, partc, nblk, nbins, out, outc, pstride,
+                                                                pcstride);
   return cudaGetLastError();
 }
 
