@@ -28,8 +28,10 @@ cosines from shell centres.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 (brute-force DFT, direct Yamamoto sums, closed forms, plane-parallel Kaiser
-and isotropy identities, brute-force triangle enumeration) except the
-thin-shell bispectrum shot noise, which is "parity unpinned" beyond a
-statistical check (uniform unclustered catalogs give B_0 ~ 0).
+and isotropy identities, brute-force triangle enumeration).  The thin-shell
+bispectrum shot noise is pinned for l = 0 by the single-object identity (one
+galaxy on a node, randoms on every node: B_0 = -2 alpha^2/nbar^2 exactly for
+every triangle); its l = 2, 4 pair terms are "parity unpinned" beyond a
+statistical check (uniform unclustered catalogs give B_l ~ 0).
 """
 from . import power, bispectrum  # noqa: F401

@@ -22,8 +22,11 @@ bispectrum      B^(l) = (2l+1) <F_l F_0 F_0>_T / I_33 - N^(l) (eqs. BispMono,
                 (Sec. II.C), i.e. shell indices a >= b >= c.
 
 Parity: shell fields, triangle sums and counts are pinned by brute-force
-enumeration; the thin-shell shot-noise term is "parity unpinned" (only a
-statistical check on unclustered catalogs stands behind it).
+enumeration; the thin-shell shot noise of l = 0 by the single-object identity
+(one galaxy on a node and randoms on every node leave B_0 = -2 alpha^2/nbar^2
+for every triangle, every term of eq. SNbisp2thin being of order one there);
+its l = 2, 4 pair terms are "parity unpinned" (only a statistical check on
+unclustered catalogs stands behind them).
 """
 from __future__ import annotations
 

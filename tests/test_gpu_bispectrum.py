@@ -173,3 +173,21 @@ def test_boss_360_bispectrum_sampled_triangles():
         assert np.array_equal(got["NT"], ref["NT"])
         err = b_errors(got, ref, ref["I33"], float(sv.N) ** 3)
         assert max(err.values()) < B_TOL, err
+
+
+@pytest.mark.parametrize("contraction", [0, 1, 2], ids=["fp32", "bf16x3_tcgen05", "bf16x6_tcgen05"])
+def test_single_object_shot_noise_identity(contraction):
+    """One galaxy on a node and randoms on every node (the oracle's pinned
+    case): every triangle's B_0 = -2 alpha^2/nbar^2 = -0.125 with N_0 = 0.625
+    and B-hat_0 = 0.5, through each contraction."""
+    from tests.test_oracle_bispectrum import single_object_case
+    fkp = _fkp()
+    gal, ran, geom, bs = single_object_case()
+    ref = ob.bispectrum(gal, ran, geom, bs, ells=(0,))
+    plan = fkp.Plan(geom, (0.0, 2 * math.pi / geom["L"], 8), bshells=bs, want=FKP_B0())
+    _, b = plan.bispectrum(to_device(gal), to_device(ran), contraction=contraction)
+    assert np.array_equal(b["tri"].astype(int), np.asarray(ref["tri"]))
+    assert np.array_equal(b["NT"], ref["NT"])
+    assert abs(b["I33"] - 2.0) < 1e-6
+    assert np.max(np.abs(b["N0"] - 0.625)) < 1e-5
+    assert np.max(np.abs(b["B0"] + 0.125)) < 1e-5

@@ -152,3 +152,40 @@ def test_unclustered_bispectrum_shot_noise_statistical():
     assert np.all(np.abs(mean_sub) < 4 * err + 1e-3 * np.abs(raws.mean(0)))
     assert np.all(np.abs(raws.mean(0)) > 3 * err)
     assert np.all(np.abs(mean_sub) < 0.3 * np.abs(raws.mean(0)))
+
+
+def single_object_case():
+    """One galaxy (w = 1) exactly on a node of a 16^3 periodic CIC grid (L = 16,
+    no compensation) and one random (w = 128) on every node, nbar = 2^-10,
+    alpha = N_g/N_r = 2^-12; shells centred on 2, 3, 4 k_f, width k_f."""
+    N = 16
+    i = np.arange(N, dtype=np.float64)
+    z, y, x = np.meshgrid(i, i, i, indexing="ij")
+    ran = dict(x=x.ravel().astype(np.float32), y=y.ravel().astype(np.float32), z=z.ravel().astype(np.float32),
+               w=np.full(N ** 3, 128.0, dtype=np.float32), nbar=np.full(N ** 3, 2.0 ** -10, dtype=np.float32))
+    gal = dict(x=np.array([5.0], np.float32), y=np.array([6.0], np.float32), z=np.array([7.0], np.float32),
+               w=np.array([1.0], np.float32), nbar=np.array([2.0 ** -10], np.float32))
+    geom = dict(L=16.0, N=N, assign=2, compensate=False, periodic=True, alpha_mode=1,
+                origin=(0.0, 0.0, 0.0), observer=(8.0, 8.0, -40.0))
+    return gal, ran, geom, (2, 1, 1, 3)
+
+
+def test_single_object_thin_shell_shot_noise_identity():
+    """A single object's bispectrum is all shot noise.  With one galaxy on a
+    node (CIC puts all of it there) F_0(q) = w e^{iq.x} on every shell mode,
+    and randoms on every node contribute nothing at q != 0.  So every closed
+    triangle sums to w^3 (B-hat_0 = w^3/I_33), and each of the three pair terms
+    of eq. SNbisp2thin is the shell mean of F_0 F^w_0* = w^3; the triple term is
+    -2 (w^3 - alpha^3 sum_r w_r^3)/I_33.  Hence, for every triangle,
+      N_0 = [3 w^3 - 2 (w^3 - alpha^3 sum_r w_r^3)] / I_33 = 0.625,
+      B_0 = B-hat_0 - N_0 = -2 alpha^3 sum_r w_r^3 / I_33 = -2 alpha^2/nbar^2 = -0.125,
+    with I_33 = alpha sum_r nbar^2 w_r^3 = 2 and B-hat_0 = 0.5: every term is
+    of order one, so a dropped or mis-weighted pair term, a wrong sign or
+    alpha power in the triple term, or a normalisation of B-hat and N_0 that
+    differ all fail."""
+    gal, ran, geom, bs = single_object_case()
+    ref = ob.bispectrum(gal, ran, geom, bs, ells=(0,))
+    assert len(ref["tri"]) >= 5
+    assert abs(ref["I33"] - 2.0) < 1e-12
+    assert np.max(np.abs(ref["N0"] - 0.625)) < 1e-12
+    assert np.max(np.abs(ref["B0"] + 0.125)) < 1e-12
