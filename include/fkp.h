@@ -148,7 +148,8 @@ int fkp_plan_create(void *ctx, const fkp_geometry_t *geom, const fkp_pbins_t *pb
 void fkp_plan_destroy(void *plan);
 
 /* Sizes the caller needs for its outputs and the plan's device footprint
- * (workspace plus the catalog buffers it keeps between calls). */
+ * (workspace plus the catalog buffers it keeps between calls and, once
+ * fkp_power_batch has run, its batch workspace). */
 int fkp_plan_sizes(const void *plan, int *nbins, int *ntriangles, size_t *workspace_bytes);
 
 /* Launch schedule of the three FFT passes of a plan: x_mult (x-pass blocks

@@ -562,9 +562,10 @@ extern "C" int fkp_plan_sizes(const void* plan, int* nbins, int* ntri, size_t* w
   if (!P) return set_error(FKP_EINVAL, "NULL plan");
   if (nbins) *nbins = P->pb.nbins;
   if (ntri) *ntri = P->ntri;
-  // workspace plus the per-call buffers the plan keeps (tile-sorted and staged catalogs)
+  // workspace plus the per-call buffers the plan keeps (tile-sorted and staged
+  // catalogs, the fused-batch workspace)
   if (ws) *ws = P->bytes_total + P->sort_cap * (sizeof(float4) + (P->d_vw2 ? sizeof(float) : 0)) +
-                P->staging_bytes[0] + P->staging_bytes[1];
+                P->staging_bytes[0] + P->staging_bytes[1] + P->batch_bytes;
   return FKP_OK;
 }
 
