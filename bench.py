@@ -145,7 +145,9 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-# per-kernel algorithmic bytes ("kernels and their rooflines")
+# per-kernel algorithmic bytes: the bytes each stage must move at the least
+# (every input read once, every output written once; half = one half-spectrum
+# field of N^2 (N/2 + 1) complex FP32 values)
 # ---------------------------------------------------------------------------
 
 def algorithmic_bytes(N, nfields, ngroups, n_obj):
