@@ -31,7 +31,7 @@ Parity status: every function is pinned by ``tests/test_oracle_*.py``
 and isotropy identities, brute-force triangle enumeration).  The thin-shell
 bispectrum shot noise is pinned for l = 0 by the single-object identity (one
 galaxy on a node, randoms on every node: B_0 = -2 alpha^2/nbar^2 exactly for
-every triangle); its l = 2, 4 pair terms are "parity unpinned" beyond a
-statistical check (uniform unclustered catalogs give B_l ~ 0).
+every triangle) and for l = 0, 2, 4 against F_l and F^w_l summed directly over
+objects placed on nodes (no grid, moments or FFT).
 """
 from . import power, bispectrum  # noqa: F401

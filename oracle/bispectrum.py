@@ -25,8 +25,9 @@ Parity: shell fields, triangle sums and counts are pinned by brute-force
 enumeration; the thin-shell shot noise of l = 0 by the single-object identity
 (one galaxy on a node and randoms on every node leave B_0 = -2 alpha^2/nbar^2
 for every triangle, every term of eq. SNbisp2thin being of order one there);
-its l = 2, 4 pair terms are "parity unpinned" (only a statistical check on
-unclustered catalogs stands behind them).
+and for l = 0, 2, 4 against F_l and F^w_l summed directly over objects on
+nodes (the definitions below eq. SNbisp2, with no grid, moment field or FFT),
+assembled per eq. SNbisp2thin.
 """
 from __future__ import annotations
 

@@ -189,3 +189,71 @@ def test_single_object_thin_shell_shot_noise_identity():
     assert abs(ref["I33"] - 2.0) < 1e-12
     assert np.max(np.abs(ref["N0"] - 0.625)) < 1e-12
     assert np.max(np.abs(ref["B0"] + 0.125)) < 1e-12
+
+
+def _leg(l, mu):
+    """Textbook Legendre polynomials L_0, L_2, L_4."""
+    return {0: np.ones_like(mu), 2: 0.5 * (3 * mu ** 2 - 1), 4: (35 * mu ** 4 - 30 * mu ** 2 + 3) / 8.0}[l]
+
+
+def test_thin_shell_shot_noise_from_direct_point_sums():
+    """Objects exactly on the nodes of a 12^3 periodic CIC grid (no
+    compensation), observer outside the box: then F_l(q) = sum_j c_j w_j
+    L_l(q^.x^_j) e^{-iq.x_j} (c = 1 for galaxies, -alpha for randoms) and
+    F^w_l(q) = sum_j c'_j w_j^2 L_l(q^.x^_j) e^{-iq.x_j} (c' = 1, alpha^2), the
+    definitions below eq. SNbisp2, summed directly over the objects with no
+    grid, moment field or FFT.  The thin-shell noise of eq. SNbisp2thin built
+    from those direct sums (shell means over every mode of each shell,
+    Legendre factors at the shell-centre cosines) equals the oracle's for
+    l = 0, 2, 4 on every triangle."""
+    N, L = 12, 12.0
+    g = mockgen.rng(5, 3)
+    gi = g.integers(0, N, size=(6, 3)).astype(np.float64)
+    ri = g.integers(0, N, size=(40, 3)).astype(np.float64)
+    wg, wr = g.uniform(0.5, 2.0, 6), g.uniform(0.5, 1.5, 40)
+    nb = np.full(46, 2.0 ** -9)
+
+    def cat(p, w, n):
+        return dict(x=p[:, 0].astype(np.float32), y=p[:, 1].astype(np.float32), z=p[:, 2].astype(np.float32),
+                    w=w.astype(np.float32), nbar=n.astype(np.float32))
+
+    gal, ran = cat(gi, wg, nb[:6]), cat(ri, wr, nb[6:])
+    obs = np.array([6.3, 5.7, -9.1])
+    geom = dict(L=L, N=N, assign=2, compensate=False, periodic=True, observer=tuple(obs), origin=(0.0, 0.0, 0.0))
+    bs = (1, 1, 1, 3)
+    ref = ob.bispectrum(gal, ran, geom, bs, ells=(0, 2, 4))
+    # direct sums (float32-rounded inputs, as the oracle reads them)
+    wg32, wr32 = wg.astype(np.float32).astype(np.float64), wr.astype(np.float32).astype(np.float64)
+    alpha = wg32.sum() / wr32.sum()
+    pos = np.concatenate([gi, ri])
+    w = np.concatenate([wg32, wr32])
+    c1 = np.concatenate([np.ones(6), -alpha * np.ones(40)])
+    c2 = np.concatenate([np.ones(6), alpha ** 2 * np.ones(40)])
+    xhat = (pos - obs) / np.linalg.norm(pos - obs, axis=1)[:, None]
+    I33 = alpha * np.sum(2.0 ** -18 * wr32 ** 3)
+    S3 = np.sum(wg32 ** 3) - alpha ** 3 * np.sum(wr32 ** 3)
+    assert abs(ref["I33"] / I33 - 1) < 1e-12
+    lo, hi, cen = ob.shell_bounds(bs)
+    r = np.arange(-(N // 2) + 1, N // 2)
+    modes = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    nn = np.linalg.norm(modes, axis=1)
+    SQ = {}
+    for s in range(bs[3]):
+        m = modes[(nn >= lo[s]) & (nn < hi[s]) & (nn > 0)]
+        q = 2 * np.pi * m / L
+        ph = np.exp(-1j * q @ pos.T)                       # [mode][object]
+        mu = (m / np.linalg.norm(m, axis=1)[:, None]) @ xhat.T
+        F = {l: (ph * _leg(l, mu) * (c1 * w)).sum(1) for l in (0, 2, 4)}
+        Fw = {l: (ph * _leg(l, mu) * (c2 * w ** 2)).sum(1) for l in (0, 2, 4)}
+        for l in (0, 2, 4):
+            SQ[(l, 0, s)] = np.mean((F[l] * np.conj(Fw[0])).real)
+            SQ[(0, l, s)] = np.mean((F[0] * np.conj(Fw[l])).real)
+    scale = max(abs(v) for v in SQ.values()) / I33
+    for t, (a, b, c) in enumerate(ref["tri"]):
+        mu12 = np.clip((cen[c] ** 2 - cen[a] ** 2 - cen[b] ** 2) / (2 * cen[a] * cen[b]), -1, 1)
+        mu13 = np.clip((cen[b] ** 2 - cen[a] ** 2 - cen[c] ** 2) / (2 * cen[a] * cen[c]), -1, 1)
+        for l in (0, 2, 4):
+            n = (2 * l + 1) / I33 * (SQ[(l, 0, a)] + _leg(l, mu12) * SQ[(0, l, b)] + _leg(l, mu13) * SQ[(0, l, c)])
+            if l == 0:
+                n -= 2 * S3 / I33
+            assert abs(ref[f"N{l}"][t] - n) < 1e-9 * scale, (l, (a, b, c), ref[f"N{l}"][t], n)
