@@ -28,7 +28,12 @@ cosines from shell centres.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 (brute-force DFT, direct Yamamoto sums, closed forms, plane-parallel Kaiser
-and isotropy identities, brute-force triangle enumeration).  The thin-shell
+and isotropy identities, brute-force triangle enumeration).  The window
+compensation is pinned against the assignment kernel's own Fourier transform
+(quadrature of the B-spline pieces) and by the compensated fields of an object
+on a node; the monopole's shot-noise subtraction by one galaxy on a node with
+randoms on every node (|F_0|^2 = w^2 on every mode, so P_0 = -alpha^2 sum_r
+w_r^2 / I_22 in every bin).  The thin-shell
 bispectrum shot noise is pinned for l = 0 by the single-object identity (one
 galaxy on a node, randoms on every node: B_0 = -2 alpha^2/nbar^2 exactly for
 every triangle) and for l = 0, 2, 4 against F_l and F^w_l summed directly over

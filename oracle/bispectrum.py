@@ -99,14 +99,29 @@ class Counter:
             self._j[s] = irfftn((self.sidx == s).astype(np.float64), (self.N,) * 3) * float(self.N) ** 3
         return self._j[s]
 
-    def count(self, a, b, c):
+    def _conv(self, b, c):
         key = (b, c)
         if key not in self._C:
             C = rfftn(self._jfield(b) * self._jfield(c)) / float(self.N) ** 3
             self._C[key] = np.rint(C.real)
-        C = self._C[key]
+        return self._C[key]
+
+    def count(self, a, b, c):
+        C = self._conv(b, c)
         m = self.sidx == a
         return int(np.rint(np.sum(self.wt[m] * C[m])))
+
+    def counts_for_pair(self, b, c, keep=True):
+        """N_T(a, b, c) for every shell a at once: the same per-mode rounded
+        convolution C_bc, summed over each shell with the full-grid weights.
+        keep=False drops C_bc afterwards (large grids)."""
+        C = self._conv(b, c)
+        sel = self.sidx >= 0
+        S = int(self.sidx.max()) + 1
+        out = np.rint(np.bincount(self.sidx[sel], weights=self.wt[sel] * C[sel], minlength=S)).astype(np.int64)
+        if not keep:
+            del self._C[(b, c)]
+        return out
 
 
 def bispectrum(gal, ran, geom, bshells, ells=(0, 2, 4), tris=None):

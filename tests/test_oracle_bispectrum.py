@@ -257,3 +257,15 @@ def test_thin_shell_shot_noise_from_direct_point_sums():
             if l == 0:
                 n -= 2 * S3 / I33
             assert abs(ref[f"N{l}"][t] - n) < 1e-9 * scale, (l, (a, b, c), ref[f"N{l}"][t], n)
+
+
+def test_counts_for_pair_equals_single_counts():
+    """The all-shells form of the exact counter (used to write the stored
+    triangle-count fixtures) gives each count() value."""
+    N, bs = 24, (2, 1, 1, 5)
+    counter = ob.Counter(N, bs)
+    for b in range(bs[3]):
+        for c in range(b + 1):
+            allc = counter.counts_for_pair(b, c)
+            for a in range(b, bs[3]):
+                assert allc[a] == counter.count(a, b, c)

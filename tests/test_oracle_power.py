@@ -320,3 +320,101 @@ def test_mockgen_counts():
     assert ran["x"].size == 200_000
     r = np.sqrt(ran["x"].astype(float) ** 2 + ran["y"].astype(float) ** 2 + ran["z"].astype(float) ** 2)
     assert r.min() >= 299.9 and r.max() <= 900.1
+
+
+# ---------------------------------------------------------------------------
+# window compensation (reading: divide each mode by the assignment window)
+# and the monopole's shot-noise subtraction (eq. P0_impl)
+# ---------------------------------------------------------------------------
+
+def kernel_ft(p, q):
+    """int B_p(t) e^{-iqt} dt of the order-p B-spline kernel (``_bspline``,
+    which test_assignment_is_the_bspline_kernel pins against the oracle's
+    gridding), by 24-point Gauss-Legendre quadrature on each polynomial piece
+    of the kernel.  The kernel is even, so the transform is real.  No sinc
+    formula is used: this derives the window from the kernel itself."""
+    x, wq = np.polynomial.legendre.leggauss(24)
+    edges = {2: [-1.0, 0.0, 1.0], 3: [-1.5, -0.5, 0.5, 1.5]}[p]
+    q = np.asarray(q, dtype=np.float64)
+    out = np.zeros_like(q)
+    for a, b in zip(edges[:-1], edges[1:]):
+        t = 0.5 * (b - a) * x + 0.5 * (a + b)
+        out += 0.5 * (b - a) * (np.cos(np.multiply.outer(q, t)) * (wq * _bspline(t, p))).sum(-1)
+    return out
+
+
+def kernel_window(N, p):
+    """prod_a W_p(2 pi n_a / N) on the rfft half-spectrum [nz][ny][nx]."""
+    n1 = np.fft.fftfreq(N, 1.0 / N)
+    nh = np.fft.rfftfreq(N, 1.0 / N)
+    wx, w1 = kernel_ft(p, 2 * np.pi * nh / N), kernel_ft(p, 2 * np.pi * n1 / N)
+    return w1[:, None, None] * w1[None, :, None] * wx[None, None, :]
+
+
+@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("N", [8, 12, 30])
+def test_window_is_the_kernel_fourier_transform(p, N):
+    """The compensation window of mode n is the product over axes of the
+    continuous Fourier transform of the assignment kernel at k_a H = 2 pi
+    n_a/N (grid units).  A window in the wrong variable (e.g. sinc of pi^2
+    n/N), the wrong power, or one axis left out fails."""
+    ref = kernel_window(N, p)
+    got = op.window(N, p)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_compensated_fields_of_an_object_on_a_node(p):
+    """One object of weight w exactly on a node, compensate on.  The node
+    weights of the kernel at integer offsets are B_p(0) and B_p(+-1) (CIC:
+    1, 0; TSC: 3/4, 1/8), so the uncompensated F_0(n) = w e^{-ik.x_j} prod_a
+    [B_p(0) + 2 B_p(1) cos(2 pi n_a/N)], and every compensated field is that
+    divided by the kernel window (quadrature above).  With the observer at
+    infinity x^ is the line of sight at every node, so F_2 and F_4 are
+    L_l(k^.los) F_0 mode by mode, compensated alike."""
+    N, L = 16, 16.0
+    los = np.array([0.3, -0.5, 0.81])
+    los = los / np.linalg.norm(los)
+    g = dict(N=N, L=L, assign=p, origin=(0.0, 0.0, 0.0), observer=None, los=tuple(los), compensate=True)
+    j = np.array([5.0, 9.0, 12.0])
+    w = 0.7
+    F = op.legendre(op.assign(j[None, :], np.array([w]), g), g, lmax=4)
+    nx, ny, nz = op.mode_vectors(N)
+    b0, b1 = float(_bspline(np.array(0.0), p)), float(_bspline(np.array(1.0), p))
+    disc = [b0 + 2 * b1 * np.cos(2 * np.pi * n / N) for n in (nx, ny, nz)]
+    ph = np.exp(-2j * np.pi * (nx * j[0] + ny * j[1] + nz * j[2]) / N)
+    F0 = w * ph * disc[0] * disc[1] * disc[2] / kernel_window(N, p)
+    assert np.max(np.abs(F[0] - F0)) < 1e-12 * np.max(np.abs(F0))
+    nn = np.sqrt(nx * nx + ny * ny + nz * nz)
+    mu = (nx * los[0] + ny * los[1] + nz * los[2]) / np.where(nn > 0, nn, 1.0)
+    m = np.broadcast_to(nn > 0, F0.shape)
+    for l in (2, 4):
+        ref = eval_legendre(l, mu) * F0
+        assert np.max(np.abs(F[l][m] - ref[m])) < 1e-12 * np.max(np.abs(F0)), l
+
+
+def test_monopole_shot_noise_subtraction_single_galaxy():
+    """One galaxy (w = 1) on a node of a 16^3 CIC grid and randoms (w_r =
+    128, nbar = 2^-10) on every node, alpha = N_g/N_r = 2^-12, compensation
+    off.  The randoms sum to zero at every k != 0 (a full lattice sum of
+    e^{-ik.x}), so |F_0|^2 = w^2 = 1 on every mode, and eq. P0_impl gives in
+    every bin
+        mono_raw = w^2 / I_22 = 1/16,
+        P_0 = (w^2 - N_0) / I_22 = -alpha^2 sum_r w_r^2 / I_22 = -1/4,
+    with I_22 = alpha sum_r nbar w_r^2 = 16 and N_0 = w^2 + alpha^2 sum_r w_r^2
+    = 5 written out here.  Subtracting N_0 before the shell average, or
+    dividing it by the mode count, fails in every bin."""
+    from tests.test_oracle_bispectrum import single_object_case
+    gal, ran, geom, _ = single_object_case()
+    nr = ran["x"].size
+    alpha = 1.0 / nr
+    I22 = alpha * nr * 2.0 ** -10 * 128.0 ** 2
+    N0 = 1.0 + alpha ** 2 * nr * 128.0 ** 2
+    assert (I22, N0) == (16.0, 5.0)
+    kf = 2 * math.pi / geom["L"]
+    res = op.power(gal, ran, geom, (0.5 * kf, kf, 7))
+    assert np.all(res["nmodes"] > 0)
+    assert abs(res["I22"] - I22) < 1e-12 and abs(res["N0"] - N0) < 1e-12
+    assert np.max(np.abs(res["mono_raw"] - 1.0 / 16)) < 1e-12
+    assert np.max(np.abs(res["P0"] + 0.25)) < 1e-12
