@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -47,6 +48,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-slots", type=int, default=2, help="server slots for the end-to-end leg (1: plain calls)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-cores", type=int, default=0, help="reference arm: cores the oracle may use (0: all)")
+    ap.add_argument("--reference-budget", type=float, default=200.0,
+                    help="reference arm: seconds of whole-mock oracle runs (at least one mock runs)")
+    ap.add_argument("--cufft", type=int, default=1, help="time cuFFT (torch.fft) as a baseline (0 skips)")
     ap.add_argument("--grid", type=int, default=512, help="grid side (512 is the benchmark workload)")
     ap.add_argument("--ran-ratio", type=float, default=50.0, help="randoms per galaxy (50 in the workload)")
     ap.add_argument("--bisp-steps", type=int, default=3, help="timed bispectrum mocks (0 skips the B leg)")
@@ -103,7 +108,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"fkp_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -145,19 +150,25 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-# per-kernel algorithmic bytes: the bytes each stage must move at the least
-# (every input read once, every output written once; half = one half-spectrum
-# field of N^2 (N/2 + 1) complex FP32 values)
+# algorithmic bytes of one mock of the power step: the least traffic the
+# method needs (catalog read once, the real grid F written once and read
+# once, the k_z-power groups that carry the moment fields through the
+# z-FFT written once and read once; half = one half-spectrum field of
+# N^2 (N/2 + 1) complex FP32 values), split by stage.  The design's own
+# extra traffic (the fixed-point grid is 8 bytes per node, the x-pass spills
+# every moment half spectrum for the y-pass to read) is not algorithmic: it
+# shows in the measured DRAM `traffic` instead.
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(N, nfields, ngroups, n_obj):
+def algorithmic_bytes(N, ngroups, n_obj, cat_bytes=16):
     half = N * N * (N // 2 + 1) * 8
+    grid = 4 * N ** 3
     return {
-        "count": 16 * n_obj,                         # catalog x,y,z,nbar read (scalars, tile counts)
-        "assign": 16 * n_obj + 8 * N ** 3,          # catalog x,y,z,nbar read; fixed-point grid written once
-        "xpass": 8 * N ** 3 + nfields * half,        # grid read; moment half-spectra written
-        "ypass": (nfields + ngroups) * half,         # moment spectra read; k_z-power groups written
-        "zpass": ngroups * half,                     # groups read (bins are negligible)
+        "count": 0,                                  # reads the catalog, but the step reads it once: counted below
+        "assign": cat_bytes * n_obj + grid,          # catalog (x, y, z, nbar) read once; F written once
+        "xpass": grid,                               # F read once
+        "ypass": ngroups * half,                     # the k_z-power groups written once
+        "zpass": ngroups * half,                     # the groups read once (bins are negligible)
     }
 
 
@@ -204,32 +215,26 @@ def peaks():
 # oracle baseline on a bounded sample
 # ---------------------------------------------------------------------------
 
-def oracle_sample(gal, ran, sv, level):
-    """Times the FP64 oracle on 1/8^level of the objects at grid N/2^level and
-    extrapolates to one full mock: gridding scales with objects (x 8^level),
-    the FFT/recombination stage with N^3 log N."""
+def oracle_full(gal, ran, sv):
+    """Wall time of the FP64 oracle (oracle.power.power, as it stands) on one
+    whole mock of the workload: scalars, gridding of every galaxy and random,
+    the 22 moment-field FFTs, recombination and binning."""
     from oracle import power as op
-    rng = np.random.default_rng(1234)
-    frac = 8 ** -level
-    sub = {}
-    for name, c in (("gal", gal), ("ran", ran)):
-        n = c["x"].size
-        idx = np.sort(rng.choice(n, size=max(1, int(n * frac)), replace=False))
-        sub[name] = {k: v[idx] for k, v in c.items()}
-    geom = dict(sv.geometry())
-    Ns = sv.N // 2 ** level
-    geom["N"] = Ns
     t0 = time.perf_counter()
-    F, _, sc = op.fkp_grids(sub["gal"], sub["ran"], geom)
-    t1 = time.perf_counter()
-    Fl = op.legendre(F, geom, lmax=4)
-    op.bin_power(Fl, geom, BINS, sc["I22"], sc["N0"])
-    t2 = time.perf_counter()
-    fft_scale = (sv.N ** 3 * math.log2(sv.N)) / (Ns ** 3 * math.log2(Ns))
-    t_mock = (t1 - t0) / frac + (t2 - t1) * fft_scale
-    desc = (f"oracle (numpy/scipy FP64) on 1/{8 ** level} of the objects at {Ns}^3, extrapolated to one "
-            f"512^3 mock (gridding x{8 ** level}, FFT stage x{fft_scale:.1f}); measured {t2 - t0:.1f} s")
-    return t_mock, desc, t2 - t0
+    op.power(gal, ran, sv.geometry(), BINS)
+    return time.perf_counter() - t0
+
+
+def restrict_cores(n):
+    """Confines this process (and the FFT worker threads it starts) to its
+    first n allowed cores; returns the cores it may now use."""
+    try:
+        allowed = sorted(os.sched_getaffinity(0))
+        if n and n < len(allowed):
+            os.sched_setaffinity(0, set(allowed[:n]))
+    except Exception:
+        pass
+    return cores_used()
 
 
 def cores_used():
@@ -242,29 +247,51 @@ def cores_used():
 # ---------------------------------------------------------------------------
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, on whole mocks of
+    the benchmark workload (one step = one whole mock; no sampling and no
+    extrapolation).  A whole mock takes about a minute, so the arm runs as
+    many of the requested steps as fit in --reference-budget seconds (at
+    least one); the line reports the steps it ran.  Warm-up: one oracle run
+    on the small 64^3 survey (imports, page faults), not a workload step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import mockgen
+    from oracle import power as op
+    cores = restrict_cores(args.oracle_cores)
+    small = mockgen.survey_small()
+    sg, sr = mockgen.catalog(small, args.seed)
+    kf = 2 * math.pi / small.L
+    op.power(sg, sr, small.geometry(), (0.5 * kf, kf, 32))
     sv = mockgen.survey_boss()
     gal, ran = mockgen.catalog(sv, args.seed)
-    level = 2 if args.steps + args.warmup > 6 else 1
-    for _ in range(args.warmup):
-        oracle_sample(gal, ran, sv, level)
-    ts, desc = [], ""
-    for _ in range(args.steps):
-        t, desc, _ = oracle_sample(gal, ran, sv, level)
-        ts.append(t)
+    ts = []
+    t_start = time.perf_counter()
+    while len(ts) < max(1, args.steps):
+        ts.append(oracle_full(gal, ran, sv))
+        if time.perf_counter() - t_start + ts[-1] > args.reference_budget:
+            break
     t_mock = float(np.mean(ts))
     value = 1.0 / t_mock
+    desc = (f"oracle (numpy/scipy FP64) on {len(ts)} whole mock(s) of the workload, {cores} core(s), "
+            f"{int(gal['x'].size)} galaxies + {int(ran['x'].size)} randoms at 512^3; per mock "
+            + ", ".join(f"{t:.1f} s" for t in ts))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "mocks/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_mock, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic lognormal mocks (mockgen)",
-            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": value, "unit": "mocks/s", "cores": cores_used(), "kind": "oracle",
-                             "sample": desc},
+            "steps": len(ts), "requested_steps": args.steps, "warmup": 0, "ms_per_step": 1000 * t_mock,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic lognormal mocks (mockgen), seeded per rank",
+            "config": workload_config(sv, gal, ran, 1),
+            "cpu_baseline": {"value": value, "unit": "mocks/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "mocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_config(sv, gal, ran, world):
+    workload = WORKLOAD if (sv.N == 512 and sv.random_ratio == 50.0) else \
+        f"reduced case: {sv.N}^3, randoms x{sv.random_ratio:g} (not the benchmark workload)"
+    return {"workload": workload, "grid": sv.N, "n_gal": int(gal["x"].size), "n_ran": int(ran["x"].size),
+            "l2": "inputs larger than L2 (no flush needed)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def run_gpu(args):
@@ -343,28 +370,28 @@ def run_gpu(args):
     h2d = 16 * n_obj
     d2h = 8 * (6 * 60 + 60) + 8 * 24
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (stage times from CUDA events recorded on
+    # the launching stream between the stages of every timed step)
     st = np.mean(np.array(stage), axis=0)
     names = {"count": st[0], "assign": st[1], "xpass": st[2], "ypass": st[3], "zpass": st[4]}
-    mt_fields, mt_groups = 16, 9  # trace-reduced moment fields, k_z-power groups
-    ab = algorithmic_bytes(sv.N, mt_fields, mt_groups, n_obj)
+    ab = algorithmic_bytes(sv.N, 9, n_obj)  # 9 k_z-power groups carry P_0,2,4 (and P_4b)
     dom = max(names, key=names.get)
     pk, src = peaks()
     achieved = ab[dom] / (names[dom] * 1e-3) / 1e9
+    step_bytes = sum(ab.values())
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": recorded_traffic(dom) if sv.N == 512 else None,
             "algorithmic_bytes": ab[dom], "peak_source": src,
             "stage_ms": {k: float(v) for k, v in names.items()},
-            "stage_GBps": {k: ab[k] / (names[k] * 1e-3) / 1e9 for k in names}}
+            "stage_algorithmic_bytes": ab,
+            "stage_frac": {k: ab[k] / (names[k] * 1e-3) / 1e9 / pk["hbm_gbs"] for k in names},
+            "step": {"algorithmic_bytes": step_bytes, "ms": ms_all,
+                     "frac": step_bytes / (ms_all * 1e-3) / 1e9 / pk["hbm_gbs"]}}
 
-    workload = WORKLOAD if (args.grid == 512 and args.ran_ratio == 50.0) else \
-        f"reduced case: {args.grid}^3, randoms x{args.ran_ratio:g} (not the benchmark workload)"
     line = {"metric": METRIC, "value": value, "unit": "mocks/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic lognormal mocks (mockgen), seeded per rank",
-            "config": {"workload": workload, "grid": sv.N, "n_gal": int(gal["x"].size),
-                       "n_ran": int(ran["x"].size), "l2": "inputs larger than L2 (no flush needed)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": workload_config(sv, gal, ran, world),
             "e2e": {"value": job_rate(world, e2e_s), "unit": "mocks/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "path": f"fkp_server_submit/wait, {args.e2e_slots} slots"
                     if args.e2e_slots > 1 else "fkp_power, one call at a time",
@@ -373,6 +400,8 @@ def run_gpu(args):
             "roofline": roof,
             "fft_schedule": plan.schedule(),
             "clocks": ck}
+    if args.cufft and world == 1 and sv.N == 512:
+        line["cufft_baseline"] = run_cufft(args, float(names["xpass"] + names["ypass"] + names["zpass"]))
     if args.small_steps > 0:
         line["small_grid"] = run_small(args, stream)
     if args.bisp_steps > 0:
@@ -388,14 +417,50 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         line["fused"] = run_fused(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_mock, desc, _ = oracle_sample(gal, ran, sv, 1)
+        t_mock = oracle_full(gal, ran, sv)
         line["cpu_baseline"] = {"value": 1.0 / t_mock, "unit": "mocks/s", "cores": cores_used(), "kind": "oracle",
-                                "sample": desc}
+                                "sample": f"oracle (numpy/scipy FP64) on one whole mock of the workload (the "
+                                          f"timed catalogs, 512^3): {t_mock:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_cufft(args, pass_ms, N=512, nfields=16):
+    """cuFFT (through torch.fft) timed as a baseline beside the hand-written
+    passes: one batched 3-D real-to-complex transform of 16 FP32 fields of
+    512^3 (the trace-reduced moment fields of one mock), CUDA events on the
+    current stream, 3 timed calls after 2 warm-ups.  cuFFT transforms the 16
+    fields and stops; the hand-written x, y and z passes also build the
+    moment fields, group them by k_z power, recombine the Legendre fields and
+    bin them (pass_ms)."""
+    import torch
+    half = N * N * (N // 2 + 1) * 8
+    x = torch.randn(nfields, N, N, N, device="cuda", dtype=torch.float32)
+    y = None
+    for _ in range(2):
+        y = torch.fft.rfftn(x, dim=(-3, -2, -1))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        y = torch.fft.rfftn(x, dim=(-3, -2, -1))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del x, y
+    torch.cuda.empty_cache()
+    pk, src = peaks()
+    moved = nfields * (4 * N ** 3 + half)
+    return {"what": f"{nfields} batched 3-D r2c FFTs of {N}^3 FP32 fields (torch.fft.rfftn -> cuFFT)",
+            "ms": ms, "io_bytes": moved, "io_frac_of_hbm": moved / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+            "hand_written_passes_ms": pass_ms,
+            "note": "the hand-written passes also build the moment fields, group them by k_z power "
+                    "(9 groups through the z-FFT), recombine and bin"}
 
 
 BSHELLS = (3, 3, 3, 37)  # centres 3(s+1) k_f, width 3 k_f, to k = 0.2 h/Mpc

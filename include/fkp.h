@@ -210,11 +210,17 @@ int fkp_bispectrum(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ra
 
 /* The estimator of fkp_power_from_grid for small grids without allocating
  * any device memory: every device buffer it uses lives in one file-scope
- * device array of about 42 MB, held by each GPU that loads the library until
- * the process exits.  The paper has no counterpart; this is for callers that
- * cannot call cudaMalloc while running (a process that reserved all device
- * memory for its own pool, a real-time loop that forbids allocation after
- * start-up, a plugin host that gives the library no allocator).
+ * device array of about 42 MB, held by each GPU that has mapped the library's
+ * device code until the process exits.  The paper has no counterpart; this is
+ * for callers that cannot call cudaMalloc while running (a process that
+ * reserved all device memory for its own pool, a real-time loop that forbids
+ * allocation after start-up, a plugin host that gives the library no
+ * allocator).
+ * With CUDA's lazy module loading (the default since CUDA 12.2) the array and
+ * the kernels are mapped onto a device by the first call there, not when the
+ * library is loaded: make one warm-up call per device (or run with
+ * CUDA_MODULE_LOADING=EAGER) before reserving the rest of the device's memory,
+ * or that first call can fail with FKP_ECUDA.
  * Arguments: geometry and P bins as for fkp_plan_create (no plan is made),
  * F_device the real field [z][y][x] (N^3 float32, device pointer), I22 and
  * N0 as for fkp_power_from_grid, results in out (caller-allocated arrays of
@@ -283,6 +289,16 @@ int fkp_server_wait(void *server, uint64_t ticket, int timeout_ms, int *status, 
 int fkp_server_stats(void *server, fkp_server_stats_t *stats);
 /* Lets queued and running requests finish, then frees everything. */
 void fkp_server_destroy(void *server);
+
+/* Diagnostic of the bounded device-side waits (the FFT passes wait on an
+ * mbarrier for each bulk tile copy, giving up after a fixed number of polls
+ * and reporting FKP_ETIMEOUT instead of hanging).  Launches one block on
+ * `device` that initialises an mbarrier, issues no copy, never arrives, and
+ * waits on it with the same bounded wait for `polls` polls (1 .. 4194304).
+ * The expected return is FKP_ETIMEOUT, with the device context left usable;
+ * FKP_ESTATE means the wait completed (it must not), FKP_EINVAL bad
+ * arguments, FKP_ECUDA a runtime failure.  Allocates and frees 4 bytes. */
+int fkp_selftest_bounded_wait(int device, unsigned polls);
 
 /* Host-only consistency check of the tables that map the moment fields to
  * the k_z-power groups (for lmax = 0, 2, 4): the field order matches the

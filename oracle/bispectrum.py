@@ -148,16 +148,27 @@ def shell_means(Fl, Fwl, sidx, wt, S, ells):
     return nm, sn1, sn2
 
 
-def bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells=(0, 2, 4), tris=None):
+def bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells=(0, 2, 4), tris=None, counts=None, cache_fields=None):
+    """B^(l), N^(l), T^(l) and N_T for the given triangles from the Legendre
+    fields.  counts: optional mapping (a, b, c) -> N_T written earlier by this
+    module's Counter (skips the convolution counter).  cache_fields: at most
+    that many shell fields are kept (least recently used dropped), for large
+    grids; None keeps them all.  Neither changes the arithmetic."""
+    from collections import OrderedDict
     S = bshells[3]
     sidx, wt = shell_index(N, bshells)
     _, _, cen = shell_bounds(bshells)
     nm, sn1, sn2 = shell_means(Fl, Fwl, sidx, wt, S, ells)
-    counter = Counter(N, bshells)
-    cache = {}
+    counter = None if counts is not None else Counter(N, bshells)
+    cache = OrderedDict()
 
     def field(l, s):
-        if (l, s) not in cache:
+        if (l, s) in cache:
+            cache.move_to_end((l, s))
+        else:
+            if cache_fields is not None:
+                while len(cache) >= max(1, cache_fields):
+                    cache.popitem(last=False)
             cache[(l, s)] = shell_field(Fl[l], sidx, s, N)
         return cache[(l, s)]
 
@@ -169,7 +180,7 @@ def bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells=(0, 2, 4), tris=None):
         out[f"N{l}"] = []
     N3 = float(N) ** 3
     for (a, b, c) in all_tris:
-        nt = counter.count(a, b, c)
+        nt = counts[(a, b, c)] if counter is None else counter.count(a, b, c)
         if tris is None and nt == 0:
             continue
         out["tri"].append((a, b, c))

@@ -26,7 +26,8 @@ EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_
            "fkp_power", "fkp_power_from_grid", "fkp_bispectrum", "fkp_last_error", "fkp_version",
            "fkp_power_from_grid_noalloc", "fkp_server_create", "fkp_server_submit", "fkp_server_poll",
            "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy", "fkp_check_tables",
-           "fkp_plan_set_graphs", "fkp_plan_schedule", "fkp_plan_set_schedule", "fkp_power_batch"]
+           "fkp_plan_set_graphs", "fkp_plan_schedule", "fkp_plan_set_schedule", "fkp_power_batch",
+           "fkp_selftest_bounded_wait"]
 
 
 class FKPError(RuntimeError):
@@ -124,6 +125,7 @@ def lib():
                                         C.POINTER(C.c_float)]
         L.fkp_plan_set_schedule.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.fkp_version.restype = C.c_char_p
+        L.fkp_selftest_bounded_wait.argtypes = [C.c_int, C.c_uint]
         _lib = L
     return _lib
 
@@ -156,9 +158,26 @@ def _ptr(a):
     return arr.ctypes.data, 0
 
 
-def make_catalog(cat):
+def check_field(F, N, device):
+    """Raises, before any launch, unless F is what the C calls read: a
+    contiguous float32 CUDA tensor of N^3 values on `device` (the plan's, or
+    the current device for the entry point without a plan).  A wrong dtype
+    or size would make the x-pass read past the end of the buffer."""
+    if not (hasattr(F, "is_cuda") and F.is_cuda and F.is_contiguous()):
+        raise TypeError("F must be a contiguous CUDA float32 tensor")
+    import torch
+    if F.dtype != torch.float32:
+        raise TypeError(f"F must be float32, not {F.dtype}")
+    if F.numel() != int(N) ** 3:
+        raise ValueError(f"F holds {F.numel()} values; the grid needs N^3 = {int(N) ** 3}")
+    if F.device.index != device:
+        raise ValueError(f"F is on cuda:{F.device.index}, the call runs on cuda:{device}")
+
+
+def make_catalog(cat, device=None):
     """Catalog struct from a dict with x, y, z, nbar and optional w (torch
-    tensors on one device, or host arrays).  Returns (struct, keepalive)."""
+    tensors on one device, or host arrays).  Returns (struct, keepalive).
+    With `device` set, device tensors must be on that CUDA device."""
     keep = []
     ptrs = {}
     dev = None
@@ -171,6 +190,8 @@ def make_catalog(cat):
         if not hasattr(a, "data_ptr"):
             a = np.ascontiguousarray(a, dtype=np.float32)
         keep.append(a)
+        if device is not None and getattr(a, "is_cuda", False) and a.device.index != device:
+            raise ValueError(f"catalog tensor on cuda:{a.device.index}, the plan runs on cuda:{device}")
         p, d = _ptr(a)
         ptrs[k] = p
         dev = d if dev is None else dev
@@ -214,6 +235,7 @@ class Plan:
     def __init__(self, geom, pbins, bshells=None, want=FKP_P0 | FKP_P2 | FKP_P4 | FKP_P4B, device=0, budget=0):
         self.geom = dict(geom)
         self.want = want
+        self.device = int(device)
         self._g = geometry(geom)
         self._pb = PBins(float(pbins[0]), float(pbins[1]), int(pbins[2]))
         self._bs = BShells(*[int(v) for v in bshells]) if bshells is not None else None
@@ -271,8 +293,8 @@ class Plan:
 
     def power(self, gal, ran, stream=None):
         """P_0, P_2, P_4, P_4b and the scalars for one survey."""
-        cg, k1 = make_catalog(gal)
-        cr, k2 = make_catalog(ran)
+        cg, k1 = make_catalog(gal, self.device)
+        cr, k2 = make_catalog(ran, self.device)
         o, arr = self._pout()
         _check(lib().fkp_power(self._h, C.byref(cg), C.byref(cr), _stream_handle(stream), C.byref(o)))
         return self._scalars(o, arr)
@@ -286,8 +308,8 @@ class Plan:
         n = len(gals)
         cg, cr, keep = (Catalog * n)(), (Catalog * n)(), []
         for k in range(n):
-            cg[k], k1 = make_catalog(gals[k])
-            cr[k], k2 = make_catalog(rans[k])
+            cg[k], k1 = make_catalog(gals[k], self.device)
+            cr[k], k2 = make_catalog(rans[k], self.device)
             keep += [k1, k2]
         outs = (PowerOut * n)()
         arrs = []
@@ -301,8 +323,7 @@ class Plan:
     def power_from_grid(self, F, I22=1.0, N0=0.0, stream=None):
         """The estimator on a given device field F (torch float32 CUDA tensor
         [N][N][N], layout [z][y][x])."""
-        if not (hasattr(F, "is_cuda") and F.is_cuda and F.is_contiguous()):
-            raise TypeError("F must be a contiguous CUDA float32 tensor")
+        check_field(F, self.geom["N"], self.device)
         o, arr = self._pout()
         _check(lib().fkp_power_from_grid(self._h, F.data_ptr(), float(I22), float(N0), _stream_handle(stream),
                                          C.byref(o)))
@@ -310,8 +331,8 @@ class Plan:
 
     def bispectrum(self, gal, ran, contraction=FKP_CONTRACT_FP32, stream=None):
         """P_l and B_l (closed triangles a >= b >= c with N_T > 0)."""
-        cg, k1 = make_catalog(gal)
-        cr, k2 = make_catalog(ran)
+        cg, k1 = make_catalog(gal, self.device)
+        cr, k2 = make_catalog(ran, self.device)
         o, parr = self._pout()
         nt = self.ntri
         b = {"tri": np.zeros((nt, 3), dtype=np.int16), "NT": np.zeros(nt, dtype=np.int64),
@@ -335,8 +356,8 @@ def power_from_grid_noalloc(geom, pbins, F, I22=1.0, N0=0.0, stream=None):
     nbins <= 64) through the entry point that allocates no device memory
     (its buffers live in a static device array shared by all calls on a
     device; calls must not overlap on the GPU)."""
-    if not (hasattr(F, "is_cuda") and F.is_cuda and F.is_contiguous()):
-        raise TypeError("F must be a contiguous CUDA float32 tensor")
+    import torch
+    check_field(F, int(geom["N"]), torch.cuda.current_device())
     g = geometry(geom)
     pb = PBins(float(pbins[0]), float(pbins[1]), int(pbins[2]))
     nb = pb.nbins
@@ -437,6 +458,13 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def selftest_bounded_wait(device=0, polls=1000):
+    """Return code of the library's bounded-wait diagnostic (FKP_ETIMEOUT,
+    -4, is the expected outcome) and its message."""
+    rc = lib().fkp_selftest_bounded_wait(int(device), int(polls))
+    return rc, lib().fkp_last_error().decode()
 
 
 def check_tables():

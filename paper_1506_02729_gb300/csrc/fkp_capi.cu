@@ -455,6 +455,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   g.assign = geom->assign;
   g.periodic = geom->periodic ? 1 : 0;
   g.P_fkp = (float)geom->P_fkp;
+  g.P_fkp_d = geom->P_fkp;
   g.alpha_mode = geom->alpha_mode;
   observer_node(g);
 
@@ -1003,6 +1004,25 @@ extern "C" int fkp_power_batch(void* plan, int nmock, const fkp_catalog_t* gals,
     }
   }
   return FKP_OK;
+}
+
+extern "C" int fkp_selftest_bounded_wait(int device, unsigned polls) {
+  if (polls < 1 || polls > kWaitLimit) return set_error(FKP_EINVAL, "polls must be in 1 .. %u", kWaitLimit);
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return set_error(FKP_EINVAL, "bad device %d", device);
+  CK(cudaSetDevice(device));
+  int* d_flag = nullptr;
+  int h_flag = 0;
+  CK(cudaMalloc(&d_flag, sizeof(int)));
+  cudaError_t e = cudaMemset(d_flag, 0, sizeof(int));
+  if (e == cudaSuccess) e = launch_wait_selftest(polls, d_flag, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_flag);
+  if (e != cudaSuccess) return set_error(FKP_ECUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
+  if (h_flag == 1)
+    return set_error(FKP_ETIMEOUT, "the bounded wait gave up after %u polls on a barrier nothing arrives at", polls);
+  return set_error(FKP_ESTATE, "bounded-wait self-test: unexpected flag %d", h_flag);
 }
 
 extern "C" int fkp_power_from_grid(void* plan, const float* F, double I22, double N0, void* stream,

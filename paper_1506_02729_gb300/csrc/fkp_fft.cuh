@@ -382,12 +382,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on phase `parity`; returns false (and sets *err |= flag) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int flag) {
-  for (unsigned it = 0; it < kWaitLimit; ++it)
+// Bounded wait on phase `parity`: at most `limit` polls; returns false (and
+// sets *err |= flag) when it gives up.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, int* err, int flag, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   if (err) atomicOr(err, flag);
   return false;
+}
+
+// The passes' wait: kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int flag) {
+  return mbar_wait_n(bar, parity, err, flag, kWaitLimit);
 }
 
 }  // namespace fkp

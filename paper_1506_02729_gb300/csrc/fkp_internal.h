@@ -134,6 +134,7 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
 cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xyzv, const float* vw2,
                               unsigned long long* grid, unsigned long long* gridw, cudaStream_t s);
 cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
+cudaError_t launch_wait_selftest(unsigned polls, int* flag, cudaStream_t s);
 // xm: x-pass blocks = SMs x resident blocks x xm; nt: threads per y- or
 // z-pass block (256 or 512).  The defaults are the 512^3 choices.  mb: the
 // mocks of one fused launch (blockIdx.z) and their buffer strides.

@@ -30,6 +30,7 @@ struct GeomDev {
   int periodic;
   float P_fkp;
   int alpha_mode;
+  double P_fkp_d;      // P_FKP in FP64 (the scalar sums)
   int obs_x, obs_y, obs_z;  // grid node at the observer (x^ = 0 there), or -1
 };
 
@@ -130,6 +131,17 @@ __device__ __forceinline__ double block_sum_f64(double v, double* sh) {
 // FKP weight w = 1/(1 + nbar P_FKP) unless the catalog carries weights.
 __device__ __forceinline__ float fkp_weight(const CatDev& c, long long i, float Pfkp) {
   return c.w ? __ldg(c.w + i) : 1.0f / (1.0f + __ldg(c.nbar + i) * Pfkp);
+}
+
+// The same weight in FP64 for the scalar sums (alpha, I_22, N_0, I_33, S_3):
+// the FP32 reciprocal of d = 1 + nbar P_FKP refined by one Newton-Raphson
+// step r1 = r0 + r0 (1 - d r0), which squares its relative error (2^-24 ->
+// about 1e-14).  Weights given with the catalog are taken as they are.
+__device__ __forceinline__ double fkp_weight_f64(const CatDev& c, long long i, double Pfkp) {
+  if (c.w) return (double)__ldg(c.w + i);
+  const double d = fma((double)__ldg(c.nbar + i), Pfkp, 1.0);
+  const double r0 = (double)__frcp_rn((float)d);
+  return fma(r0, fma(-d, r0, 1.0), r0);
 }
 
 }  // namespace fkp

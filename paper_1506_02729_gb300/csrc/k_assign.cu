@@ -3,9 +3,9 @@
 // Interpolation of the objects to the grid nodes (eq. mapFFT) with CIC or TSC
 // weights, as a counting sort by 16^3-cell tile followed by accumulation in
 // shared memory:
-//   count    per object: FKP weight and the compensated FP32 partial sums of
-//            the scalars (W, sum w^2, sum w^3, sum nbar w^2, sum nbar^2 w^3,
-//            for alpha, I_22, I_33, N_0, S_3: eqs. I22def, N0true, Noise0),
+//   count    per object: FKP weight and the FP64 partial sums of the scalars
+//            (W, sum w^2, sum w^3, sum nbar w^2, sum nbar^2 w^3, for alpha,
+//            I_22, I_33, N_0, S_3: eqs. I22def, N0true, Noise0),
 //            the geometry check and one count for the object's tile (block
 //            histogram in shared memory);
 //   scan     tile offsets (exclusive prefix sum);
@@ -77,19 +77,19 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
   __shared__ double sh[32];
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
   __syncthreads();
-  KahanF s_w, s_w2, s_w3, s_nw2, s_n2w3;
+  double s_w = 0.0, s_w2 = 0.0, s_w3 = 0.0, s_nw2 = 0.0, s_n2w3 = 0.0;
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
        i += (long long)gridDim.x * blockDim.x) {
-    const float w = fkp_weight(c, i, g.P_fkp);
-    const float w2 = w * w;
-    s_w.add(w);
-    s_w2.add(w2);
-    s_w3.add(w2 * w);
+    const double w = fkp_weight_f64(c, i, g.P_fkp_d);
+    const double w2 = w * w;
+    s_w += w;
+    s_w2 += w2;
+    s_w3 += w2 * w;
     if (is_ran) {
-      const float nb = __ldg(c.nbar + i);
-      s_nw2.add(nb * w2);
-      s_n2w3.add(nb * nb * w2 * w);
+      const double nb = (double)__ldg(c.nbar + i);
+      s_nw2 += nb * w2;
+      s_n2w3 += nb * nb * w2 * w;
     }
     int cx, cy, cz;
     if (centre_cell<P>(g, __ldg(c.x + i), __ldg(c.y + i), __ldg(c.z + i), cx, cy, cz))
@@ -103,15 +103,15 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
   double* out = part + (size_t)blockIdx.x * SC_NSUM;
   double v;
   if (!is_ran) {
-    v = block_sum_f64(s_w.value(), sh);  if (threadIdx.x == 0) out[SC_G_W] = v;
-    v = block_sum_f64(s_w2.value(), sh); if (threadIdx.x == 0) out[SC_G_W2] = v;
-    v = block_sum_f64(s_w3.value(), sh); if (threadIdx.x == 0) out[SC_G_W3] = v;
+    v = block_sum_f64(s_w, sh);  if (threadIdx.x == 0) out[SC_G_W] = v;
+    v = block_sum_f64(s_w2, sh); if (threadIdx.x == 0) out[SC_G_W2] = v;
+    v = block_sum_f64(s_w3, sh); if (threadIdx.x == 0) out[SC_G_W3] = v;
   } else {
-    v = block_sum_f64(s_w.value(), sh);    if (threadIdx.x == 0) out[SC_R_W] = v;
-    v = block_sum_f64(s_w2.value(), sh);   if (threadIdx.x == 0) out[SC_R_W2] = v;
-    v = block_sum_f64(s_w3.value(), sh);   if (threadIdx.x == 0) out[SC_R_W3] = v;
-    v = block_sum_f64(s_nw2.value(), sh);  if (threadIdx.x == 0) out[SC_R_NW2] = v;
-    v = block_sum_f64(s_n2w3.value(), sh); if (threadIdx.x == 0) out[SC_R_N2W3] = v;
+    v = block_sum_f64(s_w, sh);    if (threadIdx.x == 0) out[SC_R_W] = v;
+    v = block_sum_f64(s_w2, sh);   if (threadIdx.x == 0) out[SC_R_W2] = v;
+    v = block_sum_f64(s_w3, sh);   if (threadIdx.x == 0) out[SC_R_W3] = v;
+    v = block_sum_f64(s_nw2, sh);  if (threadIdx.x == 0) out[SC_R_NW2] = v;
+    v = block_sum_f64(s_n2w3, sh); if (threadIdx.x == 0) out[SC_R_N2W3] = v;
   }
 }
 

@@ -148,6 +148,7 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
   g.assign = geom->assign;
   g.periodic = geom->periodic ? 1 : 0;
   g.P_fkp = (float)geom->P_fkp;
+  g.P_fkp_d = geom->P_fkp;
   g.alpha_mode = geom->alpha_mode;
   observer_node(g);
 

@@ -83,6 +83,20 @@ __global__ void __launch_bounds__(256) k_reduce_bins(const double* __restrict__ 
   }
 }
 
+// Diagnostic of the bounded wait: one block initialises an mbarrier that
+// nothing ever arrives at and no copy targets, then waits on its first phase
+// with the passes' bounded wait (mbar_wait_n) for `polls` polls.  flag gets
+// 1 when the wait gave up (the expected outcome), 2 if it completed.
+__global__ void k_wait_selftest(unsigned polls, int* __restrict__ flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && mbar_wait_n(&bar, 0u, flag, 1, polls)) atomicOr(flag, 2);
+}
+
 // ----------------------------------------------------------------------------
 // host-side launch wrappers (called by the C ABI)
 // ----------------------------------------------------------------------------
@@ -90,6 +104,11 @@ __global__ void __launch_bounds__(256) k_reduce_bins(const double* __restrict__ 
 cudaError_t launch_scalars_finalize(const double* part, int nbg, int nbr, long long ng, long long nr, int amode,
                                     double* ds, cudaStream_t s) {
   k_scalars_finalize<<<1, 32, 0, s>>>(part, nbg, nbr, ng, nr, amode, ds);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(unsigned polls, int* flag, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(polls, flag);
   return cudaGetLastError();
 }
 

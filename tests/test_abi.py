@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_1506_02729_gb300 as fkp
@@ -71,3 +72,41 @@ def test_struct_layouts_match_header(tmp_path):
     sizes = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     for (n, cls), size in zip(names.items(), sizes):
         assert ctypes.sizeof(cls) == size, n
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor on a machine without a GPU: only what the
+    binding's argument checks look at."""
+    is_cuda = True
+
+    def __init__(self, dtype, n, index=0):
+        import torch
+        self.dtype, self._n, self.device = dtype, n, torch.device("cuda", index)
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):
+        raise AssertionError("the binding must reject this field before reading its pointer")
+
+
+def test_binding_rejects_bad_fields_before_any_launch():
+    """A field of the wrong dtype, size or device is refused in Python, before
+    the C call (which would read N^3 float32 values from its pointer)."""
+    torch = pytest.importorskip("torch")
+    import paper_1506_02729_gb300 as fkp
+    N = 16
+    fkp.check_field(_FakeCudaTensor(torch.float32, N ** 3), N, 0)
+    with pytest.raises(TypeError):
+        fkp.check_field(_FakeCudaTensor(torch.float16, N ** 3), N, 0)
+    with pytest.raises(TypeError):
+        fkp.check_field(_FakeCudaTensor(torch.float64, N ** 3), N, 0)
+    with pytest.raises(ValueError):
+        fkp.check_field(_FakeCudaTensor(torch.float32, N ** 3 - 1), N, 0)
+    with pytest.raises(ValueError):
+        fkp.check_field(_FakeCudaTensor(torch.float32, N ** 3, index=1), N, 0)
+    with pytest.raises(TypeError):
+        fkp.check_field(np.zeros((N, N, N), np.float32), N, 0)

@@ -85,7 +85,7 @@ def test_batch_matches_oracle(mocks):
     err = p_errors(got, ref)
     assert max(err.values()) < P_TOL, err
     for k in ("alpha", "I22", "N0"):
-        assert abs(got[k] / ref[k] - 1) < 1e-6, k
+        assert abs(got[k] / ref[k] - 1) < 1e-10, k
 
 
 def test_batch_ragged_grid_host_catalogs_and_growth(mocks):

@@ -62,7 +62,7 @@ def test_small_bispectrum_matches_oracle(small_b, contraction):
     for l in (0, 2, 4):
         d = np.maximum(np.abs(ref[f"N{l}"]), np.abs(ref["N0"]))
         assert np.max(np.abs(b[f"N{l}"] - ref[f"N{l}"]) / d) < SN_TOL, l
-    assert abs(b["I33"] / ref["I33"] - 1) < 1e-6
+    assert abs(b["I33"] / ref["I33"] - 1) < 1e-10
 
 
 def test_3way_split_matches_fp32_contraction(small_b):
@@ -188,6 +188,6 @@ def test_single_object_shot_noise_identity(contraction):
     _, b = plan.bispectrum(to_device(gal), to_device(ran), contraction=contraction)
     assert np.array_equal(b["tri"].astype(int), np.asarray(ref["tri"]))
     assert np.array_equal(b["NT"], ref["NT"])
-    assert abs(b["I33"] - 2.0) < 1e-6
+    assert abs(b["I33"] - 2.0) < 1e-12
     assert np.max(np.abs(b["N0"] - 0.625)) < 1e-5
     assert np.max(np.abs(b["B0"] + 0.125)) < 1e-5
