@@ -128,10 +128,7 @@ def bispectrum(gal, ran, geom, bshells, ells=(0, 2, 4), tris=None):
     """B^(l) for the given triangles (default: all a >= b >= c with N_T > 0)."""
     g = _pw._geom(geom)
     N = int(g["N"])
-    F, Fw, sc = _pw.fkp_grids(gal, ran, g, with_w2=True)
-    lmax = max(ells)
-    Fl = _pw.legendre(F, g, lmax=lmax)
-    Fwl = _pw.legendre(Fw, g, lmax=lmax)
+    Fl, Fwl, sc = _pw.survey_fields(gal, ran, g, lmax=max(ells), with_w2=True)
     return bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells, tris)
 
 

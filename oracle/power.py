@@ -11,7 +11,8 @@ scalars        alpha (Sec. III.A, above eq. F0; weighted reading), I_22 (eq. I22
                I_33 = alpha sum_r nbar^2 w^3 (the normalisation eq. BispMono divides by,
                left undefined by the paper; FKP-type reading), S_3 (last term of
                eq. Noise0), L^ab at k = 0 (eq. Lab).
-assign         interpolation of objects to grid nodes (eq. mapFFT): CIC or TSC.
+assign         interpolation of objects to grid nodes (eq. mapFFT): CIC, TSC or
+               PCS; interlaced pairs of grids (Sec. III.A after eq. mapFFT).
 moments        F x^_a x^_b and F x^_a x^_b x^_c x^_d about the observer
                (eqs. Qij, Qijkl, Qab) with x^ taken at the grid node.
 legendre       F_0 (eq. F0), F_2 (eqs. F2, delta2b), F_4 (eqs. delta4, delta4b) from
@@ -72,6 +73,7 @@ def _geom(g):
     out.setdefault("P_fkp", 1e4)
     out.setdefault("alpha_mode", 0)
     out.setdefault("assign", 2)
+    out.setdefault("interlace", False)
     return out
 
 
@@ -141,8 +143,11 @@ def assign(pos, values, geom):
 
     u = (x - origin)/H.  CIC: i0 = floor(u), d = u - i0, weights (1-d, d) on
     (i0, i0+1).  TSC: i0 = floor(u + 1/2), d = u - i0, weights
-    (1/2 - d)^2/2, 3/4 - d^2, (1/2 + d)^2/2 on (i0-1, i0, i0+1).  Node
-    indices are taken mod N.
+    (1/2 - d)^2/2, 3/4 - d^2, (1/2 + d)^2/2 on (i0-1, i0, i0+1).  PCS (the
+    paper's fourth-order interpolation, Sec. III.A after eq. mapFFT): i0 =
+    floor(u), d = u - i0, the cubic B-spline weights (1-d)^3/6,
+    (4 - 6d^2 + 3d^3)/6, (1 + 3d + 3d^2 - 3d^3)/6, d^3/6 on (i0-1, ..., i0+2).
+    Node indices are taken mod N.
     """
     g = _geom(geom)
     N, L, p = int(g["N"]), float(g["L"]), int(g["assign"])
@@ -159,8 +164,13 @@ def assign(pos, values, geom):
             d = u[:, a] - i0
             taps.append([(i0 - 1, 0.5 * (0.5 - d) ** 2), (i0, 0.75 - d * d),
                          (i0 + 1, 0.5 * (0.5 + d) ** 2)])
+        elif p == 4:
+            i0 = np.floor(u[:, a])
+            d = u[:, a] - i0
+            taps.append([(i0 - 1, (1.0 - d) ** 3 / 6.0), (i0, (4.0 - 6.0 * d * d + 3.0 * d ** 3) / 6.0),
+                         (i0 + 1, (1.0 + 3.0 * d + 3.0 * d * d - 3.0 * d ** 3) / 6.0), (i0 + 2, d ** 3 / 6.0)])
         else:
-            raise ValueError("assign must be 2 (CIC) or 3 (TSC)")
+            raise ValueError("assign must be 2 (CIC), 3 (TSC) or 4 (PCS)")
     grid = np.zeros(N * N * N)
     for iz, wz in taps[2]:
         jz = np.mod(iz.astype(np.int64), N)
@@ -264,6 +274,51 @@ def legendre(grid, geom, lmax=4, compensate=None):
     return out
 
 
+def shifted_geometry(geom):
+    """The second grid of an interlaced pair: nodes at origin + (i + 1/2) H."""
+    g = _geom(geom)
+    H = float(g["L"]) / int(g["N"])
+    g2 = dict(g)
+    g2["origin"] = tuple(float(o) + 0.5 * H for o in g["origin"])
+    return g2
+
+
+def interlace_fields(F1, F2, N):
+    """F_l = [F_l^(1) + e^{-i pi (n_x + n_y + n_z)/N} F_l^(2)] / 2.  The
+    second grid's nodes sit half a cell further along every axis, so its DFT
+    refers to an origin shifted by H/2 (1, 1, 1); the phase refers it back to
+    the first grid's origin, and the average cancels the aliased images of
+    odd order (the interlaced grids of Sec. III.A, after eq. mapFFT)."""
+    nx, ny, nz = mode_vectors(N)
+    ph = np.exp(-1j * np.pi * (nx + ny + nz) / N)
+    return {l: 0.5 * (F1[l] + ph * F2[l]) for l in F1}
+
+
+def survey_fields(gal, ran, geom, lmax=4, with_w2=False):
+    """F_l (and F^w_l) of a survey: the Legendre fields of its grid, or with
+    interlace=True of the interlaced pair of grids, compensated by the
+    window after the average."""
+    g = _geom(geom)
+    F, Fw, sc = fkp_grids(gal, ran, g, with_w2=with_w2)
+    if not g.get("interlace"):
+        Fl = legendre(F, g, lmax=lmax)
+        Fwl = legendre(Fw, g, lmax=lmax) if with_w2 else None
+        return Fl, Fwl, sc
+    N = int(g["N"])
+    g2 = shifted_geometry(g)
+    F2, Fw2, _ = fkp_grids(gal, ran, g2, with_w2=with_w2)
+    Fl = interlace_fields(legendre(F, g, lmax, compensate=False), legendre(F2, g2, lmax, compensate=False), N)
+    Fwl = None
+    if with_w2:
+        Fwl = interlace_fields(legendre(Fw, g, lmax, compensate=False), legendre(Fw2, g2, lmax, compensate=False), N)
+    if g["compensate"]:
+        W = window(N, int(g["assign"]))
+        Fl = {l: v / W for l, v in Fl.items()}
+        if Fwl is not None:
+            Fwl = {l: v / W for l, v in Fwl.items()}
+    return Fl, Fwl, sc
+
+
 # ---------------------------------------------------------------------------
 # a5: binning and P_l
 # ---------------------------------------------------------------------------
@@ -327,8 +382,7 @@ def bin_power(F, geom, bins, I22, N0):
 def power(gal, ran, geom, bins, lmax=4):
     """P_0, P_2, P_4, P_4b of a survey (gridded FFT estimator, FP64)."""
     g = _geom(geom)
-    F, _, sc = fkp_grids(gal, ran, g)
-    Fl = legendre(F, g, lmax=lmax)
+    Fl, _, sc = survey_fields(gal, ran, g, lmax=lmax)
     res = bin_power(Fl, g, bins, sc["I22"], sc["N0"])
     res.update({k: sc[k] for k in ("alpha", "I22", "I33", "N0", "N0_fkp", "S3", "Lab", "W_g", "W_r")})
     return res

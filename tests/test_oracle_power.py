@@ -74,16 +74,20 @@ def test_fft_is_the_dft(N):
 
 
 def _bspline(s, p):
+    """The centred B-spline of order p (textbook piecewise polynomials)."""
     s = np.abs(s)
     if p == 2:
         return np.where(s < 1, 1 - s, 0.0)
-    return np.where(s < 0.5, 0.75 - s * s, np.where(s < 1.5, 0.5 * (1.5 - s) ** 2, 0.0))
+    if p == 3:
+        return np.where(s < 0.5, 0.75 - s * s, np.where(s < 1.5, 0.5 * (1.5 - s) ** 2, 0.0))
+    return np.where(s < 1, (4 - 6 * s * s + 3 * s ** 3) / 6, np.where(s < 2, (2 - s) ** 3 / 6, 0.0))
 
 
-@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("p", [2, 3, 4])
 def test_assignment_is_the_bspline_kernel(p):
     """Each node gets w * prod_a B_p(node_a - u_a): the order-p B-spline
-    (CIC p=2, TSC p=3) of the distance in cells, with periodic wrap."""
+    (CIC p=2, TSC p=3, PCS p=4) of the distance in cells, with periodic
+    wrap."""
     N, L = 8, 8.0
     g = dict(N=N, L=L, assign=p, origin=(0.0, 0.0, 0.0))
     pts = np.array([[3.25, 4.0, 0.1], [7.9, 0.5, 2.5], [0.0, 6.49, 5.51]])
@@ -334,7 +338,7 @@ def kernel_ft(p, q):
     of the kernel.  The kernel is even, so the transform is real.  No sinc
     formula is used: this derives the window from the kernel itself."""
     x, wq = np.polynomial.legendre.leggauss(24)
-    edges = {2: [-1.0, 0.0, 1.0], 3: [-1.5, -0.5, 0.5, 1.5]}[p]
+    edges = {2: [-1.0, 0.0, 1.0], 3: [-1.5, -0.5, 0.5, 1.5], 4: [-2.0, -1.0, 0.0, 1.0, 2.0]}[p]
     q = np.asarray(q, dtype=np.float64)
     out = np.zeros_like(q)
     for a, b in zip(edges[:-1], edges[1:]):
@@ -351,7 +355,7 @@ def kernel_window(N, p):
     return w1[:, None, None] * w1[None, :, None] * wx[None, None, :]
 
 
-@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("p", [2, 3, 4])
 @pytest.mark.parametrize("N", [8, 12, 30])
 def test_window_is_the_kernel_fourier_transform(p, N):
     """The compensation window of mode n is the product over axes of the
@@ -418,3 +422,59 @@ def test_monopole_shot_noise_subtraction_single_galaxy():
     assert abs(res["I22"] - I22) < 1e-12 and abs(res["N0"] - N0) < 1e-12
     assert np.max(np.abs(res["mono_raw"] - 1.0 / 16)) < 1e-12
     assert np.max(np.abs(res["P0"] + 0.25)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# interlaced grids (Sec. III.A, after eq. mapFFT)
+# ---------------------------------------------------------------------------
+
+def alias_sums(p, N, n, u, M=4000):
+    """Per axis, A = sum_m W(n + mN) e^{-2 pi i (n + mN) u / N} and B = the
+    same sum with (-1)^m, |m| <= M, W(q) = [sin(pi q/N)/(pi q/N)]^p written out
+    here (the kernel's Fourier transform; the window test above checks it
+    against the kernel by quadrature).  By Poisson summation the grid's DFT of
+    one object at u is prod_a A_a, and the second grid's (nodes at i + 1/2),
+    referred back to the first grid's origin, is prod_a B_a."""
+    m = np.arange(-M, M + 1)
+    q = n[:, None] + m[None, :] * N
+    x = np.pi * q / N
+    with np.errstate(divide="ignore", invalid="ignore"):
+        W = np.where(q == 0, 1.0, (np.sin(x) / np.where(q == 0, 1.0, x)) ** p)
+    e = W * np.exp(-2j * np.pi * q * u / N)
+    return e.sum(1), (e * np.where(m % 2 == 0, 1.0, -1.0)[None, :]).sum(1)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_interlaced_grid_keeps_only_even_alias_images(p):
+    """One object at a generic position, compensation off.  The interlaced
+    F_0 = [F^(1) + e^{-i pi (n_x+n_y+n_z)/N} F^(2)]/2 must equal
+    (prod_a A_a + prod_a B_a)/2 = the sum over alias images m with m_x + m_y +
+    m_z even only: the odd images cancel.  A wrong sign or half-cell in the
+    phase, or the shift applied to the wrong grid, fails."""
+    N, L = 12, 12.0
+    u = np.array([3.37, 7.81, 5.06])
+    g = dict(N=N, L=L, assign=p, origin=(0.0, 0.0, 0.0), observer=(6.3, -4.0, 2.2), compensate=False,
+             interlace=True, periodic=True, alpha_mode=1)
+    w = np.array([1.0], np.float32)
+    cat = dict(x=np.array([u[0]], np.float32), y=np.array([u[1]], np.float32), z=np.array([u[2]], np.float32),
+               w=w, nbar=np.ones(1, np.float32))
+    # a zero-weight random (alpha = N_g/N_r = 1): F is the galaxy's grid alone
+    ran = dict(x=np.array([1.0], np.float32), y=np.array([1.0], np.float32), z=np.array([1.0], np.float32),
+               w=np.array([0.0], np.float32), nbar=np.ones(1, np.float32))
+    Fl, _, _ = op.survey_fields(cat, ran, g, lmax=0)
+    uu = np.array([float(np.float32(v)) for v in u])
+    n1 = np.fft.fftfreq(N, 1.0 / N)
+    nh = np.fft.rfftfreq(N, 1.0 / N)
+    M = 200000 if p == 2 else 4000  # the CIC image sum converges slowest
+    Ax, Bx = alias_sums(p, N, nh, uu[0], M)
+    Ay, By = alias_sums(p, N, n1, uu[1], M)
+    Az, Bz = alias_sums(p, N, n1, uu[2], M)
+    A = Az[:, None, None] * Ay[None, :, None] * Ax[None, None, :]
+    B = Bz[:, None, None] * By[None, :, None] * Bx[None, None, :]
+    ref = 0.5 * (A + B)
+    assert np.max(np.abs(Fl[0] - ref)) < 1e-9
+    # and not the plain (non-interlaced) grid, whose images of odd order remain
+    g1 = dict(g, interlace=False)
+    F1, _, _ = op.survey_fields(cat, ran, g1, lmax=0)
+    assert np.max(np.abs(F1[0] - A)) < 1e-9
+    assert np.max(np.abs(F1[0] - ref)) > 1e-3
