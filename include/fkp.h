@@ -14,7 +14,8 @@
  *   - Fourier sign e^{-ik.x}; the DFT phase origin is the box corner.
  *   - alpha = W_g / W_r (weighted) by default, N_g/N_r on request.
  *   - x^ (the line of sight) is taken at grid nodes about the observer.
- *   - CIC (assign = 2) or TSC (assign = 3) with nodes at origin + i*L/N.
+ *   - CIC (assign = 2), TSC (3) or PCS (4) with nodes at origin + i*L/N,
+ *     optionally interlaced (a second grid half a cell further).
  *   - Modes with any |n_a| = N/2 are excluded from every bin and shell.
  *   - P bins are half-open [kmin + i dk, kmin + (i+1) dk), decided in FP64.
  *   - P_4b = [35/2 <|F_2|^2> - 5 <Re F_2 F_0*> - 7/2 <|F_0|^2>] / I_22.
@@ -66,10 +67,17 @@ typedef struct {
 
 /* Box, grid and observer.  The grid has N^3 nodes at origin + i*L/N.
  * observer_at_infinity = 1 uses the constant unit vector los as x^.
+ * assign: 2 = CIC, 3 = TSC, 4 = PCS (the cubic B-spline: the paper's
+ * fourth-order interpolation, Sec. III.A after eq. mapFFT).
  * periodic = 0 rejects objects closer than assign/2 + 1 cells to a box face
  * (FKP_EGEOM); periodic = 1 wraps node indices mod N.
  * compensate = 1 divides every mode by prod_a sinc(pi n_a/N)^assign.
- * alpha_mode: 0 = W_g/W_r, 1 = N_g/N_r. */
+ * alpha_mode: 0 = W_g/W_r, 1 = N_g/N_r.
+ * interlace = 1 grids every field twice, the second time on nodes at
+ * origin + (i + 1/2) L/N, and averages F_l = [F_l^(1) + e^{-i pi (n_x + n_y +
+ * n_z)/N} F_l^(2)] / 2 (the paper's interlaced grids: the odd alias images
+ * cancel); it doubles the gridding and the x- and y-passes.  Not with
+ * fkp_power_from_grid, fkp_power_from_grid_noalloc or fkp_power_batch. */
 typedef struct {
   double L;
   double origin[3];
@@ -82,6 +90,7 @@ typedef struct {
   int periodic;
   double P_fkp;
   int alpha_mode;
+  int interlace;
 } fkp_geometry_t;
 
 /* P bins: edges kmin + i*dk, i = 0..nbins (h/Mpc), half-open. */
@@ -173,10 +182,26 @@ int fkp_plan_set_schedule(void *plan, int x_mult, int y_threads, int z_threads);
  * are the same either way. */
 int fkp_plan_set_graphs(void *plan, int enable);
 
+/* Random catalog shared by many mocks (Sec. III.C, Performance: gridding
+ * the randoms is most of the time, 210 s of the paper's 232 s, and mocks for
+ * a covariance estimate usually share one random catalog).  Grids `ran` once
+ * onto the plan without alpha -- R(x) = sum_r w W(x - x_r), and for
+ * bispectrum plans R^w(x) = sum_r w^2 W(x - x_r) -- and keeps its scalar sums
+ * (W_r, sum w^2, sum w^3, sum nbar w^2, sum nbar^2 w^3, L^ab) and its size.
+ * Later fkp_power, fkp_bispectrum and fkp_power_batch calls with ran (rans)
+ * == NULL grid only the galaxies and use F = G - alpha R and F^w = G^w +
+ * alpha^2 R^w with alpha from the galaxies' W_g and the cached W_r; results
+ * equal those of passing the same random catalog (up to the rounding of
+ * each random term to the grid's 2^-40 fixed point).  A new call replaces the
+ * cache; ran->n = 0 drops it.  The cached grids take 8 N^3 bytes each.
+ * FKP_EGEOM if a random lies too close to a box face (non-periodic plans). */
+int fkp_plan_cache_randoms(void *plan, const fkp_catalog_t *ran, void *cuda_stream);
+
 /* P_l of one survey (Sec. III.A).  Enqueues every step on cuda_stream (a
  * cudaStream_t, NULL = legacy default stream), then synchronizes it and
- * fills out.  FKP_EGEOM if an object lies too close to a box face
- * (non-periodic plans). */
+ * fills out.  ran == NULL uses the plan's cached random catalog
+ * (fkp_plan_cache_randoms; FKP_ESTATE without one).  FKP_EGEOM if an object
+ * lies too close to a box face (non-periodic plans). */
 int fkp_power(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
               void *cuda_stream, fkp_power_out *out);
 
@@ -193,7 +218,8 @@ int fkp_power(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
  * largest nmock seen; FKP_ENOMEM when that exceeds the context's HBM budget
  * or the device.  Stage times in outs[k].timing_ms are those of the whole
  * batch: [1] gridding of all mocks, [2..4] the fused x, y, z passes (z with
- * the bin reduction), [7] the whole batch.  nmock: 1 .. 65535. */
+ * the bin reduction), [7] the whole batch.  nmock: 1 .. 65535.  rans == NULL:
+ * every mock uses the plan's cached random catalog. */
 int fkp_power_batch(void *plan, int nmock, const fkp_catalog_t *gals, const fkp_catalog_t *rans,
                     void *cuda_stream, fkp_power_out *outs);
 
@@ -204,7 +230,8 @@ int fkp_power_from_grid(void *plan, const float *F_device, double I22, double N0
                         void *cuda_stream, fkp_power_out *out);
 
 /* P_l and B_l of one survey (Sec. III.B).  contraction is one of
- * FKP_CONTRACT_FP32, _BF16X3, _BF16X6. */
+ * FKP_CONTRACT_FP32, _BF16X3, _BF16X6.  ran == NULL uses the plan's cached
+ * random catalog. */
 int fkp_bispectrum(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
                    int contraction, void *cuda_stream, fkp_power_out *pout, fkp_bisp_out *bout);
 

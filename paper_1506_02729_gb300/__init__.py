@@ -27,7 +27,7 @@ EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_
            "fkp_power_from_grid_noalloc", "fkp_server_create", "fkp_server_submit", "fkp_server_poll",
            "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy", "fkp_check_tables",
            "fkp_plan_set_graphs", "fkp_plan_schedule", "fkp_plan_set_schedule", "fkp_power_batch",
-           "fkp_selftest_bounded_wait"]
+           "fkp_selftest_bounded_wait", "fkp_plan_cache_randoms"]
 
 
 class FKPError(RuntimeError):
@@ -44,7 +44,8 @@ class Catalog(C.Structure):
 class Geometry(C.Structure):
     _fields_ = [("L", C.c_double), ("origin", C.c_double * 3), ("observer", C.c_double * 3),
                 ("observer_at_infinity", C.c_int), ("los", C.c_double * 3), ("N", C.c_int), ("assign", C.c_int),
-                ("compensate", C.c_int), ("periodic", C.c_int), ("P_fkp", C.c_double), ("alpha_mode", C.c_int)]
+                ("compensate", C.c_int), ("periodic", C.c_int), ("P_fkp", C.c_double), ("alpha_mode", C.c_int),
+                ("interlace", C.c_int)]
 
 
 class PBins(C.Structure):
@@ -126,6 +127,7 @@ def lib():
         L.fkp_plan_set_schedule.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.fkp_version.restype = C.c_char_p
         L.fkp_selftest_bounded_wait.argtypes = [C.c_int, C.c_uint]
+        L.fkp_plan_cache_randoms.argtypes = [vp, C.POINTER(Catalog), vp]
         _lib = L
     return _lib
 
@@ -219,14 +221,14 @@ def _stream_handle(stream):
 
 def geometry(g):
     """Geometry struct from a dict (keys of mockgen.Survey.geometry() plus
-    optional observer=None/los, compensate, periodic, alpha_mode)."""
+    optional observer=None/los, compensate, periodic, alpha_mode, interlace)."""
     obs = g.get("observer", (0.0, 0.0, 0.0))
     inf = obs is None
     return Geometry(float(g["L"]), (C.c_double * 3)(*g.get("origin", (0.0, 0.0, 0.0))),
                     (C.c_double * 3)(*((0.0, 0.0, 0.0) if inf else obs)), 1 if inf else 0,
                     (C.c_double * 3)(*g.get("los", (0.0, 0.0, 1.0))), int(g["N"]), int(g.get("assign", 2)),
                     1 if g.get("compensate", True) else 0, 1 if g.get("periodic", False) else 0,
-                    float(g.get("P_fkp", 1e4)), int(g.get("alpha_mode", 0)))
+                    float(g.get("P_fkp", 1e4)), int(g.get("alpha_mode", 0)), 1 if g.get("interlace", False) else 0)
 
 
 class Plan:
@@ -291,33 +293,44 @@ class Plan:
         """CUDA-graph replay of the device-catalog power path (default on)."""
         _check(lib().fkp_plan_set_graphs(self._h, 1 if enable else 0))
 
-    def power(self, gal, ran, stream=None):
-        """P_0, P_2, P_4, P_4b and the scalars for one survey."""
-        cg, k1 = make_catalog(gal, self.device)
+    def cache_randoms(self, ran, stream=None):
+        """Grids a random catalog once onto the plan (without alpha) for later
+        calls with ran=None; an empty catalog drops the cache."""
         cr, k2 = make_catalog(ran, self.device)
+        _check(lib().fkp_plan_cache_randoms(self._h, C.byref(cr), _stream_handle(stream)))
+
+    def power(self, gal, ran, stream=None):
+        """P_0, P_2, P_4, P_4b and the scalars for one survey (ran=None: the
+        plan's cached random catalog)."""
+        cg, k1 = make_catalog(gal, self.device)
+        cr, k2 = make_catalog(ran, self.device) if ran is not None else (None, None)
         o, arr = self._pout()
-        _check(lib().fkp_power(self._h, C.byref(cg), C.byref(cr), _stream_handle(stream), C.byref(o)))
+        _check(lib().fkp_power(self._h, C.byref(cg), C.byref(cr) if cr is not None else None,
+                               _stream_handle(stream), C.byref(o)))
         return self._scalars(o, arr)
 
     def power_batch(self, gals, rans, stream=None):
         """P_0, P_2, P_4, P_4b and the scalars of several mocks on this plan's
         grid: each mock gridded on its own, then one launch per FFT pass for
         all of them.  Returns one result dict per mock."""
-        if len(gals) != len(rans) or not gals:
-            raise ValueError("need equal, non-zero numbers of galaxy and random catalogs")
+        if not gals or (rans is not None and len(gals) != len(rans)):
+            raise ValueError("need equal, non-zero numbers of galaxy and random catalogs (rans=None: the cache)")
         n = len(gals)
         cg, cr, keep = (Catalog * n)(), (Catalog * n)(), []
         for k in range(n):
             cg[k], k1 = make_catalog(gals[k], self.device)
-            cr[k], k2 = make_catalog(rans[k], self.device)
-            keep += [k1, k2]
+            keep.append(k1)
+            if rans is not None:
+                cr[k], k2 = make_catalog(rans[k], self.device)
+                keep.append(k2)
         outs = (PowerOut * n)()
         arrs = []
         for k in range(n):
             o, arr = self._pout()
             outs[k] = o
             arrs.append(arr)
-        _check(lib().fkp_power_batch(self._h, n, cg, cr, _stream_handle(stream), outs))
+        _check(lib().fkp_power_batch(self._h, n, cg, cr if rans is not None else None, _stream_handle(stream),
+                                     outs))
         return [self._scalars(outs[k], arrs[k]) for k in range(n)]
 
     def power_from_grid(self, F, I22=1.0, N0=0.0, stream=None):
@@ -332,7 +345,7 @@ class Plan:
     def bispectrum(self, gal, ran, contraction=FKP_CONTRACT_FP32, stream=None):
         """P_l and B_l (closed triangles a >= b >= c with N_T > 0)."""
         cg, k1 = make_catalog(gal, self.device)
-        cr, k2 = make_catalog(ran, self.device)
+        cr, k2 = make_catalog(ran, self.device) if ran is not None else (None, None)
         o, parr = self._pout()
         nt = self.ntri
         b = {"tri": np.zeros((nt, 3), dtype=np.int16), "NT": np.zeros(nt, dtype=np.int64),
@@ -345,8 +358,8 @@ class Plan:
         bo.centre_closed = b["centre_closed"].ctypes.data_as(C.POINTER(C.c_uint8))
         for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
             setattr(bo, k, b[k].ctypes.data_as(_DP))
-        _check(lib().fkp_bispectrum(self._h, C.byref(cg), C.byref(cr), int(contraction), _stream_handle(stream),
-                                    C.byref(o), C.byref(bo)))
+        _check(lib().fkp_bispectrum(self._h, C.byref(cg), C.byref(cr) if cr is not None else None,
+                                    int(contraction), _stream_handle(stream), C.byref(o), C.byref(bo)))
         b["I33"], b["S3"] = bo.I33, bo.S3
         return self._scalars(o, parr), b
 

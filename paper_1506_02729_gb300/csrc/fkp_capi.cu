@@ -397,7 +397,8 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   const int N = geom->N;
   if (N < 8 || N > 512 || (N & 1) || !smooth235(N))
     return set_error(FKP_EINVAL, "grid N=%d must be even, 8 <= N <= 512 and a product of 2, 3, 5", N);
-  if (geom->assign != 2 && geom->assign != 3) return set_error(FKP_EINVAL, "assign must be 2 (CIC) or 3 (TSC)");
+  if (geom->assign < 2 || geom->assign > 4)
+    return set_error(FKP_EINVAL, "assign must be 2 (CIC), 3 (TSC) or 4 (PCS)");
   if (!(geom->L > 0)) return set_error(FKP_EINVAL, "box side L must be positive");
   if (pb->nbins < 1 || pb->nbins > kMaxBins || !(pb->dk > 0) || !(pb->kmin >= 0))
     return set_error(FKP_EINVAL, "bad P bins (nbins in [1,%d], dk > 0, kmin >= 0)", kMaxBins);
@@ -455,9 +456,23 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   g.assign = geom->assign;
   g.periodic = geom->periodic ? 1 : 0;
   g.P_fkp = (float)geom->P_fkp;
-  g.P_fkp_d = geom->P_fkp;
+  g.P_fkp_lo = (float)(geom->P_fkp - (double)g.P_fkp);
   g.alpha_mode = geom->alpha_mode;
   observer_node(g);
+  P->interlace = geom->interlace != 0;
+  if (P->interlace) {
+    // the second grid: nodes at origin + (i + 1/2) H
+    GeomDev& h = P->g2;
+    h = g;
+    const double half = 0.5 * geom->L / N;
+    h.ox = (float)(geom->origin[0] + half);
+    h.oy = (float)(geom->origin[1] + half);
+    h.oz = (float)(geom->origin[2] + half);
+    h.rx = (float)(geom->origin[0] + half - geom->observer[0]);
+    h.ry = (float)(geom->origin[1] + half - geom->observer[1]);
+    h.rz = (float)(geom->origin[2] + half - geom->observer[2]);
+    observer_node(h);
+  }
 
   // FP64 tables on the host
   const double kf = 2.0 * M_PI / geom->L;
@@ -493,6 +508,12 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
       for (int a = 0; a < 3; ++a) winv[a * N + i] = (float)(1.0 / w);
     }
   }
+  std::vector<float2> hph(N);  // e^{-i pi n/N}, n the signed index of i
+  for (int i = 0; i < N; ++i) {
+    const int n = i <= N / 2 ? i : i - N;
+    const double a = M_PI * (double)n / (double)N;
+    hph[i] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
 
   // device workspace
   const size_t N3 = (size_t)N * N * N;
@@ -503,8 +524,13 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   auto A = [&](size_t bytes) { void* p = P->alloc(bytes); if (!p) ok = false; return p; };
   P->d_grid = (unsigned long long*)A(N3 * 8);
   if (wantB) P->d_gridw = (unsigned long long*)A(N3 * 8);
+  if (P->interlace) {
+    P->d_grid2 = (unsigned long long*)A(N3 * 8);
+    if (wantB) P->d_gridw2 = (unsigned long long*)A(N3 * 8);
+  }
+  P->d_hph = (float2*)A(sizeof(float2) * N);
   P->d_S1 = (float2*)A(half * sizeof(float2) * P->mt.nfields);
-  P->d_S2 = (float2*)A(half * sizeof(float2) * P->mt.ngroups);
+  P->d_S2 = (float2*)A(half * sizeof(float2) * P->mt.ngroups * (P->interlace ? 2 : 1));
   P->d_tw = (float2*)A(sizeof(float2) * N);
   P->d_lut = (short*)A(sizeof(short) * (n2max + 1));
   P->d_winv = (float*)A(sizeof(float) * 3 * N);
@@ -540,6 +566,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   CK(cudaMemcpy(P->d_tw, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(P->d_lut, lut.data(), sizeof(short) * (n2max + 1), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(P->d_winv, winv.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P->d_hph, hph.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
   const size_t hbytes = sizeof(double) * (BQ_N * pb->nbins + pb->nbins + DS_COUNT + LAB_NSUM + 8) + 64;
   CK(cudaMallocHost(&P->h_pinned, hbytes));
   for (auto& e : P->ev) CK(cudaEventCreate(&e));
@@ -625,10 +652,20 @@ static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
 // Enqueues scalars and gridding of both catalogs into d_grid (and d_gridw):
 // tile counts with the scalar sums, offsets, scatter into tile order, and
 // shared-memory accumulation per tile.
-int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s) {
+// One grid of the pair (which = 1: the interlaced second grid, nodes half a
+// cell further; no stage events).
+static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s, int which) {
+  const GeomDev& geo = which ? P->g2 : P->g;
+  unsigned long long* grid = which ? P->d_grid2 : P->d_grid;
+  unsigned long long* gridw = which ? P->d_gridw2 : P->d_gridw;
+  const unsigned long long* rgrid = which ? P->rc_grid2 : P->rc_grid;
+  const unsigned long long* rgridw = which ? P->rc_gridw2 : P->rc_gridw;
+  auto stage = [&](int e) { return which ? cudaSuccess : record_stage(P->ev[e], s); };
   const int N = P->g.N;
   const size_t N3 = (size_t)N * N * N;
-  const long long ntot = gal.n + ran.n;
+  const bool cached = ran.n < 0;  // the plan's cached random grids (fkp_plan_cache_randoms)
+  if (cached && !P->rc_valid) return set_error(FKP_ESTATE, "no cached random catalog on this plan");
+  const long long ntot = gal.n + (cached ? 0 : ran.n);
   if (ntot >= (1ll << 31)) return set_error(FKP_EINVAL, "at most 2^31-1 objects per call");
   if ((size_t)ntot > P->sort_cap) {
     // a captured graph refers to the old buffers
@@ -650,45 +687,187 @@ int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream
   // histogram spans every tile)
   const int nb = P->ctx->nsm;
   auto nblocks = [&](long long n) { return (int)std::max<long long>(1, std::min<long long>(nb, (n + 4095) / 4096)); };
-  const int nbg = nblocks(gal.n), nbr = nblocks(ran.n);
-  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
+  const int nbg = nblocks(gal.n), nbr = cached ? P->rc_nblk : nblocks(ran.n);
+  const long long nran = cached ? P->rc_n : ran.n;
+  if (!which) CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
   CK(cudaMemsetAsync(P->d_tcnt, 0, sizeof(int) * P->ntiles, s));
-  CK(record_stage(P->ev[0], s));
-  CK(launch_bin_count(gal, 0, P->g, P->d_scpart, P->d_tcnt, P->d_err, nbg, s));
-  CK(launch_bin_count(ran, 1, P->g, P->d_scpart + (size_t)nbg * SC_NSUM, P->d_tcnt, P->d_err, nbr, s));
-  CK(launch_scalars_finalize(P->d_scpart, nbg, nbr, gal.n, ran.n, P->g.alpha_mode, P->d_ds, s));
+  CK(stage(0));
+  CK(launch_bin_count(gal, 0, geo, P->d_scpart, P->d_tcnt, P->d_err, nbg, s));
+  if (cached)
+    CK(cudaMemcpyAsync(P->d_scpart + (size_t)nbg * SC_NSUM, P->rc_part, sizeof(double) * SC_NSUM * nbr,
+                       cudaMemcpyDeviceToDevice, s));
+  else
+    CK(launch_bin_count(ran, 1, geo, P->d_scpart + (size_t)nbg * SC_NSUM, P->d_tcnt, P->d_err, nbr, s));
+  CK(launch_scalars_finalize(P->d_scpart, nbg, nbr, gal.n, nran, geo.alpha_mode, P->d_ds, s));
   CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, s));
-  CK(record_stage(P->ev[1], s));
-  CK(cudaMemsetAsync(P->d_grid, 0, N3 * 8, s));
-  if (P->d_gridw) CK(cudaMemsetAsync(P->d_gridw, 0, N3 * 8, s));
+  CK(stage(1));
+  CK(cudaMemsetAsync(grid, 0, N3 * 8, s));
+  if (gridw) CK(cudaMemsetAsync(gridw, 0, N3 * 8, s));
   const double* obs = P->geom.observer;
-  float* vw2 = P->d_gridw ? P->d_vw2 : nullptr;
-  CK(launch_bin_scatter(gal, 0, P->g, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, nullptr, nbg, s));
-  CK(launch_bin_scatter(ran, 1, P->g, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s));
-  CK(launch_lab_finalize(P->d_labpart, ran.n > 0 ? nbr : 0, P->d_ds + DS_COUNT, s));
-  CK(launch_tile_accum(P->g, P->d_toff, P->d_xyzv, vw2, P->d_grid, P->d_gridw, s));
+  float* vw2 = gridw ? P->d_vw2 : nullptr;
+  CK(launch_bin_scatter(gal, 0, geo, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, nullptr, nbg, s));
+  if (cached) {
+    CK(cudaMemcpyAsync(P->d_ds + DS_COUNT, P->rc_lab, sizeof(double) * LAB_NSUM, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(launch_bin_scatter(ran, 1, geo, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s));
+    CK(launch_lab_finalize(P->d_labpart, ran.n > 0 ? nbr : 0, P->d_ds + DS_COUNT, s));
+  }
+  CK(launch_tile_accum(geo, P->d_toff, P->d_xyzv, vw2, grid, gridw, s));
+  if (cached)
+    CK(launch_combine_randoms(grid, rgrid, gridw, rgridw, P->d_ds, (long long)N3, P->ctx->nsm, s));
+  return FKP_OK;
+}
+
+// Enqueues scalars and gridding of both catalogs into d_grid (and d_gridw),
+// and for interlaced plans into the second grids too: tile counts with the
+// scalar sums, offsets, scatter into tile order, and shared-memory
+// accumulation per tile.
+int fkp::enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s) {
+  int rc = grid_pass(P, gal, ran, s, 0);
+  if (!rc && P->interlace) rc = grid_pass(P, gal, ran, s, 1);
+  if (rc) return rc;
   CK(record_stage(P->ev[2], s));
   return FKP_OK;
 }
 
-// Enqueues the three FFT passes, recombination and binning of one base grid.
-int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s) {
-  CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult));
-  CK(record_stage(P->ev[3], s));
-  CK(launch_ypass(P->d_S1, gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s, P->sched.y_threads));
-  CK(record_stage(P->ev[4], s));
-  ZParams zp;
+// The randoms' part of the grids without alpha (R = sum_r w W, and R^w =
+// sum_r w^2 W for bispectrum plans), the per-block partial scalar sums of
+// their count launch and their L^ab sums, kept on the plan for the mocks that
+// share this random catalog.
+static int cache_randoms(Plan* P, const CatDev& ran, cudaStream_t s) {
+  const int N = P->g.N;
+  const size_t N3 = (size_t)N * N * N;
+  P->rc_valid = false;
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);  // a captured graph may hold the old cache
+  P->graph_exec = nullptr;
+  P->last_valid = false;
+  if (ran.n == 0) return FKP_OK;
+  if (ran.n >= (1ll << 31)) return set_error(FKP_EINVAL, "at most 2^31-1 randoms");
+  const int nb = P->ctx->nsm;
+  const int nbr = (int)std::max<long long>(1, std::min<long long>(nb, (ran.n + 4095) / 4096));
+  if (!P->rc_grid) {
+    P->rc_grid = (unsigned long long*)P->alloc(N3 * 8);
+    if (P->d_gridw) P->rc_gridw = (unsigned long long*)P->alloc(N3 * 8);
+    if (P->interlace) {
+      P->rc_grid2 = (unsigned long long*)P->alloc(N3 * 8);
+      if (P->d_gridw) P->rc_gridw2 = (unsigned long long*)P->alloc(N3 * 8);
+    }
+    P->rc_part = (double*)P->alloc(sizeof(double) * SC_NSUM * nb);
+    P->rc_lab = (double*)P->alloc(sizeof(double) * LAB_NSUM);
+    if (!P->rc_grid || (P->d_gridw && !P->rc_gridw) || !P->rc_part || !P->rc_lab ||
+        (P->interlace && (!P->rc_grid2 || (P->d_gridw && !P->rc_gridw2))))
+      return set_error(FKP_ENOMEM, "cannot allocate the cached random grids");
+  }
+  if ((size_t)ran.n > P->sort_cap) {
+    if (P->d_xyzv) cudaFree(P->d_xyzv);
+    if (P->d_vw2) cudaFree(P->d_vw2);
+    P->d_xyzv = nullptr;
+    P->d_vw2 = nullptr;
+    P->sort_cap = 0;
+    const size_t cap = (size_t)ran.n + ran.n / 8 + 1024;
+    if (cudaMalloc(&P->d_xyzv, sizeof(float4) * cap) != cudaSuccess ||
+        (P->d_gridw && cudaMalloc(&P->d_vw2, sizeof(float) * cap) != cudaSuccess))
+      return set_error(FKP_ENOMEM, "cannot allocate the tile-sorted catalog (%lld objects)", ran.n);
+    P->sort_cap = cap;
+  }
+  float* vw2 = P->d_gridw ? P->d_vw2 : nullptr;
+  CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
+  for (int which = 0; which < (P->interlace ? 2 : 1); ++which) {
+    const GeomDev& geo = which ? P->g2 : P->g;
+    unsigned long long* rg = which ? P->rc_grid2 : P->rc_grid;
+    unsigned long long* rgw = which ? P->rc_gridw2 : P->rc_gridw;
+    CK(cudaMemsetAsync(P->d_tcnt, 0, sizeof(int) * P->ntiles, s));
+    CK(launch_bin_count(ran, 1, geo, P->rc_part, P->d_tcnt, P->d_err, nbr, s));
+    CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, s));
+    CK(cudaMemsetAsync(rg, 0, N3 * 8, s));
+    if (rgw) CK(cudaMemsetAsync(rgw, 0, N3 * 8, s));
+    CK(launch_bin_scatter(ran, 1, geo, P->geom.observer, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s,
+                          1));
+    CK(launch_lab_finalize(P->d_labpart, nbr, P->rc_lab, s));
+    CK(launch_tile_accum(geo, P->d_toff, P->d_xyzv, vw2, rg, rgw, s));
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (herr)
+    return set_error(FKP_EGEOM, "a random lies within assign/2+1 cells of a box face (or is not finite)");
+  P->rc_nblk = nbr;
+  P->rc_n = ran.n;
+  P->rc_valid = true;
+  return FKP_OK;
+}
+
+extern "C" int fkp_plan_cache_randoms(void* plan, const fkp_catalog_t* ran, void* stream) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P || !ran) return set_error(FKP_EINVAL, "NULL plan or catalog");
+  CK(cudaSetDevice(P->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CatDev r;
+  int rc = stage_catalog(P, ran, 1, r, s);
+  if (rc) return rc;
+  return cache_randoms(P, r, s);
+}
+
+// The random catalog of a call: the given one, or (ran == NULL) the plan's
+// cache, marked by n = -1.
+int fkp::randoms_of(Plan* P, const fkp_catalog_t* ran, CatDev& r, cudaStream_t s) {
+  if (!ran) {
+    if (!P->rc_valid) return set_error(FKP_ESTATE, "ran is NULL but the plan has no cached random catalog");
+    r = CatDev{};
+    r.n = -1;
+    return FKP_OK;
+  }
+  const int rc = stage_catalog(P, ran, 1, r, s);
+  if (rc) return rc;
+  if (r.n == 0) return set_error(FKP_EINVAL, "the random catalog is empty");
+  return FKP_OK;
+}
+
+// z-pass parameters of a plan (mode 0: P bins; the bispectrum path sets its
+// shell fields on top).
+ZParams fkp::zparams(const Plan* P, int mode) {
+  ZParams zp{};
   zp.nbins = P->pb.nbins;
   zp.lmax = P->lmax;
   zp.kf = (float)(2.0 * M_PI / P->geom.L);
   zp.lut = P->d_lut;
   zp.winv = P->d_winv;
-  zp.mode = 0;
+  zp.mode = mode;
   zp.nshells = 0;
   zp.nsh2 = 0;
   zp.slut = nullptr;
   zp.E = nullptr;
   zp.mm = 0;
+  zp.interlace = P->interlace ? 1 : 0;
+  zp.hph = P->d_hph;
+  zp.scale = P->interlace ? 0.5f : 1.f;
+  return zp;
+}
+
+int fkp::enqueue_xy(Plan* P, const unsigned long long* gq, const unsigned long long* gq2, const float* gf,
+                    cudaStream_t s, bool events) {
+  CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult));
+  if (events) CK(record_stage(P->ev[3], s));
+  CK(launch_ypass(P->d_S1, gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s, P->sched.y_threads));
+  if (P->interlace) {
+    // the second grid's groups follow the first's; the x- and y-passes apply
+    // its half-cell phases in x and y, the z-pass the one in z
+    float2* S2b = P->d_S2 + field_elems(P->g.N) * P->mt.ngroups;
+    CK(launch_xpass(gq2, nullptr, P->g2, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult,
+                    MockBatch(), P->d_hph));
+    CK(launch_ypass(P->d_S1, gq2, nullptr, P->g2, P->mt, P->fp, P->d_tw, S2b, P->d_err + 1, s, P->sched.y_threads,
+                    MockBatch(), P->d_hph));
+  }
+  if (events) CK(record_stage(P->ev[4], s));
+  return FKP_OK;
+}
+
+// Enqueues the three FFT passes, recombination and binning of one base grid
+// (of the interlaced pair d_grid, d_grid2 when the plan interlaces).
+int fkp::enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s) {
+  const int rc = enqueue_xy(P, gq, P->d_grid2, gf, s, true);
+  if (rc) return rc;
+  const ZParams zp = zparams(P, 0);
   CK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s,
                   P->ctx->nsm, P->sched.z_threads));
   CK(launch_reduce_bins(P->d_zpart, P->d_zpartc, zpass_blocks(P->g.N, P->sched.z_threads, P->ctx->nsm),
@@ -838,10 +1017,9 @@ extern "C" int fkp_power(void* plan, const fkp_catalog_t* gal, const fkp_catalog
   CatDev g, r;
   int rc = stage_catalog(P, gal, 0, g, s);
   if (rc) return rc;
-  rc = stage_catalog(P, ran, 1, r, s);
+  rc = randoms_of(P, ran, r, s);
   if (rc) return rc;
-  if (r.n == 0) return set_error(FKP_EINVAL, "the random catalog is empty");
-  const bool device_cats = (gal->on_device || gal->n == 0) && (ran->on_device || ran->n == 0);
+  const bool device_cats = (gal->on_device || gal->n == 0) && (!ran || ran->on_device || ran->n == 0);
   int replayed = 0;
   rc = enqueue_power(P, g, r, device_cats, s, &replayed);
   if (rc) return rc;
@@ -915,7 +1093,9 @@ extern "C" int fkp_power_batch(void* plan, int nmock, const fkp_catalog_t* gals,
   auto* P = static_cast<Plan*>(plan);
   if (!P) return set_error(FKP_EINVAL, "NULL plan");
   if (nmock < 1 || nmock > 65535) return set_error(FKP_EINVAL, "nmock = %d (1 .. 65535)", nmock);
-  if (!gals || !rans) return set_error(FKP_EINVAL, "NULL catalog array");
+  if (P->interlace) return set_error(FKP_EINVAL, "the fused batch does not interlace: use fkp_power per mock");
+  if (!gals) return set_error(FKP_EINVAL, "NULL catalog array");
+  if (!rans && !P->rc_valid) return set_error(FKP_ESTATE, "rans is NULL but the plan has no cached random catalog");
   CK(cudaSetDevice(P->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = reserve_batch(P, nmock);
@@ -930,8 +1110,7 @@ extern "C" int fkp_power_batch(void* plan, int nmock, const fkp_catalog_t* gals,
   for (int k = 0; k < nmock; ++k) {
     CatDev g, r;
     rc = stage_catalog(P, &gals[k], 0, g, s);
-    if (!rc) rc = stage_catalog(P, &rans[k], 1, r, s);
-    if (!rc && r.n == 0) rc = set_error(FKP_EINVAL, "mock %d: the random catalog is empty", k);
+    if (!rc) rc = randoms_of(P, rans ? &rans[k] : nullptr, r, s);
     if (rc) return rc;
     P->d_grid = P->b_grid + k * z.grid;
     P->d_ds = P->b_ds + k * z.ds;
@@ -954,18 +1133,7 @@ extern "C" int fkp_power_batch(void* plan, int nmock, const fkp_catalog_t* gals,
   CK(launch_ypass(P->b_S1, P->b_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->b_S2, perr, s, P->sched.y_threads,
                   my));
   CK(cudaEventRecord(P->ev[4], s));
-  ZParams zp;
-  zp.nbins = P->pb.nbins;
-  zp.lmax = P->lmax;
-  zp.kf = (float)(2.0 * M_PI / P->geom.L);
-  zp.lut = P->d_lut;
-  zp.winv = P->d_winv;
-  zp.mode = 0;
-  zp.nshells = 0;
-  zp.nsh2 = 0;
-  zp.slut = nullptr;
-  zp.E = nullptr;
-  zp.mm = 0;
+  const ZParams zp = zparams(P, 0);
   MockBatch mz;
   mz.n = nmock; mz.in = (long long)z.s2; mz.out = (long long)z.zpart; mz.out2 = (long long)z.zpartc;
   CK(launch_zpass(P->b_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->b_zpart, P->b_zpartc, perr, s, P->ctx->nsm,
@@ -1029,6 +1197,7 @@ extern "C" int fkp_power_from_grid(void* plan, const float* F, double I22, doubl
                                    fkp_power_out* out) {
   auto* P = static_cast<Plan*>(plan);
   if (!P || !F) return set_error(FKP_EINVAL, "NULL plan or grid");
+  if (P->interlace) return set_error(FKP_EINVAL, "a given field has no interlaced partner: use a plan without interlace");
   CK(cudaSetDevice(P->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));

@@ -69,6 +69,24 @@ struct Plan {
   int ntri = 0;
   void* bisp = nullptr;
 
+  // interlaced pair of grids (geom.interlace): the second grid's geometry
+  // (nodes half a cell further), its grids, and the half-cell phase table
+  // e^{-i pi n/N} by signed index
+  bool interlace = false;
+  GeomDev g2{};
+  unsigned long long *d_grid2 = nullptr, *d_gridw2 = nullptr;
+  float2* d_hph = nullptr;
+  unsigned long long *rc_grid2 = nullptr, *rc_gridw2 = nullptr;
+
+  // cached random catalog (fkp_plan_cache_randoms): its grids without alpha,
+  // R = sum_r w W and R^w = sum_r w^2 W, the per-block partial scalar sums
+  // of its count launch, its L^ab sums and its size
+  bool rc_valid = false;
+  unsigned long long *rc_grid = nullptr, *rc_gridw = nullptr;
+  double *rc_part = nullptr, *rc_lab = nullptr;
+  int rc_nblk = 0;
+  long long rc_n = 0;
+
   // host catalogs staged on the device (slot 0 galaxies, 1 randoms)
   void* staging[2] = {nullptr, nullptr};
   size_t staging_bytes[2] = {0, 0};
@@ -112,8 +130,14 @@ void build_moments(int lmax, MomentTable& mt);
 bool moments_identities_hold(const MomentTable& mt, int lmax);
 void observer_node(GeomDev& g);
 int stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, cudaStream_t s);
+int randoms_of(Plan* P, const fkp_catalog_t* ran, CatDev& r, cudaStream_t s);
 int enqueue_grids(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t s);
 int enqueue_fft_bin(Plan* P, const unsigned long long* gq, const float* gf, cudaStream_t s);
+// x- and y-passes of a field into the plan's S2: of the fixed-point grid gq
+// (and, interlaced, of gq2 on the second grid) or of the FP32 field gf.
+int enqueue_xy(Plan* P, const unsigned long long* gq, const unsigned long long* gq2, const float* gf,
+               cudaStream_t s, bool events);
+ZParams zparams(const Plan* P, int mode);
 int finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_scalars, double I22, double N0);
 int bisp_plan_init(Plan* P);
 void bisp_plan_free(Plan* P);
@@ -130,7 +154,11 @@ cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, doub
                              int nblk, cudaStream_t s);
 cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, cudaStream_t s);
 cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
-                               int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s);
+                               int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s,
+                               int raw = 0);
+cudaError_t launch_combine_randoms(unsigned long long* grid, const unsigned long long* rgrid,
+                                   unsigned long long* gridw, const unsigned long long* rgridw, const double* ds,
+                                   long long n, int nsm, cudaStream_t s);
 cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xyzv, const float* vw2,
                               unsigned long long* grid, unsigned long long* gridw, cudaStream_t s);
 cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
@@ -138,13 +166,16 @@ cudaError_t launch_wait_selftest(unsigned polls, int* flag, cudaStream_t s);
 // xm: x-pass blocks = SMs x resident blocks x xm; nt: threads per y- or
 // z-pass block (256 or 512).  The defaults are the 512^3 choices.  mb: the
 // mocks of one fused launch (blockIdx.z) and their buffer strides.
+// hph (x- and y-passes): for the second grid of an interlaced pair, the
+// table e^{-i pi n/N} by which the pass multiplies its output (its axis's
+// half-cell phase); nullptr otherwise.
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm = 2,
-                         MockBatch mb = MockBatch());
+                         MockBatch mb = MockBatch(), const float2* hph = nullptr);
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, float2* S2, int* err, cudaStream_t s, int nt = 256,
-                         MockBatch mb = MockBatch());
+                         MockBatch mb = MockBatch(), const float2* hph = nullptr);
 // The z-pass is persistent: zpass_blocks(N, nt, nsm) blocks, each writing
 // one column of the partial bins (part[key][block]); reduce over that count.
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,

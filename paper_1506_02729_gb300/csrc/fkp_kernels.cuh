@@ -30,7 +30,7 @@ struct GeomDev {
   int periodic;
   float P_fkp;
   int alpha_mode;
-  double P_fkp_d;      // P_FKP in FP64 (the scalar sums)
+  float P_fkp_lo;      // P_FKP - P_fkp (the scalar sums carry P_FKP as a float pair)
   int obs_x, obs_y, obs_z;  // grid node at the observer (x^ = 0 there), or -1
 };
 
@@ -92,6 +92,14 @@ struct ZParams {
   const signed char* slut;  // n^2 -> shell or -1
   float2* E;         // [3][2mm+1][2mm+1][mm+1]: F_0, F_2, F_4 on the shells
   int mm;            // largest |n_a| inside the outermost shell
+  // interlaced pair of grids: groups [ngroups, 2 ngroups) come from the
+  // second grid (nodes half a cell further); hph[i] = e^{-i pi n/N} with n the
+  // signed index of i, by which the z-pass multiplies those groups after its
+  // FFT (the x- and y-passes applied the x and y factors); scale = 1/2 averages
+  // the two grids (1 without interlacing)
+  int interlace = 0;
+  const float2* hph = nullptr;
+  float scale = 1.f;
 };
 
 // Catalog on the device.
@@ -133,15 +141,51 @@ __device__ __forceinline__ float fkp_weight(const CatDev& c, long long i, float 
   return c.w ? __ldg(c.w + i) : 1.0f / (1.0f + __ldg(c.nbar + i) * Pfkp);
 }
 
-// The same weight in FP64 for the scalar sums (alpha, I_22, N_0, I_33, S_3):
-// the FP32 reciprocal of d = 1 + nbar P_FKP refined by one Newton-Raphson
-// step r1 = r0 + r0 (1 - d r0), which squares its relative error (2^-24 ->
-// about 1e-14).  Weights given with the catalog are taken as they are.
-__device__ __forceinline__ double fkp_weight_f64(const CatDev& c, long long i, double Pfkp) {
-  if (c.w) return (double)__ldg(c.w + i);
-  const double d = fma((double)__ldg(c.nbar + i), Pfkp, 1.0);
-  const double r0 = (double)__frcp_rn((float)d);
-  return fma(r0, fma(-d, r0, 1.0), r0);
+// Double-single ("float-float") arithmetic for the scalar sums: a value is an
+// unevaluated pair hi + lo of FP32 numbers (about 48 significant bits), with
+// Knuth's TwoSum for exact additions and the FMA-based TwoProduct for exact
+// products.  It gives the FP64-level accuracy the normalisation and shot-noise
+// sums need at FP32 throughput (FP64 units are few on this part).
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.hi * b.hi;
+  return {p, fmaf(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi)};
+}
+__device__ __forceinline__ FF ff_mul(FF a, float b) {
+  const float p = a.hi * b;
+  return {p, fmaf(a.hi, b, -p) + a.lo * b};
+}
+// Running sum of float pairs.
+struct FFSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(FF x) {
+    const FF s = ff_two_sum(hi, x.hi);
+    hi = s.hi;
+    lo += s.lo + x.lo;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// The FKP weight as a float pair for the scalar sums: d = 1 + nbar P_FKP
+// exactly as a pair, the FP32 reciprocal r0 of its leading part, and one
+// Newton-Raphson step w = r0 + r0 (1 - d r0) with the residual formed by FMA
+// (relative error about 2^-46).  Weights given with the catalog are exact.
+__device__ __forceinline__ FF fkp_weight_ff(const CatDev& c, long long i, float Ph, float Pl) {
+  if (c.w) return {__ldg(c.w + i), 0.f};
+  const float nb = __ldg(c.nbar + i);
+  const float p = nb * Ph;
+  const float pe = fmaf(nb, Ph, -p) + nb * Pl;  // nbar P = p + pe
+  const FF d = ff_two_sum(1.f, p);               // 1 + p = d.hi + d.lo
+  const float dl = d.lo + pe;
+  const float r0 = __frcp_rn(d.hi);
+  const float res = fmaf(-dl, r0, fmaf(-d.hi, r0, 1.f));
+  return ff_two_sum(r0, r0 * res);
 }
 
 }  // namespace fkp

@@ -1,11 +1,12 @@
 // k_assign.cu - scalars and gridding of galaxies and randoms (Sec. III.A).
 //
-// Interpolation of the objects to the grid nodes (eq. mapFFT) with CIC or TSC
-// weights, as a counting sort by 16^3-cell tile followed by accumulation in
+// Interpolation of the objects to the grid nodes (eq. mapFFT) with CIC, TSC or
+// PCS (the paper's fourth-order) weights, as a counting sort by 16^3-cell tile followed by accumulation in
 // shared memory:
-//   count    per object: FKP weight and the FP64 partial sums of the scalars
-//            (W, sum w^2, sum w^3, sum nbar w^2, sum nbar^2 w^3, for alpha,
-//            I_22, I_33, N_0, S_3: eqs. I22def, N0true, Noise0),
+//   count    per object: FKP weight and the partial sums of the scalars (W,
+//            sum w^2, sum w^3, sum nbar w^2, sum nbar^2 w^3, for alpha, I_22,
+//            I_33, N_0, S_3: eqs. I22def, N0true, Noise0) in double-single
+//            arithmetic per thread and FP64 across threads,
 //            the geometry check and one count for the object's tile (block
 //            histogram in shared memory);
 //   scan     tile offsets (exclusive prefix sum);
@@ -25,14 +26,20 @@
 namespace fkp {
 
 constexpr int kTile = 16;            // cells per tile side
-constexpr int kReg = kTile + 2;      // tile plus one halo cell on each side
-constexpr int kReg3 = kReg * kReg * kReg;
+// Region a tile's objects reach, from one cell below the tile: the tile
+// plus one halo cell on each side for CIC and TSC, and one more above for
+// PCS (taps c-1 .. c+2 of the centre cell c).
+template <int P>
+__host__ __device__ constexpr int reg_side() { return P == 4 ? kTile + 3 : kTile + 2; }
+template <int P>
+__host__ __device__ constexpr int reg_cells() { return reg_side<P>() * reg_side<P>() * reg_side<P>(); }
 
 int assign_tiles_per_axis(int N) { return (N + kTile - 1) / kTile; }
 
 // Centre cell of an object: TSC taps c-1..c+1 around c = floor(u + 1/2);
-// CIC taps c, c+1 with c = floor(u).  Returns false when a tap would leave
-// [1, N-2] (non-periodic) or the position is not finite.
+// CIC taps c, c+1 with c = floor(u); PCS taps c-1..c+2 with c = floor(u).
+// Returns false when a tap would leave [1, N-2] (non-periodic) or the
+// position is not finite.
 template <int P>
 __device__ __forceinline__ bool centre_cell(const GeomDev& g, float px, float py, float pz, int& cx, int& cy,
                                             int& cz) {
@@ -44,7 +51,7 @@ __device__ __forceinline__ bool centre_cell(const GeomDev& g, float px, float py
     cx = (int)floorf(ux + sh);
     cy = (int)floorf(uy + sh);
     cz = (int)floorf(uz + sh);
-    const int lo = P == 3 ? 2 : 1, hi = N - 3;
+    const int lo = P == 2 ? 1 : 2, hi = P == 4 ? N - 4 : N - 3;
     return cx >= lo && cy >= lo && cz >= lo && cx <= hi && cy <= hi && cz <= hi;
   }
   if (!(fabsf(ux) < 1e8f && fabsf(uy) < 1e8f && fabsf(uz) < 1e8f)) return false;
@@ -77,19 +84,21 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
   __shared__ double sh[32];
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
   __syncthreads();
-  double s_w = 0.0, s_w2 = 0.0, s_w3 = 0.0, s_nw2 = 0.0, s_n2w3 = 0.0;
+  FFSum s_w, s_w2, s_w3, s_nw2, s_n2w3;
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double w = fkp_weight_f64(c, i, g.P_fkp_d);
-    const double w2 = w * w;
-    s_w += w;
-    s_w2 += w2;
-    s_w3 += w2 * w;
+    const FF w = fkp_weight_ff(c, i, g.P_fkp, g.P_fkp_lo);
+    const FF w2 = ff_mul(w, w);
+    const FF w3 = ff_mul(w2, w);
+    s_w.add(w);
+    s_w2.add(w2);
+    s_w3.add(w3);
     if (is_ran) {
-      const double nb = (double)__ldg(c.nbar + i);
-      s_nw2 += nb * w2;
-      s_n2w3 += nb * nb * w2 * w;
+      const float nb = __ldg(c.nbar + i);
+      const FF nw2 = ff_mul(w2, nb);
+      s_nw2.add(nw2);
+      s_n2w3.add(ff_mul(ff_mul(w3, nb), nb));
     }
     int cx, cy, cz;
     if (centre_cell<P>(g, __ldg(c.x + i), __ldg(c.y + i), __ldg(c.z + i), cx, cy, cz))
@@ -103,15 +112,15 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
   double* out = part + (size_t)blockIdx.x * SC_NSUM;
   double v;
   if (!is_ran) {
-    v = block_sum_f64(s_w, sh);  if (threadIdx.x == 0) out[SC_G_W] = v;
-    v = block_sum_f64(s_w2, sh); if (threadIdx.x == 0) out[SC_G_W2] = v;
-    v = block_sum_f64(s_w3, sh); if (threadIdx.x == 0) out[SC_G_W3] = v;
+    v = block_sum_f64(s_w.value(), sh);  if (threadIdx.x == 0) out[SC_G_W] = v;
+    v = block_sum_f64(s_w2.value(), sh); if (threadIdx.x == 0) out[SC_G_W2] = v;
+    v = block_sum_f64(s_w3.value(), sh); if (threadIdx.x == 0) out[SC_G_W3] = v;
   } else {
-    v = block_sum_f64(s_w, sh);    if (threadIdx.x == 0) out[SC_R_W] = v;
-    v = block_sum_f64(s_w2, sh);   if (threadIdx.x == 0) out[SC_R_W2] = v;
-    v = block_sum_f64(s_w3, sh);   if (threadIdx.x == 0) out[SC_R_W3] = v;
-    v = block_sum_f64(s_nw2, sh);  if (threadIdx.x == 0) out[SC_R_NW2] = v;
-    v = block_sum_f64(s_n2w3, sh); if (threadIdx.x == 0) out[SC_R_N2W3] = v;
+    v = block_sum_f64(s_w.value(), sh);    if (threadIdx.x == 0) out[SC_R_W] = v;
+    v = block_sum_f64(s_w2.value(), sh);   if (threadIdx.x == 0) out[SC_R_W2] = v;
+    v = block_sum_f64(s_w3.value(), sh);   if (threadIdx.x == 0) out[SC_R_W3] = v;
+    v = block_sum_f64(s_nw2.value(), sh);  if (threadIdx.x == 0) out[SC_R_NW2] = v;
+    v = block_sum_f64(s_n2w3.value(), sh); if (threadIdx.x == 0) out[SC_R_N2W3] = v;
   }
 }
 
@@ -145,15 +154,17 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ cnt
 // objects per tile in shared memory; one global atomic per touched tile then
 // reserves the chunk's range inside the tile's segment; pass 2 re-reads the
 // chunk and writes each object at its reserved slot.
+// raw = 1 (randoms only): values w and w^2 without alpha, for the cached
+// random grids that later mocks combine with their own alpha.
 template <int P>
-__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ran, GeomDev g, int ntx, int ntiles,
-                                                             float obx, float oby, float obz,
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ran, int raw, GeomDev g, int ntx,
+                                                             int ntiles, float obx, float oby, float obz,
                                                              const double* __restrict__ ds, int* __restrict__ cur,
                                                              float4* __restrict__ xyzv, float* __restrict__ vw2,
                                                              double* __restrict__ labpart) {
   extern __shared__ int hist[];
   __shared__ double sh[32];
-  const float alpha = (float)ds[DS_ALPHA];
+  const float alpha = raw ? -1.f : (float)ds[DS_ALPHA];
   const long long chunk = (c.n + gridDim.x - 1) / gridDim.x;
   const long long i0 = blockIdx.x * chunk;
   const long long i1 = i0 + chunk < c.n ? i0 + chunk : c.n;
@@ -176,7 +187,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ra
     if (centre_cell<P>(g, px, py, pz, cx, cy, cz)) {
       const int slot = atomicAdd(hist + tile_of(cx, cy, cz, g.N, ntx), 1);
       xyzv[slot] = make_float4(px, py, pz, is_ran ? -alpha * w : w);
-      if (vw2) vw2[slot] = is_ran ? alpha * alpha * w * w : w * w;
+      if (vw2) vw2[slot] = is_ran && !raw ? alpha * alpha * w * w : w * w;
     }
     if (is_ran) {
       float hx, hy, hz;
@@ -213,7 +224,7 @@ __device__ __forceinline__ void tap_weights(float u, int& i0, float* wt) {
     i0 = (int)f;
     wt[0] = 1.f - d;
     wt[1] = d;
-  } else {
+  } else if (P == 3) {
     const float f = floorf(u + 0.5f);
     const float d = u - f;
     i0 = (int)f - 1;
@@ -221,6 +232,16 @@ __device__ __forceinline__ void tap_weights(float u, int& i0, float* wt) {
     wt[0] = 0.5f * a * a;
     wt[1] = 0.75f - d * d;
     wt[2] = 0.5f * b * b;
+  } else {
+    // PCS: the cubic B-spline at distances 1 + d, d, 1 - d, 2 - d
+    const float f = floorf(u);
+    const float d = u - f;
+    i0 = (int)f - 1;
+    const float e = 1.f - d, d2 = d * d, d3 = d2 * d;
+    wt[0] = e * e * e * (1.f / 6.f);
+    wt[1] = (4.f - 6.f * d2 + 3.f * d3) * (1.f / 6.f);
+    wt[2] = (1.f + 3.f * (d + d2 - d3)) * (1.f / 6.f);
+    wt[3] = d3 * (1.f / 6.f);
   }
 }
 
@@ -231,6 +252,7 @@ __global__ void __launch_bounds__(256) k_tile_accum(GeomDev g, int ntx, const in
                                                     const float4* __restrict__ xyzv, const float* __restrict__ vw2,
                                                     unsigned long long* __restrict__ grid,
                                                     unsigned long long* __restrict__ gridw) {
+  constexpr int kReg = reg_side<P>(), kReg3 = reg_cells<P>();
   extern __shared__ unsigned long long reg[];
   unsigned long long* regw = reg + kReg3;
   const int t = blockIdx.x;
@@ -254,7 +276,7 @@ __global__ void __launch_bounds__(256) k_tile_accum(GeomDev g, int ntx, const in
     tap_weights<P>(uy, iy, wy);
     tap_weights<P>(uz, iz, wz);
     // taps relative to the region (periodic positions may lie one box away)
-    const int cx = ix + (P == 3 ? 1 : 0), cy = iy + (P == 3 ? 1 : 0), cz = iz + (P == 3 ? 1 : 0);
+    const int cx = ix + (P >= 3 ? 1 : 0), cy = iy + (P >= 3 ? 1 : 0), cz = iz + (P >= 3 ? 1 : 0);
     const int rx = ix - (cx - wrapN(cx, N)) - lx0;
     const int ry = iy - (cy - wrapN(cy, N)) - ly0;
     const int rz = iz - (cz - wrapN(cz, N)) - lz0;
@@ -285,9 +307,36 @@ __global__ void __launch_bounds__(256) k_tile_accum(GeomDev g, int ntx, const in
   }
 }
 
+// F = G - alpha R and F^w = G^w + alpha^2 R^w (eqs. mapFFT, SNbisp2) from the
+// galaxies' fixed-point grids G, G^w and the cached random grids R = sum_r w W,
+// R^w = sum_r w^2 W: each random term is rounded once to the grid's 2^-40
+// fixed point, so the result is as deterministic as a direct gridding.
+__global__ void __launch_bounds__(256) k_combine_randoms(unsigned long long* __restrict__ grid,
+                                                         const unsigned long long* __restrict__ rgrid,
+                                                         unsigned long long* __restrict__ gridw,
+                                                         const unsigned long long* __restrict__ rgridw,
+                                                         const double* __restrict__ ds, long long n) {
+  const double a = ds[DS_ALPHA];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    grid[i] = (unsigned long long)((long long)grid[i] - __double2ll_rn(a * (double)(long long)__ldg(rgrid + i)));
+    if (gridw)
+      gridw[i] = (unsigned long long)((long long)gridw[i] +
+                                      __double2ll_rn(a * a * (double)(long long)__ldg(rgridw + i)));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_combine_randoms(unsigned long long* grid, const unsigned long long* rgrid,
+                                   unsigned long long* gridw, const unsigned long long* rgridw, const double* ds,
+                                   long long n, int nsm, cudaStream_t s) {
+  long long nb = (n + 255) / 256;
+  if (nb > (long long)nsm * 16) nb = (long long)nsm * 16;
+  k_combine_randoms<<<(int)nb, 256, 0, s>>>(grid, rgrid, gridw, rgridw, ds, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, double* part, int* cnt, int* err,
                              int nblk, cudaStream_t s) {
@@ -301,9 +350,12 @@ cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, doub
   if (g.assign == 2) {
     raise_smem_limit((const void*)k_bin_count<2>, sm);
     k_bin_count<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
-  } else {
+  } else if (g.assign == 3) {
     raise_smem_limit((const void*)k_bin_count<3>, sm);
     k_bin_count<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
+  } else {
+    raise_smem_limit((const void*)k_bin_count<4>, sm);
+    k_bin_count<4><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
   }
   return cudaGetLastError();
 }
@@ -314,7 +366,8 @@ cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, cu
 }
 
 cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
-                               int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s) {
+                               int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s,
+                               int raw) {
   if (c.n == 0) {
     if (is_ran) cudaMemsetAsync(labpart, 0, sizeof(double) * LAB_NSUM * nblk, s);
     return cudaGetLastError();
@@ -324,11 +377,15 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
   const size_t sm = sizeof(int) * ntiles;
   if (g.assign == 2) {
     raise_smem_limit((const void*)k_bin_scatter<2>, sm);
-    k_bin_scatter<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, (float)obs[0], (float)obs[1],
+    k_bin_scatter<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, raw, g, ntx, ntiles, (float)obs[0], (float)obs[1],
+                                                   (float)obs[2], ds, cur, xyzv, vw2, labpart);
+  } else if (g.assign == 3) {
+    raise_smem_limit((const void*)k_bin_scatter<3>, sm);
+    k_bin_scatter<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, raw, g, ntx, ntiles, (float)obs[0], (float)obs[1],
                                                    (float)obs[2], ds, cur, xyzv, vw2, labpart);
   } else {
-    raise_smem_limit((const void*)k_bin_scatter<3>, sm);
-    k_bin_scatter<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, (float)obs[0], (float)obs[1],
+    raise_smem_limit((const void*)k_bin_scatter<4>, sm);
+    k_bin_scatter<4><<<nblk, kBinThreads, sm, s>>>(c, is_ran, raw, g, ntx, ntiles, (float)obs[0], (float)obs[1],
                                                    (float)obs[2], ds, cur, xyzv, vw2, labpart);
   }
   return cudaGetLastError();
@@ -339,16 +396,18 @@ cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xy
   const int ntx = assign_tiles_per_axis(g.N);
   const int ntiles = ntx * ntx * ntx;
   const bool w2 = gridw != nullptr;
-  const size_t sm = sizeof(unsigned long long) * kReg3 * (w2 ? 2 : 1);
 #define FKP_TA(PP, WW)                                                                                 \
   do {                                                                                                 \
-    raise_smem_limit((const void*)k_tile_accum<PP, WW>, sm); \
+    const size_t sm = sizeof(unsigned long long) * reg_cells<PP>() * (WW ? 2 : 1);                     \
+    raise_smem_limit((const void*)k_tile_accum<PP, WW>, sm);                                           \
     k_tile_accum<PP, WW><<<ntiles, 256, sm, s>>>(g, ntx, off, xyzv, vw2, grid, gridw);                 \
   } while (0)
   if (g.assign == 2) {
     if (w2) FKP_TA(2, true); else FKP_TA(2, false);
-  } else {
+  } else if (g.assign == 3) {
     if (w2) FKP_TA(3, true); else FKP_TA(3, false);
+  } else {
+    if (w2) FKP_TA(4, true); else FKP_TA(4, false);
   }
 #undef FKP_TA
   return cudaGetLastError();

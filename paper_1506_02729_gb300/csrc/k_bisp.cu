@@ -681,39 +681,28 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   CatDev g, r;
   int rc = stage_catalog(P, gal, 0, g, s);
   if (rc) return rc;
-  rc = stage_catalog(P, ran, 1, r, s);
+  rc = randoms_of(P, ran, r, s);
   if (rc) return rc;
-  if (r.n == 0) return set_error(FKP_EINVAL, "the random catalog is empty");
   rc = enqueue_grids(P, g, r, s);
   if (rc) return rc;
   const int N = P->g.N, S = st->S, mm = st->mm;
-  ZParams zp;
-  zp.nbins = P->pb.nbins;
-  zp.lmax = P->lmax;
-  zp.kf = (float)(2.0 * M_PI / P->geom.L);
-  zp.lut = P->d_lut;
-  zp.winv = P->d_winv;
+  ZParams zp = zparams(P, 1);
   zp.nshells = S;
   zp.nsh2 = st->nsh2;
   zp.slut = st->d_slut;
   zp.E = st->d_E;
   zp.mm = mm;
   // F: P bins and export on the shells
-  BCK(launch_xpass(P->d_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult));
-  BCK(cudaEventRecord(P->ev[3], s));
-  BCK(launch_ypass(P->d_S1, P->d_grid, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s,
-                   P->sched.y_threads));
-  BCK(cudaEventRecord(P->ev[4], s));
-  zp.mode = 1;
+  rc = enqueue_xy(P, P->d_grid, P->d_grid2, nullptr, s, true);
+  if (rc) return rc;
   const int nbz = zpass_blocks(N, P->sched.z_threads, P->ctx->nsm);
   BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s,
                    P->ctx->nsm, P->sched.z_threads));
   BCK(launch_reduce_bins(P->d_zpart, P->d_zpartc, nbz, P->pb.nbins, P->d_bins, P->d_binc, s));
   BCK(cudaEventRecord(P->ev[5], s));
   // F^w: shell sums against the exported F_l
-  BCK(launch_xpass(P->d_gridw, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult));
-  BCK(launch_ypass(P->d_S1, P->d_gridw, nullptr, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s,
-                   P->sched.y_threads));
+  rc = enqueue_xy(P, P->d_gridw, P->d_gridw2, nullptr, s, false);
+  if (rc) return rc;
   zp.mode = 2;
   BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, st->d_spart, st->d_spartc, P->d_err + 1, s,
                    P->ctx->nsm, P->sched.z_threads));

@@ -98,7 +98,7 @@ template <int N_, int LMAX>
 __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 1 : (N_ > 0 && N_ <= 256 ? 4 : 3))
     k_xpass2(
     const unsigned long long* __restrict__ gq, const float* __restrict__ gf, GeomDev g, FftPlan fp,
-    const float2* __restrict__ twg, float2* __restrict__ S1, MockBatch mb) {
+    const float2* __restrict__ twg, float2* __restrict__ S1, MockBatch mb, const float2* __restrict__ hph) {
   if (gq) gq += (long long)blockIdx.z * mb.in;
   if (gf) gf += (long long)blockIdx.z * mb.in;
   S1 += (long long)blockIdx.z * mb.out;
@@ -175,6 +175,11 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 
         const float2 zm = R[ilv<NP, SWZ>(k == 0 ? 0 : N - k, p)];
         o0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         o1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        if (hph) {  // second grid of an interlaced pair: its x half-cell phase
+          const float2 ph = __ldg(hph + k);
+          o0 = cmul(o0, ph);
+          o1 = cmul(o1, ph);
+        }
       }
       const size_t off = (((size_t)z * NXT + (k >> 3)) * N + y) * kT + (k & 7);
       S1[(size_t)(2 * p) * fsz + off] = o0;
@@ -198,7 +203,8 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
                                                    const unsigned long long* __restrict__ gq,
                                                    const float* __restrict__ gf, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg,
-                                                   float2* __restrict__ S2, int* __restrict__ err, MockBatch mb) {
+                                                   float2* __restrict__ S2, int* __restrict__ err, MockBatch mb,
+                                                   const float2* __restrict__ hph) {
   S1 += (long long)blockIdx.z * mb.in;
   if (gq) gq += (long long)blockIdx.z * mb.in2;
   if (gf) gf += (long long)blockIdx.z * mb.in2;
@@ -310,7 +316,11 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
 #pragma unroll
       for (int i = 0; i < PassShape<NT>::kRL; ++i) {
         const int ky = i * PassShape<NT>::kRun + run;
-        if (i < rl && ky < N) dst[(size_t)ky * tile] = o ? acc1[i] : acc0[i];
+        if (i < rl && ky < N) {
+          float2 v = o ? acc1[i] : acc0[i];
+          if (hph) v = cmul(v, __ldg(hph + ky));  // second grid of an interlaced pair: y half-cell phase
+          dst[(size_t)ky * tile] = v;
+        }
       }
     }
   }
@@ -343,14 +353,16 @@ __device__ __forceinline__ float pwsel(float v, float v2, int e) {
 // S_2 (A2), c4 nz^p4 to S_4 (A4).
 template <int RL, bool F0, bool A2, bool A4>
 __device__ __forceinline__ void zgroup(const float2* R, int z0, int rl, int N, int c, float c2, int p2, float c4,
-                                       int p4, float2 (&f0)[RL], float2 (&s2)[RL], float2 (&s4)[RL]) {
+                                       int p4, float2 (&f0)[RL], float2 (&s2)[RL], float2 (&s4)[RL],
+                                       const float2* ph) {
 #pragma unroll
   for (int i = 0; i < RL; ++i) {
     const int kz = z0 + i;
     if (i < rl && kz < N) {
-      const float2 v = R[kz * kT + c];
+      float2 v = R[kz * kT + c];
+      if (ph) v = cmul(v, ph[kz]);
       const float nz = (float)smode(kz, N), nz2 = nz * nz;
-      if (F0) f0[i] = v;
+      if (F0) f0[i] = cadd(f0[i], v);
       if (A2) {
         const float m = c2 * pwsel(nz, nz2, p2);
         s2[i].x = fmaf(m, v.x, s2[i].x);
@@ -392,14 +404,19 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   float2* work = buf1 + tile;
   float2* tw = work + tile;
   const int nkey = MODE == 2 ? zp.nshells : zp.nbins;
-  double* sbd = reinterpret_cast<double*>(tw + N);        // [BQ_N][nkey] the block's FP64 sums over its tiles
+  float2* zph = tw + N;                                   // [N] z half-cell phases (interlaced pairs)
+  double* sbd = reinterpret_cast<double*>(zph + N);       // [BQ_N][nkey] the block's FP64 sums over its tiles
   float* sb = reinterpret_cast<float*>(sbd + BQ_N * nkey);  // [BQ_N][nkey] one tile's FP32 sums
   int* sc = reinterpret_cast<int*>(sb + BQ_N * nkey);
   const int tid = threadIdx.y * kT + threadIdx.x;
   const int ntiles = NXT * N;
   const size_t gsz = (size_t)N * NXT * N * kT;
   const uint32_t bytes = (uint32_t)(tile * sizeof(float2));
-  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  for (int i = tid; i < N; i += NT) {
+    tw[i] = twg[i];
+    zph[i] = zp.interlace ? zp.hph[i] : make_float2(1.f, 0.f);
+  }
+  const int ngt = zp.interlace ? 2 * mt.ngroups : mt.ngroups;  // groups read per tile
   for (int t = tid; t < BQ_N * nkey; t += NT) {
     sb[t] = 0.f;
     sbd[t] = 0.0;
@@ -435,12 +452,12 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
     s2[i] = f0[i];
     s4[i] = f0[i];
   }
-  for (int gi = 0; gi < mt.ngroups; ++gi, ++it) {
+  for (int gi = 0; gi < ngt; ++gi, ++it) {
     const int cur = it & 1;
     float2* bc = cur ? buf1 : buf0;
     if (tid == 0) {
-      const int tn = gi + 1 < mt.ngroups ? t : t + (int)gridDim.x;
-      const int gn = gi + 1 < mt.ngroups ? gi + 1 : 0;
+      const int tn = gi + 1 < ngt ? t : t + (int)gridDim.x;
+      const int gn = gi + 1 < ngt ? gi + 1 : 0;
       if (tn < ntiles) {
         fence_proxy_async();
         mbar_expect_tx(&bar[cur ^ 1], bytes);
@@ -449,12 +466,14 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
     }
     mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 8);
     const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
-    const int p2 = mt.g_p2[gi], p4 = mt.g_p4[gi];
-    const float c2 = mt.g_c2[gi], c4 = mt.g_c4[gi];
-    if (mt.g_f0[gi]) zgroup<PassShape<NT>::kRL, true, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
-    else if (c2 != 0.f && c4 != 0.f) zgroup<PassShape<NT>::kRL, false, true, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
-    else if (c2 != 0.f) zgroup<PassShape<NT>::kRL, false, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
-    else zgroup<PassShape<NT>::kRL, false, false, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4);
+    const int gg = gi < mt.ngroups ? gi : gi - mt.ngroups;  // the group's coefficients
+    const float2* ph = gi < mt.ngroups ? nullptr : zph;     // second grid: z half-cell phase
+    const int p2 = mt.g_p2[gg], p4 = mt.g_p4[gg];
+    const float c2 = mt.g_c2[gg], c4 = mt.g_c4[gg];
+    if (mt.g_f0[gg]) zgroup<PassShape<NT>::kRL, true, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, ph);
+    else if (c2 != 0.f && c4 != 0.f) zgroup<PassShape<NT>::kRL, false, true, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, ph);
+    else if (c2 != 0.f) zgroup<PassShape<NT>::kRL, false, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, ph);
+    else zgroup<PassShape<NT>::kRL, false, false, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, ph);
     __syncthreads();
   }
   const int kx = xt * kT + c;
@@ -462,7 +481,7 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   const int nyv = smode(ky, N);
   const bool rowok = ky != N / 2;
   const float wcol = kx == 0 ? 1.f : 2.f;
-  const float wxy = colok ? zp.winv[kx] * zp.winv[N + ky] : 0.f;
+  const float wxy = colok ? zp.scale * zp.winv[kx] * zp.winv[N + ky] : 0.f;
   int curb = -1, cnt = 0;
   float acc[BQ_N];
 #pragma unroll
@@ -584,7 +603,7 @@ int yz_tiles(int N) { return tiles_x(N); }
 static size_t xsm(int N, int NP) { return sizeof(float2) * (N + N / 2 + 2 * (size_t)NP * N); }
 static size_t ysm(int N) { return 128 + sizeof(float2) * (3 * (size_t)N * kT + N); }
 static size_t zsm(int N, int nkey) {
-  return ysm(N) + (sizeof(double) + sizeof(float)) * BQ_N * nkey + sizeof(int) * nkey;
+  return ysm(N) + sizeof(float2) * N + (sizeof(double) + sizeof(float)) * BQ_N * nkey + sizeof(int) * nkey;
 }
 
 // Persistent z-pass grid: one block per resident slot (two 256-thread or one
@@ -597,7 +616,8 @@ int zpass_blocks(int N, int nt, int nsm) {
 
 template <int N_, int LMAX>
 static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                        const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb) {
+                        const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb,
+                        const float2* hph) {
   constexpr int NP = (nfields_of(LMAX) + 1) / 2;
   const size_t sm = xsm(g.N, NP);
   raise_smem_limit((const void*)k_xpass2<N_, LMAX>, sm);
@@ -605,66 +625,67 @@ static cudaError_t xrun(const unsigned long long* gq, const float* gf, const Geo
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, LMAX>, 32 * NP, sm);
   int grid = nsm * (occ > 0 ? occ : 1) * (xm > 0 ? xm : 2);
   if (grid > g.N * g.N) grid = g.N * g.N;
-  k_xpass2<N_, LMAX><<<dim3(grid, 1, mb.n), dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1, mb);
+  k_xpass2<N_, LMAX><<<dim3(grid, 1, mb.n), dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1, mb, hph);
   return cudaGetLastError();
 }
 
 template <int LMAX>
 static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb) {
+                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb,
+                             const float2* hph) {
   if (LMAX == 4) {
     switch (g.N) {
-      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
       default: break;
     }
   }
-  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
 }
 
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm,
-                         MockBatch mb) {
-  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+                         MockBatch mb, const float2* hph) {
+  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
 }
 
 template <int N_, int NT>
 static cudaError_t yrun_nt(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                            const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                           cudaStream_t s, const MockBatch& mb) {
+                           cudaStream_t s, const MockBatch& mb, const float2* hph) {
   const size_t sm = ysm(g.N);
   raise_smem_limit((const void*)k_ypass2<N_, NT>, sm);
   k_ypass2<N_, NT><<<dim3(tiles_x(g.N), g.N, mb.n), dim3(kT, NT / kT), sm, s>>>(S1, gq, gf, g, mt, fp, tw, S2, err,
-                                                                                    mb);
+                                                                                    mb, hph);
   return cudaGetLastError();
 }
 
 template <int N_>
 static cudaError_t yrun(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                         const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                        cudaStream_t s, int nt, const MockBatch& mb) {
-  return nt == 512 ? yrun_nt<N_, 512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb)
-                   : yrun_nt<N_, 256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb);
+                        cudaStream_t s, int nt, const MockBatch& mb, const float2* hph) {
+  return nt == 512 ? yrun_nt<N_, 512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb, hph)
+                   : yrun_nt<N_, 256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb, hph);
 }
 
 // gq / gf: the grid the x-pass read (for the observer node's value).
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                         cudaStream_t s, int nt, MockBatch mb) {
+                         cudaStream_t s, int nt, MockBatch mb, const float2* hph) {
   switch (g.N) {
-    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
-    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
-    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
-    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
-    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
-    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
-    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
+    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
+    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
+    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
+    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
+    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
+    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
   }
 }
 

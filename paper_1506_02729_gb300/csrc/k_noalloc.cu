@@ -113,7 +113,9 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
                                  "for that); use a plan for larger grids", N, kNaMaxN);
   if (pb->nbins < 1 || pb->nbins > kNaMaxBins || !(pb->dk > 0) || !(pb->kmin >= 0))
     return set_error(FKP_EINVAL, "bad P bins: this entry point accepts 1..%d bins, dk > 0, kmin >= 0", kNaMaxBins);
-  if (geom->assign != 2 && geom->assign != 3) return set_error(FKP_EINVAL, "assign must be 2 (CIC) or 3 (TSC)");
+  if (geom->assign < 2 || geom->assign > 4)
+    return set_error(FKP_EINVAL, "assign must be 2 (CIC), 3 (TSC) or 4 (PCS)");
+  if (geom->interlace) return set_error(FKP_EINVAL, "a given field has no interlaced partner");
   if (!(geom->L > 0)) return set_error(FKP_EINVAL, "box side L must be positive");
   FftPlan fp;
   if (!na_radix(N, fp)) return set_error(FKP_EINVAL, "grid N=%d is not a product of 2, 3 and 5", N);
@@ -148,7 +150,7 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
   g.assign = geom->assign;
   g.periodic = geom->periodic ? 1 : 0;
   g.P_fkp = (float)geom->P_fkp;
-  g.P_fkp_d = geom->P_fkp;
+  g.P_fkp_lo = (float)(geom->P_fkp - (double)g.P_fkp);
   g.alpha_mode = geom->alpha_mode;
   observer_node(g);
 

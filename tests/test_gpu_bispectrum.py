@@ -144,37 +144,6 @@ def test_aliasing_shells_are_rejected():
     assert e.value.code == -2
 
 
-@pytest.mark.slow
-def test_boss_360_bispectrum_sampled_triangles():
-    """The bispectrum workload: the BOSS-like catalog on a 360^3 TSC grid, 37
-    shells of width 3 k_f from 3 k_f (to k = 0.2): a sample of triangles
-    (equilateral, squeezed, folded, generic, largest shells) against the FP64
-    oracle, exact N_T for each."""
-    fkp = _fkp()
-    sv = mockgen.survey_boss(N=360)
-    gal, ran = mockgen.catalog(sv, 0)
-    geom = sv.geometry()
-    bs = (3, 3, 3, 37)
-    plan = fkp.Plan(geom, (0.0, 0.005, 60), bshells=bs, want=ALL)
-    dg, dr = to_device(gal), to_device(ran)
-    runs = [plan.bispectrum(dg, dr, contraction=c)[1] for c in (0, 1, 2)]
-    b = runs[0]
-    tri = [tuple(t) for t in b["tri"].astype(int)]
-    sample = [(10, 10, 10), (36, 36, 36), (36, 35, 1), (20, 10, 10), (30, 20, 12), (25, 24, 2), (36, 18, 18)]
-    sample = [t for t in sample if t in tri]
-    assert len(sample) >= 5
-    F, Fw, sc = op.fkp_grids(gal, ran, geom, with_w2=True)
-    Fl = op.legendre(F, geom, lmax=4)
-    Fwl = op.legendre(Fw, geom, lmax=4)
-    ref = ob.bispectrum_from_fields(Fl, Fwl, sc, sv.N, bs, (0, 2, 4), tris=sample)
-    idx = [tri.index(t) for t in sample]
-    for bb in runs:
-        got = {k: bb[k][idx] for k in ("NT", "B0", "B2", "B4", "T0")}
-        assert np.array_equal(got["NT"], ref["NT"])
-        err = b_errors(got, ref, ref["I33"], float(sv.N) ** 3)
-        assert max(err.values()) < B_TOL, err
-
-
 @pytest.mark.parametrize("contraction", [0, 1, 2], ids=["fp32", "bf16x3_tcgen05", "bf16x6_tcgen05"])
 def test_single_object_shot_noise_identity(contraction):
     """One galaxy on a node and randoms on every node (the oracle's pinned
@@ -191,3 +160,40 @@ def test_single_object_shot_noise_identity(contraction):
     assert abs(b["I33"] - 2.0) < 1e-12
     assert np.max(np.abs(b["N0"] - 0.625)) < 1e-5
     assert np.max(np.abs(b["B0"] + 0.125)) < 1e-5
+
+
+def test_cached_randoms_bispectrum(small_b):
+    """B_l with the plan's cached random grids (R and R^w without alpha)
+    equals B_l with the random catalog passed in, and the oracle."""
+    fkp = _fkp()
+    sv, gal, ran, geom, bs, ref, kf = small_b
+    plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
+    dg, dr = to_device(gal), to_device(ran)
+    plan.cache_randoms(dr)
+    _, full = plan.bispectrum(dg, dr, contraction=0)
+    _, cached = plan.bispectrum(dg, None, contraction=0)
+    assert np.array_equal(cached["NT"], full["NT"])
+    assert cached["I33"] == full["I33"] and cached["S3"] == full["S3"]
+    N3 = float(sv.N) ** 3
+    assert max(b_errors(cached, full, full["I33"], N3).values()) < 1e-5
+    assert max(b_errors(cached, ref, ref["I33"], N3).values()) < B_TOL
+
+
+def test_interlaced_pcs_bispectrum_matches_oracle():
+    """B_0,2,4 with PCS assignment on an interlaced pair of grids (the
+    paper's setup, Sec. III.A and III.C) against the FP64 oracle."""
+    fkp = _fkp()
+    sv = mockgen.survey_small(N=64, assign=4)
+    gal, ran = mockgen.catalog(sv, 3)
+    geom = dict(sv.geometry(), interlace=True, periodic=True)
+    kf = 2 * math.pi / sv.L
+    bs = (3, 3, 3, 6)
+    ref = ob.bispectrum(gal, ran, geom, bs)
+    plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
+    for c in (0, 2):
+        _, b = plan.bispectrum(to_device(gal), to_device(ran), contraction=c)
+        assert np.array_equal(b["NT"], ref["NT"])
+        assert max(b_errors(b, ref, ref["I33"], 64.0 ** 3).values()) < B_TOL
+        for l in (0, 2, 4):
+            d = np.maximum(np.abs(ref[f"N{l}"]), np.abs(ref["N0"]))
+            assert np.max(np.abs(b[f"N{l}"] - ref[f"N{l}"]) / d) < SN_TOL, l

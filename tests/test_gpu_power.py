@@ -228,7 +228,7 @@ def test_bad_plans_are_rejected():
     with pytest.raises(fkp.FKPError):
         fkp.Plan(dict(L=100.0, N=98), (0.0, 0.1, 4))  # 98 = 2 * 7^2
     with pytest.raises(fkp.FKPError):
-        fkp.Plan(dict(L=100.0, N=64, assign=4), (0.0, 0.1, 4))
+        fkp.Plan(dict(L=100.0, N=64, assign=5), (0.0, 0.1, 4))
     with pytest.raises(fkp.FKPError):
         fkp.Plan(dict(L=100.0, N=64), (0.0, -0.1, 4))
 
@@ -265,3 +265,94 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(small_mock):
     got = fkp.Plan(geom, bins).power(to_device(gal), to_device(ran))
     ref = _oracle_power(gal, ran, geom, bins)
     assert max(p_errors(got, ref).values()) < P_TOL
+
+
+def test_cached_randoms_equal_the_full_path_and_the_oracle(small_mock):
+    """One random catalog gridded once onto the plan without alpha (R = sum_r
+    w W), then mocks that share it grid only their galaxies and form F = G -
+    alpha R: the scalars equal those of passing the randoms (the same
+    per-block FP64 partial sums), P_l agree with that path to 1e-6 of the
+    monopole (each random term is rounded to the 2^-40 grid after the alpha
+    product rather than before) and with the FP64 oracle to the P_l bar; the
+    fused batch with rans=None likewise; an empty catalog drops the cache."""
+    fkp = _fkp()
+    sv, gal, ran = small_mock
+    geom = sv.geometry()
+    bins = _bins_small(sv.L)
+    plan = fkp.Plan(geom, bins)
+    dr = to_device(ran)
+    plan.cache_randoms(dr)
+    gals = [gal, mockgen.catalog(sv, 5, random_seed=0)[0]]
+    for gg in gals:
+        dg = to_device(gg)
+        full = plan.power(dg, dr)
+        cached = plan.power(dg, None)
+        for k in ("alpha", "I22", "I33", "N0", "S3", "W_g", "W_r", "n_ran"):
+            assert cached[k] == full[k], k
+        assert np.array_equal(cached["Lab"], full["Lab"])
+        assert np.array_equal(cached["nmodes"], full["nmodes"])
+        assert max(p_errors(cached, full).values()) < 1e-6
+        ref = _oracle_power(gg, ran, geom, bins)
+        assert max(p_errors(cached, ref).values()) < P_TOL
+    batch = plan.power_batch([to_device(gg) for gg in gals], None)
+    for gg, b in zip(gals, batch):
+        assert max(p_errors(b, plan.power(to_device(gg), None)).values()) < 1e-6
+    plan.cache_randoms({k: v[:0] for k, v in dr.items()})
+    with pytest.raises(fkp.FKPError) as e:
+        plan.power(to_device(gal), None)
+    assert e.value.code == -6
+
+
+@pytest.mark.parametrize("assign,interlace", [(4, False), (4, True), (2, True), (3, True)],
+                         ids=["pcs", "pcs_interlaced", "cic_interlaced", "tsc_interlaced"])
+def test_pcs_and_interlaced_grids_match_oracle(small_mock, assign, interlace):
+    """Fourth-order (PCS) assignment and interlaced pairs of grids (the
+    paper's choice, Sec. III.A after eq. mapFFT), window-compensated: P_l of
+    the small survey against the FP64 oracle, which averages the two grids'
+    Legendre fields with the half-cell phase and compensates by sinc^p."""
+    fkp = _fkp()
+    sv0, gal, ran = small_mock
+    geom = dict(sv0.geometry(), assign=assign, interlace=interlace, periodic=True)
+    bins = _bins_small(sv0.L)
+    ref = _oracle_power(gal, ran, geom, bins)
+    plan = fkp.Plan(geom, bins)
+    got = plan.power(to_device(gal), to_device(ran))
+    assert np.array_equal(got["nmodes"], ref["nmodes"])
+    err = p_errors(got, ref)
+    assert max(err.values()) < P_TOL, err
+    for k in ("alpha", "I22", "N0"):
+        assert abs(got[k] / ref[k] - 1) < 1e-10, k
+    if interlace:
+        # the randoms cached on both grids of the pair
+        plan.cache_randoms(to_device(ran))
+        cached = plan.power(to_device(gal), None)
+        assert max(p_errors(cached, got).values()) < 1e-6
+        with pytest.raises(fkp.FKPError):
+            plan.power_from_grid(torch.zeros((sv0.N,) * 3, device="cuda"))
+
+
+def test_interlacing_removes_odd_aliases_of_a_poisson_sample():
+    """What interlacing is for: the shot noise of an unclustered sample
+    aliases into the high-k power of a single grid (the odd images of the
+    window), and the interlaced pair cancels the odd images.  Uniform random
+    points in a periodic box, CIC, compensated: near the Nyquist frequency the
+    monopole of the interlaced estimate is closer to the Poisson level N_0
+    than that of the single grid (both through the GPU path)."""
+    fkp = _fkp()
+    N, L = 64, 1000.0
+    g = mockgen.rng(21, 0)
+    n = 300000
+    pts = {k: g.uniform(0, L, n).astype(np.float32) for k in ("x", "y", "z")}
+    gal = dict(pts, w=np.ones(n, np.float32), nbar=np.full(n, n / L ** 3, np.float32))
+    ran = {k: v[:1] for k, v in gal.items()}
+    ran["w"] = np.zeros(1, np.float32)
+    kf = 2 * math.pi / L
+    bins = (0.5 * kf, kf, 31)
+    out = {}
+    for il in (False, True):
+        geom = dict(L=L, N=N, assign=2, origin=(0.0, 0.0, 0.0), observer=(-500.0, 300.0, 2000.0),
+                    periodic=True, alpha_mode=1, interlace=il)
+        r = fkp.Plan(geom, bins).power(to_device(gal), to_device(ran))
+        out[il] = r["mono_raw"] * r["I22"] / r["N0"]  # <|F_0|^2> / N_0: 1 for pure shot noise
+    hi = slice(22, 31)
+    assert np.mean(np.abs(out[True][hi] - 1)) < 0.5 * np.mean(np.abs(out[False][hi] - 1))
