@@ -10,7 +10,8 @@ shells          thin shells of width dk about centres k_i (eq. shell), in intege
 shell_field     F_k^(l)(x) = sum_{n in shell} F_l(n) e^{+ik.x} (eq. F_k), an
                 unnormalised inverse DFT of the shell-filtered field.
 triangle_sum    sum_x F_{k1}^(l) F_{k2}^(0) F_{k3}^(0) = N^3 sum over closed
-                triangles (eq. Factorize, discrete orthogonality).
+                triangles (eq. Factorize, discrete orthogonality); with F^(2) on
+                the two larger sides for the split hexadecapole (eq. Bhexa2).
 counts          N_T (eq. NT) as an exact integer: per-mode rounded FP64
                 convolution C_bc(n) of the shell indicators, summed over shell a.
 bispectrum      B^(l) = (2l+1) <F_l F_0 F_0>_T / I_33 - N^(l) (eqs. BispMono,
@@ -124,12 +125,12 @@ class Counter:
         return out
 
 
-def bispectrum(gal, ran, geom, bshells, ells=(0, 2, 4), tris=None):
+def bispectrum(gal, ran, geom, bshells, ells=(0, 2, 4), tris=None, zero_area=False):
     """B^(l) for the given triangles (default: all a >= b >= c with N_T > 0)."""
     g = _pw._geom(geom)
     N = int(g["N"])
     Fl, Fwl, sc = _pw.survey_fields(gal, ran, g, lmax=max(ells), with_w2=True)
-    return bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells, tris)
+    return bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells, tris, zero_area=zero_area)
 
 
 def shell_means(Fl, Fwl, sidx, wt, S, ells):
@@ -145,12 +146,19 @@ def shell_means(Fl, Fwl, sidx, wt, S, ells):
     return nm, sn1, sn2
 
 
-def bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells=(0, 2, 4), tris=None, counts=None, cache_fields=None):
+def bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells=(0, 2, 4), tris=None, counts=None, cache_fields=None,
+                           zero_area=False):
     """B^(l), N^(l), T^(l) and N_T for the given triangles from the Legendre
     fields.  counts: optional mapping (a, b, c) -> N_T written earlier by this
     module's Counter (skips the convolution counter).  cache_fields: at most
     that many shell fields are kept (least recently used dropped), for large
-    grids; None keeps them all.  Neither changes the arithmetic."""
+    grids; None keeps them all.  Neither changes the arithmetic.
+    zero_area=True (needs l = 0 and 2) adds the split hexadecapole of eq.
+    Bhexa2: T22 = sum_x F_a^(2) F_b^(2) F_c^(0) (delta_2 on the two larger
+    sides) and B4b = [35/2 T22 - 5 T2 - 7/2 T0] / (N^3 N_T I_33), the
+    combination of eq. Bhexa2 formed from the raw sums (no shot-noise
+    subtraction: as for P_4b, the self terms of the split product cancel
+    against the 7/2 monopole term on zero-area triangles)."""
     from collections import OrderedDict
     S = bshells[3]
     sidx, wt = shell_index(N, bshells)
@@ -175,6 +183,8 @@ def bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells=(0, 2, 4), tris=None, c
         out[f"T{l}"] = []
         out[f"B{l}"] = []
         out[f"N{l}"] = []
+    if zero_area:
+        out["T22"], out["B4b"] = [], []
     N3 = float(N) ** 3
     for (a, b, c) in all_tris:
         nt = counts[(a, b, c)] if counter is None else counter.count(a, b, c)
@@ -196,6 +206,12 @@ def bispectrum_from_fields(Fl, Fwl, sc, N, bshells, ells=(0, 2, 4), tris=None, c
             out[f"T{l}"].append(T)
             out[f"N{l}"].append(noise)
             out[f"B{l}"].append(pref * T / (N3 * nt * sc["I33"]) - noise if nt > 0 else float("nan"))
+        if zero_area:
+            T22 = float(np.sum(field(2, a) * field(2, b) * I0c))
+            out["T22"].append(T22)
+            T0, T2 = out["T0"][-1], out["T2"][-1]
+            out["B4b"].append((17.5 * T22 - 5.0 * T2 - 3.5 * T0) / (N3 * nt * sc["I33"]) if nt > 0
+                              else float("nan"))
     for k in list(out):
         if isinstance(out[k], list):
             out[k] = np.asarray(out[k])

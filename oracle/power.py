@@ -19,7 +19,8 @@ legendre       F_0 (eq. F0), F_2 (eqs. F2, delta2b), F_4 (eqs. delta4, delta4b) 
                one 3-D FFT per moment field, sign e^{-ik.x}.
 bin_power      shell average (eq. shell) in half-open bins and P_0, P_2, P_4
                (eqs. P0_impl, P2_impl, P4_impl), P_4b (eqs. P4fast, P4_implb; constant
-               35/2 and the 7/2 N_0 self-pair term of |F_2|^2).
+               35/2 and the 7/2 N_0 self-pair term of |F_2|^2), and P_6b, P_8b by
+               the same line-of-sight split (Sec. II.B after eq. P4fast).
 """
 from __future__ import annotations
 
@@ -376,6 +377,21 @@ def bin_power(F, geom, bins, I22, N0):
         if 4 in F:
             s40 = acc((F[4] * np.conj(F0)).real)
             res["P4"] = 9.0 * s40 / nmodes / I22
+            # l = 6 and 8 by the line-of-sight split of Sec. II.B (the remark
+            # after eq. P4fast): L_6 and L_8 written through L_2 L_4 and L_4^2,
+            #   L_2 L_4 = 2/7 L_2 + 20/77 L_4 + 5/11 L_6,
+            #   L_4^2 = 1/9 + 100/693 L_2 + 162/1001 L_4 + 20/99 L_6 + 490/1287 L_8,
+            # with each product's two factors taken about different lines of
+            # sight (F_2 F_4*, |F_4|^2).  The L_6 term of L_4^2 uses the split
+            # L_6; the self-pair shot noise of |F_4|^2 (N_0/9) cancels against
+            # the 1/9 |F_0|^2 term.
+            s42 = acc((F[4] * np.conj(F[2])).real)
+            s44 = acc(np.abs(F[4]) ** 2)
+            s60 = 11.0 / 5.0 * (s42 - 2.0 / 7.0 * s20 - 20.0 / 77.0 * s40)
+            s80 = 1287.0 / 490.0 * (s44 - s00 / 9.0 - 100.0 / 693.0 * s20 - 162.0 / 1001.0 * s40
+                                    - 20.0 / 99.0 * s60)
+            res["P6b"] = 13.0 * s60 / nmodes / I22
+            res["P8b"] = 17.0 * s80 / nmodes / I22
     return res
 
 

@@ -269,3 +269,31 @@ def test_counts_for_pair_equals_single_counts():
             allc = counter.counts_for_pair(b, c)
             for a in range(b, bs[3]):
                 assert allc[a] == counter.count(a, b, c)
+
+
+def test_split_hexadecapole_sum_brute_force():
+    """The triangle sum of eq. Bhexa2 (delta_2 on the two larger sides),
+    T22 = sum_x F_a^(2) F_b^(2) F_c^(0), equals N^3 times the k-space sum over
+    closed triangles of F_2(n1) F_2(n2) F_0(n3), and B4b is
+    [35/2 T22 - 5 T2 - 7/2 T0] / (N^3 N_T I_33)."""
+    N, bs = 16, (1, 1, 1, 4)
+    f = mockgen.rng(4, N).standard_normal((N, N, N))
+    g = dict(N=N, L=100.0, assign=2, origin=(0, 0, 0), observer=(-40.0, 13.0, 77.0), compensate=False)
+    F = op.legendre(f, g, lmax=2)
+    full = {l: full_spectrum(F[l], N) for l in (0, 2)}
+    S = bs[3]
+    shells = [shell_modes(N, bs, s) for s in range(S)]
+    lo, hi, _ = ob.shell_bounds(bs)
+    sc = dict(I33=1.7, S3=0.0)
+    res = ob.bispectrum_from_fields(F, F, sc, N, bs, ells=(0, 2), zero_area=True)
+    for t, (a, b, c) in enumerate(res["tri"]):
+        na, nb = shells[a], shells[b]
+        n3 = -(na[:, None, :] + nb[None, :, :])
+        q = (n3 ** 2).sum(-1)
+        ia, ib = np.nonzero((q >= lo[c] ** 2) & (q < hi[c] ** 2))
+        ref = sum(full[2][tuple(na[i])] * full[2][tuple(nb[j])] * full[0][tuple(n3[i, j])] for i, j in zip(ia, ib))
+        assert abs(ref.imag) < 1e-9 * max(1.0, abs(ref.real))
+        assert abs(res["T22"][t] / N ** 3 - ref.real) < 1e-9 * max(1.0, abs(ref.real)), (a, b, c)
+        nt = res["NT"][t]
+        b4b = (17.5 * res["T22"][t] - 5 * res["T2"][t] - 3.5 * res["T0"][t]) / (N ** 3 * nt * 1.7)
+        assert abs(res["B4b"][t] - b4b) < 1e-12 * max(1.0, abs(b4b))

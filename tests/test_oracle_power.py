@@ -202,6 +202,39 @@ def test_plane_parallel_kaiser_fixed_amplitude():
             scale = np.mean(A[s])
             assert abs(res[key][i] - ref) < 1e-11 * scale, (i, l)
         assert abs(res["P4b"][i] - res["P4"][i]) < 1e-11 * np.mean(A[s])
+        # the split hexacontatetrapole and l = 8 multipoles: with F_l = L_l F_0
+        # the split products are the one-line-of-sight ones, so P_6b and P_8b
+        # are (2l+1) <L_l(mu) (1 + f mu^2)^2 A> exactly (which vanish in the
+        # continuum for the Kaiser factor, but not on the lattice)
+        for l, key in ((6, "P6b"), (8, "P8b")):
+            ref = (2 * l + 1) * np.mean(eval_legendre(l, mu[s]) * A[s])
+            assert abs(res[key][i] - ref) < 1e-10 * np.mean(A[s]), (i, l)
+
+
+def test_split_multipoles_of_one_object_have_no_shot_noise_on_a_sphere():
+    """One object on a node, plane-parallel (observer at infinity), no
+    compensation: F_l = L_l(mu) w e^{-ik.x} mode by mode, so the split
+    multipoles are (2l+1) <L_l(mu)> w^2 over each bin's modes: the shot-noise
+    self-pair terms of |F_4|^2 and F_4 F_2* cancel as they do for P_4b, and
+    what is left is the lattice's anisotropy, which the direct mode sum
+    gives.  Checks the normalisations of the l = 6 and 8 combinations
+    independently of the Kaiser factor."""
+    N, L = 24, 24.0
+    g = dict(N=N, L=L, assign=2, origin=(0.0, 0.0, 0.0), observer=None, los=(0.2, -0.3, 0.93), compensate=False)
+    grid = op.assign(np.array([[4.0, 7.0, 11.0]]), np.array([0.9]), g)
+    kf = 2 * math.pi / L
+    bins = (0.5 * kf, kf, 11)
+    res = op.power_from_grid(grid, g, bins)
+    los = np.array(g["los"]) / np.linalg.norm(g["los"])
+    modes = full_modes(N)
+    b = lattice_bins(modes, kf, *bins)
+    n2 = (modes ** 2).sum(1)
+    mu = np.where(n2 > 0, modes @ los / np.sqrt(np.where(n2 > 0, n2, 1)), 0)
+    for i in range(bins[2]):
+        s = b == i
+        for l, key in ((4, "P4b"), (6, "P6b"), (8, "P8b")):
+            ref = (2 * l + 1) * np.mean(eval_legendre(l, mu[s])) * 0.81
+            assert abs(res[key][i] - ref) < 1e-11, (i, l, res[key][i], ref)
 
 
 def test_plane_parallel_isotropic_quadrupole_vanishes():
