@@ -49,10 +49,15 @@ enum {
   FKP_ESTATE = -6    /* call not valid in the plan's state                 */
 };
 
-/* What to compute (bit flags). */
+/* What to compute (bit flags).  FKP_P6B, FKP_P8B: the l = 6 and 8 power
+ * multipoles by the line-of-sight split of Sec. II.B (the remark after eq.
+ * P4fast: the 22 fields of l <= 4 give l = 6 and 8 too).  FKP_B4B: the split
+ * hexadecapole bispectrum of eq. Bhexa2 (delta_2 on the two larger sides;
+ * a true multipole on zero-area triangles). */
 enum {
   FKP_P0 = 1, FKP_P2 = 2, FKP_P4 = 4, FKP_P4B = 8,
-  FKP_B0 = 16, FKP_B2 = 32, FKP_B4 = 64
+  FKP_B0 = 16, FKP_B2 = 32, FKP_B4 = 64,
+  FKP_P6B = 128, FKP_P8B = 256, FKP_B4B = 512
 };
 
 /* One catalog {x_j, w_j, nbar_j} (Sec. III.A, around eq. F0), structure of
@@ -118,6 +123,13 @@ typedef struct {
   float timing_ms[8];   /* scalars, assign, xpass, ypass, zpass, bisp ifft (the F^w passes and the shell
                          * IFFTs), contraction, total */
   int graph;            /* 1 when the call replayed the plan's CUDA graph (see fkp_plan_set_graphs) */
+  /* split multipoles (FKP_P6B, FKP_P8B; nbins entries, may be NULL):
+   *   P_6b = 13 s60 / I_22,  s60 = 11/5 [<Re F_4 F_2*> - 2/7 <Re F_2 F_0*> - 20/77 <Re F_4 F_0*>]
+   *   P_8b = 17 s80 / I_22,  s80 = 1287/490 [<|F_4|^2> - 1/9 <|F_0|^2> - 100/693 <Re F_2 F_0*>
+   *                                          - 162/1001 <Re F_4 F_0*> - 20/99 s60]
+   * (L_2 L_4 and L_4^2 in Legendre polynomials, each product's factors about
+   * two lines of sight; no shot-noise subtraction is needed). */
+  double *P6b, *P8b;
 } fkp_power_out;
 
 /* Bispectrum results, ntri entries each (caller-allocated host arrays, any
@@ -131,6 +143,11 @@ typedef struct {
   double *N0, *N2, *N4; /* thin-shell shot noise of eq. SNbisp2thin          */
   double *T0, *T2, *T4; /* raw sums sum_x F_a^(l) F_b^(0) F_c^(0) (eq. Factorize) */
   double I33, S3;
+  /* split hexadecapole (FKP_B4B; ntri entries, may be NULL): T22 = sum_x
+   * F_a^(2) F_b^(2) F_c^(0) and B4b = [35/2 T22 - 5 T2 - 7/2 T0] / (N^3 N_T
+   * I_33), eq. Bhexa2 from the raw sums (the self terms cancel on zero-area
+   * triangles as for P_4b; no thin-shell noise is subtracted). */
+  double *B4b, *T22;
 } fkp_bisp_out;
 
 /* Contraction of the triangle sums (eq. Factorize):

@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "fkp.h")
 
 FKP_P0, FKP_P2, FKP_P4, FKP_P4B = 1, 2, 4, 8
 FKP_B0, FKP_B2, FKP_B4 = 16, 32, 64
+FKP_P6B, FKP_P8B, FKP_B4B = 128, 256, 512
 FKP_CONTRACT_FP32, FKP_CONTRACT_BF16X3, FKP_CONTRACT_BF16X6 = 0, 1, 2
 ERRORS = {-1: "FKP_EINVAL", -2: "FKP_EGEOM", -3: "FKP_ENOMEM", -4: "FKP_ETIMEOUT", -5: "FKP_ECUDA",
           -6: "FKP_ESTATE"}
@@ -64,13 +65,14 @@ class PowerOut(C.Structure):
                 ("nmodes", C.POINTER(C.c_int64)), ("alpha", C.c_double), ("I22", C.c_double), ("I33", C.c_double),
                 ("N0", C.c_double), ("N0_fkp", C.c_double), ("S3", C.c_double), ("W_g", C.c_double),
                 ("W_r", C.c_double), ("Lab", C.c_double * 6), ("n_gal", C.c_int64), ("n_ran", C.c_int64),
-                ("timing_ms", C.c_float * 8), ("graph", C.c_int)]
+                ("timing_ms", C.c_float * 8), ("graph", C.c_int), ("P6b", _DP), ("P8b", _DP)]
 
 
 class BispOut(C.Structure):
     _fields_ = [("tri", C.POINTER(C.c_int16)), ("NT", C.POINTER(C.c_int64)), ("centre_closed", C.POINTER(C.c_uint8)),
                 ("B0", _DP), ("B2", _DP), ("B4", _DP), ("N0", _DP), ("N2", _DP), ("N4", _DP),
-                ("T0", _DP), ("T2", _DP), ("T4", _DP), ("I33", C.c_double), ("S3", C.c_double)]
+                ("T0", _DP), ("T2", _DP), ("T4", _DP), ("I33", C.c_double), ("S3", C.c_double),
+                ("B4b", _DP), ("T22", _DP)]
 
 
 class Request(C.Structure):
@@ -261,10 +263,10 @@ class Plan:
 
     def _pout(self):
         nb = self.nbins
-        arr = {k: np.full(nb, np.nan) for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw")}
+        arr = {k: np.full(nb, np.nan) for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw", "P6b", "P8b")}
         arr["nmodes"] = np.zeros(nb, dtype=np.int64)
         o = PowerOut()
-        for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw"):
+        for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw", "P6b", "P8b"):
             setattr(o, k, arr[k].ctypes.data_as(_DP))
         o.nmodes = arr["nmodes"].ctypes.data_as(C.POINTER(C.c_int64))
         return o, arr
@@ -350,13 +352,13 @@ class Plan:
         nt = self.ntri
         b = {"tri": np.zeros((nt, 3), dtype=np.int16), "NT": np.zeros(nt, dtype=np.int64),
              "centre_closed": np.zeros(nt, dtype=np.uint8)}
-        for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
+        for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4", "B4b", "T22"):
             b[k] = np.full(nt, np.nan)
         bo = BispOut()
         bo.tri = b["tri"].ctypes.data_as(C.POINTER(C.c_int16))
         bo.NT = b["NT"].ctypes.data_as(C.POINTER(C.c_int64))
         bo.centre_closed = b["centre_closed"].ctypes.data_as(C.POINTER(C.c_uint8))
-        for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
+        for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4", "B4b", "T22"):
             setattr(bo, k, b[k].ctypes.data_as(_DP))
         _check(lib().fkp_bispectrum(self._h, C.byref(cg), C.byref(cr) if cr is not None else None,
                                     int(contraction), _stream_handle(stream), C.byref(o), C.byref(bo)))
@@ -374,10 +376,10 @@ def power_from_grid_noalloc(geom, pbins, F, I22=1.0, N0=0.0, stream=None):
     g = geometry(geom)
     pb = PBins(float(pbins[0]), float(pbins[1]), int(pbins[2]))
     nb = pb.nbins
-    arr = {k: np.full(nb, np.nan) for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw")}
+    arr = {k: np.full(nb, np.nan) for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw", "P6b", "P8b")}
     arr["nmodes"] = np.zeros(nb, dtype=np.int64)
     o = PowerOut()
-    for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw"):
+    for k in ("k_eff", "P0", "P2", "P4", "P4b", "mono_raw", "P6b", "P8b"):
         setattr(o, k, arr[k].ctypes.data_as(_DP))
     o.nmodes = arr["nmodes"].ctypes.data_as(C.POINTER(C.c_int64))
     _check(lib().fkp_power_from_grid_noalloc(C.byref(g), C.byref(pb), F.data_ptr(), float(I22), float(N0),
@@ -388,13 +390,13 @@ def power_from_grid_noalloc(geom, pbins, F, I22=1.0, N0=0.0, stream=None):
 def _bout(nt):
     b = {"tri": np.zeros((nt, 3), dtype=np.int16), "NT": np.zeros(nt, dtype=np.int64),
          "centre_closed": np.zeros(nt, dtype=np.uint8)}
-    for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
+    for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4", "B4b", "T22"):
         b[k] = np.full(nt, np.nan)
     bo = BispOut()
     bo.tri = b["tri"].ctypes.data_as(C.POINTER(C.c_int16))
     bo.NT = b["NT"].ctypes.data_as(C.POINTER(C.c_int64))
     bo.centre_closed = b["centre_closed"].ctypes.data_as(C.POINTER(C.c_uint8))
-    for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4"):
+    for k in ("B0", "B2", "B4", "N0", "N2", "N4", "T0", "T2", "T4", "B4b", "T22"):
         setattr(bo, k, b[k].ctypes.data_as(_DP))
     return bo, b
 

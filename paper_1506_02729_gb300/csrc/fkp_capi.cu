@@ -402,7 +402,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   if (!(geom->L > 0)) return set_error(FKP_EINVAL, "box side L must be positive");
   if (pb->nbins < 1 || pb->nbins > kMaxBins || !(pb->dk > 0) || !(pb->kmin >= 0))
     return set_error(FKP_EINVAL, "bad P bins (nbins in [1,%d], dk > 0, kmin >= 0)", kMaxBins);
-  const bool wantB = (want & (FKP_B0 | FKP_B2 | FKP_B4)) != 0;
+  const bool wantB = (want & (FKP_B0 | FKP_B2 | FKP_B4 | FKP_B4B)) != 0;
   if (wantB) {
     if (!bs || bs->nshells < 1 || bs->nshells > kMaxShells || bs->width < 1 || bs->step < 1 ||
         bs->first < 1 || 2 * bs->first < bs->width)
@@ -424,8 +424,8 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   P->want = want;
   P->wantB = wantB;
   int lmax = 0;
-  if (want & (FKP_P2 | FKP_P4B | FKP_B2)) lmax = 2;
-  if (want & (FKP_P4 | FKP_B4)) lmax = 4;
+  if (want & (FKP_P2 | FKP_P4B | FKP_B2 | FKP_B4B)) lmax = 2;
+  if (want & (FKP_P4 | FKP_B4 | FKP_P6B | FKP_P8B)) lmax = 4;
   P->lmax = lmax;
   build_moments(lmax, P->mt);
   if (!moments_match(P->mt) || !moments_identities_hold(P->mt, lmax)) {
@@ -925,6 +925,12 @@ int fkp::finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_sca
     if (out->P2) out->P2[b] = n > 0 && P->lmax >= 2 ? 5.0 * s20 / n / I22 : nan;
     if (out->P4) out->P4[b] = n > 0 && P->lmax >= 4 ? 9.0 * s40 / n / I22 : nan;
     if (out->P4b) out->P4b[b] = n > 0 && P->lmax >= 2 ? (17.5 * s22 - 5.0 * s20 - 3.5 * s00) / n / I22 : nan;
+    // split l = 6, 8 (Sec. II.B after eq. P4fast): L_2 L_4 and L_4^2 in Legendre polynomials
+    const double s42 = hb[BQ_F42 * nb + b], s44 = hb[BQ_F44 * nb + b];
+    const double s60 = 11.0 / 5.0 * (s42 - 2.0 / 7.0 * s20 - 20.0 / 77.0 * s40);
+    const double s80 = 1287.0 / 490.0 * (s44 - s00 / 9.0 - 100.0 / 693.0 * s20 - 162.0 / 1001.0 * s40 - 20.0 / 99.0 * s60);
+    if (out->P6b) out->P6b[b] = n > 0 && P->lmax >= 4 ? 13.0 * s60 / n / I22 : nan;
+    if (out->P8b) out->P8b[b] = n > 0 && P->lmax >= 4 ? 17.0 * s80 / n / I22 : nan;
   }
   float t = 0.f;
   for (int i = 0; i < 8; ++i) out->timing_ms[i] = 0.f;

@@ -63,7 +63,7 @@ enum { LAB_NSUM = 6 };
 // Device scalars written by the finalize kernel (FP64).
 enum { DS_ALPHA = 0, DS_I22, DS_I33, DS_N0, DS_N0FKP, DS_S3, DS_WG, DS_WR, DS_NG, DS_NR, DS_COUNT };
 // Per-bin quantities accumulated by the z-pass.
-enum { BQ_K = 0, BQ_F00, BQ_F20, BQ_F40, BQ_F22, BQ_N };
+enum { BQ_K = 0, BQ_F00, BQ_F20, BQ_F40, BQ_F22, BQ_F42, BQ_F44, BQ_N };
 // Per-shell quantities of the F^w pass (same slots): Re F_0 F^w_0*, Re F_2 F^w_0*,
 // Re F_4 F^w_0*, Re F_0 F^w_2*, Re F_0 F^w_4*.
 enum { SQ_00 = 0, SQ_20, SQ_40, SQ_02, SQ_04 };

@@ -31,7 +31,7 @@ constexpr int kCA = 16;      // outputs (values of a) per contraction thread
 
 struct ContractItem {
   int ell_i, b, c, a0, na;
-  int out[kCA];              // triangle index * 3 + ell_i, or -1
+  int out[kCA];              // triangle index * nq + quantity, or -1
 };
 
 struct BispState {
@@ -41,6 +41,8 @@ struct BispState {
   std::vector<long long> nt;         // exact counts
   std::vector<unsigned char> cc;     // centre closed
   int nl = 0;                        // number of multipoles computed (1..3)
+  int nq = 3;                        // triangle sums per triangle: T0, T2, T4 (and T22 for FKP_B4B)
+  bool zero_area = false;            // FKP_B4B: T22 = sum_x F_a^(2) F_b^(2) F_c^(0) (eq. Bhexa2)
   int ells[3] = {0, 2, 4};
   std::vector<ContractItem> items;
   int nslices = 1;
@@ -506,8 +508,10 @@ int bisp_plan_init(Plan* P) {
   st->mm = (int)std::ceil(hmax) - 1;
   while ((double)(st->mm + 1) * (st->mm + 1) < hmax * hmax) ++st->mm;
   st->nl = 1;
-  if (P->want & FKP_B2) st->nl = 2;
+  if (P->want & (FKP_B2 | FKP_B4B)) st->nl = 2;
   if (P->want & FKP_B4) st->nl = 3;
+  st->zero_area = (P->want & FKP_B4B) != 0;
+  st->nq = st->zero_area ? 4 : 3;
   if (st->nl > 1 && P->lmax < 2 * (st->nl - 1)) return set_error(FKP_EINVAL, "internal: lmax too small");
 
   cudaStream_t s0 = nullptr;
@@ -540,7 +544,14 @@ int bisp_plan_init(Plan* P) {
   // with N_T > 0 in runs of kCA
   std::map<long long, int> tindex;
   for (int t = 0; t < ntri; ++t) tindex[((long long)st->ta[t] * S + st->tb[t]) * S + st->tc[t]] = t;
-  for (int li = 0; li < st->nl; ++li)
+  // quantity q < nl: rows F^(2q)_a, second factor F^(0)_b; q = 3 (T22): rows
+  // F^(2)_a, second factor F^(2)_b (field index S + b)
+  const int nq = st->nq;
+  std::vector<int> qs;
+  for (int li = 0; li < st->nl; ++li) qs.push_back(li);
+  if (st->zero_area) qs.push_back(3);
+  for (int q : qs) {
+    const int li = q == 3 ? 1 : q;
     for (int b = 0; b < S; ++b)
       for (int c = 0; c <= b; ++c) {
         int amin = -1, amax = -1;
@@ -549,31 +560,42 @@ int bisp_plan_init(Plan* P) {
         if (amin < 0) continue;
         for (int a0 = amin; a0 <= amax; a0 += kCA) {
           ContractItem it;
-          it.ell_i = li; it.b = b; it.c = c; it.a0 = a0; it.na = std::min(kCA, amax - a0 + 1);
+          it.ell_i = li; it.b = q == 3 ? S + b : b; it.c = c; it.a0 = a0; it.na = std::min(kCA, amax - a0 + 1);
           for (int i = 0; i < kCA; ++i) {
             auto f = tindex.find(((long long)(a0 + i) * S + b) * S + c);
-            it.out[i] = (i < it.na && f != tindex.end()) ? f->second * 3 + li : -1;
+            it.out[i] = (i < it.na && f != tindex.end()) ? f->second * nq + q : -1;
           }
           st->items.push_back(it);
         }
       }
-  // pair columns of the tensor-core contraction and each output's (row, column)
+  }
+  // pair columns of the tensor-core contraction (field indices of the two
+  // factors) and each output's (row, column)
   std::map<long long, int> pidx;
   std::vector<short2> pairs;
+  auto column = [&](int fb, int fc) {
+    const long long key = (long long)fb * 4 * S + fc;
+    auto f = pidx.find(key);
+    if (f != pidx.end()) return f->second;
+    pidx[key] = (int)pairs.size();
+    pairs.push_back(make_short2((short)fb, (short)fc));
+    return (int)pairs.size() - 1;
+  };
+  for (int t = 0; t < ntri; ++t) column(st->tb[t], st->tc[t]);
+  if (st->zero_area)
+    for (int t = 0; t < ntri; ++t) column(S + st->tb[t], st->tc[t]);
+  st->npairs = (int)pairs.size();
+  std::vector<int> om(std::max(1, ntri) * nq, -1), on(std::max(1, ntri) * nq, 0);
   for (int t = 0; t < ntri; ++t) {
-    const long long key = (long long)st->tb[t] * S + st->tc[t];
-    if (!pidx.count(key)) {
-      pidx[key] = (int)pairs.size();
-      pairs.push_back(make_short2((short)st->tb[t], (short)st->tc[t]));
+    for (int li = 0; li < st->nl; ++li) {
+      om[t * nq + li] = li * S + st->ta[t];
+      on[t * nq + li] = column(st->tb[t], st->tc[t]);
+    }
+    if (st->zero_area) {
+      om[t * nq + 3] = S + st->ta[t];
+      on[t * nq + 3] = column(S + st->tb[t], st->tc[t]);
     }
   }
-  st->npairs = (int)pairs.size();
-  std::vector<int> om(std::max(1, ntri) * 3, -1), on(std::max(1, ntri) * 3, 0);
-  for (int t = 0; t < ntri; ++t)
-    for (int li = 0; li < st->nl; ++li) {
-      om[t * 3 + li] = li * S + st->ta[t];
-      on[t * 3 + li] = pidx[(long long)st->tb[t] * S + st->tc[t]];
-    }
   const long long N3 = (long long)N * N * N;
   st->tc_tiles = (st->npairs + tc_tile_cols() - 1) / tc_tile_cols();
   tc_slicing(N3, std::max(1, st->tc_tiles), P->ctx->nsm, &st->tc_slices, &st->tc_chunks);
@@ -624,8 +646,8 @@ int bisp_plan_init(Plan* P) {
   st->d_T2 = (float2*)A(sizeof(float2) * (size_t)S * N * N * m1);
   st->d_I = (float*)A(sizeof(float) * (size_t)st->nl * S * N3);
   st->d_items = (ContractItem*)A(sizeof(ContractItem) * std::max<size_t>(1, st->items.size()));
-  st->d_cpart = (double*)A(sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * 3);
-  st->d_T = (double*)A(sizeof(double) * std::max(1, ntri) * 3);
+  st->d_cpart = (double*)A(sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * st->nq);
+  st->d_T = (double*)A(sizeof(double) * std::max(1, ntri) * st->nq);
   st->d_spart = (double*)A(sizeof(double) * BQ_N * S * (size_t)P->nblk_z);
   st->d_spartc = (int*)A(sizeof(int) * S * (size_t)P->nblk_z);
   st->d_shell = (double*)A(sizeof(double) * BQ_N * S);
@@ -647,7 +669,7 @@ int bisp_plan_init(Plan* P) {
   BCK(cudaMemcpy(st->d_kmax, kmax.data(), sizeof(int) * S, cudaMemcpyHostToDevice));
   if (!st->items.empty())
     BCK(cudaMemcpy(st->d_items, st->items.data(), sizeof(ContractItem) * st->items.size(), cudaMemcpyHostToDevice));
-  BCK(cudaMemset(st->d_cpart, 0, sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * 3));
+  BCK(cudaMemset(st->d_cpart, 0, sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * st->nq));
   if (st->d_pairs) {
     BCK(cudaMemcpy(st->d_pairs, pairs.data(), sizeof(short2) * pairs.size(), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(st->d_om, om.data(), sizeof(int) * om.size(), cudaMemcpyHostToDevice));
@@ -731,7 +753,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   }
   BCK(cudaEventRecord(P->ev[7], s));
   // contraction
-  const int ntri = P->ntri, nout = std::max(1, ntri) * 3;
+  const int ntri = P->ntri, nout = std::max(1, ntri) * st->nq;
   if (tensor && st->npairs > 0) {
     BCK(launch_contract_tc(st->d_I, N3, st->nl * S, S, st->d_pairs, st->npairs, st->d_tcpart, P->d_err + 1,
                            st->tc_slices, st->tc_chunks, contraction == FKP_CONTRACT_BF16X3 ? 2 : 3, s));
@@ -798,11 +820,18 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
       const int q2 = li == 0 ? SQ_00 : (li == 1 ? SQ_02 : SQ_04);
       double noise = (2 * l + 1) / I33 * (mean(q1, a) + L(l, mu12) * mean(q2, b) + L(l, mu13) * mean(q2, c));
       if (l == 0) noise -= 2.0 * S3 / I33;
-      const double Tv = T[3 * t + li];
+      const double Tv = T[st->nq * t + li];
       if (Tp) Tp[t] = Tv;
       if (Np) Np[t] = noise;
       if (Bp) Bp[t] = (2 * l + 1) * Tv / (N3d * (double)st->nt[t] * I33) - noise;
     }
+    // split hexadecapole (eq. Bhexa2) from the raw sums
+    const double T22 = st->zero_area ? T[st->nq * t + 3] : std::nan("");
+    if (bout->T22) bout->T22[t] = T22;
+    if (bout->B4b)
+      bout->B4b[t] = st->zero_area ? (17.5 * T22 - 5.0 * T[st->nq * t + 1] - 3.5 * T[st->nq * t]) /
+                                         (N3d * (double)st->nt[t] * I33)
+                                   : std::nan("");
   }
   return FKP_OK;
 }

@@ -518,6 +518,8 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
           vals[BQ_F20] = F2.x * F0.x + F2.y * F0.y;
           vals[BQ_F40] = F4.x * F0.x + F4.y * F0.y;
           vals[BQ_F22] = F2.x * F2.x + F2.y * F2.y;
+          vals[BQ_F42] = F4.x * F2.x + F4.y * F2.y;
+          vals[BQ_F44] = F4.x * F4.x + F4.y * F4.y;
         }
         if (MODE != 0 && sh >= 0) {
           const int w2 = 2 * zp.mm + 1;

@@ -243,6 +243,12 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
     if (out->P2) out->P2[b] = n > 0 ? 5.0 * s20 / n / I22 : nan;
     if (out->P4) out->P4[b] = n > 0 ? 9.0 * s40 / n / I22 : nan;
     if (out->P4b) out->P4b[b] = n > 0 ? (17.5 * s22 - 5.0 * s20 - 3.5 * s00) / n / I22 : nan;
+    // split l = 6, 8 (Sec. II.B after eq. P4fast): L_2 L_4 and L_4^2 in Legendre polynomials
+    const double s42 = hb[BQ_F42 * nb + b], s44 = hb[BQ_F44 * nb + b];
+    const double s60 = 11.0 / 5.0 * (s42 - 2.0 / 7.0 * s20 - 20.0 / 77.0 * s40);
+    const double s80 = 1287.0 / 490.0 * (s44 - s00 / 9.0 - 100.0 / 693.0 * s20 - 162.0 / 1001.0 * s40 - 20.0 / 99.0 * s60);
+    if (out->P6b) out->P6b[b] = n > 0 && true ? 13.0 * s60 / n / I22 : nan;
+    if (out->P8b) out->P8b[b] = n > 0 && true ? 17.0 * s80 / n / I22 : nan;
   }
   return FKP_OK;
 }

@@ -197,3 +197,21 @@ def test_interlaced_pcs_bispectrum_matches_oracle():
         for l in (0, 2, 4):
             d = np.maximum(np.abs(ref[f"N{l}"]), np.abs(ref["N0"]))
             assert np.max(np.abs(b[f"N{l}"] - ref[f"N{l}"]) / d) < SN_TOL, l
+
+
+@pytest.mark.parametrize("contraction", [0, 2], ids=["fp32", "bf16x6_tcgen05"])
+def test_split_hexadecapole_bispectrum_matches_oracle(small_b, contraction):
+    """B_4b of eq. Bhexa2 (delta_2 on the two larger sides: T22 = sum_x
+    F_a^(2) F_b^(2) F_c^(0), extra columns of the contraction) against the
+    FP64 oracle, graded by |T0|/(N^3 N_T I_33) like the other multipoles."""
+    fkp = _fkp()
+    sv, gal, ran, geom, bs, _, kf = small_b
+    ref = ob.bispectrum(gal, ran, geom, bs, zero_area=True)
+    plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL | fkp.FKP_B4B)
+    _, b = plan.bispectrum(to_device(gal), to_device(ran), contraction=contraction)
+    assert np.array_equal(b["NT"], ref["NT"])
+    m = ref["NT"] >= 100
+    N3 = float(sv.N) ** 3
+    den = np.maximum(np.abs(ref["B4b"][m]), np.abs(ref["T0"][m]) / (N3 * ref["NT"][m] * ref["I33"]))
+    assert np.max(np.abs(b["B4b"][m] - ref["B4b"][m]) / den) < B_TOL
+    assert max(b_errors(b, ref, ref["I33"], N3).values()) < B_TOL

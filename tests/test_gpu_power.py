@@ -361,3 +361,18 @@ def test_interlacing_removes_odd_aliases_of_a_poisson_sample():
     hi = slice(24, 31)
     assert np.mean(np.abs(out[False][hi] - 1)) > 0.1
     assert np.mean(np.abs(out[True][hi] - 1)) < 0.3 * np.mean(np.abs(out[False][hi] - 1))
+
+
+def test_split_multipoles_p6b_p8b_match_oracle(small_mock):
+    """P_6b and P_8b by the line-of-sight split (Sec. II.B after eq. P4fast:
+    the 22 fields of l <= 4 also give l = 6 and 8) against the FP64 oracle,
+    graded like the other multipoles (by max(|P_ref|, raw monopole))."""
+    fkp = _fkp()
+    sv, gal, ran = small_mock
+    geom = sv.geometry()
+    bins = _bins_small(sv.L)
+    want = fkp.FKP_P0 | fkp.FKP_P2 | fkp.FKP_P4 | fkp.FKP_P4B | fkp.FKP_P6B | fkp.FKP_P8B
+    got = fkp.Plan(geom, bins, want=want).power(to_device(gal), to_device(ran))
+    ref = _oracle_power(gal, ran, geom, bins)
+    err = p_errors(got, ref, keys=("P0", "P2", "P4", "P4b", "P6b", "P8b"))
+    assert max(err.values()) < P_TOL, err
