@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--reference-budget", type=float, default=200.0,
                     help="reference arm: seconds of whole-mock oracle runs (at least one mock runs)")
     ap.add_argument("--cufft", type=int, default=1, help="time cuFFT (torch.fft) as a baseline (0 skips)")
+    ap.add_argument("--experiment", default="", choices=["", "p4b", "qell"],
+                    help="run a synthetic version of one of the paper's experiments instead of the benchmark")
+    ap.add_argument("--experiment-mocks", type=int, default=64)
+    ap.add_argument("--experiment-workers", type=int, default=8)
     ap.add_argument("--cached-steps", type=int, default=10,
                     help="timed mocks with the randoms cached on the plan (0 skips that leg)")
     ap.add_argument("--grid", type=int, default=512, help="grid side (512 is the benchmark workload)")
@@ -844,9 +848,127 @@ def run_serve(args, gal, ran):
             "peak_running": st["peak_running"], "peak_bytes": int(st["peak_bytes"])}
 
 
+# ---------------------------------------------------------------------------
+# synthetic versions of the paper's experiments (--experiment; not part of the
+# default run): many mocks that share one random catalog, the randoms
+# gridded once onto the plan (fkp_plan_cache_randoms), galaxies generated on
+# the host by a spawn pool while the GPU measures the previous mocks
+# ---------------------------------------------------------------------------
+
+def _gen_galaxies(task):
+    import mockgen
+    sv, seed = task
+    return seed, mockgen.galaxies(sv, seed)
+
+
+def _mock_stream(sv, seeds, workers):
+    """Galaxy catalogs of the given seeds, generated in a spawn pool."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        for seed, gal in pool.imap(_gen_galaxies, [(sv, s) for s in seeds]):
+            yield seed, gal
+
+
+def experiment_p4b(args):
+    """The two hexadecapole estimators over an ensemble of mocks (the analogue
+    of Sec. III.A's comparison on the LasDamas and PTHalos mocks, Figs. 1-2):
+    per k bin the bias ratio b_4 = <P_4b>/<P_4> and the cosmic-variance ratio
+    sigma_4^2 = var(P_4b)/var(P_4), with the standard error of b_4.  BOSS-like
+    mocks (512^3 TSC unless --grid), one random catalog (50x) for all."""
+    import torch
+
+    import mockgen
+    import paper_1506_02729_gb300 as fkp
+    sv = mockgen.survey_boss(N=args.grid, random_ratio=args.ran_ratio)
+    ran = mockgen.randoms(sv, 0)
+    plan = fkp.Plan(sv.geometry(), BINS)
+    plan.cache_randoms({k: torch.from_numpy(v).cuda() for k, v in ran.items()})
+    P4, P4b, k = [], [], None
+    t0 = time.perf_counter()
+    for seed, gal in _mock_stream(sv, range(1000, 1000 + args.experiment_mocks), args.experiment_workers):
+        r = plan.power({kk: torch.from_numpy(v).cuda() for kk, v in gal.items()}, None)
+        P4.append(r["P4"])
+        P4b.append(r["P4b"])
+        k = r["k_eff"]
+    P4, P4b = np.array(P4), np.array(P4b)
+    M = P4.shape[0]
+    m4, m4b = P4.mean(0), P4b.mean(0)
+    b4 = m4b / m4
+    # standard error of the ratio of means (delta method with the covariance)
+    cov = np.array([np.cov(P4[:, i], P4b[:, i]) for i in range(P4.shape[1])])
+    se = np.abs(b4) * np.sqrt(np.maximum(cov[:, 0, 0] / m4 ** 2 + cov[:, 1, 1] / m4b ** 2
+                                         - 2 * cov[:, 0, 1] / (m4 * m4b), 0.0) / M)
+    return {"experiment": "P_4b vs P_4 over mocks (Sec. III.A, Figs. 1-2 analogue)",
+            "workload": f"{M} BOSS-like mocks, {sv.N}^3 TSC, galaxies seeds 1000..{999 + M}, one random catalog "
+                        f"({int(ran['x'].size)} randoms, cached on the plan)",
+            "wall_s": time.perf_counter() - t0, "k": k.tolist(), "b4": b4.tolist(), "b4_se": se.tolist(),
+            "sigma4_sq_ratio": (P4b.var(0, ddof=1) / P4.var(0, ddof=1)).tolist(),
+            "mean_P4": m4.tolist(), "mean_P4b": m4b.tolist()}
+
+
+def experiment_qell(args):
+    """The reduced bispectrum multipoles Q^(l) = B_l/(P_0(k1) P_0(k2) +
+    P_0(k2) P_0(k3) + P_0(k3) P_0(k1)) (eq. Qelldef) for k1 = 0.047 h/Mpc,
+    k2 = 2 k1 as a function of the angle theta between k1 and k2 (the
+    analogue of Sec. III.B's Fig. 3), averaged over mocks: 360^3 TSC, shells
+    of 3 k_f, P_0 in bins that are the shells themselves; the l-th multipole
+    is about the largest side (k1 >= k2 >= k3 order of the triangle)."""
+    import torch
+
+    import mockgen
+    import paper_1506_02729_gb300 as fkp
+    sv = mockgen.survey_boss(N=360, random_ratio=args.ran_ratio)
+    kf = 2 * math.pi / sv.L
+    bs = (3, 3, 3, 37)
+    pb = (1.5 * kf, 3 * kf, 37)  # P bins = the bispectrum shells
+    s1 = int(round(0.047 / (3 * kf))) - 1
+    s2 = 2 * (s1 + 1) - 1        # centre exactly twice s1's
+    ran = mockgen.randoms(sv, 0)
+    plan = fkp.Plan(sv.geometry(), pb, bshells=bs, want=fkp.FKP_P0 | fkp.FKP_B0 | fkp.FKP_B2 | fkp.FKP_B4)
+    plan.cache_randoms({k: torch.from_numpy(v).cuda() for k, v in ran.items()})
+    rows, Q = None, []
+    t0 = time.perf_counter()
+    for seed, gal in _mock_stream(sv, range(2000, 2000 + args.experiment_mocks), args.experiment_workers):
+        p, b = plan.bispectrum({kk: torch.from_numpy(v).cuda() for kk, v in gal.items()}, None,
+                               contraction=fkp.FKP_CONTRACT_BF16X6)
+        tri = b["tri"].astype(int)
+        if rows is None:
+            rows = [i for i, t in enumerate(tri) if s1 in t and s2 in t]
+        P0 = p["P0"]
+        q = []
+        for i in rows:
+            a, bb, c = tri[i]
+            den = P0[a] * P0[bb] + P0[bb] * P0[c] + P0[c] * P0[a]
+            q.append([b["B0"][i] / den, b["B2"][i] / den, b["B4"][i] / den])
+        Q.append(q)
+    Q = np.array(Q)
+    cen = 3 * (np.arange(37) + 1) * kf
+    out = []
+    for j, i in enumerate(rows):
+        sides = list(tri[i])
+        rest = list(sides)
+        rest.remove(s1)
+        rest.remove(s2)
+        s3 = rest[0]
+        cth = (cen[s3] ** 2 - cen[s1] ** 2 - cen[s2] ** 2) / (2 * cen[s1] * cen[s2])
+        out.append({"shells": [int(v) for v in sides], "theta_over_pi": float(np.arccos(np.clip(cth, -1, 1)) / np.pi),
+                    "NT": int(b["NT"][i]), "Q0": float(Q[:, j, 0].mean()), "Q2": float(Q[:, j, 1].mean()),
+                    "Q4": float(Q[:, j, 2].mean()), "Q0_se": float(Q[:, j, 0].std(ddof=1) / np.sqrt(len(Q))),
+                    "Q2_se": float(Q[:, j, 1].std(ddof=1) / np.sqrt(len(Q))),
+                    "Q4_se": float(Q[:, j, 2].std(ddof=1) / np.sqrt(len(Q)))})
+    out.sort(key=lambda r: r["theta_over_pi"])
+    return {"experiment": "Q^(l)(theta) for k1 = 0.047, k2 = 2 k1 (eq. Qelldef; Sec. III.B, Fig. 3 analogue)",
+            "workload": f"{len(Q)} BOSS-like mocks, 360^3 TSC, 37 shells of 3 k_f, one cached random catalog",
+            "k1": float(cen[s1]), "k2": float(cen[s2]), "wall_s": time.perf_counter() - t0, "triangles": out}
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.experiment:
+        out = {"p4b": experiment_p4b, "qell": experiment_qell}[args.experiment](args)
+        print(json.dumps(out), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

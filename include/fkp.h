@@ -181,12 +181,16 @@ int fkp_plan_sizes(const void *plan, int *nbins, int *ntriangles, size_t *worksp
 /* Launch schedule of the three FFT passes of a plan: x_mult (x-pass blocks
  * per SM = resident blocks x x_mult: 1, 2, 4 or 8), and the threads per block
  * of the y- and z-passes (256 or 512).  The first plan of a given grid and
- * multipole order in a context times every candidate on its own workspace
- * (about 12 launches of each pass) and keeps the fastest of each; later
- * plans of that kind reuse the choice.  tuned_ms (3 floats, may be NULL)
- * receives the chosen passes' times.  fkp_plan_set_schedule overrides the
- * choice for one plan (FKP_EINVAL outside those values).  Results do not
- * depend on the schedule. */
+ * multipole order in a context times the x- and y-pass candidates on its own
+ * workspace (about 12 launches of each pass) and keeps the fastest; later
+ * plans of that kind reuse the choice.  The z-pass shape is fixed per grid
+ * (256 threads up to N = 256, 512 above): it sets how the bin sums are
+ * split into FP32 runs, so with it fixed every result is the same bit for bit
+ * whatever the tuning picks (every reduction of the path has a fixed order or
+ * is integer).  tuned_ms (3 floats, may be NULL) receives the passes' times.
+ * fkp_plan_set_schedule overrides the choice for one plan (FKP_EINVAL
+ * outside those values); another z_threads changes the bins' FP32 run
+ * rounding (~1e-7). */
 int fkp_plan_schedule(const void *plan, int *x_mult, int *y_threads, int *z_threads, float *tuned_ms);
 int fkp_plan_set_schedule(void *plan, int x_mult, int y_threads, int z_threads);
 
@@ -229,8 +233,7 @@ int fkp_power(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
  * shaped by its own catalogs; then the three FFT passes and the bin
  * reduction run once for all mocks (one launch each, the mock index in the
  * grid).  Every mock's results are those of fkp_power on the same catalogs:
- * the same grid and scalars, bins equal up to the run-to-run order of the
- * FP32 per-block sums (~1e-7).  The plan keeps a batch workspace (grid, pass buffers and bins
+ * the same grid, scalars and bins, bit for bit.  The plan keeps a batch workspace (grid, pass buffers and bins
  * per mock: about 15 GB per mock at 512^3, 1.9 GB at 256^3) sized for the
  * largest nmock seen; FKP_ENOMEM when that exceeds the context's HBM budget
  * or the device.  Stage times in outs[k].timing_ms are those of the whole
@@ -293,8 +296,8 @@ int fkp_power_from_grid_noalloc(const fkp_geometry_t *geom, const fkp_pbins_t *p
  * (least recently used first) when that makes room; the queue is first-in
  * first-out with skip-ahead.  Requests on different slots
  * run concurrently on the device.  Every result equals the one the same
- * request gives alone (gridding is order independent; bin sums agree to FP32
- * rounding of per-block partial sums).
+ * request gives alone, bit for bit (integer gridding, fixed-order or integer
+ * reductions, the z-pass shape fixed per grid).
  * ------------------------------------------------------------------------- */
 
 /* One request: the arguments of fkp_plan_create plus catalogs and outputs.

@@ -286,6 +286,10 @@ fkp::Plan::~Plan() {
   for (auto& e : ev) if (e) cudaEventDestroy(e);
 }
 
+// z-pass threads per block for a grid: 256 (two blocks per SM) up to 256^3,
+// 512 (one per SM: its three accumulators per point need the registers) above.
+int fkp::z_threads_for(int N) { return N <= 256 ? 256 : 512; }
+
 // Times the candidate launch schedules of the three FFT passes on the plan's
 // own workspace (zeroed: the passes' cost does not depend on the values) and
 // keeps the fastest of each; the choice is shared by later plans of the same
@@ -343,11 +347,12 @@ static int tune_schedule(Plan* P) {
                                                       P->d_S2, P->d_err + 1, s, nt); }, "y-pass");
       if (t < by) { by = t; best.y_threads = nt; }
     }
-    for (int nt : {256, 512}) {
-      const float t = timed([&] { return launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart,
-                                                      P->d_zpartc, P->d_err + 1, s, P->ctx->nsm, nt); }, "z-pass");
-      if (t < bz) { bz = t; best.z_threads = nt; }
-    }
+    // the z-pass block shape sets the partition of each k_z column into the
+    // FP32 runs of the bin sums, so it is fixed per grid rather than tuned:
+    // results then do not depend on the tuning (bit for bit)
+    best.z_threads = z_threads_for(N);
+    bz = timed([&] { return launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc,
+                                         P->d_err + 1, s, P->ctx->nsm, best.z_threads); }, "z-pass");
     best.ms[0] = bx;
     best.ms[1] = by;
     best.ms[2] = bz;

@@ -17,7 +17,7 @@ namespace fkp {
 struct PassSchedule {
   int x_mult = 2;       // x-pass blocks per SM = resident blocks x x_mult (1, 2, 4 or 8)
   int y_threads = 256;  // y-pass block: 256 (two per SM) or 512
-  int z_threads = 512;  // z-pass block: 256 or 512
+  int z_threads = 512;  // z-pass block: 256 or 512 (fixed per grid by z_threads_for, not tuned)
   float ms[3] = {0, 0, 0};  // the chosen x, y, z times when tuned (ms)
   bool tuned = false;
 };
@@ -127,6 +127,7 @@ int set_error(int code, const char* fmt, ...);
 // here, so a launch with a smaller need on another thread stays valid.
 cudaError_t raise_smem_limit(const void* func, size_t bytes);
 void build_moments(int lmax, MomentTable& mt);
+int z_threads_for(int N);
 bool moments_identities_hold(const MomentTable& mt, int lmax);
 void observer_node(GeomDev& g);
 int stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, cudaStream_t s);

@@ -383,9 +383,11 @@ __device__ __forceinline__ void zgroup(const float2* R, int z0, int rl, int N, i
 
 // Block (8, 64): threadIdx.x is the k_x column, threadIdx.y the run of k_z.
 // The epilogue walks each thread's run of consecutive k_z (|n| is monotone
-// along it), sums a run in FP32 and adds it
-// to the block's FP32 bins in shared memory when the bin changes; blocks'
-// bins are reduced in FP64 in a fixed order.
+// along it), sums a run in FP32 and adds it to the tile's fixed-point bins
+// in shared memory when the bin changes (integer adds: the result does not
+// depend on the order of the threads); each tile's bins join the block's
+// FP64 sums in tile order, and blocks' bins are reduced in FP64 in a fixed
+// order, so the bins are bit-reproducible for a given launch shape.
 template <int N_, int MODE, int NT>
 __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const float2* __restrict__ S2, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg, ZParams zp,
@@ -406,8 +408,9 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   const int nkey = MODE == 2 ? zp.nshells : zp.nbins;
   float2* zph = tw + N;                                   // [N] z half-cell phases (interlaced pairs)
   double* sbd = reinterpret_cast<double*>(zph + N);       // [BQ_N][nkey] the block's FP64 sums over its tiles
-  float* sb = reinterpret_cast<float*>(sbd + BQ_N * nkey);  // [BQ_N][nkey] one tile's FP32 sums
-  int* sc = reinterpret_cast<int*>(sb + BQ_N * nkey);
+  long long* sbi = reinterpret_cast<long long*>(sbd + BQ_N * nkey);  // [BQ_N][nkey] one tile's fixed-point sums
+  int* sc = reinterpret_cast<int*>(sbi + BQ_N * nkey);
+  unsigned* tmax = reinterpret_cast<unsigned*>(sc + nkey);  // the tile's bound on |value| (FP32 bits)
   const int tid = threadIdx.y * kT + threadIdx.x;
   const int ntiles = NXT * N;
   const size_t gsz = (size_t)N * NXT * N * kT;
@@ -418,10 +421,15 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   }
   const int ngt = zp.interlace ? 2 * mt.ngroups : mt.ngroups;  // groups read per tile
   for (int t = tid; t < BQ_N * nkey; t += NT) {
-    sb[t] = 0.f;
+    sbi[t] = 0;
     sbd[t] = 0.0;
   }
   for (int t = tid; t < nkey; t += NT) sc[t] = 0;
+  if (tid == 0) *tmax = 0u;
+  // fixed-point exponent of the k sums: k <= kf sqrt(3) N/2 < kf N
+  int ek;
+  frexpf(zp.kf * (float)N, &ek);
+  const int sk = 49 - ek;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -482,6 +490,51 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   const bool rowok = ky != N / 2;
   const float wcol = kx == 0 ? 1.f : 2.f;
   const float wxy = colok ? zp.scale * zp.winv[kx] * zp.winv[N + ky] : 0.f;
+  // Bin sums are made order independent (bit-reproducible): each thread's
+  // runs are summed in FP32 in k_z order, then added to the tile's sums as
+  // 64-bit fixed-point integers at a scale 2^st set by a bound M on every
+  // |value| of the tile (|Re a b*| <= max(|a|^2, |b|^2)), so that a tile's bin
+  // sum stays below 2^62; integer adds commute.  First pass: the bound.
+  float mloc = 0.f;
+#pragma unroll
+  for (int i = 0; i < PassShape<NT>::kRL; ++i) {
+    const int kz = z0 + i;
+    if (colok && rowok && i < rl && kz < N && kz != N / 2) {
+      const int nzv = smode(kz, N);
+      const int n2 = kx * kx + nyv * nyv + nzv * nzv;
+      if (n2 > 0) {
+        const float wc = wxy * zp.winv[2 * N + kz], wc2 = wc * wc;
+        const float a0 = f0[i].x * f0[i].x + f0[i].y * f0[i].y;
+        float m = wc2 * a0;
+        if (zp.lmax >= 2) {
+          const float i2 = 1.0f / (float)n2;
+          const float a2 = s2[i].x * s2[i].x + s2[i].y * s2[i].y;
+          const float b2 = 2.f * wc2 * (2.25f * a2 * i2 * i2 + 0.25f * a0);
+          m = fmaxf(m, b2);
+          if (zp.lmax >= 4) {
+            const float a4 = s4[i].x * s4[i].x + s4[i].y * s4[i].y;
+            m = fmaxf(m, 3.f * (19.140625f * wc2 * a4 * i2 * i2 * i2 * i2 + 6.25f * b2 + 0.765625f * wc2 * a0));
+          }
+        }
+        if (MODE == 2 && n2 < zp.nsh2 && zp.slut[n2] >= 0) {
+          const int w2 = 2 * zp.mm + 1;
+          const size_t e = ((size_t)(nzv + zp.mm) * w2 + (nyv + zp.mm)) * (zp.mm + 1) + kx;
+          const size_t es = (size_t)w2 * w2 * (zp.mm + 1);
+          const float2 E0 = zp.E[e], E2 = zp.E[es + e], E4 = zp.E[2 * es + e];
+          m = fmaxf(m, fmaxf(E0.x * E0.x + E0.y * E0.y, fmaxf(E2.x * E2.x + E2.y * E2.y, E4.x * E4.x + E4.y * E4.y)));
+        }
+        mloc = fmaxf(mloc, m);
+      }
+    }
+  }
+  {
+    const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(mloc));
+    if ((threadIdx.x | (threadIdx.y & 3)) == 0) atomicMax(tmax, mb);  // lane 0 of each warp
+  }
+  __syncthreads();
+  int et;
+  frexpf(__uint_as_float(*tmax), &et);
+  const int st = 49 - et;  // tile sum <= 2 * 8 N * M < 2^(13 + et) * 2^(49 - et) <= 2^62 (N <= 512)
   int curb = -1, cnt = 0;
   float acc[BQ_N];
 #pragma unroll
@@ -545,7 +598,9 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
       if (curb >= 0) {
         atomicAdd(sc + curb, cnt);
 #pragma unroll
-        for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, acc[q]);
+        for (int q = 0; q < BQ_N; ++q)
+          atomicAdd(reinterpret_cast<unsigned long long*>(sbi + q * nkey + curb),
+                    (unsigned long long)__float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
       }
       curb = b;
       cnt = 0;
@@ -561,14 +616,18 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   if (curb >= 0) {
     atomicAdd(sc + curb, cnt);
 #pragma unroll
-    for (int q = 0; q < BQ_N; ++q) atomicAdd(sb + q * nkey + curb, acc[q]);
+    for (int q = 0; q < BQ_N; ++q)
+      atomicAdd(reinterpret_cast<unsigned long long*>(sbi + q * nkey + curb),
+                (unsigned long long)__float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
   }
   __syncthreads();
-  // the tile's FP32 bin sums join the block's FP64 sums (each slot by one thread)
+  // the tile's fixed-point bin sums join the block's FP64 sums (each slot by
+  // one thread, tiles in the block's order)
   for (int q = tid; q < BQ_N * nkey; q += NT) {
-    sbd[q] += (double)sb[q];
-    sb[q] = 0.f;
+    sbd[q] += ldexp((double)sbi[q], (q / nkey == BQ_K && MODE != 2) ? -sk : -st);
+    sbi[q] = 0;
   }
+  if (tid == 0) *tmax = 0u;
   __syncthreads();
   }
   const int blk = blockIdx.x, nblk = gridDim.x;
@@ -605,7 +664,7 @@ int yz_tiles(int N) { return tiles_x(N); }
 static size_t xsm(int N, int NP) { return sizeof(float2) * (N + N / 2 + 2 * (size_t)NP * N); }
 static size_t ysm(int N) { return 128 + sizeof(float2) * (3 * (size_t)N * kT + N); }
 static size_t zsm(int N, int nkey) {
-  return ysm(N) + sizeof(float2) * N + (sizeof(double) + sizeof(float)) * BQ_N * nkey + sizeof(int) * nkey;
+  return ysm(N) + sizeof(float2) * N + (sizeof(double) + sizeof(long long)) * BQ_N * nkey + sizeof(int) * nkey + 16;
 }
 
 // Persistent z-pass grid: one block per resident slot (two 256-thread or one

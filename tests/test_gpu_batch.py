@@ -44,13 +44,13 @@ def mocks():
 
 
 def _same(a, b):
-    """Batch against single call: identical grid and scalars; the bins up to the
-    run-to-run order of the FP32 per-block sums."""
+    """Batch against single call: identical grid, scalars and bins, bit for bit
+    (integer gridding, order-independent bin sums)."""
     assert np.array_equal(a["nmodes"], b["nmodes"])
     for k in ("alpha", "I22", "I33", "N0", "W_g", "W_r", "n_gal", "n_ran"):
         assert a[k] == b[k], k
     for k in ("P0", "P2", "P4", "P4b", "k_eff", "mono_raw"):
-        assert np.allclose(a[k], b[k], rtol=1e-6, atol=1e-6 * np.nanmax(np.abs(b["P0"])), equal_nan=True), k
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
 
 
 def test_batch_equals_single_calls(mocks):

@@ -175,7 +175,10 @@ def test_cached_randoms_bispectrum(small_b):
     assert np.array_equal(cached["NT"], full["NT"])
     assert cached["I33"] == full["I33"] and cached["S3"] == full["S3"]
     N3 = float(sv.N) ** 3
-    assert max(b_errors(cached, full, full["I33"], N3).values()) < 1e-5
+    # each random term is rounded to the grid's fixed point after, not before,
+    # the alpha product: relative input differences ~1e-8, which the B_4 sums'
+    # cancellations enlarge
+    assert max(b_errors(cached, full, full["I33"], N3).values()) < 5e-5
     assert max(b_errors(cached, ref, ref["I33"], N3).values()) < B_TOL
 
 
