@@ -63,11 +63,15 @@ def parse():
     ap.add_argument("--bisp-steps", type=int, default=3, help="timed bispectrum mocks (0 skips the B leg)")
     ap.add_argument("--bisp-grid", type=int, default=360, help="bispectrum grid (360 is the workload)")
     ap.add_argument("--bisp-nshells", type=int, default=37, help="bispectrum shells (37 reach k = 0.2)")
-    ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving leg (0 skips it)")
+    ap.add_argument("--serve-requests", type=int, default=64, help="requests in the serving leg (0 skips it)")
+    ap.add_argument("--serve-plain-requests", type=int, default=32,
+                    help="the first this many requests also run through the plain sequential path")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving leg (req/s)")
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--small-steps", type=int, default=200, help="timed 64^3 mocks per mode (0 skips that leg)")
     ap.add_argument("--batch-mocks", type=int, default=32, help="mocks in the batched leg (0 skips it)")
+    ap.add_argument("--batch-oracle-mocks", type=int, default=0,
+                    help="batched-leg mocks also compared with the FP64 oracle (tens of seconds each)")
     ap.add_argument("--fused-mocks", type=int, default=64,
                     help="64^3 mocks per fused call in the fused leg (0 skips it; 256^3: a quarter)")
     return ap.parse_args()
@@ -744,13 +748,47 @@ def run_batch(args):
         N3 = float(m["geom"]["N"]) ** 3
         den = np.where(bp["NT"] >= 100, np.abs(bp["T0"]) / (N3 * np.maximum(bp["NT"], 1) * bp["I33"]), np.nan)
         db.append(_rel_diff(bs, bp, ("B0",), den))
+    # each output against the FP64 oracle for a sample of the mocks (the
+    # oracle takes tens of seconds per mock, so not all of them)
+    vs_fp64 = []
+    for j in range(min(args.batch_oracle_mocks, len(mocks))):
+        m = mocks[j]
+        hg = {k: v.cpu().numpy() for k, v in m["gal"].items()}
+        hr = {k: v.cpu().numpy() for k, v in m["ran"].items()}
+        vs_fp64.append(dict(mock=j, grid=m["geom"]["N"], **_vs_oracle(hg, hr, m["geom"], bshells, served[j][0],
+                                                                      served[j][1], plain[j][1])))
     return {"workload": f"{len(mocks)} mocks: grids {{256,384,512}}, N_g in [5e5, 1.2e6] + 30x randoms (device "
                         "catalogs), P_0,2,4 + B_0 to k=0.15 (27 shells)",
             "unit": "mocks/s", "batched_mocks_per_s": len(mocks) / wall_b,
             "plain_mocks_per_s": len(mocks) / wall_p,
             "objects_per_mock_mean": float(np.mean([m["n_obj"] for m in mocks])),
             "batched_vs_plain_max_rel_diff": {"P": max(dp), "B0": max(db)},
-            "per_mock_rel_diff_P": dp, "per_mock_rel_diff_B0": db}
+            "per_mock_rel_diff_P": dp, "per_mock_rel_diff_B0": db, "per_mock_error_vs_fp64": vs_fp64}
+
+
+def _vs_oracle(gal, ran, geom, bshells, p_served, b_served, b_plain):
+    """Largest error of P_0,2,4 (graded by max(|P|, raw monopole)) and of B_0
+    (graded by max(|B_0|, |T_0|/(N^3 N_T I_33)), N_T >= 100) of one mock's
+    served and plain outputs against the FP64 oracle."""
+    from oracle import bispectrum as ob
+    from oracle import power as op
+    N = int(geom["N"])
+    Fl, Fwl, sc = op.survey_fields(gal, ran, geom, lmax=4, with_w2=True)
+    ref = op.bin_power(Fl, geom, BINS, sc["I22"], sc["N0"])
+    m = ref["nmodes"] > 0
+    den = np.maximum(np.abs(ref["P0"][m]), np.abs(ref["mono_raw"][m]))
+    eP = max(float(np.max(np.abs(p_served[k][m] - ref[k][m]) / np.maximum(np.abs(ref[k][m]), den)))
+             for k in ("P0", "P2", "P4"))
+    tri = [tuple(t) for t in b_served["tri"].astype(int)]
+    g = np.random.default_rng(N)
+    sample = sorted(tri[i] for i in g.permutation(len(tri))[:40])
+    rb = ob.bispectrum_from_fields({0: Fl[0]}, {0: Fwl[0]}, sc, N, bshells, ells=(0,), tris=sample, cache_fields=8)
+    idx = [tri.index(t) for t in sample]
+    mm = rb["NT"] >= 100
+    dB = np.maximum(np.abs(rb["B0"][mm]), np.abs(rb["T0"][mm]) / (float(N) ** 3 * rb["NT"][mm] * rb["I33"]))
+    eB = {name: float(np.max(np.abs(b["B0"][idx][mm] - rb["B0"][mm]) / dB))
+          for name, b in (("served_bf16x6", b_served), ("plain_fp32", b_plain))}
+    return {"P_max_err": eP, "B0_max_err_40_triangles": eB}
 
 
 def run_serve(args, gal, ran):
@@ -770,15 +808,20 @@ def run_serve(args, gal, ran):
     import mockgen
     import paper_1506_02729_gb300 as fkp
     g = np.random.default_rng(args.seed + 77)
+    # the catalogs are in random order (galaxies shuffled, randoms drawn
+    # independently), so a contiguous slice at a random offset is a random
+    # subsample: every request is a view into one pinned copy of the catalogs
+    pg = {k: torch.from_numpy(v).pin_memory() for k, v in gal.items()}
+    pr = {k: torch.from_numpy(v).pin_memory() for k, v in ran.items()}
     reqs = []
     for i in range(args.serve_requests):
         N = int(g.choice([256, 384, 512]))
         ng = int(gal["x"].size * g.uniform(0.5, 1.0))
         nr = min(ran["x"].size, 30 * ng)
-        gi = np.sort(g.choice(gal["x"].size, ng, replace=False))
-        ri = np.sort(g.choice(ran["x"].size, nr, replace=False))
-        hg = {k: torch.from_numpy(np.ascontiguousarray(v[gi])).pin_memory() for k, v in gal.items()}
-        hr = {k: torch.from_numpy(np.ascontiguousarray(v[ri])).pin_memory() for k, v in ran.items()}
+        og = int(g.integers(0, gal["x"].size - ng + 1))
+        orr = int(g.integers(0, ran["x"].size - nr + 1))
+        hg = {k: v[og:og + ng] for k, v in pg.items()}
+        hr = {k: v[orr:orr + nr] for k, v in pr.items()}
         B = bool(i % 2)
         S = 37 if 3 * (3 * 37 + 1.5) < N else 27
         reqs.append(dict(geom=mockgen.survey_boss(N=N).geometry(), gal=hg, ran=hr, B=B, S=S, n_obj=ng + nr))
@@ -823,11 +866,12 @@ def run_serve(args, gal, ran):
                           else fkp.Plan(r["geom"], pb))
         return plans[key]
 
-    for r in reqs:
+    plain_reqs = reqs[:max(1, min(len(reqs), args.serve_plain_requests))]
+    for r in plain_reqs:
         plan_for(r)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    for r in reqs:
+    for r in plain_reqs:
         plan = plan_for(r)
         if r["B"]:
             plan.bispectrum(r["gal"], r["ran"], contraction=fkp.FKP_CONTRACT_FP32)
@@ -844,7 +888,8 @@ def run_serve(args, gal, ran):
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "poisson_wall_s": wall_poisson,
             "saturated_mocks_per_s": n / wall_sat, "saturated_p50_ms": float(np.percentile(lat_sat, 50)),
-            "plain_sequential_mocks_per_s": n / wall_seq,
+            "plain_sequential_mocks_per_s": len(plain_reqs) / wall_seq,
+            "plain_sequential_requests": len(plain_reqs),
             "peak_running": st["peak_running"], "peak_bytes": int(st["peak_bytes"])}
 
 

@@ -392,6 +392,7 @@ extern "C" int fkp_plan_set_schedule(void* plan, int x_mult, int y_threads, int 
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);  // captured with the old launches
   P->graph_exec = nullptr;
   P->last_valid = false;
+  bisp_drop_graph(P);
   return FKP_OK;
 }
 
@@ -646,7 +647,7 @@ int fkp::stage_catalog(Plan* P, const fkp_catalog_t* c, int slot, CatDev& out, c
 // Records a stage event on s.  Inside a stream capture it is recorded as an
 // external event, so that the graph keeps it as a timed event node (a plain
 // record only orders the captured work).
-static cudaError_t record_stage(cudaEvent_t ev, cudaStream_t s) {
+cudaError_t fkp::record_stage(cudaEvent_t ev, cudaStream_t s) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   const cudaError_t e = cudaStreamIsCapturing(s, &st);
   if (e != cudaSuccess) return e;
@@ -676,6 +677,7 @@ static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t
     // a captured graph refers to the old buffers
     if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
     P->graph_exec = nullptr;
+    bisp_drop_graph(P);
     if (P->d_xyzv) cudaFree(P->d_xyzv);
     if (P->d_vw2) cudaFree(P->d_vw2);
     P->d_xyzv = nullptr;
@@ -746,6 +748,7 @@ static int cache_randoms(Plan* P, const CatDev& ran, cudaStream_t s) {
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);  // a captured graph may hold the old cache
   P->graph_exec = nullptr;
   P->last_valid = false;
+  bisp_drop_graph(P);
   if (ran.n == 0) return FKP_OK;
   if (ran.n >= (1ll << 31)) return set_error(FKP_EINVAL, "at most 2^31-1 randoms");
   const int nb = P->ctx->nsm;
@@ -1015,6 +1018,7 @@ extern "C" int fkp_plan_set_graphs(void* plan, int enable) {
     cudaGraphExecDestroy(P->graph_exec);
     P->graph_exec = nullptr;
   }
+  if (!P->graphs) bisp_drop_graph(P);
   P->last_valid = false;
   return FKP_OK;
 }

@@ -40,6 +40,12 @@ struct BispState {
   std::vector<int> ta, tb, tc;       // triangle list
   std::vector<long long> nt;         // exact counts
   std::vector<unsigned char> cc;     // centre closed
+  // CUDA graph of the device part of a call (catalogs and contraction it was
+  // captured with; the previous call's, to capture on a repeat)
+  cudaGraphExec_t graph_exec = nullptr;
+  CatDev graph_key[2] = {}, last_key[2] = {};
+  int graph_contraction = -1, last_contraction = -1;
+  bool last_valid = false;
   int nl = 0;                        // number of multipoles computed (1..3)
   int nq = 3;                        // triangle sums per triangle: T0, T2, T4 (and T22 for FKP_B4B)
   bool zero_area = false;            // FKP_B4B: T22 = sum_x F_a^(2) F_b^(2) F_c^(0) (eq. Bhexa2)
@@ -679,33 +685,29 @@ int bisp_plan_init(Plan* P) {
 }
 
 void bisp_plan_free(Plan* P) {
+  bisp_drop_graph(P);
   delete static_cast<BispState*>(P->bisp);
   P->bisp = nullptr;
+}
+
+void bisp_drop_graph(Plan* P) {
+  auto* st = static_cast<BispState*>(P->bisp);
+  if (!st) return;
+  if (st->graph_exec) cudaGraphExecDestroy(st->graph_exec);
+  st->graph_exec = nullptr;
+  st->last_valid = false;
 }
 
 }  // namespace fkp
 
 using namespace fkp;
 
-extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_catalog_t* ran, int contraction,
-                              void* stream, fkp_power_out* pout, fkp_bisp_out* bout) {
-  auto* P = static_cast<Plan*>(plan);
-  if (!P) return set_error(FKP_EINVAL, "NULL plan");
-  if (!P->wantB || !P->bisp) return set_error(FKP_ESTATE, "plan was created without FKP_B* flags");
-  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3 && contraction != FKP_CONTRACT_BF16X6)
-    return set_error(FKP_EINVAL, "unknown contraction mode %d", contraction);
+// Enqueues the device part of one bispectrum call (gridding, the F and F^w
+// passes, the shell IFFTs, the contraction) on s.
+static int enqueue_bisp(Plan* P, const CatDev& g, const CatDev& r, int contraction, cudaStream_t s) {
   auto* st = static_cast<BispState*>(P->bisp);
   const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6;
-  if (tensor && !st->d_pairs && st->npairs > 0)
-    return set_error(FKP_EINVAL, "the tensor-core contraction needs (multipoles x shells) <= %d rows", tc_rows());
-  BCK(cudaSetDevice(P->ctx->device));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  CatDev g, r;
-  int rc = stage_catalog(P, gal, 0, g, s);
-  if (rc) return rc;
-  rc = randoms_of(P, ran, r, s);
-  if (rc) return rc;
-  rc = enqueue_grids(P, g, r, s);
+  int rc = enqueue_grids(P, g, r, s);
   if (rc) return rc;
   const int N = P->g.N, S = st->S, mm = st->mm;
   ZParams zp = zparams(P, 1);
@@ -721,7 +723,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, P->d_zpart, P->d_zpartc, P->d_err + 1, s,
                    P->ctx->nsm, P->sched.z_threads));
   BCK(launch_reduce_bins(P->d_zpart, P->d_zpartc, nbz, P->pb.nbins, P->d_bins, P->d_binc, s));
-  BCK(cudaEventRecord(P->ev[5], s));
+  BCK(record_stage(P->ev[5], s));
   // F^w: shell sums against the exported F_l
   rc = enqueue_xy(P, P->d_gridw, P->d_gridw2, nullptr, s, false);
   if (rc) return rc;
@@ -729,7 +731,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   BCK(launch_zpass(P->d_S2, P->g, P->mt, P->fp, P->d_tw, zp, st->d_spart, st->d_spartc, P->d_err + 1, s,
                    P->ctx->nsm, P->sched.z_threads));
   BCK(launch_reduce_bins(st->d_spart, st->d_spartc, nbz, S, st->d_shell, st->d_shellc, s));
-  BCK(cudaEventRecord(P->ev[6], s));
+  BCK(record_stage(P->ev[6], s));
   // shell IFFTs
   const long long N3 = (long long)N * N * N;
   {
@@ -751,7 +753,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
       BCK(shell_passes(L, s));
     }
   }
-  BCK(cudaEventRecord(P->ev[7], s));
+  BCK(record_stage(P->ev[7], s));
   // contraction
   const int ntri = P->ntri, nout = std::max(1, ntri) * st->nq;
   if (tensor && st->npairs > 0) {
@@ -770,7 +772,91 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
     k_reduce_slices<<<(nout + 255) / 256, 256, 0, s>>>(st->d_cpart, st->nslices, nout, st->d_T);
     BCK(cudaGetLastError());
   }
-  BCK(cudaEventRecord(P->ev[8], s));
+  BCK(record_stage(P->ev[8], s));
+  return FKP_OK;
+}
+
+// Captures enqueue_bisp for these catalogs and contraction into the plan's
+// bispectrum graph, on the plan's own capture stream.
+static int capture_bisp(Plan* P, const CatDev& g, const CatDev& r, int contraction) {
+  auto* st = static_cast<BispState*>(P->bisp);
+  if (!P->cap_stream) BCK(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  if (st->graph_exec) cudaGraphExecDestroy(st->graph_exec);
+  st->graph_exec = nullptr;
+  BCK(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue_bisp(P, g, r, contraction, P->cap_stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(P->cap_stream, &graph);
+  if (rc || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc ? rc : set_error(FKP_ECUDA, "bispectrum graph capture failed: %s", cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&st->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    st->graph_exec = nullptr;
+    return set_error(FKP_ECUDA, "bispectrum graph instantiation failed: %s", cudaGetErrorString(ei));
+  }
+  st->graph_key[0] = g;
+  st->graph_key[1] = r;
+  st->graph_contraction = contraction;
+  return FKP_OK;
+}
+
+static bool same_cat_b(const CatDev& a, const CatDev& b) { return std::memcmp(&a, &b, sizeof(CatDev)) == 0; }
+
+extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_catalog_t* ran, int contraction,
+                              void* stream, fkp_power_out* pout, fkp_bisp_out* bout) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P) return set_error(FKP_EINVAL, "NULL plan");
+  if (!P->wantB || !P->bisp) return set_error(FKP_ESTATE, "plan was created without FKP_B* flags");
+  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3 && contraction != FKP_CONTRACT_BF16X6)
+    return set_error(FKP_EINVAL, "unknown contraction mode %d", contraction);
+  auto* st = static_cast<BispState*>(P->bisp);
+  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6;
+  if (tensor && !st->d_pairs && st->npairs > 0)
+    return set_error(FKP_EINVAL, "the tensor-core contraction needs (multipoles x shells) <= %d rows", tc_rows());
+  BCK(cudaSetDevice(P->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CatDev g, r;
+  int rc = stage_catalog(P, gal, 0, g, s);
+  if (rc) return rc;
+  rc = randoms_of(P, ran, r, s);
+  if (rc) return rc;
+  const bool device_cats = (gal->on_device || gal->n == 0) && (!ran || ran->on_device || ran->n == 0);
+  // CUDA graph of the device part: replayed when the catalogs and the
+  // contraction are those it was captured with; captured on the second
+  // identical call in a row (the same rule as the power path)
+  bool replayed = false;
+  if (P->graphs && device_cats) {
+    const bool hit = st->graph_exec && same_cat_b(g, st->graph_key[0]) && same_cat_b(r, st->graph_key[1]) &&
+                     st->graph_contraction == contraction;
+    if (!hit && st->last_valid && same_cat_b(g, st->last_key[0]) && same_cat_b(r, st->last_key[1]) &&
+        st->last_contraction == contraction) {
+      if (capture_bisp(P, g, r, contraction) != FKP_OK) {
+        cudaGetLastError();
+        if (st->graph_exec) cudaGraphExecDestroy(st->graph_exec);
+        st->graph_exec = nullptr;
+      }
+    }
+    if (st->graph_exec && same_cat_b(g, st->graph_key[0]) && same_cat_b(r, st->graph_key[1]) &&
+        st->graph_contraction == contraction) {
+      BCK(cudaGraphLaunch(st->graph_exec, s));
+      replayed = true;
+    } else {
+      st->last_key[0] = g;
+      st->last_key[1] = r;
+      st->last_contraction = contraction;
+      st->last_valid = true;
+    }
+  }
+  if (!replayed) {
+    rc = enqueue_bisp(P, g, r, contraction, s);
+    if (rc) return rc;
+  }
+  const int N = P->g.N, S = st->S;
+  const long long N3 = (long long)N * N * N;
+  const int ntri = P->ntri, nout = std::max(1, ntri) * st->nq;
   std::vector<double> T(nout, 0.0), sh(BQ_N * S);
   std::vector<long long> shc(S);
   BCK(cudaMemcpyAsync(T.data(), st->d_T, sizeof(double) * nout, cudaMemcpyDeviceToHost, s));
@@ -780,6 +866,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   if (rc) return rc;
   float t = 0.f;
   if (pout) {
+    pout->graph = replayed ? 1 : 0;
     if (cudaEventElapsedTime(&t, P->ev[5], P->ev[7]) == cudaSuccess) pout->timing_ms[5] = t;  // F^w + shell IFFTs
     if (cudaEventElapsedTime(&t, P->ev[7], P->ev[8]) == cudaSuccess) pout->timing_ms[6] = t;
     if (cudaEventElapsedTime(&t, P->ev[0], P->ev[8]) == cudaSuccess) pout->timing_ms[7] = t;

@@ -218,3 +218,24 @@ def test_split_hexadecapole_bispectrum_matches_oracle(small_b, contraction):
     den = np.maximum(np.abs(ref["B4b"][m]), np.abs(ref["T0"][m]) / (N3 * ref["NT"][m] * ref["I33"]))
     assert np.max(np.abs(b["B4b"][m] - ref["B4b"][m]) / den) < B_TOL
     assert max(b_errors(b, ref, ref["I33"], N3).values()) < B_TOL
+
+
+def test_bispectrum_graph_replay_equals_plain_launches(small_b):
+    """The bispectrum path is captured into a CUDA graph on the second call
+    with the same device catalogs and contraction and replayed afterwards;
+    another contraction mode runs plain launches.  Replays equal plain
+    launches bit for bit."""
+    fkp = _fkp()
+    sv, gal, ran, geom, bs, ref, kf = small_b
+    plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
+    dg, dr = to_device(gal), to_device(ran)
+    runs = [plan.bispectrum(dg, dr, contraction=c) for c in (2, 2, 2, 0, 2)]
+    assert [p["graph"] for p, _ in runs] == [0, 1, 1, 0, 1]
+    plan.set_graphs(False)
+    p0, b0 = plan.bispectrum(dg, dr, contraction=2)
+    assert p0["graph"] == 0
+    for p, b in (runs[0], runs[1], runs[2], runs[4]):
+        for k in ("B0", "B2", "B4", "N0", "T0"):
+            assert np.array_equal(b[k], b0[k], equal_nan=True), k
+        assert np.array_equal(p["P0"], p0["P0"], equal_nan=True)
+    assert max(b_errors(b0, ref, ref["I33"], float(sv.N) ** 3).values()) < B_TOL
