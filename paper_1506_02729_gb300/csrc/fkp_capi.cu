@@ -858,13 +858,11 @@ int fkp::enqueue_xy(Plan* P, const unsigned long long* gq, const unsigned long l
   if (events) CK(record_stage(P->ev[3], s));
   CK(launch_ypass(P->d_S1, gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s, P->sched.y_threads));
   if (P->interlace) {
-    // the second grid's groups follow the first's; the x- and y-passes apply
-    // its half-cell phases in x and y, the z-pass the one in z
+    // the second grid's groups follow the first's; the z-pass applies its
+    // half-cell phase e^{-i pi (n_x + n_y + n_z)/N}
     float2* S2b = P->d_S2 + field_elems(P->g.N) * P->mt.ngroups;
-    CK(launch_xpass(gq2, nullptr, P->g2, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult,
-                    MockBatch(), P->d_hph));
-    CK(launch_ypass(P->d_S1, gq2, nullptr, P->g2, P->mt, P->fp, P->d_tw, S2b, P->d_err + 1, s, P->sched.y_threads,
-                    MockBatch(), P->d_hph));
+    CK(launch_xpass(gq2, nullptr, P->g2, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult));
+    CK(launch_ypass(P->d_S1, gq2, nullptr, P->g2, P->mt, P->fp, P->d_tw, S2b, P->d_err + 1, s, P->sched.y_threads));
   }
   if (events) CK(record_stage(P->ev[4], s));
   return FKP_OK;

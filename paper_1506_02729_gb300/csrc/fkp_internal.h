@@ -172,16 +172,13 @@ cudaError_t launch_wait_selftest(unsigned polls, int* flag, cudaStream_t s);
 // xm: x-pass blocks = SMs x resident blocks x xm; nt: threads per y- or
 // z-pass block (256 or 512).  The defaults are the 512^3 choices.  mb: the
 // mocks of one fused launch (blockIdx.z) and their buffer strides.
-// hph (x- and y-passes): for the second grid of an interlaced pair, the
-// table e^{-i pi n/N} by which the pass multiplies its output (its axis's
-// half-cell phase); nullptr otherwise.
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm = 2,
-                         MockBatch mb = MockBatch(), const float2* hph = nullptr);
+                         MockBatch mb = MockBatch());
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, float2* S2, int* err, cudaStream_t s, int nt = 256,
-                         MockBatch mb = MockBatch(), const float2* hph = nullptr);
+                         MockBatch mb = MockBatch());
 // The z-pass is persistent: zpass_blocks(N, nt, nsm) blocks, each writing
 // one column of the partial bins (part[key][block]); reduce over that count.
 cudaError_t launch_zpass(const float2* S2, const GeomDev& g, const MomentTable& mt, const FftPlan& fp,

@@ -94,9 +94,9 @@ struct ZParams {
   int mm;            // largest |n_a| inside the outermost shell
   // interlaced pair of grids: groups [ngroups, 2 ngroups) come from the
   // second grid (nodes half a cell further); hph[i] = e^{-i pi n/N} with n the
-  // signed index of i, by which the z-pass multiplies those groups after its
-  // FFT (the x- and y-passes applied the x and y factors); scale = 1/2 averages
-  // the two grids (1 without interlacing)
+  // signed index of i: the z-pass multiplies those groups after its FFT by
+  // hph[k_x] hph[k_y] hph[k_z]; scale = 1/2 averages the two grids (1 without
+  // interlacing)
   int interlace = 0;
   const float2* hph = nullptr;
   float scale = 1.f;

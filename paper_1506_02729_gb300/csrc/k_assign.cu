@@ -164,7 +164,12 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ra
                                                              double* __restrict__ labpart) {
   extern __shared__ int hist[];
   __shared__ double sh[32];
-  const float alpha = raw ? -1.f : (float)ds[DS_ALPHA];
+  // alpha and alpha^2 as float pairs (hi + lo): each random's value is then
+  // rounded once, at random, instead of carrying the FP32 rounding of alpha
+  // into every random alike (a systematic scale of the random field)
+  const double ad = raw ? 0.0 : ds[DS_ALPHA];
+  const float alpha = (float)ad, alo = (float)(ad - (double)alpha);
+  const float a2 = (float)(ad * ad), a2lo = (float)(ad * ad - (double)a2);
   const long long chunk = (c.n + gridDim.x - 1) / gridDim.x;
   const long long i0 = blockIdx.x * chunk;
   const long long i1 = i0 + chunk < c.n ? i0 + chunk : c.n;
@@ -186,8 +191,11 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ra
     int cx, cy, cz;
     if (centre_cell<P>(g, px, py, pz, cx, cy, cz)) {
       const int slot = atomicAdd(hist + tile_of(cx, cy, cz, g.N, ntx), 1);
-      xyzv[slot] = make_float4(px, py, pz, is_ran ? -alpha * w : w);
-      if (vw2) vw2[slot] = is_ran && !raw ? alpha * alpha * w * w : w * w;
+      xyzv[slot] = make_float4(px, py, pz, is_ran && !raw ? -fmaf(alpha, w, alo * w) : w);
+      if (vw2) {
+        const float ww = w * w;
+        vw2[slot] = is_ran && !raw ? fmaf(a2, ww, a2lo * ww) : ww;
+      }
     }
     if (is_ran) {
       float hx, hy, hz;

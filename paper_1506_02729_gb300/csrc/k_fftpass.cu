@@ -98,7 +98,7 @@ template <int N_, int LMAX>
 __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 1 : (N_ > 0 && N_ <= 256 ? 4 : 3))
     k_xpass2(
     const unsigned long long* __restrict__ gq, const float* __restrict__ gf, GeomDev g, FftPlan fp,
-    const float2* __restrict__ twg, float2* __restrict__ S1, MockBatch mb, const float2* __restrict__ hph) {
+    const float2* __restrict__ twg, float2* __restrict__ S1, MockBatch mb) {
   if (gq) gq += (long long)blockIdx.z * mb.in;
   if (gf) gf += (long long)blockIdx.z * mb.in;
   S1 += (long long)blockIdx.z * mb.out;
@@ -175,11 +175,6 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 
         const float2 zm = R[ilv<NP, SWZ>(k == 0 ? 0 : N - k, p)];
         o0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         o1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        if (hph) {  // second grid of an interlaced pair: its x half-cell phase
-          const float2 ph = __ldg(hph + k);
-          o0 = cmul(o0, ph);
-          o1 = cmul(o1, ph);
-        }
       }
       const size_t off = (((size_t)z * NXT + (k >> 3)) * N + y) * kT + (k & 7);
       S1[(size_t)(2 * p) * fsz + off] = o0;
@@ -203,8 +198,7 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
                                                    const unsigned long long* __restrict__ gq,
                                                    const float* __restrict__ gf, GeomDev g, MomentTable mt,
                                                    FftPlan fp, const float2* __restrict__ twg,
-                                                   float2* __restrict__ S2, int* __restrict__ err, MockBatch mb,
-                                                   const float2* __restrict__ hph) {
+                                                   float2* __restrict__ S2, int* __restrict__ err, MockBatch mb) {
   S1 += (long long)blockIdx.z * mb.in;
   if (gq) gq += (long long)blockIdx.z * mb.in2;
   if (gf) gf += (long long)blockIdx.z * mb.in2;
@@ -316,11 +310,7 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
 #pragma unroll
       for (int i = 0; i < PassShape<NT>::kRL; ++i) {
         const int ky = i * PassShape<NT>::kRun + run;
-        if (i < rl && ky < N) {
-          float2 v = o ? acc1[i] : acc0[i];
-          if (hph) v = cmul(v, __ldg(hph + ky));  // second grid of an interlaced pair: y half-cell phase
-          dst[(size_t)ky * tile] = v;
-        }
+        if (i < rl && ky < N) dst[(size_t)ky * tile] = o ? acc1[i] : acc0[i];
       }
     }
   }
@@ -351,16 +341,16 @@ __device__ __forceinline__ float pwsel(float v, float v2, int e) {
 
 // One group's contribution to the thread's run of k_z: F_0 (F0), c2 nz^p2 to
 // S_2 (A2), c4 nz^p4 to S_4 (A4).
-template <int RL, bool F0, bool A2, bool A4>
+template <int RL, bool F0, bool A2, bool A4, bool PH>
 __device__ __forceinline__ void zgroup(const float2* R, int z0, int rl, int N, int c, float c2, int p2, float c4,
                                        int p4, float2 (&f0)[RL], float2 (&s2)[RL], float2 (&s4)[RL],
-                                       const float2* ph) {
+                                       const float2* ph, float2 phxy) {
 #pragma unroll
   for (int i = 0; i < RL; ++i) {
     const int kz = z0 + i;
     if (i < rl && kz < N) {
       float2 v = R[kz * kT + c];
-      if (ph) v = cmul(v, ph[kz]);
+      if (PH) v = cmul(v, cmul(phxy, ph[kz]));
       const float nz = (float)smode(kz, N), nz2 = nz * nz;
       if (F0) f0[i] = cadd(f0[i], v);
       if (A2) {
@@ -475,13 +465,24 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
     mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 8);
     const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
     const int gg = gi < mt.ngroups ? gi : gi - mt.ngroups;  // the group's coefficients
-    const float2* ph = gi < mt.ngroups ? nullptr : zph;     // second grid: z half-cell phase
+    // second grid of an interlaced pair: its half-cell phase
+    // e^{-i pi (n_x + n_y + n_z)/N}, the n_x, n_y part fixed per thread
+    const float2 phxy = gi < mt.ngroups ? make_float2(1.f, 0.f)
+                                        : cmul(zph[(t % NXT) * kT + c < N ? (t % NXT) * kT + c : 0], zph[t / NXT]);
     const int p2 = mt.g_p2[gg], p4 = mt.g_p4[gg];
     const float c2 = mt.g_c2[gg], c4 = mt.g_c4[gg];
-    if (mt.g_f0[gg]) zgroup<PassShape<NT>::kRL, true, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, ph);
-    else if (c2 != 0.f && c4 != 0.f) zgroup<PassShape<NT>::kRL, false, true, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, ph);
-    else if (c2 != 0.f) zgroup<PassShape<NT>::kRL, false, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, ph);
-    else zgroup<PassShape<NT>::kRL, false, false, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, ph);
+    constexpr int RLc = PassShape<NT>::kRL;
+    if (gi < mt.ngroups) {
+      if (mt.g_f0[gg]) zgroup<RLc, true, true, false, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, zph, phxy);
+      else if (c2 != 0.f && c4 != 0.f) zgroup<RLc, false, true, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, zph, phxy);
+      else if (c2 != 0.f) zgroup<RLc, false, true, false, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, zph, phxy);
+      else zgroup<RLc, false, false, true, false>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, zph, phxy);
+    } else {  // second grid of an interlaced pair: its z half-cell phase
+      if (mt.g_f0[gg]) zgroup<RLc, true, true, false, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, zph, phxy);
+      else if (c2 != 0.f && c4 != 0.f) zgroup<RLc, false, true, true, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, zph, phxy);
+      else if (c2 != 0.f) zgroup<RLc, false, true, false, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, zph, phxy);
+      else zgroup<RLc, false, false, true, true>(R, z0, rl, N, c, c2, p2, c4, p4, f0, s2, s4, zph, phxy);
+    }
     __syncthreads();
   }
   const int kx = xt * kT + c;
@@ -503,19 +504,17 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
       const int nzv = smode(kz, N);
       const int n2 = kx * kx + nyv * nyv + nzv * nzv;
       if (n2 > 0) {
-        const float wc = wxy * zp.winv[2 * N + kz], wc2 = wc * wc;
-        const float a0 = f0[i].x * f0[i].x + f0[i].y * f0[i].y;
-        float m = wc2 * a0;
+        // |F_0|^2 = wc^2 a0, |F_2|^2 <= 5 wc^2 max(a0, a2/n^4), |F_4|^2 <= 155 wc^2 max(a0, a2/n^4, a4/n^8)
+        // (triangle inequality on eqs. F2, delta4); the approximate reciprocal's
+        // error is far inside the factor 2 of headroom in the scale below
+        const float wc = wxy * zp.winv[2 * N + kz];
+        float a = f0[i].x * f0[i].x + f0[i].y * f0[i].y;
         if (zp.lmax >= 2) {
-          const float i2 = 1.0f / (float)n2;
-          const float a2 = s2[i].x * s2[i].x + s2[i].y * s2[i].y;
-          const float b2 = 2.f * wc2 * (2.25f * a2 * i2 * i2 + 0.25f * a0);
-          m = fmaxf(m, b2);
-          if (zp.lmax >= 4) {
-            const float a4 = s4[i].x * s4[i].x + s4[i].y * s4[i].y;
-            m = fmaxf(m, 3.f * (19.140625f * wc2 * a4 * i2 * i2 * i2 * i2 + 6.25f * b2 + 0.765625f * wc2 * a0));
-          }
+          const float i2 = __fdividef(1.f, (float)n2), i4 = i2 * i2;
+          a = fmaxf(a, (s2[i].x * s2[i].x + s2[i].y * s2[i].y) * i4);
+          if (zp.lmax >= 4) a = fmaxf(a, (s4[i].x * s4[i].x + s4[i].y * s4[i].y) * i4 * i4);
         }
+        float m = wc * wc * a * (zp.lmax >= 4 ? 155.f : (zp.lmax >= 2 ? 5.f : 1.f));
         if (MODE == 2 && n2 < zp.nsh2 && zp.slut[n2] >= 0) {
           const int w2 = 2 * zp.mm + 1;
           const size_t e = ((size_t)(nzv + zp.mm) * w2 + (nyv + zp.mm)) * (zp.mm + 1) + kx;
@@ -677,8 +676,7 @@ int zpass_blocks(int N, int nt, int nsm) {
 
 template <int N_, int LMAX>
 static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                        const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb,
-                        const float2* hph) {
+                        const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb) {
   constexpr int NP = (nfields_of(LMAX) + 1) / 2;
   const size_t sm = xsm(g.N, NP);
   raise_smem_limit((const void*)k_xpass2<N_, LMAX>, sm);
@@ -686,67 +684,66 @@ static cudaError_t xrun(const unsigned long long* gq, const float* gf, const Geo
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, LMAX>, 32 * NP, sm);
   int grid = nsm * (occ > 0 ? occ : 1) * (xm > 0 ? xm : 2);
   if (grid > g.N * g.N) grid = g.N * g.N;
-  k_xpass2<N_, LMAX><<<dim3(grid, 1, mb.n), dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1, mb, hph);
+  k_xpass2<N_, LMAX><<<dim3(grid, 1, mb.n), dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1, mb);
   return cudaGetLastError();
 }
 
 template <int LMAX>
 static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb,
-                             const float2* hph) {
+                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb) {
   if (LMAX == 4) {
     switch (g.N) {
-      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
-      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
-      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
-      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
-      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
-      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+      case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 384: return xrun<384, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 360: return xrun<360, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 256: return xrun<256, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 128: return xrun<128, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+      case 64: return xrun<64, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
       default: break;
     }
   }
-  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+  return xrun<0, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
 }
 
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm,
-                         MockBatch mb, const float2* hph) {
-  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
-  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
-  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, hph);
+                         MockBatch mb) {
+  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
 }
 
 template <int N_, int NT>
 static cudaError_t yrun_nt(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                            const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                           cudaStream_t s, const MockBatch& mb, const float2* hph) {
+                           cudaStream_t s, const MockBatch& mb) {
   const size_t sm = ysm(g.N);
   raise_smem_limit((const void*)k_ypass2<N_, NT>, sm);
   k_ypass2<N_, NT><<<dim3(tiles_x(g.N), g.N, mb.n), dim3(kT, NT / kT), sm, s>>>(S1, gq, gf, g, mt, fp, tw, S2, err,
-                                                                                    mb, hph);
+                                                                                    mb);
   return cudaGetLastError();
 }
 
 template <int N_>
 static cudaError_t yrun(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                         const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                        cudaStream_t s, int nt, const MockBatch& mb, const float2* hph) {
-  return nt == 512 ? yrun_nt<N_, 512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb, hph)
-                   : yrun_nt<N_, 256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb, hph);
+                        cudaStream_t s, int nt, const MockBatch& mb) {
+  return nt == 512 ? yrun_nt<N_, 512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb)
+                   : yrun_nt<N_, 256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, mb);
 }
 
 // gq / gf: the grid the x-pass read (for the observer node's value).
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
-                         cudaStream_t s, int nt, MockBatch mb, const float2* hph) {
+                         cudaStream_t s, int nt, MockBatch mb) {
   switch (g.N) {
-    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
-    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
-    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
-    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
-    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
-    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
-    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb, hph);
+    case 512: return yrun<512>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 384: return yrun<384>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 360: return yrun<360>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 256: return yrun<256>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 128: return yrun<128>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    case 64: return yrun<64>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
+    default: return yrun<0>(S1, gq, gf, g, mt, fp, tw, S2, err, s, nt, mb);
   }
 }
 
