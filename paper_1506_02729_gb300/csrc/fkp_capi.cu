@@ -849,6 +849,7 @@ ZParams fkp::zparams(const Plan* P, int mode) {
   zp.interlace = P->interlace ? 1 : 0;
   zp.hph = P->d_hph;
   zp.scale = P->interlace ? 0.5f : 1.f;
+  zp.split68 = (P->want & (FKP_P6B | FKP_P8B)) && P->lmax >= 4 ? 1 : 0;
   return zp;
 }
 
@@ -935,8 +936,9 @@ int fkp::finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_sca
     const double s42 = hb[BQ_F42 * nb + b], s44 = hb[BQ_F44 * nb + b];
     const double s60 = 11.0 / 5.0 * (s42 - 2.0 / 7.0 * s20 - 20.0 / 77.0 * s40);
     const double s80 = 1287.0 / 490.0 * (s44 - s00 / 9.0 - 100.0 / 693.0 * s20 - 162.0 / 1001.0 * s40 - 20.0 / 99.0 * s60);
-    if (out->P6b) out->P6b[b] = n > 0 && P->lmax >= 4 ? 13.0 * s60 / n / I22 : nan;
-    if (out->P8b) out->P8b[b] = n > 0 && P->lmax >= 4 ? 17.0 * s80 / n / I22 : nan;
+    const bool split = P->lmax >= 4 && (P->want & (FKP_P6B | FKP_P8B));
+    if (out->P6b) out->P6b[b] = n > 0 && split ? 13.0 * s60 / n / I22 : nan;
+    if (out->P8b) out->P8b[b] = n > 0 && split ? 17.0 * s80 / n / I22 : nan;
   }
   float t = 0.f;
   for (int i = 0; i < 8; ++i) out->timing_ms[i] = 0.f;

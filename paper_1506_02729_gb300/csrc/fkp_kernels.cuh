@@ -100,6 +100,7 @@ struct ZParams {
   int interlace = 0;
   const float2* hph = nullptr;
   float scale = 1.f;
+  int split68 = 0;   // accumulate Re F_4 F_2* and |F_4|^2 (P_6b, P_8b)
 };
 
 // Catalog on the device.

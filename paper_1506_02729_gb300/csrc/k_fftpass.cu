@@ -410,6 +410,9 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
     zph[i] = zp.interlace ? zp.hph[i] : make_float2(1.f, 0.f);
   }
   const int ngt = zp.interlace ? 2 * mt.ngroups : mt.ngroups;  // groups read per tile
+  // bin quantities accumulated: the five of P_0..P_4b (or the F^w shell
+  // products), and Re F_4 F_2*, |F_4|^2 when the split l = 6, 8 are wanted
+  const int nq = MODE == 2 ? SQ_04 + 1 : (zp.split68 ? BQ_N : BQ_F22 + 1);
   for (int t = tid; t < BQ_N * nkey; t += NT) {
     sbi[t] = 0;
     sbd[t] = 0.0;
@@ -570,8 +573,10 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
           vals[BQ_F20] = F2.x * F0.x + F2.y * F0.y;
           vals[BQ_F40] = F4.x * F0.x + F4.y * F0.y;
           vals[BQ_F22] = F2.x * F2.x + F2.y * F2.y;
-          vals[BQ_F42] = F4.x * F2.x + F4.y * F2.y;
-          vals[BQ_F44] = F4.x * F4.x + F4.y * F4.y;
+          if (nq > BQ_F42) {
+            vals[BQ_F42] = F4.x * F2.x + F4.y * F2.y;
+            vals[BQ_F44] = F4.x * F4.x + F4.y * F4.y;
+          }
         }
         if (MODE != 0 && sh >= 0) {
           const int w2 = 2 * zp.mm + 1;
@@ -598,8 +603,9 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
         atomicAdd(sc + curb, cnt);
 #pragma unroll
         for (int q = 0; q < BQ_N; ++q)
-          atomicAdd(reinterpret_cast<unsigned long long*>(sbi + q * nkey + curb),
-                    (unsigned long long)__float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
+          if (q < nq)
+            atomicAdd(reinterpret_cast<unsigned long long*>(sbi + q * nkey + curb),
+                      (unsigned long long)__float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
       }
       curb = b;
       cnt = 0;
@@ -609,15 +615,17 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
     if (b >= 0) {
       cnt += (int)wcol;
 #pragma unroll
-      for (int q = 0; q < BQ_N; ++q) acc[q] = fmaf(wcol, vals[q], acc[q]);
+      for (int q = 0; q < BQ_N; ++q)
+        if (q < nq) acc[q] = fmaf(wcol, vals[q], acc[q]);
     }
   }
   if (curb >= 0) {
     atomicAdd(sc + curb, cnt);
 #pragma unroll
     for (int q = 0; q < BQ_N; ++q)
-      atomicAdd(reinterpret_cast<unsigned long long*>(sbi + q * nkey + curb),
-                (unsigned long long)__float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
+      if (q < nq)
+        atomicAdd(reinterpret_cast<unsigned long long*>(sbi + q * nkey + curb),
+                  (unsigned long long)__float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
   }
   __syncthreads();
   // the tile's fixed-point bin sums join the block's FP64 sums (each slot by

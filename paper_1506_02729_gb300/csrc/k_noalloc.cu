@@ -212,6 +212,7 @@ extern "C" int fkp_power_from_grid_noalloc(const fkp_geometry_t* geom, const fkp
   zp.slut = nullptr;
   zp.E = nullptr;
   zp.mm = 0;
+  zp.split68 = 1;
   NCK(launch_zpass(S2, g, mt, fp, d_tw, zp, d_part, d_partc, d_err + 1, s, dsm, z_threads_for(N)));
   NCK(launch_reduce_bins(d_part, d_partc, zpass_blocks(N, z_threads_for(N), dsm), pb->nbins, d_bins, d_binc, s));
 
