@@ -142,7 +142,8 @@ ZParams zparams(const Plan* P, int mode);
 int finish_power(Plan* P, cudaStream_t s, fkp_power_out* out, bool have_scalars, double I22, double N0);
 int bisp_plan_init(Plan* P);
 void bisp_plan_free(Plan* P);
-// Frees the plan's bispectrum graph (its buffers changed, or graphs were turned off).
+// Frees the plan's bispectrum graph (its buffers changed, or graphs were
+// turned off); the next repeat of a call captures a new one.
 void bisp_drop_graph(Plan* P);
 // Records a stage event on s; inside a stream capture as an external event
 // node, so that a replayed graph still times its stages.

@@ -695,7 +695,6 @@ void bisp_drop_graph(Plan* P) {
   if (!st) return;
   if (st->graph_exec) cudaGraphExecDestroy(st->graph_exec);
   st->graph_exec = nullptr;
-  st->last_valid = false;
 }
 
 }  // namespace fkp
