@@ -182,27 +182,31 @@ def algorithmic_bytes(N, ngroups, n_obj, cat_bytes=16):
     }
 
 
-def source_sha():
-    """First 12 hex of sha1 of the FFT-pass sources (k_fftpass.cu, fkp_fft.cuh)
-    with comments and blank lines removed, so that only code changes disown a
-    recorded capture."""
+PASS_SOURCES = {"xpass": "k_xpass.cu", "ypass": "k_ypass.cu", "zpass": "k_zpass.cu"}
+
+
+def source_sha(kernel):
+    """First 12 hex of sha1 of a pass's sources (its .cu file and the shared
+    headers k_fftpass.cuh, fkp_fft.cuh, fkp_kernels.cuh) with comments and
+    blank lines removed, so that only code changes disown a recorded capture."""
     import hashlib
     import re
-    out = []
-    for f in ("k_fftpass.cu", "fkp_fft.cuh"):
+    h = hashlib.sha1()
+    for f in (PASS_SOURCES[kernel], "k_fftpass.cuh", "fkp_fft.cuh", "fkp_kernels.cuh"):
         src = open(os.path.join(ROOT, "paper_1506_02729_gb300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         lines = [re.sub(r"//.*", "", ln).rstrip() for ln in src.splitlines()]
-        code = "\n".join(ln for ln in lines if ln.strip())
-        out.append(hashlib.sha1(code.encode()).hexdigest()[:12])
-    return ",".join(out)
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
+    return h.hexdigest()[:12]
 
 
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
     when the kernel's sources changed since the counters were taken."""
     try:
-        sha = source_sha()
+        if kernel not in PASS_SOURCES:
+            return None
+        sha = source_sha(kernel)
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             if line.startswith("#") or not line.strip():
                 continue

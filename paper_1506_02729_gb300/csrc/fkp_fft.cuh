@@ -221,9 +221,26 @@ __device__ __forceinline__ int ilv(int i, int p) {
   }
 }
 
+// Row permutation of the interleaved layout with P = 8 pencils (a row is
+// the 8 values of one index i, 64 bytes, half of the shared-memory banks):
+// rows i and i ^ 1 swap when bit 3 of i is set.  A first radix-8 stage writes
+// rows 8j + r for four consecutive j per warp, all of one parity, i.e. all
+// into the same half of the banks (two wavefronts too many); with the
+// permutation consecutive j alternate halves, while runs of four
+// consecutive rows (every other access of the stages) stay spread over both.
+__host__ __device__ __forceinline__ constexpr int rowx(int i) { return i ^ ((i >> 3) & 1); }
+
+// Shared-memory index of element i of pencil p in the row-permuted layout.
+template <int P, bool SWZ, bool RX>
+__device__ __forceinline__ int ilvx(int i, int p) {
+  if constexpr (RX) return rowx(i) * P + p;
+  else return ilv<P, SWZ>(i, p);
+}
+
 // The block is 2-D: threadIdx.x = pencil (blockDim.x == P), threadIdx.y
 // strides over the N/R butterflies of a stage (blockDim.y == NT / P).
-template <int N, int P, int NT, int DIR, int R, int NS, bool SWZ>
+// RXI / RXO: the stage reads / writes the row-permuted layout.
+template <int N, int P, int NT, int DIR, int R, int NS, bool SWZ, bool RXI = false, bool RXO = false>
 __device__ __forceinline__ void fft_ct_stage(const float2* __restrict__ src, float2* __restrict__ dst,
                                              const float2* __restrict__ tw) {
   constexpr int NB = N / R;
@@ -237,7 +254,7 @@ __device__ __forceinline__ void fft_ct_stage(const float2* __restrict__ src, flo
       const int k = j % NS;
       float2 v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = src[ilv<P, SWZ>(j + r * NB, p)];
+      for (int r = 0; r < R; ++r) v[r] = src[ilvx<P, SWZ, RXI>(j + r * NB, p)];
       if (NS > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -249,29 +266,32 @@ __device__ __forceinline__ void fft_ct_stage(const float2* __restrict__ src, flo
       dftR<R, DIR>(v);
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[ilv<P, SWZ>(base + r * NS, p)] = v[r];
+      for (int r = 0; r < R; ++r) dst[ilvx<P, SWZ, RXO>(base + r * NS, p)] = v[r];
     }
   }
 }
 
-template <int N, int P, int NT, int DIR, int S, int NS, bool SWZ>
+template <int N, int P, int NT, int DIR, int S, int NS, bool SWZ, bool RX = false>
 __device__ __forceinline__ float2* fft_ct_run(float2* a, float2* b, const float2* tw) {
   if constexpr (S == radix_count(N)) {
     return a;
   } else {
     constexpr int R = radix_at(N, S);
-    fft_ct_stage<N, P, NT, DIR, R, NS, SWZ>(a, b, tw);
+    fft_ct_stage<N, P, NT, DIR, R, NS, SWZ, (RX && (S > 0)), RX>(a, b, tw);
     __syncthreads();
-    return fft_ct_run<N, P, NT, DIR, S + 1, NS * R, SWZ>(b, a, tw);
+    return fft_ct_run<N, P, NT, DIR, S + 1, NS * R, SWZ, RX>(b, a, tw);
   }
 }
 
 // Transforms P interleaved pencils held in a (b is scratch of the same size).
 // Returns the buffer holding the result.  All NT threads of the (P, NT/P)
-// block call it; it ends with a __syncthreads().
-template <int N, int P, int NT, int DIR, bool SWZ = false>
+// block call it; it ends with a __syncthreads().  RX (P = 8, no swizzle):
+// the input is in the natural interleave and the result in the
+// row-permuted one (element i of pencil p at rowx(i) * 8 + p).
+template <int N, int P, int NT, int DIR, bool SWZ = false, bool RX = false>
 __device__ __forceinline__ float2* fft_ct(float2* a, float2* b, const float2* tw) {
-  return fft_ct_run<N, P, NT, DIR, 0, 1, SWZ>(a, b, tw);
+  static_assert(!RX || (P == 8 && !SWZ), "the row permutation is for 8 unswizzled pencils");
+  return fft_ct_run<N, P, NT, DIR, 0, 1, SWZ, RX>(a, b, tw);
 }
 
 // Runtime-N version on the same interleaved layout (sizes without a
@@ -330,10 +350,19 @@ __device__ float2* fft_rt(float2* a, float2* b, int P, const FftPlan& fp, const 
 }
 
 // N = 0 selects the runtime version.  SWZ: swizzled interleave (see ilv).
-template <int N, int P, int NT, int DIR, bool SWZ = false>
+// RX: the compile-time version leaves its result row-permuted (see fft_ct);
+// the runtime version ignores it, so read results through res_row<N, RX>.
+template <int N, int P, int NT, int DIR, bool SWZ = false, bool RX = false>
 __device__ __forceinline__ float2* fft_any(float2* a, float2* b, const FftPlan& fp, const float2* tw) {
-  if constexpr (N > 0) return fft_ct<N, P, NT, DIR, SWZ>(a, b, tw);
+  if constexpr (N > 0) return fft_ct<N, P, NT, DIR, SWZ, RX>(a, b, tw);
   else return fft_rt<DIR, SWZ>(a, b, P, fp, tw);
+}
+
+// Row of index i in the result of fft_any<N, ..., RX>.
+template <int N, bool RX>
+__device__ __forceinline__ int res_row(int i) {
+  if constexpr (N > 0 && RX) return rowx(i);
+  else return i;
 }
 
 // ----------------------------------------------------------------------------
