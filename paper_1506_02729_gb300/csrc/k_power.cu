@@ -3,8 +3,8 @@
 //   the FP64 finalize of the scalars (alpha, I_22, I_33, N_0, S_3; eqs.
 //   I22def, N0true, Noise0) and of L^ab (eq. Lab), and the fixed-order FP64
 //   reduction of the z-pass's per-block bin sums.  Gridding is in
-//   k_assign.cu, the FFT passes in k_fftpass.cu.
-// The three FFT passes are in k_fftpass.cu.
+//   k_assign.cu, the three FFT passes in k_xpass.cu, k_ypass.cu and
+//   k_zpass.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

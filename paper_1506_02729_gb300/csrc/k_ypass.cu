@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
         tma_load_1d(cur ? buf0 : buf1, src_of(mt.s_field[s2][m2]), bytes, &bar[cur ^ 1]);
       }
       mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 4);
-      const float2* R = fft_any<N_, kT, NT, -1, false, true>(bc, work, fp, tw);
+      const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
       // coefficients a[o][j] of n_y^j for this member and column
       float a[2][5];
 #pragma unroll
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
         const int ky = i * PassShape<NT>::kRun + run;
         if (i < rl && ky < N) {
           const float ny = (float)smode(ky, N);
-          const float2 v = R[res_row<N_, true>(ky) * kT + c];
+          const float2 v = R[ky * kT + c];
           const float s0 = fmaf(fmaf(fmaf(fmaf(a[0][4], ny, a[0][3]), ny, a[0][2]), ny, a[0][1]), ny, a[0][0]);
           acc0[i].x = fmaf(s0, v.x, acc0[i].x);
           acc0[i].y = fmaf(s0, v.y, acc0[i].y);
