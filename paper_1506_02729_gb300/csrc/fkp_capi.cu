@@ -551,6 +551,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   P->d_tcnt = (int*)A(sizeof(int) * P->ntiles);
   P->d_toff = (int*)A(sizeof(int) * (P->ntiles + 1));
   P->d_tcur = (int*)A(sizeof(int) * P->ntiles);
+  P->d_titem = (int*)A(sizeof(int) * (P->ntiles + 1));
   P->d_zpart = (double*)A(sizeof(double) * BQ_N * pb->nbins * (size_t)P->nblk_z);
   P->d_zpartc = (int*)A(sizeof(int) * pb->nbins * (size_t)P->nblk_z);
   P->d_bins = (double*)A(sizeof(double) * BQ_N * pb->nbins);
@@ -706,7 +707,7 @@ static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t
   else
     CK(launch_bin_count(ran, 1, geo, P->d_scpart + (size_t)nbg * SC_NSUM, P->d_tcnt, P->d_err, nbr, s));
   CK(launch_scalars_finalize(P->d_scpart, nbg, nbr, gal.n, nran, geo.alpha_mode, P->d_ds, s));
-  CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, s));
+  CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, P->d_titem, s));
   CK(stage(1));
   CK(cudaMemsetAsync(grid, 0, N3 * 8, s));
   if (gridw) CK(cudaMemsetAsync(gridw, 0, N3 * 8, s));
@@ -719,7 +720,7 @@ static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t
     CK(launch_bin_scatter(ran, 1, geo, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s));
     CK(launch_lab_finalize(P->d_labpart, ran.n > 0 ? nbr : 0, P->d_ds + DS_COUNT, s));
   }
-  CK(launch_tile_accum(geo, P->d_toff, P->d_xyzv, vw2, grid, gridw, s));
+  CK(launch_tile_accum(geo, P->d_toff, P->d_titem, gal.n + (cached ? 0 : ran.n), P->d_xyzv, vw2, grid, gridw, s));
   if (cached)
     CK(launch_combine_randoms(grid, rgrid, gridw, rgridw, P->d_ds, (long long)N3, P->ctx->nsm, s));
   return FKP_OK;
@@ -786,13 +787,13 @@ static int cache_randoms(Plan* P, const CatDev& ran, cudaStream_t s) {
     unsigned long long* rgw = which ? P->rc_gridw2 : P->rc_gridw;
     CK(cudaMemsetAsync(P->d_tcnt, 0, sizeof(int) * P->ntiles, s));
     CK(launch_bin_count(ran, 1, geo, P->rc_part, P->d_tcnt, P->d_err, nbr, s));
-    CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, s));
+    CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, P->d_titem, s));
     CK(cudaMemsetAsync(rg, 0, N3 * 8, s));
     if (rgw) CK(cudaMemsetAsync(rgw, 0, N3 * 8, s));
     CK(launch_bin_scatter(ran, 1, geo, P->geom.observer, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s,
                           1));
     CK(launch_lab_finalize(P->d_labpart, nbr, P->rc_lab, s));
-    CK(launch_tile_accum(geo, P->d_toff, P->d_xyzv, vw2, rg, rgw, s));
+    CK(launch_tile_accum(geo, P->d_toff, P->d_titem, ran.n, P->d_xyzv, vw2, rg, rgw, s));
   }
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

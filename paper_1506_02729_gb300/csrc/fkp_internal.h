@@ -56,7 +56,7 @@ struct Plan {
   int* d_err = nullptr;
   // tile binning of the catalogs (gridding)
   int ntiles = 0;
-  int *d_tcnt = nullptr, *d_toff = nullptr, *d_tcur = nullptr;
+  int *d_tcnt = nullptr, *d_toff = nullptr, *d_tcur = nullptr, *d_titem = nullptr;
   float4* d_xyzv = nullptr;
   float* d_vw2 = nullptr;
   size_t sort_cap = 0;
@@ -159,15 +159,15 @@ cudaError_t launch_scalars_finalize(const double* part, int nbg, int nbr, long l
 int assign_tiles_per_axis(int N);
 cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, double* part, int* cnt, int* err,
                              int nblk, cudaStream_t s);
-cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, cudaStream_t s);
+cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, int* items, cudaStream_t s);
 cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
                                int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s,
                                int raw = 0);
 cudaError_t launch_combine_randoms(unsigned long long* grid, const unsigned long long* rgrid,
                                    unsigned long long* gridw, const unsigned long long* rgridw, const double* ds,
                                    long long n, int nsm, cudaStream_t s);
-cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xyzv, const float* vw2,
-                              unsigned long long* grid, unsigned long long* gridw, cudaStream_t s);
+cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const int* items, long long nobj, const float4* xyzv,
+                              const float* vw2, unsigned long long* grid, unsigned long long* gridw, cudaStream_t s);
 cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
 cudaError_t launch_wait_selftest(unsigned polls, int* flag, cudaStream_t s);
 // xm: x-pass blocks = SMs x resident blocks x xm; nt: threads per y- or

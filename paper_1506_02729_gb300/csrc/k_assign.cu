@@ -21,11 +21,18 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "fkp_internal.h"
 
 namespace fkp {
 
 constexpr int kTile = 16;            // cells per tile side
+// Objects per work item of the tile accumulation: a tile's objects are split
+// into items of at most this many, so that the few tiles of the densest
+// parts of a survey do not hold up the end of the launch.
+constexpr int kAccumChunk = 2048;
+constexpr int kAccumThreads = 512;
 // Region a tile's objects reach, from one cell below the tile: the tile
 // plus one halo cell on each side for CIC and TSC, and one more above for
 // PCS (taps c-1 .. c+2 of the centre cell c).
@@ -125,29 +132,42 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
 }
 
 // Exclusive scan of the tile counts into offsets (off[ntiles] = total) and
-// the scatter cursors (cur = off).  One block of 1024 threads.
+// the scatter cursors (cur = off), and of the tiles' work items (one per
+// kAccumChunk objects or part of it) into item offsets (items[ntiles] = the
+// number of items).  One block of 1024 threads.
 __global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ cnt, int ntiles, int* __restrict__ off,
-                                                     int* __restrict__ cur) {
-  __shared__ int part[1024];
+                                                     int* __restrict__ cur, int* __restrict__ items) {
+  __shared__ int part[1024], parti[1024];
   const int per = (ntiles + blockDim.x - 1) / blockDim.x;
   const int a = threadIdx.x * per, b = min(ntiles, a + per);
-  int s = 0;
-  for (int i = a; i < b; ++i) s += cnt[i];
+  int s = 0, si = 0;
+  for (int i = a; i < b; ++i) {
+    s += cnt[i];
+    si += (cnt[i] + kAccumChunk - 1) / kAccumChunk;
+  }
   part[threadIdx.x] = s;
+  parti[threadIdx.x] = si;
   __syncthreads();
   for (int o = 1; o < (int)blockDim.x; o <<= 1) {
     const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    const int vi = threadIdx.x >= (unsigned)o ? parti[threadIdx.x - o] : 0;
     __syncthreads();
     part[threadIdx.x] += v;
+    parti[threadIdx.x] += vi;
     __syncthreads();
   }
-  int run = part[threadIdx.x] - s;
+  int run = part[threadIdx.x] - s, runi = parti[threadIdx.x] - si;
   for (int i = a; i < b; ++i) {
     off[i] = run;
     cur[i] = run;
+    items[i] = runi;
     run += cnt[i];
+    runi += (cnt[i] + kAccumChunk - 1) / kAccumChunk;
   }
-  if (threadIdx.x == blockDim.x - 1) off[ntiles] = part[threadIdx.x];
+  if (threadIdx.x == blockDim.x - 1) {
+    off[ntiles] = part[threadIdx.x];
+    items[ntiles] = parti[threadIdx.x];
+  }
 }
 
 // Each block owns a contiguous chunk of objects.  Pass 1 counts the chunk's
@@ -253,25 +273,45 @@ __device__ __forceinline__ void tap_weights(float u, int& i0, float* wt) {
   }
 }
 
-// One block per tile.  The tile's region [t*16 - 1, t*16 + 17)^3 covers the
-// taps of every object whose centre cell lies in the tile.
+// One block per work item: up to kAccumChunk objects of one tile (items in
+// tile order; items[t] is tile t's first).  The tile's region, from one cell
+// below the tile to the end of its reach (reg_side cells a side), covers the
+// taps of every object whose centre cell lies in the tile.  Blocks past the
+// last item return at once (the grid is sized from an upper bound).  The
+// integer sums make the result independent of how a tile is split.
 template <int P, bool W2>
-__global__ void __launch_bounds__(256) k_tile_accum(GeomDev g, int ntx, const int* __restrict__ off,
-                                                    const float4* __restrict__ xyzv, const float* __restrict__ vw2,
-                                                    unsigned long long* __restrict__ grid,
-                                                    unsigned long long* __restrict__ gridw) {
+__global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDev g, int ntx, int ntiles,
+                                                                        const int* __restrict__ off,
+                                                                        const int* __restrict__ items,
+                                                                        const float4* __restrict__ xyzv,
+                                                                        const float* __restrict__ vw2,
+                                                                        unsigned long long* __restrict__ grid,
+                                                                        unsigned long long* __restrict__ gridw) {
   constexpr int kReg = reg_side<P>(), kReg3 = reg_cells<P>();
   extern __shared__ unsigned long long reg[];
+  __shared__ int s_tile;
   unsigned long long* regw = reg + kReg3;
-  const int t = blockIdx.x;
-  const int a = off[t], b = off[t + 1];
-  if (a == b) return;
+  const int item = blockIdx.x;
+  if (item >= items[ntiles]) return;
+  if (threadIdx.x == 0) {
+    // last tile whose first item is at or before this one
+    int lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    s_tile = lo;
+  }
   const int N = g.N;
   for (int i = threadIdx.x; i < kReg3; i += blockDim.x) {
     reg[i] = 0ull;
     if (W2) regw[i] = 0ull;
   }
   __syncthreads();
+  const int t = s_tile;
+  const int a = off[t] + (item - items[t]) * kAccumChunk;
+  const int b = min(off[t + 1], a + kAccumChunk);
   const int tx = t % ntx, ty = (t / ntx) % ntx, tz = t / (ntx * ntx);
   const int lx0 = tx * kTile - 1, ly0 = ty * kTile - 1, lz0 = tz * kTile - 1;
   for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
@@ -368,8 +408,8 @@ cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, cudaStream_t s) {
-  k_scan_tiles<<<1, 1024, 0, s>>>(cnt, ntiles, off, cur);
+cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, int* items, cudaStream_t s) {
+  k_scan_tiles<<<1, 1024, 0, s>>>(cnt, ntiles, off, cur, items);
   return cudaGetLastError();
 }
 
@@ -399,16 +439,22 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const float4* xyzv, const float* vw2,
-                              unsigned long long* grid, unsigned long long* gridw, cudaStream_t s) {
+// nobj: the objects scattered into tile order (bounds the number of items).
+cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const int* items, long long nobj, const float4* xyzv,
+                              const float* vw2, unsigned long long* grid, unsigned long long* gridw, cudaStream_t s) {
   const int ntx = assign_tiles_per_axis(g.N);
   const int ntiles = ntx * ntx * ntx;
+  // every non-empty tile has one item that may be partial, the rest are full
+  const long long nitems = std::min<long long>((long long)ntiles, nobj) + nobj / kAccumChunk;
+  if (nitems <= 0) return cudaSuccess;
+  if (nitems > INT32_MAX) return cudaErrorInvalidValue;
   const bool w2 = gridw != nullptr;
 #define FKP_TA(PP, WW)                                                                                 \
   do {                                                                                                 \
     const size_t sm = sizeof(unsigned long long) * reg_cells<PP>() * (WW ? 2 : 1);                     \
     raise_smem_limit((const void*)k_tile_accum<PP, WW>, sm);                                           \
-    k_tile_accum<PP, WW><<<ntiles, 256, sm, s>>>(g, ntx, off, xyzv, vw2, grid, gridw);                 \
+    k_tile_accum<PP, WW><<<(int)nitems, kAccumThreads, sm, s>>>(g, ntx, ntiles, off, items, xyzv, vw2, grid, \
+                                                                gridw);                                \
   } while (0)
   if (g.assign == 2) {
     if (w2) FKP_TA(2, true); else FKP_TA(2, false);
