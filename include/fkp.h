@@ -226,6 +226,23 @@ int fkp_plan_cache_randoms(void *plan, const fkp_catalog_t *ran, void *cuda_stre
 int fkp_power(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
               void *cuda_stream, fkp_power_out *out);
 
+/* The gridded fields of one survey (eq. mapFFT and the F^w of eq. SNbisp2):
+ * F(x) = sum_g w W(x - x_g) - alpha sum_r w W(x - x_r) and, for bispectrum
+ * plans, F^w(x) = sum_g w^2 W(x - x_g) + alpha^2 sum_r w^2 W(x - x_r), with
+ * the plan's assignment W and alpha = W_g / W_r, exactly as fkp_power and
+ * fkp_bispectrum grid them.  Every tap's value is rounded to a multiple of
+ * 2^-40 and the rounded values are summed as integers, so the grid is the
+ * same whatever the order of the objects.  F and Fw (host or device, N^3
+ * int64 each, [z][y][x] with x fastest, owned by the caller) receive the
+ * fields in units of 2^-40; Fw may be NULL and must be NULL for plans
+ * without bispectrum outputs (FKP_EINVAL).  which = 1 selects the second
+ * grid of an interlaced plan (origin shifted by half a cell along each axis;
+ * FKP_EINVAL otherwise).  ran == NULL uses the cached random catalog as
+ * fkp_power does.  Synchronizes cuda_stream before it returns.  FKP_EGEOM if
+ * an object lies too close to a box face (non-periodic plans). */
+int fkp_grid(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran, int which,
+             long long *F, long long *Fw, void *cuda_stream);
+
 /* P_l of nmock independent surveys (mocks) on one plan's grid, for the
  * ensembles that covariance estimates need (abstract; Sec. III.C, Performance): gals[k] and
  * rans[k] (host or device, any sizes, randoms non-empty) give mock k, whose

@@ -28,7 +28,7 @@ EXPORTS = ["fkp_context_create", "fkp_context_destroy", "fkp_plan_create", "fkp_
            "fkp_power_from_grid_noalloc", "fkp_server_create", "fkp_server_submit", "fkp_server_poll",
            "fkp_server_wait", "fkp_server_stats", "fkp_server_destroy", "fkp_check_tables",
            "fkp_plan_set_graphs", "fkp_plan_schedule", "fkp_plan_set_schedule", "fkp_power_batch",
-           "fkp_selftest_bounded_wait", "fkp_plan_cache_randoms"]
+           "fkp_selftest_bounded_wait", "fkp_plan_cache_randoms", "fkp_grid"]
 
 
 class FKPError(RuntimeError):
@@ -130,6 +130,7 @@ def lib():
         L.fkp_version.restype = C.c_char_p
         L.fkp_selftest_bounded_wait.argtypes = [C.c_int, C.c_uint]
         L.fkp_plan_cache_randoms.argtypes = [vp, C.POINTER(Catalog), vp]
+        L.fkp_grid.argtypes = [vp, C.POINTER(Catalog), C.POINTER(Catalog), C.c_int, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -310,6 +311,19 @@ class Plan:
         _check(lib().fkp_power(self._h, C.byref(cg), C.byref(cr) if cr is not None else None,
                                _stream_handle(stream), C.byref(o)))
         return self._scalars(o, arr)
+
+    def grid(self, gal, ran, which=0, with_w=False, stream=None):
+        """The gridded fields F (and F^w with with_w) of one survey as int64
+        numpy arrays [z][y][x] in units of 2^-40 (ran=None: the plan's cached
+        random catalog; which=1: an interlaced plan's second grid)."""
+        N = self.geom["N"]
+        cg, k1 = make_catalog(gal, self.device)
+        cr, k2 = make_catalog(ran, self.device) if ran is not None else (None, None)
+        F = np.empty((N, N, N), dtype=np.int64)
+        Fw = np.empty((N, N, N), dtype=np.int64) if with_w else None
+        _check(lib().fkp_grid(self._h, C.byref(cg), C.byref(cr) if cr is not None else None, int(which),
+                              F.ctypes.data, Fw.ctypes.data if Fw is not None else None, _stream_handle(stream)))
+        return (F, Fw) if with_w else F
 
     def power_batch(self, gals, rans, stream=None):
         """P_0, P_2, P_4, P_4b and the scalars of several mocks on this plan's

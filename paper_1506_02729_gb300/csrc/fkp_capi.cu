@@ -1044,6 +1044,34 @@ extern "C" int fkp_power(void* plan, const fkp_catalog_t* gal, const fkp_catalog
   return rc;
 }
 
+extern "C" int fkp_grid(void* plan, const fkp_catalog_t* gal, const fkp_catalog_t* ran, int which, long long* F,
+                        long long* Fw, void* stream) {
+  auto* P = static_cast<Plan*>(plan);
+  if (!P || !gal || !F) return set_error(FKP_EINVAL, "NULL plan, catalog or output");
+  if (which != 0 && !(which == 1 && P->interlace))
+    return set_error(FKP_EINVAL, "which = %d: 0, or 1 for the second grid of an interlaced plan", which);
+  if (Fw && !P->d_gridw) return set_error(FKP_EINVAL, "the plan keeps no F^w grid (no bispectrum outputs)");
+  CK(cudaSetDevice(P->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CatDev g, r;
+  int rc = stage_catalog(P, gal, 0, g, s);
+  if (rc) return rc;
+  rc = randoms_of(P, ran, r, s);
+  if (rc) return rc;
+  rc = enqueue_grids(P, g, r, s);
+  if (rc) return rc;
+  const size_t N = (size_t)P->g.N, bytes = N * N * N * sizeof(long long);
+  CK(cudaMemcpyAsync(F, which ? P->d_grid2 : P->d_grid, bytes, cudaMemcpyDefault, s));
+  if (Fw) CK(cudaMemcpyAsync(Fw, which ? P->d_gridw2 : P->d_gridw, bytes, cudaMemcpyDefault, s));
+  int* herr = reinterpret_cast<int*>(P->h_pinned);
+  CK(cudaMemcpyAsync(herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (herr[0] != 0)
+    return set_error(FKP_EGEOM, "an object lies within assign/2+1 cells of a box face (or is not finite); "
+                                "enlarge the box or set periodic=1 (flags 0x%x)", herr[0]);
+  return FKP_OK;
+}
+
 // Per-mock element counts of the fused batch workspace.
 namespace {
 struct BatchSizes {

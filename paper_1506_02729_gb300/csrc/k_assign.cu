@@ -277,8 +277,18 @@ __device__ __forceinline__ void tap_weights(float u, int& i0, float* wt) {
 // tile order; items[t] is tile t's first).  The tile's region, from one cell
 // below the tile to the end of its reach (reg_side cells a side), covers the
 // taps of every object whose centre cell lies in the tile.  Blocks past the
-// last item return at once (the grid is sized from an upper bound).  The
-// integer sums make the result independent of how a tile is split.
+// last item return at once (the grid is sized from an upper bound).
+//
+// Each tap adds x = round(v 2^40) to its cell.  Shared-memory adds of 64 bits
+// are several times slower than adds of 32 bits, so a cell is held as two
+// 32-bit words: L sums the low 20 bits of each x (at most kAccumChunk terms
+// below 2^20, so L cannot wrap) and H the rest, x >> 20 (arithmetic shift).
+// H stays exact while the item's sum of |v| (an upper bound for any cell's
+// sum of |v|, every tap weight being at most 1) is below 2^10: then
+// |sum of x >> 20| < 2^30 + kAccumChunk.  Items above that bound add x as one
+// 64-bit word instead.  Both forms give the exact integer sum of the x, so
+// the grid does not depend on how the objects are split into items or in
+// which order they are added.
 template <int P, bool W2>
 __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDev g, int ntx, int ntiles,
                                                                         const int* __restrict__ off,
@@ -288,9 +298,15 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
                                                                         unsigned long long* __restrict__ grid,
                                                                         unsigned long long* __restrict__ gridw) {
   constexpr int kReg = reg_side<P>(), kReg3 = reg_cells<P>();
+  static_assert(kAccumChunk <= 4096, "the low words would wrap");
   extern __shared__ unsigned long long reg[];
   __shared__ int s_tile;
+  __shared__ float s_abs;
   unsigned long long* regw = reg + kReg3;
+  unsigned* L = reinterpret_cast<unsigned*>(reg);
+  unsigned* H = L + kReg3;
+  unsigned* Lw = reinterpret_cast<unsigned*>(regw);
+  unsigned* Hw = Lw + kReg3;
   const int item = blockIdx.x;
   if (item >= items[ntiles]) return;
   if (threadIdx.x == 0) {
@@ -302,6 +318,7 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
       else hi = mid - 1;
     }
     s_tile = lo;
+    s_abs = 0.f;
   }
   const int N = g.N;
   for (int i = threadIdx.x; i < kReg3; i += blockDim.x) {
@@ -314,7 +331,18 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
   const int b = min(off[t + 1], a + kAccumChunk);
   const int tx = t % ntx, ty = (t / ntx) % ntx, tz = t / (ntx * ntx);
   const int lx0 = tx * kTile - 1, ly0 = ty * kTile - 1, lz0 = tz * kTile - 1;
-  for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
+  // the item's objects are read twice: for the bound, then for the taps (the
+  // second read mostly from L1)
+  float sa = 0.f;
+  for (int i = a + threadIdx.x; i < b; i += kAccumThreads)
+    sa += fmaxf(fabsf(xyzv[i].w), W2 ? fabsf(vw2[i]) : 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&s_abs, sa);
+  __syncthreads();
+  // the bound, with room for the rounding of the FP32 sums above
+  const bool split = s_abs < 1000.f;
+  for (int i = a + threadIdx.x; i < b; i += kAccumThreads) {
     const float4 o = xyzv[i];
     const float wv = W2 ? vw2[i] : 0.f;
     const float ux = (o.x - g.ox) * g.invH, uy = (o.y - g.oy) * g.invH, uz = (o.z - g.oz) * g.invH;
@@ -337,16 +365,33 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
 #pragma unroll
         for (int r = 0; r < P; ++r) {
           const float tw = wzy * wx[r];
-          atomicAdd(reg + base + r, (unsigned long long)__float2ll_rn(o.w * tw * kFixScaleF));
-          if (W2) atomicAdd(regw + base + r, (unsigned long long)__float2ll_rn(wv * tw * kFixScaleF));
+          const long long x = __float2ll_rn(o.w * tw * kFixScaleF);
+          const long long xw = W2 ? __float2ll_rn(wv * tw * kFixScaleF) : 0ll;
+          if (split) {
+            atomicAdd(L + base + r, (unsigned)x & 0xFFFFFu);
+            atomicAdd(H + base + r, (unsigned)(x >> 20));
+            if (W2) {
+              atomicAdd(Lw + base + r, (unsigned)xw & 0xFFFFFu);
+              atomicAdd(Hw + base + r, (unsigned)(xw >> 20));
+            }
+          } else {
+            atomicAdd(reg + base + r, (unsigned long long)x);
+            if (W2) atomicAdd(regw + base + r, (unsigned long long)xw);
+          }
         }
       }
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kReg3; i += blockDim.x) {
-    const unsigned long long v = reg[i];
-    const unsigned long long vw = W2 ? regw[i] : 0ull;
+    unsigned long long v, vw = 0ull;
+    if (split) {
+      v = (unsigned long long)((long long)(int)H[i] * 1048576ll + (long long)L[i]);
+      if (W2) vw = (unsigned long long)((long long)(int)Hw[i] * 1048576ll + (long long)Lw[i]);
+    } else {
+      v = reg[i];
+      if (W2) vw = regw[i];
+    }
     if (v == 0ull && vw == 0ull) continue;
     const int lx = i % kReg, ly = (i / kReg) % kReg, lz = i / (kReg * kReg);
     const size_t gi = ((size_t)wrapN(lz0 + lz, N) * N + wrapN(ly0 + ly, N)) * N + wrapN(lx0 + lx, N);
