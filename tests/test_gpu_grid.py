@@ -42,12 +42,21 @@ def _plan(geom):
     return fkp.Plan(geom, (0.5 * kf, kf, 8), bshells=(3, 3, 3, 4), want=B_ALL)
 
 
-# The GPU forms u = (x - origin) / H in FP32: the difference (|x - origin| <
-# 1024 here) is within 3e-5 of exact, about 2e-6 cells, and the FP32 1/H and
-# the product add up to 64 * 2^-24 each, so u is within about 1e-5 cells.  A
-# tap weight moves by at most that much per axis (slopes <= 1), so a cell's
-# error stays below 3e-5 of its sum of |w| W; the tolerance is twice that.
-REL = 6e-5
+def _exact_setup(assign, seed=4, interlace=False):
+    """The small survey's catalogs on a box whose cell is 16 (L = 1024, N =
+    64, origin -48), positions rounded to multiples of 2^-10: then the GPU's
+    FP32 u = (x - origin)/H is exact, and only the tap weights' and values'
+    FP32 roundings (a few 2^-24 of each term) separate it from the oracle."""
+    sv = mockgen.survey_small(N=64, assign=assign)
+    gal, ran = mockgen.catalog(sv, seed)
+    for c in (gal, ran):
+        for k in ("x", "y", "z"):
+            c[k] = (np.round(c[k].astype(np.float64) * 1024.0) / 1024.0).astype(np.float32)
+    geom = dict(sv.geometry(), L=1024.0, origin=(-48.0, -48.0, -48.0), periodic=True, interlace=interlace)
+    return sv, gal, ran, geom
+
+
+REL = 1e-6   # of each cell's sum of |terms|: a few FP32 roundings per term
 
 
 @pytest.mark.parametrize("assign,interlace", [(2, False), (3, False), (4, False), (4, True)],
@@ -56,22 +65,18 @@ def test_grid_matches_oracle_assignment(assign, interlace):
     """F and F^w cell by cell against the oracle's assignment (CIC, TSC, PCS;
     for the interlaced plan, its second grid against the oracle's grid with
     the origin moved by half a cell)."""
-    sv = mockgen.survey_small(N=64, assign=assign)
-    gal, ran = mockgen.catalog(sv, 4)
-    geom = dict(sv.geometry(), periodic=True, interlace=interlace)
+    sv, gal, ran, geom = _exact_setup(assign, interlace=interlace)
     plan = _plan(geom)
     F, Fw = plan.grid(_dev(gal), _dev(ran), which=1 if interlace else 0, with_w=True)
     g_or = op.shifted_geometry(dict(geom, interlace=False)) if interlace else dict(geom, interlace=False)
     Fo, Fwo, sc = op.fkp_grids(gal, ran, g_or, with_w2=True)
-    N = sv.N
-    Fo, Fwo = Fo.reshape(N, N, N), Fwo.reshape(N, N, N)
     A, Aw = _abs_fields(gal, ran, g_or, sc["alpha"])
-    A, Aw = A.reshape(N, N, N), Aw.reshape(N, N, N)
     got, gotw = F * UNIT, Fw * UNIT
-    assert np.all(np.abs(got - Fo) <= REL * A + 1e-9), float(np.max(np.abs(got - Fo) - REL * A))
-    assert np.all(np.abs(gotw - Fwo) <= REL * Aw + 1e-9), float(np.max(np.abs(gotw - Fwo) - REL * Aw))
+    assert np.all(np.abs(got - Fo) <= REL * A + 1e-11), float(np.max(np.abs(got - Fo) - REL * A))
+    assert np.all(np.abs(gotw - Fwo) <= REL * Aw + 1e-11), float(np.max(np.abs(gotw - Fwo) - REL * Aw))
     # cells no tap reaches are exactly zero
     assert np.all(F[A == 0] == 0) and np.all(Fw[Aw == 0] == 0)
+    assert np.count_nonzero(A) > 50000
 
 
 def test_grid_does_not_depend_on_object_order_or_accumulation_form():
@@ -83,13 +88,13 @@ def test_grid_does_not_depend_on_object_order_or_accumulation_form():
     order.  Both forms and every order give the same grid, bit for bit (the
     weights keep W_g and W_r, hence alpha, exact whatever the order of their
     sums); the oracle agrees within the rounding bound."""
-    sv = mockgen.survey_small(N=64, assign=3)
-    gal = mockgen.randoms(sv, 11)
-    ran = mockgen.randoms(sv, 12)
+    # two random catalogs (200000 objects, thousands per tile), one as the
+    # galaxies
+    sv, _, gal, geom = _exact_setup(3, seed=11)
+    _, _, ran, _ = _exact_setup(3, seed=12)
     r = np.random.default_rng(1506)
     gal["w"] = (r.integers(0, 1004, len(gal["x"])) / 1024.0).astype(np.float32)
     ran["w"] = np.ones(len(ran["x"]), dtype=np.float32)
-    geom = dict(sv.geometry(), periodic=True)
     plan = _plan(geom)
     F1, Fw1 = plan.grid(_dev(gal), _dev(ran), with_w=True)
     pg, pr = r.permutation(len(gal["x"])), r.permutation(len(ran["x"]))
@@ -100,10 +105,9 @@ def test_grid_does_not_depend_on_object_order_or_accumulation_form():
     assert np.array_equal(F1, F2) and np.array_equal(Fw1, Fw2)
     assert np.array_equal(F1, F3) and np.array_equal(Fw1, Fw3)
     Fo, Fwo, sc = op.fkp_grids(gal, ran, geom, with_w2=True)
-    N = sv.N
     A, Aw = _abs_fields(gal, ran, geom, sc["alpha"])
-    assert np.all(np.abs(F1 * UNIT - Fo.reshape(N, N, N)) <= REL * A.reshape(N, N, N) + 1e-9)
-    assert np.all(np.abs(Fw1 * UNIT - Fwo.reshape(N, N, N)) <= REL * Aw.reshape(N, N, N) + 1e-9)
+    assert np.all(np.abs(F1 * UNIT - Fo) <= REL * A + 1e-11)
+    assert np.all(np.abs(Fw1 * UNIT - Fwo) <= REL * Aw + 1e-11)
 
 
 def test_grid_rejects_bad_requests():
