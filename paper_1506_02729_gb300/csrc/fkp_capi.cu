@@ -550,8 +550,8 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   }
   P->d_tcnt = (int*)A(sizeof(int) * P->ntiles);
   P->d_toff = (int*)A(sizeof(int) * (P->ntiles + 1));
-  P->d_tcur = (int*)A(sizeof(int) * P->ntiles);
   P->d_titem = (int*)A(sizeof(int) * (P->ntiles + 1));
+  P->d_bhist = (int*)A(sizeof(int) * (size_t)P->ntiles * 2 * P->ctx->nsm);
   P->d_zpart = (double*)A(sizeof(double) * BQ_N * pb->nbins * (size_t)P->nblk_z);
   P->d_zpartc = (int*)A(sizeof(int) * pb->nbins * (size_t)P->nblk_z);
   P->d_bins = (double*)A(sizeof(double) * BQ_N * pb->nbins);
@@ -698,26 +698,27 @@ static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t
   const int nbg = nblocks(gal.n), nbr = cached ? P->rc_nblk : nblocks(ran.n);
   const long long nran = cached ? P->rc_n : ran.n;
   if (!which) CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
-  CK(cudaMemsetAsync(P->d_tcnt, 0, sizeof(int) * P->ntiles, s));
   CK(stage(0));
-  CK(launch_bin_count(gal, 0, geo, P->d_scpart, P->d_tcnt, P->d_err, nbg, s));
+  int* bh_ran = P->d_bhist + (size_t)nbg * P->ntiles;
+  CK(launch_bin_count(gal, 0, geo, P->d_scpart, P->d_bhist, P->d_err, nbg, s));
   if (cached)
     CK(cudaMemcpyAsync(P->d_scpart + (size_t)nbg * SC_NSUM, P->rc_part, sizeof(double) * SC_NSUM * nbr,
                        cudaMemcpyDeviceToDevice, s));
   else
-    CK(launch_bin_count(ran, 1, geo, P->d_scpart + (size_t)nbg * SC_NSUM, P->d_tcnt, P->d_err, nbr, s));
+    CK(launch_bin_count(ran, 1, geo, P->d_scpart + (size_t)nbg * SC_NSUM, bh_ran, P->d_err, nbr, s));
   CK(launch_scalars_finalize(P->d_scpart, nbg, nbr, gal.n, nran, geo.alpha_mode, P->d_ds, s));
-  CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, P->d_titem, s));
+  CK(launch_tile_prefix(P->d_bhist, nbg + (cached ? 0 : nbr), P->ntiles, P->d_tcnt, s));
+  CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_titem, s));
   CK(stage(1));
   CK(cudaMemsetAsync(grid, 0, N3 * 8, s));
   if (gridw) CK(cudaMemsetAsync(gridw, 0, N3 * 8, s));
   const double* obs = P->geom.observer;
   float* vw2 = gridw ? P->d_vw2 : nullptr;
-  CK(launch_bin_scatter(gal, 0, geo, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, nullptr, nbg, s));
+  CK(launch_bin_scatter(gal, 0, geo, obs, P->d_ds, P->d_toff, P->d_bhist, P->d_xyzv, vw2, nullptr, nbg, s));
   if (cached) {
     CK(cudaMemcpyAsync(P->d_ds + DS_COUNT, P->rc_lab, sizeof(double) * LAB_NSUM, cudaMemcpyDeviceToDevice, s));
   } else {
-    CK(launch_bin_scatter(ran, 1, geo, obs, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s));
+    CK(launch_bin_scatter(ran, 1, geo, obs, P->d_ds, P->d_toff, bh_ran, P->d_xyzv, vw2, P->d_labpart, nbr, s));
     CK(launch_lab_finalize(P->d_labpart, ran.n > 0 ? nbr : 0, P->d_ds + DS_COUNT, s));
   }
   CK(launch_tile_accum(geo, P->d_toff, P->d_titem, gal.n + (cached ? 0 : ran.n), P->d_xyzv, vw2, grid, gridw, s));
@@ -785,12 +786,12 @@ static int cache_randoms(Plan* P, const CatDev& ran, cudaStream_t s) {
     const GeomDev& geo = which ? P->g2 : P->g;
     unsigned long long* rg = which ? P->rc_grid2 : P->rc_grid;
     unsigned long long* rgw = which ? P->rc_gridw2 : P->rc_gridw;
-    CK(cudaMemsetAsync(P->d_tcnt, 0, sizeof(int) * P->ntiles, s));
-    CK(launch_bin_count(ran, 1, geo, P->rc_part, P->d_tcnt, P->d_err, nbr, s));
-    CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_tcur, P->d_titem, s));
+    CK(launch_bin_count(ran, 1, geo, P->rc_part, P->d_bhist, P->d_err, nbr, s));
+    CK(launch_tile_prefix(P->d_bhist, nbr, P->ntiles, P->d_tcnt, s));
+    CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_titem, s));
     CK(cudaMemsetAsync(rg, 0, N3 * 8, s));
     if (rgw) CK(cudaMemsetAsync(rgw, 0, N3 * 8, s));
-    CK(launch_bin_scatter(ran, 1, geo, P->geom.observer, P->d_ds, P->d_tcur, P->d_xyzv, vw2, P->d_labpart, nbr, s,
+    CK(launch_bin_scatter(ran, 1, geo, P->geom.observer, P->d_ds, P->d_toff, P->d_bhist, P->d_xyzv, vw2, P->d_labpart, nbr, s,
                           1));
     CK(launch_lab_finalize(P->d_labpart, nbr, P->rc_lab, s));
     CK(launch_tile_accum(geo, P->d_toff, P->d_titem, ran.n, P->d_xyzv, vw2, rg, rgw, s));

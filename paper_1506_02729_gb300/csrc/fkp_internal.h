@@ -56,7 +56,8 @@ struct Plan {
   int* d_err = nullptr;
   // tile binning of the catalogs (gridding)
   int ntiles = 0;
-  int *d_tcnt = nullptr, *d_toff = nullptr, *d_tcur = nullptr, *d_titem = nullptr;
+  int *d_tcnt = nullptr, *d_toff = nullptr, *d_titem = nullptr;
+  int* d_bhist = nullptr;  // per-block tile counts of the count launches (2 nsm rows)
   float4* d_xyzv = nullptr;
   float* d_vw2 = nullptr;
   size_t sort_cap = 0;
@@ -157,12 +158,13 @@ size_t field_elems(int N);
 cudaError_t launch_scalars_finalize(const double* part, int nbg, int nbr, long long ng, long long nr, int amode,
                                     double* ds, cudaStream_t s);
 int assign_tiles_per_axis(int N);
-cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, double* part, int* cnt, int* err,
+cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, double* part, int* bh, int* err,
                              int nblk, cudaStream_t s);
-cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, int* items, cudaStream_t s);
+cudaError_t launch_tile_prefix(int* bh, int nrows, int ntiles, int* cnt, cudaStream_t s);
+cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* items, cudaStream_t s);
 cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
-                               int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s,
-                               int raw = 0);
+                               const int* off, const int* bpref, float4* xyzv, float* vw2, double* labpart, int nblk,
+                               cudaStream_t s, int raw = 0);
 cudaError_t launch_combine_randoms(unsigned long long* grid, const unsigned long long* rgrid,
                                    unsigned long long* gridw, const unsigned long long* rgridw, const double* ds,
                                    long long n, int nsm, cudaStream_t s);

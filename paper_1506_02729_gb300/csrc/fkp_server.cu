@@ -74,6 +74,9 @@ size_t estimate_plan(const fkp_request_t& r) {
   const size_t half = field_elems(N) * sizeof(float2);
   size_t b = N3 * 8 * (B ? 2 : 1) + half * (nf + ng);
   b += sizeof(double) * (BQ_N + 1) * (size_t)r.pbins.nbins * tiles_x(N) * N;
+  // per-block tile counts of the gridding: two rows per SM (256 bounds the SM count)
+  const size_t nt = (size_t)assign_tiles_per_axis(N);
+  b += nt * nt * nt * sizeof(int) * 2 * 256;
   if (B) {
     const int S = r.bshells.nshells;
     const int nl = (r.want & FKP_B4) ? 3 : ((r.want & FKP_B2) ? 2 : 1);

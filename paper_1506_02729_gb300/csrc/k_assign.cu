@@ -31,7 +31,7 @@ constexpr int kTile = 16;            // cells per tile side
 // Objects per work item of the tile accumulation: a tile's objects are split
 // into items of at most this many, so that the few tiles of the densest
 // parts of a survey do not hold up the end of the launch.
-constexpr int kAccumChunk = 2048;
+constexpr int kAccumChunk = 8192;
 constexpr int kAccumThreads = 512;
 // Region a tile's objects reach, from one cell below the tile: the tile
 // plus one halo cell on each side for CIC and TSC, and one more above for
@@ -79,13 +79,14 @@ __device__ __forceinline__ int tile_of(int cx, int cy, int cz, int N, int ntx) {
 
 // ---------------------------------------------------------------------------
 
-// Counts go to a shared-memory histogram over all tiles and are added to the
-// global counts once per block and tile.
+// Each block owns a contiguous chunk of objects (the same chunks as the
+// scatter launch on the same catalog): its counts go to a shared-memory
+// histogram over all tiles, written out whole as the block's row of bh.
 constexpr int kBinThreads = 1024;
 
 template <int P>
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran, GeomDev g, int ntx, int ntiles,
-                                                           double* __restrict__ part, int* __restrict__ cnt,
+                                                           double* __restrict__ part, int* __restrict__ bh,
                                                            int* __restrict__ err) {
   extern __shared__ int hist[];
   __shared__ double sh[32];
@@ -93,8 +94,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
   __syncthreads();
   FFSum s_w, s_w2, s_w3, s_nw2, s_n2w3;
   bool bad = false;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long chunk = (c.n + gridDim.x - 1) / gridDim.x;
+  const long long i0 = blockIdx.x * chunk;
+  const long long i1 = i0 + chunk < c.n ? i0 + chunk : c.n;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const FF w = fkp_weight_ff(c, i, g.P_fkp, g.P_fkp_lo);
     const FF w2 = ff_mul(w, w);
     const FF w3 = ff_mul(w2, w);
@@ -114,8 +117,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
       bad = true;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, 1);
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-    if (hist[t]) atomicAdd(cnt + t, hist[t]);
+  int* row = bh + (size_t)blockIdx.x * ntiles;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = hist[t];
   double* out = part + (size_t)blockIdx.x * SC_NSUM;
   double v;
   if (!is_ran) {
@@ -131,55 +134,100 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
   }
 }
 
-// Exclusive scan of the tile counts into offsets (off[ntiles] = total) and
-// the scatter cursors (cur = off), and of the tiles' work items (one per
+// Per tile t, over the rows of bh (one per block of the count launches,
+// galaxies' blocks first): each row's entry becomes the exclusive prefix of
+// the rows above it, and cnt[t] the tile's total.  Rows are read in batches
+// of 16 independent loads.
+__global__ void __launch_bounds__(256) k_tile_prefix(int* __restrict__ bh, int nrows, int ntiles,
+                                                     int* __restrict__ cnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  int run = 0;
+  for (int r0 = 0; r0 < nrows; r0 += 16) {
+    int v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = r0 + q < nrows ? bh[(size_t)(r0 + q) * ntiles + t] : 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (r0 + q < nrows) bh[(size_t)(r0 + q) * ntiles + t] = run;
+      run += v[q];
+    }
+  }
+  cnt[t] = run;
+}
+
+// Exclusive scan of the tile counts into offsets (off[ntiles] = total), and
+// of the tiles' work items (one per
 // kAccumChunk objects or part of it) into item offsets (items[ntiles] = the
-// number of items).  One block of 1024 threads.
+// number of items).  One block of 1024 threads walks the tiles in rounds of
+// 1024 (coalesced loads, the next round's counts loaded during this round's
+// warp-shuffle scan).
 __global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ cnt, int ntiles, int* __restrict__ off,
-                                                     int* __restrict__ cur, int* __restrict__ items) {
-  __shared__ int part[1024], parti[1024];
-  const int per = (ntiles + blockDim.x - 1) / blockDim.x;
-  const int a = threadIdx.x * per, b = min(ntiles, a + per);
-  int s = 0, si = 0;
-  for (int i = a; i < b; ++i) {
-    s += cnt[i];
-    si += (cnt[i] + kAccumChunk - 1) / kAccumChunk;
-  }
-  part[threadIdx.x] = s;
-  parti[threadIdx.x] = si;
-  __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-    const int vi = threadIdx.x >= (unsigned)o ? parti[threadIdx.x - o] : 0;
+                                                     int* __restrict__ items) {
+  __shared__ int wsum[32], wsumi[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int carry = 0, carryi = 0;  // totals of the earlier rounds (the same in every thread)
+  int c = (int)threadIdx.x < ntiles ? cnt[threadIdx.x] : 0;
+  for (int base = 0; base < ntiles; base += 1024) {
+    const int i = base + (int)threadIdx.x;
+    const int cn = i + 1024 < ntiles ? cnt[i + 1024] : 0;
+    const int ci = (c + kAccumChunk - 1) / kAccumChunk;
+    int s = c, si = ci;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, s, o), vi = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) {
+        s += v;
+        si += vi;
+      }
+    }
+    if (lane == 31) {
+      wsum[warp] = s;
+      wsumi[warp] = si;
+    }
     __syncthreads();
-    part[threadIdx.x] += v;
-    parti[threadIdx.x] += vi;
+    if (warp == 0) {
+      int w = wsum[lane], wi = wsumi[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, w, o), vi = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) {
+          w += v;
+          wi += vi;
+        }
+      }
+      wsum[lane] = w;
+      wsumi[lane] = wi;
+    }
     __syncthreads();
+    if (i < ntiles) {
+      const int e = carry + (warp ? wsum[warp - 1] : 0) + s - c;
+      off[i] = e;
+      items[i] = carryi + (warp ? wsumi[warp - 1] : 0) + si - ci;
+    }
+    carry += wsum[31];
+    carryi += wsumi[31];
+    __syncthreads();
+    c = cn;
   }
-  int run = part[threadIdx.x] - s, runi = parti[threadIdx.x] - si;
-  for (int i = a; i < b; ++i) {
-    off[i] = run;
-    cur[i] = run;
-    items[i] = runi;
-    run += cnt[i];
-    runi += (cnt[i] + kAccumChunk - 1) / kAccumChunk;
-  }
-  if (threadIdx.x == blockDim.x - 1) {
-    off[ntiles] = part[threadIdx.x];
-    items[ntiles] = parti[threadIdx.x];
+  if (threadIdx.x == 0) {
+    off[ntiles] = carry;
+    items[ntiles] = carryi;
   }
 }
 
-// Each block owns a contiguous chunk of objects.  Pass 1 counts the chunk's
-// objects per tile in shared memory; one global atomic per touched tile then
-// reserves the chunk's range inside the tile's segment; pass 2 re-reads the
-// chunk and writes each object at its reserved slot.
+// Each block owns the contiguous chunk of objects its count block counted:
+// its range inside tile t's segment starts at off[t] plus the counts of the
+// blocks before it (its row of the prefixed bh), so one pass over the chunk
+// writes each object at the next slot of its tile's range.
 // raw = 1 (randoms only): values w and w^2 without alpha, for the cached
 // random grids that later mocks combine with their own alpha.
 template <int P>
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ran, int raw, GeomDev g, int ntx,
                                                              int ntiles, float obx, float oby, float obz,
-                                                             const double* __restrict__ ds, int* __restrict__ cur,
+                                                             const double* __restrict__ ds,
+                                                             const int* __restrict__ off,
+                                                             const int* __restrict__ bpref,
                                                              float4* __restrict__ xyzv, float* __restrict__ vw2,
                                                              double* __restrict__ labpart) {
   extern __shared__ int hist[];
@@ -193,16 +241,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ra
   const long long chunk = (c.n + gridDim.x - 1) / gridDim.x;
   const long long i0 = blockIdx.x * chunk;
   const long long i1 = i0 + chunk < c.n ? i0 + chunk : c.n;
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
-  __syncthreads();
-  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    int cx, cy, cz;
-    if (centre_cell<P>(g, __ldg(c.x + i), __ldg(c.y + i), __ldg(c.z + i), cx, cy, cz))
-      atomicAdd(hist + tile_of(cx, cy, cz, g.N, ntx), 1);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-    if (hist[t]) hist[t] = atomicAdd(cur + t, hist[t]);
+  const int* brow = bpref + (size_t)blockIdx.x * ntiles;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = off[t] + brow[t];
   __syncthreads();
   KahanF lab[LAB_NSUM];
   for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
@@ -281,14 +321,14 @@ __device__ __forceinline__ void tap_weights(float u, int& i0, float* wt) {
 //
 // Each tap adds x = round(v 2^40) to its cell.  Shared-memory adds of 64 bits
 // are several times slower than adds of 32 bits, so a cell is held as two
-// 32-bit words: L sums the low 20 bits of each x (at most kAccumChunk terms
-// below 2^20, so L cannot wrap) and H the rest, x >> 20 (arithmetic shift).
-// H stays exact while the item's sum of |v| (an upper bound for any cell's
-// sum of |v|, every tap weight being at most 1) is below 2^10: then
-// |sum of x >> 20| < 2^30 + kAccumChunk.  Items above that bound add x as one
-// 64-bit word instead.  Both forms give the exact integer sum of the x, so
-// the grid does not depend on how the objects are split into items or in
-// which order they are added.
+// 32-bit words: L sums the low 19 bits of each x (at most kAccumChunk = 2^13
+// terms below 2^19, so L cannot wrap) and H the rest, x >> 19 (arithmetic
+// shift).  H stays exact while the item's sum S of |v| (an upper bound for any
+// cell's sum of |v|, every tap weight being at most 1) is below 2^10 - 1:
+// then |sum of x >> 19| <= 2^21 S + 2^13 < 2^31.  Items above that bound add
+// x as one 64-bit word instead.  Both forms give the exact integer sum of the
+// x, so the grid does not depend on how the objects are split into items or
+// in which order they are added.
 template <int P, bool W2>
 __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDev g, int ntx, int ntiles,
                                                                         const int* __restrict__ off,
@@ -298,7 +338,7 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
                                                                         unsigned long long* __restrict__ grid,
                                                                         unsigned long long* __restrict__ gridw) {
   constexpr int kReg = reg_side<P>(), kReg3 = reg_cells<P>();
-  static_assert(kAccumChunk <= 4096, "the low words would wrap");
+  static_assert(kAccumChunk <= 8192, "the low words would wrap");
   extern __shared__ unsigned long long reg[];
   __shared__ int s_tile;
   __shared__ float s_abs;
@@ -368,11 +408,11 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
           const long long x = __float2ll_rn(o.w * tw * kFixScaleF);
           const long long xw = W2 ? __float2ll_rn(wv * tw * kFixScaleF) : 0ll;
           if (split) {
-            atomicAdd(L + base + r, (unsigned)x & 0xFFFFFu);
-            atomicAdd(H + base + r, (unsigned)(x >> 20));
+            atomicAdd(L + base + r, (unsigned)x & 0x7FFFFu);
+            atomicAdd(H + base + r, (unsigned)(x >> 19));
             if (W2) {
-              atomicAdd(Lw + base + r, (unsigned)xw & 0xFFFFFu);
-              atomicAdd(Hw + base + r, (unsigned)(xw >> 20));
+              atomicAdd(Lw + base + r, (unsigned)xw & 0x7FFFFu);
+              atomicAdd(Hw + base + r, (unsigned)(xw >> 19));
             }
           } else {
             atomicAdd(reg + base + r, (unsigned long long)x);
@@ -386,8 +426,8 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
   for (int i = threadIdx.x; i < kReg3; i += blockDim.x) {
     unsigned long long v, vw = 0ull;
     if (split) {
-      v = (unsigned long long)((long long)(int)H[i] * 1048576ll + (long long)L[i]);
-      if (W2) vw = (unsigned long long)((long long)(int)Hw[i] * 1048576ll + (long long)Lw[i]);
+      v = (unsigned long long)((long long)(int)H[i] * 524288ll + (long long)L[i]);
+      if (W2) vw = (unsigned long long)((long long)(int)Hw[i] * 524288ll + (long long)Lw[i]);
     } else {
       v = reg[i];
       if (W2) vw = regw[i];
@@ -431,36 +471,44 @@ cudaError_t launch_combine_randoms(unsigned long long* grid, const unsigned long
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, double* part, int* cnt, int* err,
+// bh: the nblk rows (ntiles ints each) this launch fills.
+cudaError_t launch_bin_count(const CatDev& c, int is_ran, const GeomDev& g, double* part, int* bh, int* err,
                              int nblk, cudaStream_t s) {
-  if (c.n == 0) {
-    cudaMemsetAsync(part, 0, sizeof(double) * SC_NSUM * nblk, s);
-    return cudaGetLastError();
-  }
   const int ntx = assign_tiles_per_axis(g.N);
   const int ntiles = ntx * ntx * ntx;
+  if (c.n == 0) {
+    cudaMemsetAsync(part, 0, sizeof(double) * SC_NSUM * nblk, s);
+    cudaMemsetAsync(bh, 0, sizeof(int) * (size_t)ntiles * nblk, s);
+    return cudaGetLastError();
+  }
   const size_t sm = sizeof(int) * ntiles;
   if (g.assign == 2) {
     raise_smem_limit((const void*)k_bin_count<2>, sm);
-    k_bin_count<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
+    k_bin_count<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, bh, err);
   } else if (g.assign == 3) {
     raise_smem_limit((const void*)k_bin_count<3>, sm);
-    k_bin_count<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
+    k_bin_count<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, bh, err);
   } else {
     raise_smem_limit((const void*)k_bin_count<4>, sm);
-    k_bin_count<4><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, cnt, err);
+    k_bin_count<4><<<nblk, kBinThreads, sm, s>>>(c, is_ran, g, ntx, ntiles, part, bh, err);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* cur, int* items, cudaStream_t s) {
-  k_scan_tiles<<<1, 1024, 0, s>>>(cnt, ntiles, off, cur, items);
+cudaError_t launch_tile_prefix(int* bh, int nrows, int ntiles, int* cnt, cudaStream_t s) {
+  k_tile_prefix<<<(ntiles + 255) / 256, 256, 0, s>>>(bh, nrows, ntiles, cnt);
   return cudaGetLastError();
 }
 
+cudaError_t launch_scan_tiles(const int* cnt, int ntiles, int* off, int* items, cudaStream_t s) {
+  k_scan_tiles<<<1, 1024, 0, s>>>(cnt, ntiles, off, items);
+  return cudaGetLastError();
+}
+
+// off: the tile offsets; bpref: the nblk prefixed count rows of this catalog.
 cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, const double obs[3], const double* ds,
-                               int* cur, float4* xyzv, float* vw2, double* labpart, int nblk, cudaStream_t s,
-                               int raw) {
+                               const int* off, const int* bpref, float4* xyzv, float* vw2, double* labpart, int nblk,
+                               cudaStream_t s, int raw) {
   if (c.n == 0) {
     if (is_ran) cudaMemsetAsync(labpart, 0, sizeof(double) * LAB_NSUM * nblk, s);
     return cudaGetLastError();
@@ -471,15 +519,15 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
   if (g.assign == 2) {
     raise_smem_limit((const void*)k_bin_scatter<2>, sm);
     k_bin_scatter<2><<<nblk, kBinThreads, sm, s>>>(c, is_ran, raw, g, ntx, ntiles, (float)obs[0], (float)obs[1],
-                                                   (float)obs[2], ds, cur, xyzv, vw2, labpart);
+                                                   (float)obs[2], ds, off, bpref, xyzv, vw2, labpart);
   } else if (g.assign == 3) {
     raise_smem_limit((const void*)k_bin_scatter<3>, sm);
     k_bin_scatter<3><<<nblk, kBinThreads, sm, s>>>(c, is_ran, raw, g, ntx, ntiles, (float)obs[0], (float)obs[1],
-                                                   (float)obs[2], ds, cur, xyzv, vw2, labpart);
+                                                   (float)obs[2], ds, off, bpref, xyzv, vw2, labpart);
   } else {
     raise_smem_limit((const void*)k_bin_scatter<4>, sm);
     k_bin_scatter<4><<<nblk, kBinThreads, sm, s>>>(c, is_ran, raw, g, ntx, ntiles, (float)obs[0], (float)obs[1],
-                                                   (float)obs[2], ds, cur, xyzv, vw2, labpart);
+                                                   (float)obs[2], ds, off, bpref, xyzv, vw2, labpart);
   }
   return cudaGetLastError();
 }

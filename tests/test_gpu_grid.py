@@ -82,18 +82,19 @@ def test_grid_matches_oracle_assignment(assign, interlace):
 def test_grid_does_not_depend_on_object_order_or_accumulation_form():
     """The gridding adds each tap's rounded value as an integer: as two 32-bit
     words, or as one 64-bit word for a work item whose sum of |w| passes 1000.
-    Galaxy weights k/1024 (k uniform in 0..1003) and randoms of weight 1
-    (alpha near 0.49) put the tiles' work items of 2048 objects on both sides
-    of that bound, and which objects share an item follows the objects'
-    order.  Both forms and every order give the same grid, bit for bit (the
-    weights keep W_g and W_r, hence alpha, exact whatever the order of their
-    sums); the oracle agrees within the rounding bound."""
+    Galaxy weights k/1024 (k uniform in 0..250, mean 0.122) and randoms of
+    weight 1 (alpha near 0.122) put the tiles' full work items of 8192
+    objects on both sides of that bound (29 of them here), and which objects
+    share an item follows the objects' order.  Both forms and every order
+    give the same grid, bit for bit (the weights keep W_g and W_r, hence
+    alpha, exact whatever the order of their sums); the oracle agrees within
+    the rounding bound."""
     # two random catalogs (200000 objects, thousands per tile), one as the
     # galaxies
     sv, _, gal, geom = _exact_setup(3, seed=11)
     _, _, ran, _ = _exact_setup(3, seed=12)
     r = np.random.default_rng(1506)
-    gal["w"] = (r.integers(0, 1004, len(gal["x"])) / 1024.0).astype(np.float32)
+    gal["w"] = (r.integers(0, 251, len(gal["x"])) / 1024.0).astype(np.float32)
     ran["w"] = np.ones(len(ran["x"]), dtype=np.float32)
     plan = _plan(geom)
     F1, Fw1 = plan.grid(_dev(gal), _dev(ran), with_w=True)
