@@ -31,7 +31,7 @@ constexpr int kTile = 16;            // cells per tile side
 // Objects per work item of the tile accumulation: a tile's objects are split
 // into items of at most this many, so that the few tiles of the densest
 // parts of a survey do not hold up the end of the launch.
-constexpr int kAccumChunk = 8192;
+constexpr int kAccumChunk = 8160;
 constexpr int kAccumThreads = 512;
 // Region a tile's objects reach, from one cell below the tile: the tile
 // plus one halo cell on each side for CIC and TSC, and one more above for
@@ -313,22 +313,40 @@ __device__ __forceinline__ void tap_weights(float u, int& i0, float* wt) {
   }
 }
 
+// x = round(v 2^40) as h 2^19 + l with FP32 arithmetic only (no conversion
+// instructions): for |v| < 2, adding M = 1.5 2^23 to v 2^21 (one FMA, one
+// rounding to nearest even) leaves h = round(v 2^21) in the low bits of the
+// sum; the remainder v 2^21 - h is exact and lies in [-1/2, 1/2], and a
+// second FMA leaves l = round((v 2^21 - h) 2^19) in [-2^18, 2^18] the same
+// way.  h 2^19 + l is round(v 2^40), rounded to nearest even, exactly.
+constexpr float kMagic = 12582912.0f;   // 1.5 2^23
+constexpr int kMagicBits = 0x4B400000;  // its bit pattern
+__device__ __forceinline__ void split_fixed(float v, int& h, int& l) {
+  const float a = fmaf(v, 2097152.0f, kMagic);  // v 2^21 + M
+  const float hf = a - kMagic;
+  const float rem = fmaf(v, 2097152.0f, -hf);
+  h = __float_as_int(a) - kMagicBits;
+  l = __float_as_int(fmaf(rem, 524288.0f, kMagic)) - kMagicBits;
+}
+
 // One block per work item: up to kAccumChunk objects of one tile (items in
 // tile order; items[t] is tile t's first).  The tile's region, from one cell
 // below the tile to the end of its reach (reg_side cells a side), covers the
 // taps of every object whose centre cell lies in the tile.  Blocks past the
 // last item return at once (the grid is sized from an upper bound).
 //
-// Each tap adds x = round(v 2^40) to its cell.  Shared-memory adds of 64 bits
-// are several times slower than adds of 32 bits, so a cell is held as two
-// 32-bit words: L sums the low 19 bits of each x (at most kAccumChunk = 2^13
-// terms below 2^19, so L cannot wrap) and H the rest, x >> 19 (arithmetic
-// shift).  H stays exact while the item's sum S of |v| (an upper bound for any
-// cell's sum of |v|, every tap weight being at most 1) is below 2^10 - 1:
-// then |sum of x >> 19| <= 2^21 S + 2^13 < 2^31.  Items above that bound add
-// x as one 64-bit word instead.  Both forms give the exact integer sum of the
-// x, so the grid does not depend on how the objects are split into items or
-// in which order they are added.
+// Each tap adds x = round(v 2^40) to its cell (v = w times the tap weight).
+// Shared-memory adds of 64 bits are several times slower than adds of 32
+// bits, and conversions to 64-bit integers run on a narrow pipe, so when the
+// item allows it a cell is held as two signed 32-bit words from split_fixed:
+// L sums the l (at most kAccumChunk < 2^13 terms of magnitude <= 2^18: |L| <
+// 2^31) and H the h.  H stays exact while the item's sum S of |w| (an upper
+// bound for any cell's sum of |v|, every tap weight being at most 1) is
+// below 2^10 - 1: then |H| <= 2^21 S + 2^12 < 2^31.  split_fixed needs |v| <
+// 2.  Items that fail either bound add x = round(v 2^40) as one 64-bit word
+// instead.  Both forms give the exact integer sum of the x, so the grid does
+// not depend on how the objects are split into items or in which order they
+// are added.
 template <int P, bool W2>
 __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDev g, int ntx, int ntiles,
                                                                         const int* __restrict__ off,
@@ -338,15 +356,16 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
                                                                         unsigned long long* __restrict__ grid,
                                                                         unsigned long long* __restrict__ gridw) {
   constexpr int kReg = reg_side<P>(), kReg3 = reg_cells<P>();
-  static_assert(kAccumChunk <= 8192, "the low words would wrap");
+  static_assert(kAccumChunk * 262144ll < 2147483648ll, "the low words would wrap");
   extern __shared__ unsigned long long reg[];
   __shared__ int s_tile;
   __shared__ float s_abs;
+  __shared__ int s_max;
   unsigned long long* regw = reg + kReg3;
-  unsigned* L = reinterpret_cast<unsigned*>(reg);
-  unsigned* H = L + kReg3;
-  unsigned* Lw = reinterpret_cast<unsigned*>(regw);
-  unsigned* Hw = Lw + kReg3;
+  int* L = reinterpret_cast<int*>(reg);
+  int* H = L + kReg3;
+  int* Lw = reinterpret_cast<int*>(regw);
+  int* Hw = Lw + kReg3;
   const int item = blockIdx.x;
   if (item >= items[ntiles]) return;
   if (threadIdx.x == 0) {
@@ -359,6 +378,7 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
     }
     s_tile = lo;
     s_abs = 0.f;
+    s_max = 0;
   }
   const int N = g.N;
   for (int i = threadIdx.x; i < kReg3; i += blockDim.x) {
@@ -371,17 +391,25 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
   const int b = min(off[t + 1], a + kAccumChunk);
   const int tx = t % ntx, ty = (t / ntx) % ntx, tz = t / (ntx * ntx);
   const int lx0 = tx * kTile - 1, ly0 = ty * kTile - 1, lz0 = tz * kTile - 1;
-  // the item's objects are read twice: for the bound, then for the taps (the
-  // second read mostly from L1)
-  float sa = 0.f;
-  for (int i = a + threadIdx.x; i < b; i += kAccumThreads)
-    sa += fmaxf(fabsf(xyzv[i].w), W2 ? fabsf(vw2[i]) : 0.f);
+  // the item's objects are read twice: for the bounds, then for the taps
+  float sa = 0.f, ma = 0.f;
+  for (int i = a + threadIdx.x; i < b; i += kAccumThreads) {
+    const float m = fmaxf(fabsf(xyzv[i].w), W2 ? fabsf(vw2[i]) : 0.f);
+    sa += m;
+    ma = fmaxf(ma, m);
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&s_abs, sa);
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_abs, sa);
+    atomicMax(&s_max, __float_as_int(ma));  // non-negative: ordered as integers (NaN above +inf)
+  }
   __syncthreads();
-  // the bound, with room for the rounding of the FP32 sums above
-  const bool split = s_abs < 1000.f;
+  // the bounds, with room for the rounding of the FP32 sums above
+  const bool split = s_abs < 1000.f && __int_as_float(s_max) < 2.f;
   for (int i = a + threadIdx.x; i < b; i += kAccumThreads) {
     const float4 o = xyzv[i];
     const float wv = W2 ? vw2[i] : 0.f;
@@ -396,27 +424,40 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
     const int rx = ix - (cx - wrapN(cx, N)) - lx0;
     const int ry = iy - (cy - wrapN(cy, N)) - ly0;
     const int rz = iz - (cz - wrapN(cz, N)) - lz0;
+    if (split) {
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
+      for (int p = 0; p < P; ++p) {
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const float wzy = wz[p] * wy[q];
-        const int base = ((rz + p) * kReg + (ry + q)) * kReg + rx;
+        for (int q = 0; q < P; ++q) {
+          const float wzy = wz[p] * wy[q];
+          const int base = ((rz + p) * kReg + (ry + q)) * kReg + rx;
 #pragma unroll
-        for (int r = 0; r < P; ++r) {
-          const float tw = wzy * wx[r];
-          const long long x = __float2ll_rn(o.w * tw * kFixScaleF);
-          const long long xw = W2 ? __float2ll_rn(wv * tw * kFixScaleF) : 0ll;
-          if (split) {
-            atomicAdd(L + base + r, (unsigned)x & 0x7FFFFu);
-            atomicAdd(H + base + r, (unsigned)(x >> 19));
+          for (int r = 0; r < P; ++r) {
+            const float tw = wzy * wx[r];
+            int h, l;
+            split_fixed(o.w * tw, h, l);
+            atomicAdd(L + base + r, l);
+            atomicAdd(H + base + r, h);
             if (W2) {
-              atomicAdd(Lw + base + r, (unsigned)xw & 0x7FFFFu);
-              atomicAdd(Hw + base + r, (unsigned)(xw >> 19));
+              split_fixed(wv * tw, h, l);
+              atomicAdd(Lw + base + r, l);
+              atomicAdd(Hw + base + r, h);
             }
-          } else {
-            atomicAdd(reg + base + r, (unsigned long long)x);
-            if (W2) atomicAdd(regw + base + r, (unsigned long long)xw);
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const float wzy = wz[p] * wy[q];
+          const int base = ((rz + p) * kReg + (ry + q)) * kReg + rx;
+#pragma unroll
+          for (int r = 0; r < P; ++r) {
+            const float tw = wzy * wx[r];
+            atomicAdd(reg + base + r, (unsigned long long)__float2ll_rn(o.w * tw * kFixScaleF));
+            if (W2) atomicAdd(regw + base + r, (unsigned long long)__float2ll_rn(wv * tw * kFixScaleF));
           }
         }
       }
@@ -426,8 +467,8 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
   for (int i = threadIdx.x; i < kReg3; i += blockDim.x) {
     unsigned long long v, vw = 0ull;
     if (split) {
-      v = (unsigned long long)((long long)(int)H[i] * 524288ll + (long long)L[i]);
-      if (W2) vw = (unsigned long long)((long long)(int)Hw[i] * 524288ll + (long long)Lw[i]);
+      v = (unsigned long long)((long long)H[i] * 524288ll + (long long)L[i]);
+      if (W2) vw = (unsigned long long)((long long)Hw[i] * 524288ll + (long long)Lw[i]);
     } else {
       v = reg[i];
       if (W2) vw = regw[i];
