@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(CatDev c, int is_ran,
   const long long chunk = (c.n + gridDim.x - 1) / gridDim.x;
   const long long i0 = blockIdx.x * chunk;
   const long long i1 = i0 + chunk < c.n ? i0 + chunk : c.n;
+  // unrolled: the loads of several objects in flight at once
+#pragma unroll 4
   for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const FF w = fkp_weight_ff(c, i, g.P_fkp, g.P_fkp_lo);
     const FF w2 = ff_mul(w, w);
@@ -245,6 +247,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(CatDev c, int is_ra
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = off[t] + brow[t];
   __syncthreads();
   KahanF lab[LAB_NSUM];
+  // unrolled: the loads of several objects in flight at once
+#pragma unroll 4
   for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const float w = fkp_weight(c, i, g.P_fkp);
     const float px = __ldg(c.x + i), py = __ldg(c.y + i), pz = __ldg(c.z + i);
