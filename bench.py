@@ -586,6 +586,36 @@ def run_bisp(args, gal, ran, dg, dr, stream):
     # 1e-4 bar like the FP32 contraction); the hi/lo split is the fast mode,
     # with a random per-product error of ~2^-18
     out["value"], out["mode"] = out["modes"]["bf16x6_tcgen05"]["value"], "bf16x6_tcgen05"
+    # rooflines (the survey's accounting for this workload): the contraction's
+    # useful tensor work, 2 x (triangles x 3 multipoles) x N^3 multiply-adds
+    # times the BF16 products per term (3 hi/lo, 6 for the 3-way split),
+    # against the sustained BF16 peak; the rest of the step's algorithmic bytes
+    # (catalog 20 B per object, the F and F^w grids written and read, the k_z
+    # groups of both pass sets written and read, the 3 S shell fields of both
+    # the fields' shell IFFTs written and read) against HBM
+    pk, src = peaks()
+    N = args.bisp_grid
+    N3 = float(N) ** 3
+    nout = 3 * int(plan.ntri)
+    roof = {}
+    for name, nprod in (("bf16x3_tcgen05", 3), ("bf16x6_tcgen05", 6)):
+        cms = out["modes"][name]["stage_ms"]["contraction"]
+        fl = 2.0 * nout * N3 * nprod
+        ach = fl / (cms * 1e-3) / 1e12
+        roof[name] = {"bound": "tensor", "kernel": "contraction", "useful_flop": fl, "achieved": ach,
+                      "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                      "frac": ach / pk["bf16_tflops_sustained"], "peak_source": src}
+    half = N * N * (N // 2 + 1) * 8.0
+    nmax = int(3 * args.bisp_nshells + 1.5)
+    nobj = int(len(gal["x"]) + len(ran["x"]))
+    bts = (20.0 * nobj + 2 * 2 * 4 * N3 + 2 * (2 * 9 * half)
+           + 2 * 3 * args.bisp_nshells * ((nmax + 1) * N * N * 8.0))
+    st = out["modes"]["bf16x6_tcgen05"]["stage_ms"]
+    oms = st["grids"] + st["F_passes"] + st["Fw_passes_and_shell_ifft"]
+    roof["grids_passes_shell_ifft"] = {"bound": "hbm", "algorithmic_bytes": bts, "ms": oms,
+                                       "achieved": bts / (oms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                       "frac": bts / (oms * 1e-3) / 1e9 / pk["hbm_gbs"], "peak_source": src}
+    out["roofline"] = roof
     out["accuracy"] = {"fp32": "within 1e-4 of the FP64 oracle", "bf16x6_tcgen05": "within 1e-4 of the FP64 oracle",
                        "bf16x3_tcgen05": "random per-product error ~2^-18 (triangle sums within 6 x 2^-17 "
                                          "sqrt(sum_x t^2) of the 3-way split)"}
