@@ -20,8 +20,6 @@
 #include <cstring>
 #include <map>
 #include <mutex>
-#include <set>
-#include <utility>
 #include <vector>
 
 #include "fkp_internal.h"
@@ -68,13 +66,9 @@ struct BispState {
   int* d_spartc = nullptr;
   double* d_shell = nullptr;
   long long* d_shellc = nullptr;
-  // tensor-core contraction: tiles of 128 pairs (b, c) on the M side, each
-  // with the fields (l, a) its triangles need on the N side; outputs ->
-  // (tile * 128 + row, column)
+  // tensor-core contraction: columns = pairs (b >= c), outputs -> (row, column)
   int npairs = 0, tc_slices = 0, tc_tiles = 0, tc_chunks = 0;
-  short2* d_pairs = nullptr;  // [tile][128] field indices of the two factors, -1 padding
-  short* d_tcols = nullptr;   // [tile][256] field indices of the columns, -1 padding
-  int* d_tncol = nullptr;     // [tile] column count rounded up to 32
+  short2* d_pairs = nullptr;
   int *d_om = nullptr, *d_on = nullptr;
   float* d_tcpart = nullptr;
   // shell IFFT work lists: z tiles (s, n_y + mm, n_x0), y tiles (s, n_x0, |n_y| range); floor(r_s)
@@ -581,76 +575,35 @@ int bisp_plan_init(Plan* P) {
         }
       }
   }
-  // tensor-core tiles.  Each pair (field of the first factor, field of the
-  // second) needs the columns (field indices) of the outputs that use it.
-  // Pairs in order of their first field, then the second, fill tiles of up to
-  // 128 rows while the union of their columns, rounded up to 32, stays
-  // within 256.
-  std::map<std::pair<int, int>, std::vector<int>> need;
-  auto add_need = [&](int fb, int fc, int col) { need[{fb, fc}].push_back(col); };
-  for (int t = 0; t < ntri; ++t) {
-    for (int li = 0; li < st->nl; ++li) add_need(st->tb[t], st->tc[t], li * S + st->ta[t]);
-    if (st->zero_area) add_need(S + st->tb[t], st->tc[t], S + st->ta[t]);
-  }
-  std::vector<short2> tpairs;
-  std::vector<short> tcols;
-  std::vector<int> tncol;
-  std::map<std::pair<int, int>, std::pair<int, int>> where;  // pair -> (tile, row)
-  std::vector<std::map<int, int>> colpos;                     // per tile: field -> column
-  {
-    std::vector<std::pair<int, int>> cur;
-    std::set<int> cs;
-    bool fits = true;
-    auto flush = [&]() {
-      if (cur.empty()) return;
-      const int tile = (int)tncol.size();
-      colpos.emplace_back();
-      int j = 0;
-      for (int f : cs) colpos.back()[f] = j++;
-      for (int r = 0; r < tc_rows(); ++r) {
-        if (r < (int)cur.size()) {
-          tpairs.push_back(make_short2((short)cur[r].first, (short)cur[r].second));
-          where[cur[r]] = {tile, r};
-        } else {
-          tpairs.push_back(make_short2(-1, -1));
-        }
-      }
-      std::vector<short> cols(tc_tile_cols(), (short)-1);
-      for (const auto& kv : colpos.back()) cols[kv.second] = (short)kv.first;
-      tcols.insert(tcols.end(), cols.begin(), cols.end());
-      tncol.push_back(((int)cs.size() + 31) / 32 * 32);
-      cur.clear();
-      cs.clear();
-    };
-    for (const auto& kv : need) {
-      std::set<int> u = cs;
-      u.insert(kv.second.begin(), kv.second.end());
-      if ((int)cur.size() == tc_rows() || ((int)u.size() + 31) / 32 * 32 > tc_tile_cols()) {
-        flush();
-        u = std::set<int>(kv.second.begin(), kv.second.end());
-        if (((int)u.size() + 31) / 32 * 32 > tc_tile_cols()) fits = false;
-      }
-      cur.push_back(kv.first);
-      cs = u;
-    }
-    flush();
-    if (!fits) tncol.clear();
-  }
-  st->npairs = (int)need.size();
-  std::vector<int> om(std::max(1, ntri) * nq, -1), on(std::max(1, ntri) * nq, 0);
-  auto place = [&](int o, int fb, int fc, int col) {
-    const auto w = where.find({fb, fc});
-    if (w == where.end()) return;
-    om[o] = w->second.first * tc_rows() + w->second.second;
-    on[o] = colpos[w->second.first][col];
+  // pair columns of the tensor-core contraction (field indices of the two
+  // factors) and each output's (row, column)
+  std::map<long long, int> pidx;
+  std::vector<short2> pairs;
+  auto column = [&](int fb, int fc) {
+    const long long key = (long long)fb * 4 * S + fc;
+    auto f = pidx.find(key);
+    if (f != pidx.end()) return f->second;
+    pidx[key] = (int)pairs.size();
+    pairs.push_back(make_short2((short)fb, (short)fc));
+    return (int)pairs.size() - 1;
   };
-  if (!tncol.empty())
-    for (int t = 0; t < ntri; ++t) {
-      for (int li = 0; li < st->nl; ++li) place(t * nq + li, st->tb[t], st->tc[t], li * S + st->ta[t]);
-      if (st->zero_area) place(t * nq + 3, S + st->tb[t], st->tc[t], S + st->ta[t]);
+  for (int t = 0; t < ntri; ++t) column(st->tb[t], st->tc[t]);
+  if (st->zero_area)
+    for (int t = 0; t < ntri; ++t) column(S + st->tb[t], st->tc[t]);
+  st->npairs = (int)pairs.size();
+  std::vector<int> om(std::max(1, ntri) * nq, -1), on(std::max(1, ntri) * nq, 0);
+  for (int t = 0; t < ntri; ++t) {
+    for (int li = 0; li < st->nl; ++li) {
+      om[t * nq + li] = li * S + st->ta[t];
+      on[t * nq + li] = column(st->tb[t], st->tc[t]);
     }
+    if (st->zero_area) {
+      om[t * nq + 3] = S + st->ta[t];
+      on[t * nq + 3] = column(S + st->tb[t], st->tc[t]);
+    }
+  }
   const long long N3 = (long long)N * N * N;
-  st->tc_tiles = (int)tncol.size();
+  st->tc_tiles = (st->npairs + tc_tile_cols() - 1) / tc_tile_cols();
   tc_slicing(N3, std::max(1, st->tc_tiles), P->ctx->nsm, &st->tc_slices, &st->tc_chunks);
   const int iblocks = std::max<int>(1, ((int)st->items.size() + 255) / 256);
   st->nslices = std::max(1, (P->ctx->nsm * 8) / iblocks);
@@ -705,12 +658,9 @@ int bisp_plan_init(Plan* P) {
   st->d_spartc = (int*)A(sizeof(int) * S * (size_t)P->nblk_z);
   st->d_shell = (double*)A(sizeof(double) * BQ_N * S);
   st->d_shellc = (long long*)A(sizeof(long long) * S);
-  // the ring of every field's chunk values must fit beside the operand stages
-  const bool tc_ok = st->nl * S <= tc_rows() && st->tc_tiles > 0;
+  const bool tc_ok = st->nl * S <= tc_rows();
   if (tc_ok && st->npairs > 0) {
-    st->d_pairs = (short2*)A(sizeof(short2) * tpairs.size());
-    st->d_tcols = (short*)A(sizeof(short) * tcols.size());
-    st->d_tncol = (int*)A(sizeof(int) * tncol.size());
+    st->d_pairs = (short2*)A(sizeof(short2) * st->npairs);
     st->d_om = (int*)A(sizeof(int) * om.size());
     st->d_on = (int*)A(sizeof(int) * on.size());
     st->d_tcpart = (float*)A(sizeof(float) * (size_t)st->tc_slices * st->tc_tiles * tc_rows() * tc_tile_cols());
@@ -727,9 +677,7 @@ int bisp_plan_init(Plan* P) {
     BCK(cudaMemcpy(st->d_items, st->items.data(), sizeof(ContractItem) * st->items.size(), cudaMemcpyHostToDevice));
   BCK(cudaMemset(st->d_cpart, 0, sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * st->nq));
   if (st->d_pairs) {
-    BCK(cudaMemcpy(st->d_pairs, tpairs.data(), sizeof(short2) * tpairs.size(), cudaMemcpyHostToDevice));
-    BCK(cudaMemcpy(st->d_tcols, tcols.data(), sizeof(short) * tcols.size(), cudaMemcpyHostToDevice));
-    BCK(cudaMemcpy(st->d_tncol, tncol.data(), sizeof(int) * tncol.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(st->d_pairs, pairs.data(), sizeof(short2) * pairs.size(), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(st->d_om, om.data(), sizeof(int) * om.size(), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(st->d_on, on.data(), sizeof(int) * on.size(), cudaMemcpyHostToDevice));
   }
@@ -808,9 +756,8 @@ static int enqueue_bisp(Plan* P, const CatDev& g, const CatDev& r, int contracti
   // contraction
   const int ntri = P->ntri, nout = std::max(1, ntri) * st->nq;
   if (tensor && st->npairs > 0) {
-    BCK(launch_contract_tc(st->d_I, N3, st->nl * S, st->d_pairs, st->d_tcols, st->d_tncol, st->tc_tiles,
-                           st->d_tcpart, P->d_err + 1, st->tc_slices, st->tc_chunks,
-                           contraction == FKP_CONTRACT_BF16X3 ? 2 : 3, s));
+    BCK(launch_contract_tc(st->d_I, N3, st->nl * S, S, st->d_pairs, st->npairs, st->d_tcpart, P->d_err + 1,
+                           st->tc_slices, st->tc_chunks, contraction == FKP_CONTRACT_BF16X3 ? 2 : 3, s));
     BCK(launch_tc_reduce(st->d_tcpart, st->tc_slices, st->tc_tiles, st->d_om, st->d_on, nout, st->d_T, s));
   } else if (!st->items.empty()) {
     const int nf = st->nl * S;
@@ -867,7 +814,7 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   auto* st = static_cast<BispState*>(P->bisp);
   const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6;
   if (tensor && !st->d_pairs && st->npairs > 0)
-    return set_error(FKP_EINVAL, "the tensor-core contraction needs (multipoles x shells) <= %d fields", tc_rows());
+    return set_error(FKP_EINVAL, "the tensor-core contraction needs (multipoles x shells) <= %d rows", tc_rows());
   BCK(cudaSetDevice(P->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CatDev g, r;

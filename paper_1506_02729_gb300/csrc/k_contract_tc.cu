@@ -3,14 +3,8 @@
 //
 //   T^(l)(a,b,c) = sum_x F_a^(l)(x) F_b^(0)(x) F_c^(0)(x)
 //
-// is the skinny GEMM D[(b,c), (l,a)] = sum_x A[(b,c), x] B[(l,a), x] with
-// A = the Khatri-Rao products F_b^(0) F_c^(0) and B = the shell fields.  The
-// pairs (b, c) are cut into tiles of 128 (the MMA's M) in order of b, and a
-// tile's N side holds only the fields (l, a) that close a triangle with one
-// of its pairs (a from b to about b + c): since a >= b, tiles of large b need
-// few columns, and the launched MMA work is about 2.5 times the triangles'
-// instead of 6 times.  (The zero-area hexadecapole's sums F_a^(2) F_b^(2)
-// F_c^(0) are more pairs (field of F_b^(2), c) with columns F_a^(2).)  Each
+// is the skinny GEMM D[(l,a), (b,c)] = sum_x A[(l,a), x] B[(b,c), x] with
+// A = the shell fields and B = the Khatri-Rao products F_b^(0) F_c^(0).  Each
 // FP32 operand v is split into BF16 v_hi = bf16(v), v_lo = bf16(v - v_hi); the
 // three products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor
 // memory (the lo*lo term and the rounding of lo, each ~2^-18 relative, are
@@ -21,18 +15,17 @@
 // the triangle sums cancel strongly (sum |t| >> |sum t|), so the 3-way split
 // is the accurate mode and the 2-way split the fast one.
 //
-// One CTA of 16 warps per (tile, K slice).  The slices (up to about 4,096
-// chunks of 32 points) are sized at plan time so that tiles x slices CTAs
-// fill whole waves of the SMs.
+// One CTA of 16 warps per (256-column N tile, K slice).  The slices (up to
+// about 4,096 chunks of 32 points) are sized at plan time so that tiles x
+// slices CTAs fill whole waves of the SMs.
 // The shell fields of a chunk of 32 points are fetched two chunks ahead with
 // cp.async into a 3-slot ring; operand stages are double buffered: all
 // threads form the products and the BF16 splits into K-major tiles with the
 // 64-byte swizzle (one 64-byte row of K per operand row); one thread issues
-// the tcgen05.mma instructions (M = 128, N = the tile's column count, K = 16)
-// and commits them to the stage's mbarrier.  After every run of 96
-// accumulating MMAs (16 chunks, 8 for the 3-way split) the FP32 tile is read
-// from tensor memory (tcgen05.ld; each warp its lane quarter and up to two
-// groups of 32 columns), added with
+// the tcgen05.mma instructions (M = 128, N = 256, K = 16) and commits them to
+// the stage's mbarrier.  After every run of 96 accumulating MMAs (16 chunks,
+// 8 for the 3-way split) the 128 x 256 FP32 tile is read from tensor memory
+// (tcgen05.ld; each warp its lane quarter and 64 columns), added with
 // round-to-nearest to a running FP32 sum held in the other 256 tensor-memory
 // columns (tcgen05.ld, add, tcgen05.st) and the MMA accumulation restarts.
 // In-tensor-core accumulation runs were measured to drift linearly with their
@@ -53,8 +46,8 @@
 
 namespace fkp {
 
-constexpr int kTcM = 128;              // MMA rows (pairs (b, c)) per tile
-constexpr int kTcN = 256;              // MMA columns (fields (l, a)) per tile, at most
+constexpr int kTcM = 128;              // MMA rows (l, a)
+constexpr int kTcN = 256;              // MMA columns (pairs b >= c) per tile
 constexpr int kTcKC = 32;              // K points per chunk
 constexpr int kTcSliceTarget = 4096;   // chunks per K slice, at most (about)
 constexpr int kTcThreads = 512;
@@ -200,9 +193,9 @@ __device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t 
 }
 
 // Instruction descriptor for kind::f16: D FP32, A and B BF16, both K-major,
-// M = 128, N = n (a multiple of 16 up to 256).
-__host__ __device__ constexpr uint32_t tc_idesc(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+// N = 256, M = 128.
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
 
 // Byte offset of the 16-byte segment (row, k-group kg) of an operand tile in
@@ -239,27 +232,22 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
 
 // ---------------------------------------------------------------------------
 
-// One CTA per (tile, K slice).  A tile holds up to 128 pairs (b, c) on the M
-// side (tpairs: the two field indices of each row's Khatri-Rao product, -1
-// for padding rows) and the fields its triangles need on the N side (tcols:
-// up to 256 field indices, -1 for padding; tncol: their count rounded up to
-// 32).  Part layout [slice][tile][128][256] FP32, columns beyond the tile's
-// count unused.
+// pairs: (b, c) of the tile's columns (b < 0 marks padding); part layout
+// [slice][tile][128][256] FP32.
 //
 // Every thread has a fixed share of each chunk: A row t % 128, k-group t / 128
 // (8 points); B row t % 256, k-groups 2 (t / 256) and 2 (t / 256) + 1 (16
 // points); its field copies are f = i / 8, points 4 (i % 8) of i = t, t + 512.
-// Offsets and field indices are therefore computed once.  Padding rows of A
-// and of B are zeroed once in both stages and never rewritten.  The running
-// FP32 sum of the drained tiles sits in tensor memory columns 256-511 (each
-// drain: tcgen05.ld tile and sum, add, tcgen05.st), so no accumulator
-// occupies registers through the chunk loop.
+// Offsets and pair indices are therefore computed once.  Rows of A beyond nf
+// and padding columns of B are zeroed once in both stages and never
+// rewritten.  The running FP32 sum of the drained tiles sits in tensor memory
+// columns 256-511 (each drain: tcgen05.ld tile and sum, add, tcgen05.st), so
+// no accumulator occupies registers through the chunk loop.
 template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
-                                                               const short2* __restrict__ tpairs,
-                                                               const short* __restrict__ tcols,
-                                                               const int* __restrict__ tncol, int chunks,
-                                                               float* __restrict__ part, int* __restrict__ err) {
+                                                               int S, const short2* __restrict__ pairs, int npairs,
+                                                               int chunks, float* __restrict__ part,
+                                                               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   constexpr int kStage = tc_stage_bytes<NS>();
   unsigned char* stage0 = smraw;                                  // 2 stages: A parts, then B parts
@@ -269,7 +257,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int tile = blockIdx.x, slice = blockIdx.y, ntiles = gridDim.x;
-  const int ncol = tncol[tile];  // a multiple of 32, at most kTcN
   // zero both stages once: rows that are never written stay zero
   for (int i = tid; i < 2 * kStage / 16; i += kTcThreads) reinterpret_cast<uint4*>(stage0)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) {
@@ -285,33 +272,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *tslot;
-  // this thread's share of the tile: TMEM lane quarter (warp % 4) and the
-  // 32-column groups warp / 4 and warp / 4 + 4 that lie below ncol; its
-  // running sum 256 columns further on
+  // this thread's slice of the tile: TMEM lane quarter (warp % 4) and 64 of
+  // the 256 columns (warp / 4); its running sum 256 columns further on
   const int q4 = warp & 3, h2 = warp >> 2;
-  const uint32_t tlane = taddr + ((uint32_t)(q4 * 32) << 16);
+  const uint32_t tcol = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 64);
   {
     float z[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) z[i] = 0.f;
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-      if ((h2 + 4 * j) * 32 < ncol) tmem_st32(tlane + kTcN + (h2 + 4 * j) * 32, z);
+    tmem_st32(tcol + kTcN, z);
+    tmem_st32(tcol + kTcN + 32, z);
   }
   const long long x0 = (long long)slice * kTcKC * chunks;
   const long long xend = (x0 + (long long)kTcKC * chunks < N3) ? x0 + (long long)kTcKC * chunks : N3;
   const int nch = x0 < xend ? (int)((xend - x0 + kTcKC - 1) / kTcKC) : 0;
-  const uint32_t idesc = tc_idesc(ncol);
-  // fixed roles: A rows are the tile's pairs, B rows its fields
+  const uint32_t idesc = tc_idesc();
+  // fixed roles
   const int rowA = tid & (kTcM - 1), kgA = tid / kTcM;
-  const short2 bc = tpairs[tile * kTcM + rowA];
-  const bool actA = bc.x >= 0;
-  const int srcA1 = (actA ? bc.x : 0) * kTcRow + kgA * 8, srcA2 = (actA ? bc.y : 0) * kTcRow + kgA * 8;
-  const int dstA = canon_off(rowA, kgA);
+  const bool actA = rowA < nf;
+  const int srcA = rowA * kTcRow + kgA * 8, dstA = canon_off(rowA, kgA);
   const int rowB = tid & (kTcN - 1), khB = tid / kTcN;
-  const int fB = rowB < ncol ? tcols[tile * kTcN + rowB] : -1;
-  const bool actB = fB >= 0;
-  const int srcB = (actB ? fB : 0) * kTcRow + khB * 16;
+  short2 bc = make_short2(-1, -1);
+  if (tile * kTcN + rowB < npairs) bc = pairs[tile * kTcN + rowB];
+  const bool actB = bc.x >= 0;
+  const int srcB1 = (actB ? bc.x : 0) * kTcRow + khB * 16, srcB2 = (actB ? bc.y : 0) * kTcRow + khB * 16;
   const int dstB0 = canon_off(rowB, 2 * khB), dstB1 = canon_off(rowB, 2 * khB + 1);
   const int cf0 = tid >> 3, cf1 = (tid + kTcThreads) >> 3, ck4 = (tid & 7) * 4;
   const bool cp0 = cf0 < nf, cp1 = cf1 < nf;
@@ -338,7 +322,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   };
   // drain of the run ending with chunk cl: wait for that chunk's MMAs, add
   // the tile to the running sum (ok is made block-uniform: tcgen05.ld is a
-  // warp-collective, and the column test is warp-uniform)
+  // warp-collective)
   constexpr int kDrain = tc_drain<NS>();
   auto drain = [&](int cl) {
     const bool w = ok && mbar_wait(&bar[cl & 1], (uint32_t)((cl >> 1) & 1), err, 16);
@@ -347,17 +331,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     if (ok) {
       // per 32 columns: both loads, one wait, add, store; one store wait
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int cg = h2 + 4 * j;
-        if (cg * 32 >= ncol) continue;
+      for (int cg = 0; cg < 2; ++cg) {
         uint32_t v[32], u[32];
-        tmem_ld32_async(tlane + cg * 32, v);
-        tmem_ld32_async(tlane + kTcN + cg * 32, u);
+        tmem_ld32_async(tcol + cg * 32, v);
+        tmem_ld32_async(tcol + kTcN + cg * 32, u);
         tmem_wait_ld(v);
         tmem_wait_ld(u);
 #pragma unroll
         for (int i = 0; i < 32; ++i) u[i] = __float_as_uint(__uint_as_float(u[i]) + __uint_as_float(v[i]));
-        tmem_st32_async(tlane + kTcN + cg * 32, u);
+        tmem_st32_async(tcol + kTcN + cg * 32, u);
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
@@ -377,28 +359,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     // the MMAs that read this stage two chunks ago must have finished
     if (c >= 2 && ok) ok = mbar_wait(&bar[s], (uint32_t)(((c - 2) >> 1) & 1), err, 16);
     ok = __syncthreads_and(ok) != 0;
-    // A: rows = the tile's pairs (b, c), Khatri-Rao products of their fields;
-    // a quarter-warp stores 8 consecutive rows of one k-group (one
-    // contiguous, conflict-free 128-byte span)
+    // A: rows (l, a) = field index; a quarter-warp stores 8 consecutive rows
+    // of one k-group (one contiguous, conflict-free 128-byte span)
     if (actA) {
-      const float4 b0 = *reinterpret_cast<const float4*>(Ist + srcA1);
-      const float4 b1 = *reinterpret_cast<const float4*>(Ist + srcA1 + 4);
-      const float4 c0 = *reinterpret_cast<const float4*>(Ist + srcA2);
-      const float4 c1 = *reinterpret_cast<const float4*>(Ist + srcA2 + 4);
-      const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
-                          b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
+      const float4 p = *reinterpret_cast<const float4*>(Ist + srcA);
+      const float4 q = *reinterpret_cast<const float4*>(Ist + srcA + 4);
+      const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
       uint4 parts[NS];
       split8<NS>(v, parts);
 #pragma unroll
       for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Ap + k * kTcABytes + dstA) = parts[k];
     }
-    // B: rows = the fields (l, a) the tile's triangles need
+    // B: rows = pairs (b, c) of this tile, products of the l = 0 fields
     if (actB) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const float4 p = *reinterpret_cast<const float4*>(Ist + srcB + 8 * h);
-        const float4 q = *reinterpret_cast<const float4*>(Ist + srcB + 8 * h + 4);
-        const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+        const float4 b0 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h);
+        const float4 b1 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h + 4);
+        const float4 c0 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h);
+        const float4 c1 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h + 4);
+        const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
+                            b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
         uint4 parts[NS];
         split8<NS>(v, parts);
         const int d = h ? dstB1 : dstB0;
@@ -436,13 +417,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   if (nch > 0) drain(nch - 1);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   // the last drain waited for every MMA of the slice
-  float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + (tid & 31)) * kTcN;
+  float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + (tid & 31)) * kTcN + h2 * 64;
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int cg = h2 + 4 * j;
-    if (cg * 32 >= ncol) continue;
+  for (int cg = 0; cg < 2; ++cg) {
     float u[32];
-    tmem_ld32(tlane + kTcN + cg * 32, u);
+    tmem_ld32(tcol + kTcN + cg * 32, u);
 #pragma unroll
     for (int i = 0; i < 32; i += 4)
       *reinterpret_cast<float4*>(dst + cg * 32 + i) = make_float4(u[i], u[i + 1], u[i + 2], u[i + 3]);
@@ -452,8 +431,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   if (warp == 0) tmem_dealloc(taddr, 2 * kTcN);
 }
 
-// out[o] = sum over slices of D[tile, row, col] with om[o] = tile * 128 + row
-// (-1: no output) and on[o] = col.
+// out[t * 3 + li] = sum over slices of D[m = li * S + a][n = pair(b, c)].
 __global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int ntiles, const int* __restrict__ om,
                             const int* __restrict__ on, int nout, double* __restrict__ out) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -463,9 +441,9 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int nti
     out[o] = 0.0;
     return;
   }
-  const int tile = m / kTcM, row = m - tile * kTcM;
+  const int tile = n / kTcN, col = n - tile * kTcN;
   double s = 0.0;
-  for (int k = 0; k < nslices; ++k) s += (double)part[(((size_t)k * ntiles + tile) * kTcM + row) * kTcN + n];
+  for (int k = 0; k < nslices; ++k) s += (double)part[(((size_t)k * ntiles + tile) * kTcM + m) * kTcN + col];
   out[o] = s;
 }
 
@@ -474,18 +452,18 @@ static size_t tc_smem_bytes(int nf) {
   return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * (size_t)nf * kTcRow + 2 * sizeof(uint64_t) + 16;
 }
 
-cudaError_t launch_contract_tc(const float* I, long long N3, int nf, const short2* tpairs, const short* tcols,
-                               const int* tncol, int ntiles, float* part, int* err, int nslices, int chunks,
-                               int nsplit, cudaStream_t s) {
+cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, const short2* pairs, int npairs,
+                               float* part, int* err, int nslices, int chunks, int nsplit, cudaStream_t s) {
+  const int ntiles = (npairs + kTcN - 1) / kTcN;
   const dim3 grid(ntiles, nslices);
   if (nsplit == 2) {
     const size_t sm = tc_smem_bytes<2>(nf);
     raise_smem_limit((const void*)k_contract_tc<2>, sm);
-    k_contract_tc<2><<<grid, kTcThreads, sm, s>>>(I, N3, nf, tpairs, tcols, tncol, chunks, part, err);
+    k_contract_tc<2><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   } else {
     const size_t sm = tc_smem_bytes<3>(nf);
     raise_smem_limit((const void*)k_contract_tc<3>, sm);
-    k_contract_tc<3><<<grid, kTcThreads, sm, s>>>(I, N3, nf, tpairs, tcols, tncol, chunks, part, err);
+    k_contract_tc<3><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   }
   return cudaGetLastError();
 }
