@@ -64,7 +64,12 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   const int nkey = MODE == 2 ? zp.nshells : zp.nbins;
   float2* zph = tw + N;                                   // [N] z half-cell phases (interlaced pairs)
   double* sbd = reinterpret_cast<double*>(zph + N);       // [BQ_N][nkey] the block's FP64 sums over its tiles
-  long long* sbi = reinterpret_cast<long long*>(sbd + BQ_N * nkey);  // [BQ_N][nkey] one tile's fixed-point sums
+  // one tile's fixed-point sums, [BQ_N][nkey] 64-bit integers held as low
+  // words (sbl) and high words (sbh): 32-bit shared adds are native, a 64-bit
+  // add is a compare-and-swap loop that contending threads repeat
+  long long* sbi = reinterpret_cast<long long*>(sbd + BQ_N * nkey);
+  unsigned* sbl = reinterpret_cast<unsigned*>(sbi);
+  int* sbh = reinterpret_cast<int*>(sbl + BQ_N * nkey);
   int* sc = reinterpret_cast<int*>(sbi + BQ_N * nkey);
   unsigned* tmax = reinterpret_cast<unsigned*>(sc + nkey);  // the tile's bound on |value| (FP32 bits)
   const int tid = threadIdx.y * kT + threadIdx.x;
@@ -203,6 +208,13 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
   int et;
   frexpf(__uint_as_float(*tmax), &et);
   const int st = 49 - et;  // tile sum <= 2 * 8 N * M < 2^(13 + et) * 2^(49 - et) <= 2^62 (N <= 512)
+  // x added to slot j: the low word's carry out goes to the high word, so
+  // sbh 2^32 + sbl is the exact sum (mod 2^64) whatever the order of adds
+  auto add_fixed = [&](int j, long long x) {
+    const unsigned lo = (unsigned)x;
+    const unsigned old = atomicAdd(sbl + j, lo);
+    atomicAdd(sbh + j, (int)(x >> 32) + (old + lo < old ? 1 : 0));
+  };
   int curb = -1, cnt = 0;
   float acc[BQ_N];
 #pragma unroll
@@ -270,8 +282,7 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
 #pragma unroll
         for (int q = 0; q < BQ_N; ++q)
           if (q < nq)
-            atomicAdd(reinterpret_cast<unsigned long long*>(sbi + q * nkey + curb),
-                      (unsigned long long)__float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
+            add_fixed(q * nkey + curb, __float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
       }
       curb = b;
       cnt = 0;
@@ -290,15 +301,16 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_zpass2(const 
 #pragma unroll
     for (int q = 0; q < BQ_N; ++q)
       if (q < nq)
-        atomicAdd(reinterpret_cast<unsigned long long*>(sbi + q * nkey + curb),
-                  (unsigned long long)__float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
+        add_fixed(q * nkey + curb, __float2ll_rn(ldexpf(acc[q], q == BQ_K && MODE != 2 ? sk : st)));
   }
   __syncthreads();
   // the tile's fixed-point bin sums join the block's FP64 sums (each slot by
   // one thread, tiles in the block's order)
   for (int q = tid; q < BQ_N * nkey; q += NT) {
-    sbd[q] += ldexp((double)sbi[q], (q / nkey == BQ_K && MODE != 2) ? -sk : -st);
-    sbi[q] = 0;
+    const long long v = (long long)sbh[q] * 4294967296ll + (long long)sbl[q];
+    sbd[q] += ldexp((double)v, (q / nkey == BQ_K && MODE != 2) ? -sk : -st);
+    sbl[q] = 0u;
+    sbh[q] = 0;
   }
   if (tid == 0) *tmax = 0u;
   __syncthreads();
