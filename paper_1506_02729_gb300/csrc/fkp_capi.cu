@@ -284,6 +284,9 @@ fkp::Plan::~Plan() {
   if (h_pinned) cudaFreeHost(h_pinned);
   if (batch_mem) cudaFree(batch_mem);
   for (auto& e : ev) if (e) cudaEventDestroy(e);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (side) cudaStreamDestroy(side);
 }
 
 // z-pass threads per block for a grid: 256 (two blocks per SM) up to 256^3,
@@ -577,6 +580,9 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   const size_t hbytes = sizeof(double) * (BQ_N * pb->nbins + pb->nbins + DS_COUNT + LAB_NSUM + 8) + 64;
   CK(cudaMallocHost(&P->h_pinned, hbytes));
   for (auto& e : P->ev) CK(cudaEventCreate(&e));
+  CK(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
   {
     const int rc = tune_schedule(P);
     if (rc) { delete P; return rc; }
@@ -699,6 +705,12 @@ static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t
   const long long nran = cached ? P->rc_n : ran.n;
   if (!which) CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));
   CK(stage(0));
+  // zero the grids on the side stream while the counts run
+  CK(cudaEventRecord(P->ev_fork, s));
+  CK(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+  CK(cudaMemsetAsync(grid, 0, N3 * 8, P->side));
+  if (gridw) CK(cudaMemsetAsync(gridw, 0, N3 * 8, P->side));
+  CK(cudaEventRecord(P->ev_join, P->side));
   int* bh_ran = P->d_bhist + (size_t)nbg * P->ntiles;
   CK(launch_bin_count(gal, 0, geo, P->d_scpart, P->d_bhist, P->d_err, nbg, s));
   if (cached)
@@ -710,8 +722,7 @@ static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t
   CK(launch_tile_prefix(P->d_bhist, nbg + (cached ? 0 : nbr), P->ntiles, P->d_tcnt, s));
   CK(launch_scan_tiles(P->d_tcnt, P->ntiles, P->d_toff, P->d_titem, s));
   CK(stage(1));
-  CK(cudaMemsetAsync(grid, 0, N3 * 8, s));
-  if (gridw) CK(cudaMemsetAsync(gridw, 0, N3 * 8, s));
+  CK(cudaStreamWaitEvent(s, P->ev_join, 0));
   const double* obs = P->geom.observer;
   float* vw2 = gridw ? P->d_vw2 : nullptr;
   CK(launch_bin_scatter(gal, 0, geo, obs, P->d_ds, P->d_toff, P->d_bhist, P->d_xyzv, vw2, nullptr, nbg, s));

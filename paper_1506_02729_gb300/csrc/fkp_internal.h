@@ -93,6 +93,10 @@ struct Plan {
   size_t staging_bytes[2] = {0, 0};
   void* h_pinned = nullptr;
   cudaEvent_t ev[12] = {};
+  // the grids' zeroing runs on a side stream beside the count launches
+  // (fork and join events, no timing)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // CUDA graph of the device-catalog power path (gridding, FFT passes,
   // binning), keyed by the catalogs it was captured with
