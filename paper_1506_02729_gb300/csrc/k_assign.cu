@@ -68,7 +68,12 @@ __device__ __forceinline__ bool centre_cell(const GeomDev& g, float px, float py
   return true;
 }
 
+// i mod N in [0, N): indices within one box of the grid (all but periodic
+// positions several boxes away) take the compare-and-add path, not a division.
 __device__ __forceinline__ int wrapN(int i, int N) {
+  if (i >= 0 && i < N) return i;
+  if (i < 0 && i >= -N) return i + N;
+  if (i >= N && i < 2 * N) return i - N;
   i %= N;
   return i < 0 ? i + N : i;
 }

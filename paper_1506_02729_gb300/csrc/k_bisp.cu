@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(256) k_counts(const int* __restrict__ ball, co
 constexpr int kSP = 8;      // pencils per block
 constexpr int kSNT = 256;   // threads per block: (kSP, 32)
 constexpr int kSRL = 16;    // points per thread along a pencil (N <= 512)
+constexpr int kXGap = 16;   // float2 of slack after each FFT buffer of the x shell pass
 
 struct ShellParams {
   int N, mm, S, nsh2;
@@ -237,12 +238,15 @@ __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2,
   extern __shared__ float2 sm[];
   const int N = N_ ? N_ : sp.N;
   float2* tw = sm;
+  // A and B each followed by kXGap float2 of slack: the transposed rows
+  // (stride N + 2 floats, so that the eight pencils' stores fall in distinct
+  // banks) need 2 kSP (N + 2) floats of the free buffer
   float2* A = sm + N;
-  float2* B = A + kSP * N;
+  float2* B = A + kSP * N + kXGap;
   // the next iteration's rows of T2: its 2 kSP rows are one contiguous span
   // (row 2 g0 with g0 a multiple of kSP = 8, so 16-byte aligned) fetched with
   // cp.async while this iteration transforms and stores
-  float2* stg = B + kSP * N;
+  float2* stg = B + kSP * N + kXGap;
   const int tid = threadIdx.y * kSP + threadIdx.x;
   const int m1 = sp.mm + 1;
   for (int i = tid; i < N; i += kSNT) tw[i] = twg[i];
@@ -293,17 +297,25 @@ __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2,
     __syncthreads();
     stage(g0 + (long long)gridDim.x * kSP);
     const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
-    // transpose through the free buffer into rows, then coalesced stores
+    // transpose through the free buffer into rows of stride N + 2 floats
+    // (row 2p starts 20p banks further on: a warp's 8 pencils x 4 points hit
+    // 32 distinct banks), then coalesced 8-byte stores (N even)
     float* rows = reinterpret_cast<float*>(R == A ? B : A);
+    const int rs = N + 2;
     for (int t = tid; t < kSP * N; t += kSNT) {
       const int p = t % kSP, x = t / kSP;
       const float2 v = R[t];
-      rows[(2 * p) * N + x] = v.x;
-      rows[(2 * p + 1) * N + x] = v.y;
+      rows[(2 * p) * rs + x] = v.x;
+      rows[(2 * p + 1) * rs + x] = v.y;
     }
     __syncthreads();
     const long long r0 = 2 * g0;
-    for (int t = tid; t < 2 * np * N; t += kSNT) I[r0 * N + t] = rows[t];
+    const int hn = N / 2;
+    float2* dst = reinterpret_cast<float2*>(I + r0 * N);
+    for (int t = tid; t < 2 * np * hn; t += kSNT) {
+      const int row = t / hn, x2 = t - row * hn;
+      dst[t] = *reinterpret_cast<const float2*>(rows + row * rs + 2 * x2);
+    }
   }
 }
 
@@ -318,7 +330,8 @@ static cudaError_t shell_passes_n(const BispLaunch& L, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (L.ny > 0) k_shell_y<N_><<<dim3(L.ny, L.sp.N), blk, sm, s>>>(L.T1, L.sp, L.fp, L.tw, L.yjobs, L.T2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t smx = sm + sizeof(float2) * 2 * kSP * (size_t)(L.sp.mm + 1);  // + the row staging
+  // + the slack after A and B, and the row staging
+  const size_t smx = sm + sizeof(float2) * (2 * kXGap + 2 * kSP * (size_t)(L.sp.mm + 1));
   if ((e = raise_smem_limit((const void*)k_shell_x<N_>, smx)) != cudaSuccess) return e;
   k_shell_x<N_><<<L.xblocks, blk, smx, s>>>(L.T2, L.sp, L.fp, L.tw, L.I);
   return cudaGetLastError();

@@ -83,7 +83,7 @@ def test_grid_does_not_depend_on_object_order_or_accumulation_form():
     """The gridding adds each tap's rounded value as an integer: as two 32-bit
     words, or as one 64-bit word for a work item whose sum of |w| passes 1000.
     Galaxy weights k/1024 (k uniform in 0..250, mean 0.122) and randoms of
-    weight 1 (alpha near 0.122) put the tiles' full work items of 8192
+    weight 1 (alpha near 0.122) put the tiles' full work items of 8160
     objects on both sides of that bound (29 of them here), and which objects
     share an item follows the objects' order.  Both forms and every order
     give the same grid, bit for bit (the weights keep W_g and W_r, hence
