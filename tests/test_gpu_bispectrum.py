@@ -46,7 +46,7 @@ def small_b():
     return sv, gal, ran, geom, bs, ref, kf
 
 
-@pytest.mark.parametrize("contraction", [0, 2], ids=["fp32", "bf16x6_tcgen05"])
+@pytest.mark.parametrize("contraction", [0, 2, 3], ids=["fp32", "bf16x6_tcgen05", "tf32x3_tcgen05"])
 def test_small_bispectrum_matches_oracle(small_b, contraction):
     fkp = _fkp()
     sv, gal, ran, geom, bs, ref, kf = small_b
@@ -78,6 +78,23 @@ def test_3way_split_matches_fp32_contraction(small_b):
     b6 = plan.bispectrum(dg, dr, contraction=2)[1]
     err = b_errors(b6, b32, float(b32["I33"]), float(sv.N) ** 3)
     assert max(err.values()) < B_TOL, err
+
+
+def test_tf32_split_matches_3way_split(small_b):
+    """The TF32 split (hi = v with the 13 mantissa bits TF32 drops cleared,
+    lo = v - hi; products hi*hi + hi*lo + lo*hi) drops lo*lo and the tensor
+    core's truncation of lo, each at most 2^-20 of a product, with random
+    sign: on the same device shell fields every triangle sum (N_T >= 100) stays
+    within 1e-5 of the 3-way BF16 split in the units of the oracle
+    comparison, a tenth of the 1e-4 bar."""
+    fkp = _fkp()
+    sv, gal, ran, geom, bs, ref, kf = small_b
+    plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
+    dg, dr = to_device(gal), to_device(ran)
+    b6 = plan.bispectrum(dg, dr, contraction=2)[1]
+    bt = plan.bispectrum(dg, dr, contraction=3)[1]
+    err = b_errors(bt, b6, float(b6["I33"]), float(sv.N) ** 3)
+    assert max(err.values()) < 1e-5, err
 
 
 def test_hi_lo_split_follows_its_error_model(small_b):
@@ -144,7 +161,8 @@ def test_aliasing_shells_are_rejected():
     assert e.value.code == -2
 
 
-@pytest.mark.parametrize("contraction", [0, 1, 2], ids=["fp32", "bf16x3_tcgen05", "bf16x6_tcgen05"])
+@pytest.mark.parametrize("contraction", [0, 1, 2, 3],
+                         ids=["fp32", "bf16x3_tcgen05", "bf16x6_tcgen05", "tf32x3_tcgen05"])
 def test_single_object_shot_noise_identity(contraction):
     """One galaxy on a node and randoms on every node (the oracle's pinned
     case): every triangle's B_0 = -2 alpha^2/nbar^2 = -0.125 with N_0 = 0.625
@@ -202,7 +220,7 @@ def test_interlaced_pcs_bispectrum_matches_oracle():
             assert np.max(np.abs(b[f"N{l}"] - ref[f"N{l}"]) / d) < SN_TOL, l
 
 
-@pytest.mark.parametrize("contraction", [0, 2], ids=["fp32", "bf16x6_tcgen05"])
+@pytest.mark.parametrize("contraction", [0, 2, 3], ids=["fp32", "bf16x6_tcgen05", "tf32x3_tcgen05"])
 def test_split_hexadecapole_bispectrum_matches_oracle(small_b, contraction):
     """B_4b of eq. Bhexa2 (delta_2 on the two larger sides: T22 = sum_x
     F_a^(2) F_b^(2) F_c^(0), extra columns of the contraction) against the
