@@ -80,21 +80,42 @@ def test_3way_split_matches_fp32_contraction(small_b):
     assert max(err.values()) < B_TOL, err
 
 
-def test_tf32_split_matches_3way_split(small_b):
-    """The TF32 split (hi = v with the 13 mantissa bits TF32 drops cleared,
-    lo = v - hi; products hi*hi + hi*lo + lo*hi) drops lo*lo and the tensor
-    core's truncation of lo, each at most 2^-20 of a product, with random
-    sign: on the same device shell fields every triangle sum (N_T >= 100) stays
-    within 1e-5 of the 3-way BF16 split in the units of the oracle
-    comparison, a tenth of the 1e-4 bar."""
+def _split_diff_units(small_b, mode_a, mode_b):
+    """Largest |T_a - T_b| over the triangle sums (N_T >= 100, l = 0, 2, 4) of
+    two contraction modes on the same device fields, in units of 2^-17
+    sqrt(sum_x t^2), t = F_a^(l) F_b^(0) F_c^(0) (shell fields from the
+    oracle)."""
     fkp = _fkp()
     sv, gal, ran, geom, bs, ref, kf = small_b
     plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
     dg, dr = to_device(gal), to_device(ran)
-    b6 = plan.bispectrum(dg, dr, contraction=2)[1]
-    bt = plan.bispectrum(dg, dr, contraction=3)[1]
-    err = b_errors(bt, b6, float(b6["I33"]), float(sv.N) ** 3)
-    assert max(err.values()) < 1e-5, err
+    ba = plan.bispectrum(dg, dr, contraction=mode_a)[1]
+    bb = plan.bispectrum(dg, dr, contraction=mode_b)[1]
+    F = op.fkp_grids(gal, ran, geom)[0]
+    Fl = op.legendre(F, geom, lmax=4)
+    sidx, _ = ob.shell_index(sv.N, bs)
+    I = {(l, s): ob.shell_field(Fl[l], sidx, s, sv.N) for l in (0, 2, 4) for s in range(bs[3])}
+    worst = 0.0
+    for t, (a, b, c) in enumerate(ref["tri"]):
+        if ref["NT"][t] < 100:
+            continue
+        for l in (0, 2, 4):
+            q = math.sqrt(float(np.sum((I[(l, a)] * I[(0, b)] * I[(0, c)]) ** 2)))
+            worst = max(worst, abs(ba[f"T{l}"][t] - bb[f"T{l}"][t]) / (2.0 ** -17 * q))
+    return worst
+
+
+def test_tf32_split_follows_its_error_model(small_b):
+    """The TF32 split (hi = v with the 13 mantissa bits TF32 drops cleared,
+    lo = v - hi; products hi*hi + hi*lo + lo*hi) drops lo*lo and the tensor
+    core's truncation of lo, each at most 2^-20 of a product, with random
+    sign: 1/8 of the 2-way BF16 split's error.  Against the 3-way split on the
+    same fields the difference is then set by the FP32 rounding of the
+    tensor-memory accumulation (runs of 256 points in both modes, about 1.6
+    units of 2^-17 sqrt(sum_x t^2) each): every triangle sum stays within 4
+    units, half the bound of the 2-way BF16 split."""
+    w = _split_diff_units(small_b, 3, 2)
+    assert w < 4.0, w
 
 
 def test_hi_lo_split_follows_its_error_model(small_b):
@@ -109,24 +130,8 @@ def test_hi_lo_split_follows_its_error_model(small_b):
     Against the 3-way split on the same
     fields, every triangle sum (N_T >= 100, l = 0, 2, 4) stays within 8 units;
     the shell fields for sum_x t^2 come from the oracle."""
-    fkp = _fkp()
-    sv, gal, ran, geom, bs, ref, kf = small_b
-    plan = fkp.Plan(geom, (0.5 * kf, kf, 32), bshells=bs, want=ALL)
-    dg, dr = to_device(gal), to_device(ran)
-    b3 = plan.bispectrum(dg, dr, contraction=1)[1]
-    b6 = plan.bispectrum(dg, dr, contraction=2)[1]
-    F = op.fkp_grids(gal, ran, geom)[0]
-    Fl = op.legendre(F, geom, lmax=4)
-    sidx, _ = ob.shell_index(sv.N, bs)
-    I = {(l, s): ob.shell_field(Fl[l], sidx, s, sv.N) for l in (0, 2, 4) for s in range(bs[3])}
-    worst = 0.0
-    for t, (a, b, c) in enumerate(ref["tri"]):
-        if ref["NT"][t] < 100:
-            continue
-        for l in (0, 2, 4):
-            q = math.sqrt(float(np.sum((I[(l, a)] * I[(0, b)] * I[(0, c)]) ** 2)))
-            worst = max(worst, abs(b3[f"T{l}"][t] - b6[f"T{l}"][t]) / (2.0 ** -17 * q))
-    assert worst < 8.0, worst
+    w = _split_diff_units(small_b, 1, 2)
+    assert w < 8.0, w
 
 
 def test_counts_match_oracle_convolution():
