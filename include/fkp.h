@@ -155,13 +155,9 @@ typedef struct {
  *   BF16X3 tcgen05 tensor cores, operands split v = hi + lo in BF16, products
  *          hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory;
  *   BF16X6 tcgen05 tensor cores, 3-way split hi + mid + lo, the six products of
- *          order <= 2^-16: per-term error near FP32 rounding;
- *   TF32X3 tcgen05 tensor cores, operands split v = hi + lo in TF32 (hi: v
- *          with the 13 mantissa bits TF32 drops cleared, lo = v - hi), products
- *          hi*hi + hi*lo + lo*hi: per-term error about 2^-20.
- * The BF16 modes need (number of multipoles) x (shells) <= 128, TF32X3 <= 120
- * (FKP_EINVAL otherwise). */
-enum { FKP_CONTRACT_FP32 = 0, FKP_CONTRACT_BF16X3 = 1, FKP_CONTRACT_BF16X6 = 2, FKP_CONTRACT_TF32X3 = 3 };
+ *          order <= 2^-16: per-term error near FP32 rounding.
+ * The tensor-core modes need (number of multipoles) x (shells) <= 128. */
+enum { FKP_CONTRACT_FP32 = 0, FKP_CONTRACT_BF16X3 = 1, FKP_CONTRACT_BF16X6 = 2 };
 
 /* Context: binds a CUDA device.  hbm_budget_bytes = 0 means no limit.
  * Returns FKP_EINVAL for a bad device index, FKP_ECUDA on runtime errors. */
@@ -271,7 +267,7 @@ int fkp_power_from_grid(void *plan, const float *F_device, double I22, double N0
                         void *cuda_stream, fkp_power_out *out);
 
 /* P_l and B_l of one survey (Sec. III.B).  contraction is one of
- * FKP_CONTRACT_FP32, _BF16X3, _BF16X6, _TF32X3.  ran == NULL uses the plan's cached
+ * FKP_CONTRACT_FP32, _BF16X3, _BF16X6.  ran == NULL uses the plan's cached
  * random catalog. */
 int fkp_bispectrum(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
                    int contraction, void *cuda_stream, fkp_power_out *pout, fkp_bisp_out *bout);

@@ -718,8 +718,7 @@ using namespace fkp;
 // passes, the shell IFFTs, the contraction) on s.
 static int enqueue_bisp(Plan* P, const CatDev& g, const CatDev& r, int contraction, cudaStream_t s) {
   auto* st = static_cast<BispState*>(P->bisp);
-  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6 ||
-                      contraction == FKP_CONTRACT_TF32X3;
+  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6;
   int rc = enqueue_grids(P, g, r, s);
   if (rc) return rc;
   const int N = P->g.N, S = st->S, mm = st->mm;
@@ -771,8 +770,7 @@ static int enqueue_bisp(Plan* P, const CatDev& g, const CatDev& r, int contracti
   const int ntri = P->ntri, nout = std::max(1, ntri) * st->nq;
   if (tensor && st->npairs > 0) {
     BCK(launch_contract_tc(st->d_I, N3, st->nl * S, S, st->d_pairs, st->npairs, st->d_tcpart, P->d_err + 1,
-                           st->tc_slices, st->tc_chunks,
-                           contraction == FKP_CONTRACT_BF16X3 ? 2 : (contraction == FKP_CONTRACT_TF32X3 ? 4 : 3), s));
+                           st->tc_slices, st->tc_chunks, contraction == FKP_CONTRACT_BF16X3 ? 2 : 3, s));
     BCK(launch_tc_reduce(st->d_tcpart, st->tc_slices, st->tc_tiles, st->d_om, st->d_on, nout, st->d_T, s));
   } else if (!st->items.empty()) {
     const int nf = st->nl * S;
@@ -824,16 +822,12 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   auto* P = static_cast<Plan*>(plan);
   if (!P) return set_error(FKP_EINVAL, "NULL plan");
   if (!P->wantB || !P->bisp) return set_error(FKP_ESTATE, "plan was created without FKP_B* flags");
-  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3 && contraction != FKP_CONTRACT_BF16X6 &&
-      contraction != FKP_CONTRACT_TF32X3)
+  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3 && contraction != FKP_CONTRACT_BF16X6)
     return set_error(FKP_EINVAL, "unknown contraction mode %d", contraction);
   auto* st = static_cast<BispState*>(P->bisp);
-  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6 ||
-                      contraction == FKP_CONTRACT_TF32X3;
+  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6;
   if (tensor && !st->d_pairs && st->npairs > 0)
     return set_error(FKP_EINVAL, "the tensor-core contraction needs (multipoles x shells) <= %d rows", tc_rows());
-  if (contraction == FKP_CONTRACT_TF32X3 && st->nl * st->S > tc_tf32_max_fields())
-    return set_error(FKP_EINVAL, "the TF32 contraction needs (multipoles x shells) <= %d", tc_tf32_max_fields());
   BCK(cudaSetDevice(P->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CatDev g, r;

@@ -53,24 +53,14 @@ constexpr int kTcSliceTarget = 4096;   // chunks per K slice, at most (about)
 constexpr int kTcThreads = 512;
 constexpr int kTcABytes = kTcM * kTcKC * 2;    // one BF16 operand tile: 8 KB
 constexpr int kTcBBytes = kTcN * kTcKC * 2;    // 16 KB
-// One split part of an operand: BF16 rows of 64 bytes (the chunk's 32
-// points); TF32 rows of 128 bytes held as two 64-byte-row sub-tiles (points
-// 0-15 and 16-31), each laid out like a BF16 tile.
-template <bool TF>
-__host__ __device__ constexpr int tc_part_a() { return TF ? 2 * kTcABytes : kTcABytes; }
-template <bool TF>
-__host__ __device__ constexpr int tc_part_b() { return TF ? 2 * kTcBBytes : kTcBBytes; }
-template <int NS, bool TF>
-__host__ __device__ constexpr int tc_stage_bytes() { return NS * (tc_part_a<TF>() + tc_part_b<TF>()); }
-// slots of the ring of raw field chunks (TF32: one chunk ahead, for room)
-template <bool TF>
-__host__ __device__ constexpr int tc_ring() { return TF ? 2 : 3; }
+template <int NS>
+__host__ __device__ constexpr int tc_stage_bytes() { return NS * (kTcABytes + kTcBBytes); }
 constexpr int kTcRow = kTcKC + 4;      // staged row stride (floats): 16-byte aligned, shifts banks by 4 per field
 
 // chunks per tensor-memory accumulation run: 96 accumulating MMAs per run for
-// every split (3 products x 2 K steps x 16 chunks; 6 x 2 x 8; TF32 3 x 4 x 8)
-template <int NS, bool TF>
-__host__ __device__ constexpr int tc_drain() { return (TF || NS == 3) ? 8 : 16; }
+// every split (3 products x 2 K steps x 16 chunks; 6 x 2 x 8)
+template <int NS>
+__host__ __device__ constexpr int tc_drain() { return NS == 3 ? 8 : 16; }
 // K slicing: the fewest whole waves of the SMs (tiles x slices CTAs, one per
 // SM at a time) whose slices hold at most about kTcSliceTarget chunks; slices
 // of equal length (the last one shorter), none empty.
@@ -103,16 +93,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// D[tmem] (+)= A * B^T, A and B K-major TF32 in shared memory, FP32 accumulate.
-__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
 
 // D[tmem] (+)= A * B^T, A and B K-major BF16 in shared memory, FP32 accumulate.
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -212,11 +192,10 @@ __device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t 
   return a | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-// Instruction descriptor: D FP32, A and B both BF16 (kind::f16, type 1) or
-// both TF32 (kind::tf32, type 2), both K-major, N = 256, M = 128.
-__host__ __device__ constexpr uint32_t tc_idesc(bool tf) {
-  return (1u << 4) | ((tf ? 2u : 1u) << 7) | ((tf ? 2u : 1u) << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-         ((uint32_t)(kTcM >> 4) << 24);
+// Instruction descriptor for kind::f16: D FP32, A and B BF16, both K-major,
+// N = 256, M = 128.
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
 
 // Byte offset of the 16-byte segment (row, k-group kg) of an operand tile in
@@ -251,22 +230,6 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
   for (int p = 0; p < NS; ++p) out[p] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
-// TF32 split of 8 values: hi = v with the 13 mantissa bits that TF32 drops
-// cleared (exactly a TF32 value), lo = v - hi (exact in FP32; the tensor core
-// keeps its leading 11 bits), packed 16 bytes per 4 values.
-__device__ __forceinline__ void split8_tf32(const float* v, uint4 (&hi)[2], uint4 (&lo)[2]) {
-  uint32_t h[8], l[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    h[i] = __float_as_uint(v[i]) & 0xFFFFE000u;
-    l[i] = __float_as_uint(v[i] - __uint_as_float(h[i]));
-  }
-  hi[0] = make_uint4(h[0], h[1], h[2], h[3]);
-  hi[1] = make_uint4(h[4], h[5], h[6], h[7]);
-  lo[0] = make_uint4(l[0], l[1], l[2], l[3]);
-  lo[1] = make_uint4(l[4], l[5], l[6], l[7]);
-}
-
 // ---------------------------------------------------------------------------
 
 // pairs: (b, c) of the tile's columns (b < 0 marks padding); part layout
@@ -280,21 +243,17 @@ __device__ __forceinline__ void split8_tf32(const float* v, uint4 (&hi)[2], uint
 // rewritten.  The running FP32 sum of the drained tiles sits in tensor memory
 // columns 256-511 (each drain: tcgen05.ld tile and sum, add, tcgen05.st), so
 // no accumulator occupies registers through the chunk loop.
-// TF: TF32 operands split in two (NS = 2), products hi*hi + hi*lo + lo*hi.
-template <int NS, bool TF>
+template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
                                                                int S, const short2* __restrict__ pairs, int npairs,
                                                                int chunks, float* __restrict__ part,
                                                                int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  static_assert(!TF || NS == 2, "the TF32 split has two parts");
-  constexpr int kStage = tc_stage_bytes<NS, TF>();
-  constexpr int kPA = tc_part_a<TF>(), kPB = tc_part_b<TF>();
-  constexpr int kRing = tc_ring<TF>();
+  constexpr int kStage = tc_stage_bytes<NS>();
   unsigned char* stage0 = smraw;                                  // 2 stages: A parts, then B parts
-  float* Iring = reinterpret_cast<float*>(smraw + 2 * kStage);   // kRing x [nf][kTcRow], kRing - 1 chunks ahead
+  float* Iring = reinterpret_cast<float*>(smraw + 2 * kStage);   // 3 x [nf][kTcRow], prefetched 2 chunks ahead
   const int ring = nf * kTcRow;                                   // floats per ring slot
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Iring + kRing * ring);  // [2]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Iring + 3 * ring);  // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int tile = blockIdx.x, slice = blockIdx.y, ntiles = gridDim.x;
@@ -327,13 +286,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   const long long x0 = (long long)slice * kTcKC * chunks;
   const long long xend = (x0 + (long long)kTcKC * chunks < N3) ? x0 + (long long)kTcKC * chunks : N3;
   const int nch = x0 < xend ? (int)((xend - x0 + kTcKC - 1) / kTcKC) : 0;
-  const uint32_t idesc = tc_idesc(TF);
+  const uint32_t idesc = tc_idesc();
   // fixed roles
   const int rowA = tid & (kTcM - 1), kgA = tid / kTcM;
   const bool actA = rowA < nf;
   const int srcA = rowA * kTcRow + kgA * 8, dstA = canon_off(rowA, kgA);
-  // TF32: the two 16-byte chunks of this thread's 8 points in their sub-tile
-  const int dstAt[2] = {canon_off(rowA, 2 * (kgA & 1)), canon_off(rowA, 2 * (kgA & 1) + 1)};
   const int rowB = tid & (kTcN - 1), khB = tid / kTcN;
   short2 bc = make_short2(-1, -1);
   if (tile * kTcN + rowB < npairs) bc = pairs[tile * kTcN + rowB];
@@ -353,7 +310,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
       const long long x = x0 + (long long)cc * kTcKC + ck4;
       const int bytes = x + 4 <= xend ? 16 : (x < xend ? (int)(xend - x) * 4 : 0);
       const long long xs = x < xend ? x : 0;
-      const uint32_t so = (uint32_t)((cc % kRing) * ring * 4);
+      const uint32_t so = (uint32_t)((cc % 3) * ring * 4);
       if (cp0)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(cdst0 + so), "l"(csrc0 + xs), "r"(bytes)
                      : "memory");
@@ -366,7 +323,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   // drain of the run ending with chunk cl: wait for that chunk's MMAs, add
   // the tile to the running sum (ok is made block-uniform: tcgen05.ld is a
   // warp-collective)
-  constexpr int kDrain = tc_drain<NS, TF>();
+  constexpr int kDrain = tc_drain<NS>();
   auto drain = [&](int cl) {
     const bool w = ok && mbar_wait(&bar[cl & 1], (uint32_t)((cl >> 1) & 1), err, 16);
     ok = __syncthreads_and(w) != 0;
@@ -390,16 +347,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     __syncthreads();
   };
   prefetch(0);
-  if constexpr (kRing == 3) prefetch(1);
+  prefetch(1);
   for (int c = 0; c < nch; ++c) {
     const int s = c & 1;
     unsigned char* st = stage0 + s * kStage;
-    unsigned char* Ap = st;                      // NS parts of kPA bytes
-    unsigned char* Bp = st + NS * kPA;           // NS parts of kPB bytes
-    prefetch(c + kRing - 1);
-    if constexpr (kRing == 3) asm volatile("cp.async.wait_group 2;" ::: "memory");
-    else asm volatile("cp.async.wait_group 1;" ::: "memory");
-    const float* Ist = Iring + (c % kRing) * ring;
+    unsigned char* Ap = st;                      // NS tiles of kTcABytes
+    unsigned char* Bp = st + NS * kTcABytes;     // NS tiles of kTcBBytes
+    prefetch(c + 2);
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+    const float* Ist = Iring + (c % 3) * ring;
     // the MMAs that read this stage two chunks ago must have finished
     if (c >= 2 && ok) ok = mbar_wait(&bar[s], (uint32_t)(((c - 2) >> 1) & 1), err, 16);
     ok = __syncthreads_and(ok) != 0;
@@ -409,22 +365,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
       const float4 p = *reinterpret_cast<const float4*>(Ist + srcA);
       const float4 q = *reinterpret_cast<const float4*>(Ist + srcA + 4);
       const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
-      if constexpr (TF) {
-        // points 8 kgA .. 8 kgA + 7: sub-tile kgA / 2, 16-byte chunks 2 (kgA % 2) and + 1
-        uint4 hi[2], lo[2];
-        split8_tf32(v, hi, lo);
-        unsigned char* a0 = Ap + (kgA >> 1) * kTcABytes;
+      uint4 parts[NS];
+      split8<NS>(v, parts);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          *reinterpret_cast<uint4*>(a0 + dstAt[h]) = hi[h];
-          *reinterpret_cast<uint4*>(a0 + kPA + dstAt[h]) = lo[h];
-        }
-      } else {
-        uint4 parts[NS];
-        split8<NS>(v, parts);
-#pragma unroll
-        for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Ap + k * kTcABytes + dstA) = parts[k];
-      }
+      for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Ap + k * kTcABytes + dstA) = parts[k];
     }
     // B: rows = pairs (b, c) of this tile, products of the l = 0 fields
     if (actB) {
@@ -436,24 +380,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
         const float4 c1 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h + 4);
         const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
                             b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
-        if constexpr (TF) {
-          // points 16 khB + 8 h ..: sub-tile khB, 16-byte chunks 2 h and 2 h + 1
-          uint4 hi[2], lo[2];
-          split8_tf32(v, hi, lo);
-          unsigned char* b0 = Bp + khB * kTcBBytes;
+        uint4 parts[NS];
+        split8<NS>(v, parts);
+        const int d = h ? dstB1 : dstB0;
 #pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int d = canon_off(rowB, 2 * h + e);
-            *reinterpret_cast<uint4*>(b0 + d) = hi[e];
-            *reinterpret_cast<uint4*>(b0 + kPB + d) = lo[e];
-          }
-        } else {
-          uint4 parts[NS];
-          split8<NS>(v, parts);
-          const int d = h ? dstB1 : dstB0;
-#pragma unroll
-          for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Bp + k * kTcBBytes + d) = parts[k];
-        }
+        for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Bp + k * kTcBBytes + d) = parts[k];
       }
     }
     fence_proxy_async();
@@ -467,28 +398,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
       constexpr int NP = NS == 2 ? 3 : 6;
       constexpr int pi[6] = {0, 0, 1, 0, 2, 1};
       constexpr int pj[6] = {0, 1, 0, 2, 0, 1};
-      if constexpr (TF) {
-        // K steps of 8 TF32 (32 bytes): steps 0, 1 in sub-tile 0, steps 2, 3 in sub-tile 1
 #pragma unroll
-        for (int ks = 0; ks < kTcKC / 8; ++ks) {
-          const int so = (ks >> 1) * kTcABytes + (ks & 1) * 32, sb = (ks >> 1) * kTcBBytes + (ks & 1) * 32;
+      for (int ks = 0; ks < kTcKC / 16; ++ks) {
+        // K step ks covers k-groups 2 ks and 2 ks + 1 (32 bytes further along the rows)
 #pragma unroll
-          for (int q = 0; q < NP; ++q) {
-            const uint64_t ad = sdesc(Ap + pi[q] * kPA + so, 16, 512);
-            const uint64_t bd = sdesc(Bp + pj[q] * kPB + sb, 16, 512);
-            umma_tf32(taddr, ad, bd, idesc, ((c % kDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int ks = 0; ks < kTcKC / 16; ++ks) {
-          // K step ks covers k-groups 2 ks and 2 ks + 1 (32 bytes further along the rows)
-#pragma unroll
-          for (int q = 0; q < NP; ++q) {
-            const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 32, 16, 512);
-            const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 32, 16, 512);
-            umma_bf16(taddr, ad, bd, idesc, ((c % kDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
-          }
+        for (int q = 0; q < NP; ++q) {
+          const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 32, 16, 512);
+          const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 32, 16, 512);
+          umma_bf16(taddr, ad, bd, idesc, ((c % kDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
         }
       }
       umma_commit(&bar[s]);
@@ -530,40 +447,23 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int nti
   out[o] = s;
 }
 
-template <int NS, bool TF>
+template <int NS>
 static size_t tc_smem_bytes(int nf) {
-  return 2 * (size_t)tc_stage_bytes<NS, TF>() + tc_ring<TF>() * sizeof(float) * (size_t)nf * kTcRow +
-         2 * sizeof(uint64_t) + 16;
+  return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * (size_t)nf * kTcRow + 2 * sizeof(uint64_t) + 16;
 }
 
-// Fields (multipoles x shells) the TF32 contraction takes: its two stages of
-// 96 KB and the two-slot ring of field chunks within 227 KB of shared memory.
-int tc_tf32_max_fields() {
-  int nf = kTcM;
-  while (nf > 0 && tc_smem_bytes<2, true>(nf) > 232448) --nf;
-  return nf;
-}
-
-// mode: 2 = BF16 hi/lo, 3 = BF16 3-way, 4 = TF32 hi/lo.
 cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, const short2* pairs, int npairs,
-                               float* part, int* err, int nslices, int chunks, int mode, cudaStream_t s) {
+                               float* part, int* err, int nslices, int chunks, int nsplit, cudaStream_t s) {
   const int ntiles = (npairs + kTcN - 1) / kTcN;
   const dim3 grid(ntiles, nslices);
-  if (mode == 2) {
-    const size_t sm = tc_smem_bytes<2, false>(nf);
-    raise_smem_limit((const void*)k_contract_tc<2, false>, sm);
-    k_contract_tc<2, false><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
-  } else if (mode == 3) {
-    const size_t sm = tc_smem_bytes<3, false>(nf);
-    raise_smem_limit((const void*)k_contract_tc<3, false>, sm);
-    k_contract_tc<3, false><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
-  } else if (mode == 4) {
-    if (nf > tc_tf32_max_fields()) return cudaErrorInvalidValue;
-    const size_t sm = tc_smem_bytes<2, true>(nf);
-    raise_smem_limit((const void*)k_contract_tc<2, true>, sm);
-    k_contract_tc<2, true><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
+  if (nsplit == 2) {
+    const size_t sm = tc_smem_bytes<2>(nf);
+    raise_smem_limit((const void*)k_contract_tc<2>, sm);
+    k_contract_tc<2><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   } else {
-    return cudaErrorInvalidValue;
+    const size_t sm = tc_smem_bytes<3>(nf);
+    raise_smem_limit((const void*)k_contract_tc<3>, sm);
+    k_contract_tc<3><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   }
   return cudaGetLastError();
 }
