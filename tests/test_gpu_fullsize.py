@@ -146,4 +146,5 @@ def test_bispectrum_360_stratified_triangles_and_exact_counts():
     for mode, (_, bb) in zip(("fp32", "bf16x3", "bf16x6", "fp16x3"), runs):
         got = {k: bb[k][idx] for k in ("B0", "B2", "B4")}
         err = b_errors(got, rb, rb["I33"], 360.0 ** 3)
+        print(f"B errors against the oracle, {mode}: " + ", ".join(f"B{l} {v:.2e}" for l, v in err.items()))
         assert max(err.values()) < B_TOL, (mode, err)
