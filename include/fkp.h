@@ -155,16 +155,9 @@ typedef struct {
  *   BF16X3 tcgen05 tensor cores, operands split v = hi + lo in BF16, products
  *          hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory;
  *   BF16X6 tcgen05 tensor cores, 3-way split hi + mid + lo, the six products of
- *          order <= 2^-16: per-term error near FP32 rounding;
- *   FP16X3 tcgen05 tensor cores, each shell field and each product of two
- *          scaled by a power of two that puts its largest |value| below 2^14
- *          (the maxima are taken in the shell IFFT pass), split v = hi + lo in
- *          FP16 (11-bit significands), products hi*hi + hi*lo + lo*hi: each
- *          operand value is kept to about 2^-22 of itself or 2^-39 of its
- *          scale's bound (FP16 subnormals), whichever is larger, at the cost of
- *          the BF16 hi/lo mode.
+ *          order <= 2^-16: per-term error near FP32 rounding.
  * The tensor-core modes need (number of multipoles) x (shells) <= 128. */
-enum { FKP_CONTRACT_FP32 = 0, FKP_CONTRACT_BF16X3 = 1, FKP_CONTRACT_BF16X6 = 2, FKP_CONTRACT_FP16X3 = 3 };
+enum { FKP_CONTRACT_FP32 = 0, FKP_CONTRACT_BF16X3 = 1, FKP_CONTRACT_BF16X6 = 2 };
 
 /* Context: binds a CUDA device.  hbm_budget_bytes = 0 means no limit.
  * Returns FKP_EINVAL for a bad device index, FKP_ECUDA on runtime errors. */
@@ -274,7 +267,7 @@ int fkp_power_from_grid(void *plan, const float *F_device, double I22, double N0
                         void *cuda_stream, fkp_power_out *out);
 
 /* P_l and B_l of one survey (Sec. III.B).  contraction is one of
- * FKP_CONTRACT_FP32, _BF16X3, _BF16X6, _FP16X3.  ran == NULL uses the plan's cached
+ * FKP_CONTRACT_FP32, _BF16X3, _BF16X6.  ran == NULL uses the plan's cached
  * random catalog. */
 int fkp_bispectrum(void *plan, const fkp_catalog_t *gal, const fkp_catalog_t *ran,
                    int contraction, void *cuda_stream, fkp_power_out *pout, fkp_bisp_out *bout);

@@ -201,9 +201,8 @@ void tc_slicing(long long N3, int ntiles, int nsm, int* nslices, int* chunks);
 int tc_tile_cols();
 int tc_rows();
 cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, const short2* pairs, int npairs,
-                               float* part, int* err, int nslices, int chunks, int mode, const unsigned* fmax,
-                               cudaStream_t s);
+                               float* part, int* err, int nslices, int chunks, int nsplit, cudaStream_t s);
 cudaError_t launch_tc_reduce(const float* part, int nslices, int ntiles, const int* om, const int* on, int nout,
-                             double* out, const unsigned* fmax, const short2* pairs, cudaStream_t s);
+                             double* out, cudaStream_t s);
 
 }  // namespace fkp

@@ -71,7 +71,6 @@ struct BispState {
   short2* d_pairs = nullptr;
   int *d_om = nullptr, *d_on = nullptr;
   float* d_tcpart = nullptr;
-  unsigned* d_fmax = nullptr;  // per shell field: the largest |I| (FP32 bits), from the x shell pass
   // shell IFFT work lists: z tiles (s, n_y + mm, n_x0), y tiles (s, n_x0, |n_y| range); floor(r_s)
   int nzjobs = 0, nyjobs = 0;
   int4 *d_zjobs = nullptr, *d_yjobs = nullptr;
@@ -160,7 +159,6 @@ struct BispLaunch {
   int ny;
   float2 *T1, *T2;
   float* I;                 // this multipole's S real shell fields
-  unsigned* fmax;           // per field of I: the largest |value| (FP32 bits), atomically raised
   int xblocks;
 };
 
@@ -236,8 +234,7 @@ __global__ void __launch_bounds__(kSNT) k_shell_y(const float2* __restrict__ T1,
 // and 2(g0+p)+1 (same shell: N^2 is even) as x1 + i x2.
 template <int N_>
 __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2, ShellParams sp, FftPlan fp,
-                                                  const float2* __restrict__ twg, float* __restrict__ I,
-                                                  unsigned* __restrict__ fmax) {
+                                                  const float2* __restrict__ twg, float* __restrict__ I) {
   extern __shared__ float2 sm[];
   const int N = N_ ? N_ : sp.N;
   float2* tw = sm;
@@ -315,16 +312,10 @@ __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2,
     const long long r0 = 2 * g0;
     const int hn = N / 2;
     float2* dst = reinterpret_cast<float2*>(I + r0 * N);
-    float m = 0.f;
     for (int t = tid; t < 2 * np * hn; t += kSNT) {
       const int row = t / hn, x2 = t - row * hn;
-      const float2 v = *reinterpret_cast<const float2*>(rows + row * rs + 2 * x2);
-      dst[t] = v;
-      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+      dst[t] = *reinterpret_cast<const float2*>(rows + row * rs + 2 * x2);
     }
-    // the iteration's rows all lie in shell s (N^2 rows a shell, 2 kSP an iteration)
-    const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));  // non-negative: ordered as integers
-    if ((tid & 31) == 0 && mb != 0u) atomicMax(fmax + s, mb);
   }
 }
 
@@ -342,7 +333,7 @@ static cudaError_t shell_passes_n(const BispLaunch& L, cudaStream_t s) {
   // + the slack after A and B, and the row staging
   const size_t smx = sm + sizeof(float2) * (2 * kXGap + 2 * kSP * (size_t)(L.sp.mm + 1));
   if ((e = raise_smem_limit((const void*)k_shell_x<N_>, smx)) != cudaSuccess) return e;
-  k_shell_x<N_><<<L.xblocks, blk, smx, s>>>(L.T2, L.sp, L.fp, L.tw, L.I, L.fmax);
+  k_shell_x<N_><<<L.xblocks, blk, smx, s>>>(L.T2, L.sp, L.fp, L.tw, L.I);
   return cudaGetLastError();
 }
 
@@ -676,7 +667,6 @@ int bisp_plan_init(Plan* P) {
   st->d_items = (ContractItem*)A(sizeof(ContractItem) * std::max<size_t>(1, st->items.size()));
   st->d_cpart = (double*)A(sizeof(double) * (size_t)st->nslices * std::max(1, ntri) * st->nq);
   st->d_T = (double*)A(sizeof(double) * std::max(1, ntri) * st->nq);
-  st->d_fmax = (unsigned*)A(sizeof(unsigned) * st->nl * S);
   st->d_spart = (double*)A(sizeof(double) * BQ_N * S * (size_t)P->nblk_z);
   st->d_spartc = (int*)A(sizeof(int) * S * (size_t)P->nblk_z);
   st->d_shell = (double*)A(sizeof(double) * BQ_N * S);
@@ -728,8 +718,7 @@ using namespace fkp;
 // passes, the shell IFFTs, the contraction) on s.
 static int enqueue_bisp(Plan* P, const CatDev& g, const CatDev& r, int contraction, cudaStream_t s) {
   auto* st = static_cast<BispState*>(P->bisp);
-  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6 ||
-                      contraction == FKP_CONTRACT_FP16X3;
+  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6;
   int rc = enqueue_grids(P, g, r, s);
   if (rc) return rc;
   const int N = P->g.N, S = st->S, mm = st->mm;
@@ -770,11 +759,9 @@ static int enqueue_bisp(Plan* P, const CatDev& g, const CatDev& r, int contracti
     L.T1 = st->d_T1;
     L.T2 = st->d_T2;
     L.xblocks = P->ctx->nsm * 6;
-    BCK(cudaMemsetAsync(st->d_fmax, 0, sizeof(unsigned) * st->nl * S, s));
     for (int li = 0; li < st->nl; ++li) {
       L.E = st->d_E + li * es;
       L.I = st->d_I + (size_t)li * S * N3;
-      L.fmax = st->d_fmax + li * S;
       BCK(shell_passes(L, s));
     }
   }
@@ -782,12 +769,9 @@ static int enqueue_bisp(Plan* P, const CatDev& g, const CatDev& r, int contracti
   // contraction
   const int ntri = P->ntri, nout = std::max(1, ntri) * st->nq;
   if (tensor && st->npairs > 0) {
-    const bool f16 = contraction == FKP_CONTRACT_FP16X3;
     BCK(launch_contract_tc(st->d_I, N3, st->nl * S, S, st->d_pairs, st->npairs, st->d_tcpart, P->d_err + 1,
-                           st->tc_slices, st->tc_chunks, contraction == FKP_CONTRACT_BF16X3 ? 2 : (f16 ? 4 : 3),
-                           st->d_fmax, s));
-    BCK(launch_tc_reduce(st->d_tcpart, st->tc_slices, st->tc_tiles, st->d_om, st->d_on, nout, st->d_T,
-                         f16 ? st->d_fmax : nullptr, st->d_pairs, s));
+                           st->tc_slices, st->tc_chunks, contraction == FKP_CONTRACT_BF16X3 ? 2 : 3, s));
+    BCK(launch_tc_reduce(st->d_tcpart, st->tc_slices, st->tc_tiles, st->d_om, st->d_on, nout, st->d_T, s));
   } else if (!st->items.empty()) {
     const int nf = st->nl * S;
     const size_t smc = sizeof(float) * (size_t)kCTK * (nf | 1);
@@ -838,12 +822,10 @@ extern "C" int fkp_bispectrum(void* plan, const fkp_catalog_t* gal, const fkp_ca
   auto* P = static_cast<Plan*>(plan);
   if (!P) return set_error(FKP_EINVAL, "NULL plan");
   if (!P->wantB || !P->bisp) return set_error(FKP_ESTATE, "plan was created without FKP_B* flags");
-  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3 && contraction != FKP_CONTRACT_BF16X6 &&
-      contraction != FKP_CONTRACT_FP16X3)
+  if (contraction != FKP_CONTRACT_FP32 && contraction != FKP_CONTRACT_BF16X3 && contraction != FKP_CONTRACT_BF16X6)
     return set_error(FKP_EINVAL, "unknown contraction mode %d", contraction);
   auto* st = static_cast<BispState*>(P->bisp);
-  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6 ||
-                      contraction == FKP_CONTRACT_FP16X3;
+  const bool tensor = contraction == FKP_CONTRACT_BF16X3 || contraction == FKP_CONTRACT_BF16X6;
   if (tensor && !st->d_pairs && st->npairs > 0)
     return set_error(FKP_EINVAL, "the tensor-core contraction needs (multipoles x shells) <= %d rows", tc_rows());
   BCK(cudaSetDevice(P->ctx->device));

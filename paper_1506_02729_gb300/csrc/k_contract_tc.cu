@@ -39,7 +39,6 @@
 #include <algorithm>
 
 #include <cuda_bf16.h>
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -193,25 +192,11 @@ __device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t 
   return a | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-// Instruction descriptor for kind::f16: D FP32, A and B both BF16 (type 1) or
-// both FP16 (type 0), both K-major, N = 256, M = 128.
-__host__ __device__ constexpr uint32_t tc_idesc(bool f16) {
-  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-         ((uint32_t)(kTcM >> 4) << 24);
+// Instruction descriptor for kind::f16: D FP32, A and B BF16, both K-major,
+// N = 256, M = 128.
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
-
-// Power-of-two scale of a field (or of a product of two fields) for the FP16
-// split: with m < 2^e the largest |value| of the field (from its shell pass),
-// 2^(14 - e) puts every scaled value below 2^14, inside FP16's range with
-// room for the rounding; the exponent is clamped so that the scale stays a
-// normal FP32 number.  Fields that are zero everywhere get 2^14.
-__device__ __forceinline__ int tc_fexp(unsigned mbits) {
-  if (mbits == 0u) return 0;
-  int e;
-  frexpf(__uint_as_float(mbits), &e);
-  return e;
-}
-__device__ __forceinline__ float tc_scale(int e) { return ldexpf(1.f, max(-120, min(120, 14 - e))); }
 
 // Byte offset of the 16-byte segment (row, k-group kg) of an operand tile in
 // the 64-byte-swizzled K-major layout: row r at 64 r, its 16-byte chunk kg
@@ -245,22 +230,6 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
   for (int p = 0; p < NS; ++p) out[p] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
-// FP16 split of 8 (scaled) values into hi = f16(v), lo = f16(v - hi), packed
-// 16 bytes per part.
-__device__ __forceinline__ void split8_f16(const float* v, uint4* out) {
-  uint32_t w[2][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
-    w[0][i] = *reinterpret_cast<const uint32_t*>(&h);
-    w[1][i] = *reinterpret_cast<const uint32_t*>(&l);
-  }
-  out[0] = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
-  out[1] = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
-}
-
 // ---------------------------------------------------------------------------
 
 // pairs: (b, c) of the tile's columns (b < 0 marks padding); part layout
@@ -274,15 +243,11 @@ __device__ __forceinline__ void split8_f16(const float* v, uint4* out) {
 // rewritten.  The running FP32 sum of the drained tiles sits in tensor memory
 // columns 256-511 (each drain: tcgen05.ld tile and sum, add, tcgen05.st), so
 // no accumulator occupies registers through the chunk loop.
-// H16: FP16 operands split in two (NS = 2), each field and each pair product
-// scaled by its power of two (tc_scale of fmax); k_tc_reduce divides by them.
-template <int NS, bool H16>
+template <int NS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
                                                                int S, const short2* __restrict__ pairs, int npairs,
                                                                int chunks, float* __restrict__ part,
-                                                               int* __restrict__ err,
-                                                               const unsigned* __restrict__ fmax) {
-  static_assert(!H16 || NS == 2, "the FP16 split has two parts");
+                                                               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   constexpr int kStage = tc_stage_bytes<NS>();
   unsigned char* stage0 = smraw;                                  // 2 stages: A parts, then B parts
@@ -321,7 +286,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   const long long x0 = (long long)slice * kTcKC * chunks;
   const long long xend = (x0 + (long long)kTcKC * chunks < N3) ? x0 + (long long)kTcKC * chunks : N3;
   const int nch = x0 < xend ? (int)((xend - x0 + kTcKC - 1) / kTcKC) : 0;
-  const uint32_t idesc = tc_idesc(H16);
+  const uint32_t idesc = tc_idesc();
   // fixed roles
   const int rowA = tid & (kTcM - 1), kgA = tid / kTcM;
   const bool actA = rowA < nf;
@@ -332,12 +297,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   const bool actB = bc.x >= 0;
   const int srcB1 = (actB ? bc.x : 0) * kTcRow + khB * 16, srcB2 = (actB ? bc.y : 0) * kTcRow + khB * 16;
   const int dstB0 = canon_off(rowB, 2 * khB), dstB1 = canon_off(rowB, 2 * khB + 1);
-  // FP16: this thread's field scale (A row) and pair-product scale (B row)
-  float scA = 1.f, scB = 1.f;
-  if (H16) {
-    scA = tc_scale(actA ? tc_fexp(fmax[rowA]) : 0);
-    scB = tc_scale(actB ? tc_fexp(fmax[bc.x]) + tc_fexp(fmax[bc.y]) : 0);
-  }
   const int cf0 = tid >> 3, cf1 = (tid + kTcThreads) >> 3, ck4 = (tid & 7) * 4;
   const bool cp0 = cf0 < nf, cp1 = cf1 < nf;
   const float* csrc0 = I + (size_t)(cp0 ? cf0 : 0) * N3;
@@ -405,14 +364,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
     if (actA) {
       const float4 p = *reinterpret_cast<const float4*>(Ist + srcA);
       const float4 q = *reinterpret_cast<const float4*>(Ist + srcA + 4);
+      const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
       uint4 parts[NS];
-      if constexpr (H16) {
-        const float v[8] = {p.x * scA, p.y * scA, p.z * scA, p.w * scA, q.x * scA, q.y * scA, q.z * scA, q.w * scA};
-        split8_f16(v, parts);
-      } else {
-        const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
-        split8<NS>(v, parts);
-      }
+      split8<NS>(v, parts);
 #pragma unroll
       for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Ap + k * kTcABytes + dstA) = parts[k];
     }
@@ -424,16 +378,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
         const float4 b1 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h + 4);
         const float4 c0 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h);
         const float4 c1 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h + 4);
+        const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
+                            b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
         uint4 parts[NS];
-        if constexpr (H16) {
-          const float v[8] = {b0.x * c0.x * scB, b0.y * c0.y * scB, b0.z * c0.z * scB, b0.w * c0.w * scB,
-                              b1.x * c1.x * scB, b1.y * c1.y * scB, b1.z * c1.z * scB, b1.w * c1.w * scB};
-          split8_f16(v, parts);
-        } else {
-          const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
-                              b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
-          split8<NS>(v, parts);
-        }
+        split8<NS>(v, parts);
         const int d = h ? dstB1 : dstB0;
 #pragma unroll
         for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Bp + k * kTcBBytes + d) = parts[k];
@@ -483,11 +431,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __re
   if (warp == 0) tmem_dealloc(taddr, 2 * kTcN);
 }
 
-// out[t * 3 + li] = sum over slices of D[m = li * S + a][n = pair(b, c)],
-// divided by the row's and the column's FP16 scales when fmax is given.
+// out[t * 3 + li] = sum over slices of D[m = li * S + a][n = pair(b, c)].
 __global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int ntiles, const int* __restrict__ om,
-                            const int* __restrict__ on, int nout, double* __restrict__ out,
-                            const unsigned* __restrict__ fmax, const short2* __restrict__ pairs) {
+                            const int* __restrict__ on, int nout, double* __restrict__ out) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nout) return;
   const int m = om[o], n = on[o];
@@ -498,46 +444,33 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int nti
   const int tile = n / kTcN, col = n - tile * kTcN;
   double s = 0.0;
   for (int k = 0; k < nslices; ++k) s += (double)part[(((size_t)k * ntiles + tile) * kTcM + m) * kTcN + col];
-  if (fmax) {
-    const short2 bc = pairs[n];
-    s /= (double)tc_scale(tc_fexp(fmax[m])) * (double)tc_scale(tc_fexp(fmax[bc.x]) + tc_fexp(fmax[bc.y]));
-  }
   out[o] = s;
 }
 
-template <int NS, bool H16>
+template <int NS>
 static size_t tc_smem_bytes(int nf) {
   return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * (size_t)nf * kTcRow + 2 * sizeof(uint64_t) + 16;
 }
 
-// mode: 2 = BF16 hi/lo, 3 = BF16 3-way, 4 = scaled FP16 hi/lo (fmax: the
-// fields' largest |values|).
 cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, const short2* pairs, int npairs,
-                               float* part, int* err, int nslices, int chunks, int mode, const unsigned* fmax,
-                               cudaStream_t s) {
+                               float* part, int* err, int nslices, int chunks, int nsplit, cudaStream_t s) {
   const int ntiles = (npairs + kTcN - 1) / kTcN;
   const dim3 grid(ntiles, nslices);
-  if (mode == 2) {
-    const size_t sm = tc_smem_bytes<2, false>(nf);
-    raise_smem_limit((const void*)k_contract_tc<2, false>, sm);
-    k_contract_tc<2, false><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err, nullptr);
-  } else if (mode == 3) {
-    const size_t sm = tc_smem_bytes<3, false>(nf);
-    raise_smem_limit((const void*)k_contract_tc<3, false>, sm);
-    k_contract_tc<3, false><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err, nullptr);
-  } else if (mode == 4 && fmax) {
-    const size_t sm = tc_smem_bytes<2, true>(nf);
-    raise_smem_limit((const void*)k_contract_tc<2, true>, sm);
-    k_contract_tc<2, true><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err, fmax);
+  if (nsplit == 2) {
+    const size_t sm = tc_smem_bytes<2>(nf);
+    raise_smem_limit((const void*)k_contract_tc<2>, sm);
+    k_contract_tc<2><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   } else {
-    return cudaErrorInvalidValue;
+    const size_t sm = tc_smem_bytes<3>(nf);
+    raise_smem_limit((const void*)k_contract_tc<3>, sm);
+    k_contract_tc<3><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_reduce(const float* part, int nslices, int ntiles, const int* om, const int* on, int nout,
-                             double* out, const unsigned* fmax, const short2* pairs, cudaStream_t s) {
-  k_tc_reduce<<<(nout + 255) / 256, 256, 0, s>>>(part, nslices, ntiles, om, on, nout, out, fmax, pairs);
+                             double* out, cudaStream_t s) {
+  k_tc_reduce<<<(nout + 255) / 256, 256, 0, s>>>(part, nslices, ntiles, om, on, nout, out);
   return cudaGetLastError();
 }
 

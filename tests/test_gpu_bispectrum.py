@@ -46,7 +46,7 @@ def small_b():
     return sv, gal, ran, geom, bs, ref, kf
 
 
-@pytest.mark.parametrize("contraction", [0, 2, 3], ids=["fp32", "bf16x6_tcgen05", "fp16x3_tcgen05"])
+@pytest.mark.parametrize("contraction", [0, 2], ids=["fp32", "bf16x6_tcgen05"])
 def test_small_bispectrum_matches_oracle(small_b, contraction):
     fkp = _fkp()
     sv, gal, ran, geom, bs, ref, kf = small_b
@@ -105,18 +105,6 @@ def _split_diff_units(small_b, mode_a, mode_b):
     return worst
 
 
-def test_fp16_split_follows_its_error_model(small_b):
-    """The scaled FP16 split keeps each operand value to about 2^-22 of itself
-    (hi and lo of 11-bit significands; lo*lo dropped at 2^-22 of a product):
-    1/16 of the BF16 hi/lo split's per-product error.  Against the 3-way BF16
-    split on the same fields the difference is then the FP32 rounding of the
-    two modes' tensor-memory accumulation (runs of 512 and 256 points):
-    every triangle sum (N_T >= 100) stays within 4 units of 2^-17
-    sqrt(sum_x t^2), half the bound of the BF16 hi/lo split."""
-    w = _split_diff_units(small_b, 3, 2)
-    assert w < 4.0, w
-
-
 def test_hi_lo_split_follows_its_error_model(small_b):
     """The 2-way split (3 products) drops lo*lo and the rounding of lo, each
     ~2^-18 of a product, with random sign: over the N^3 points the error of a
@@ -165,8 +153,7 @@ def test_aliasing_shells_are_rejected():
     assert e.value.code == -2
 
 
-@pytest.mark.parametrize("contraction", [0, 1, 2, 3],
-                         ids=["fp32", "bf16x3_tcgen05", "bf16x6_tcgen05", "fp16x3_tcgen05"])
+@pytest.mark.parametrize("contraction", [0, 1, 2], ids=["fp32", "bf16x3_tcgen05", "bf16x6_tcgen05"])
 def test_single_object_shot_noise_identity(contraction):
     """One galaxy on a node and randoms on every node (the oracle's pinned
     case): every triangle's B_0 = -2 alpha^2/nbar^2 = -0.125 with N_0 = 0.625
@@ -224,7 +211,7 @@ def test_interlaced_pcs_bispectrum_matches_oracle():
             assert np.max(np.abs(b[f"N{l}"] - ref[f"N{l}"]) / d) < SN_TOL, l
 
 
-@pytest.mark.parametrize("contraction", [0, 2, 3], ids=["fp32", "bf16x6_tcgen05", "fp16x3_tcgen05"])
+@pytest.mark.parametrize("contraction", [0, 2], ids=["fp32", "bf16x6_tcgen05"])
 def test_split_hexadecapole_bispectrum_matches_oracle(small_b, contraction):
     """B_4b of eq. Bhexa2 (delta_2 on the two larger sides: T22 = sum_x
     F_a^(2) F_b^(2) F_c^(0), extra columns of the contraction) against the

@@ -126,7 +126,7 @@ def test_bispectrum_360_stratified_triangles_and_exact_counts():
     bs = (3, 3, 3, 37)
     plan = fkp.Plan(geom, BINS, bshells=bs, want=127)
     dg, dr = to_device(gal), to_device(ran)
-    runs = [plan.bispectrum(dg, dr, contraction=c) for c in (0, 1, 2, 3)]
+    runs = [plan.bispectrum(dg, dr, contraction=c) for c in (0, 1, 2)]
     counts = stored_counts(37)
     tri = _check_triangle_list(runs[0][1], counts)
     F, Fw, sc = op.fkp_grids(gal, ran, geom, with_w2=True)
@@ -143,7 +143,7 @@ def test_bispectrum_360_stratified_triangles_and_exact_counts():
     rb = ob.bispectrum_from_fields(Fl, Fwl, sc, 360, bs, ells=(0, 2, 4), tris=sample, counts=counts,
                                    cache_fields=16)
     idx = [tri.index(t) for t in sample]
-    for mode, (_, bb) in zip(("fp32", "bf16x3", "bf16x6", "fp16x3"), runs):
+    for mode, (_, bb) in zip(("fp32", "bf16x3", "bf16x6"), runs):
         got = {k: bb[k][idx] for k in ("B0", "B2", "B4")}
         err = b_errors(got, rb, rb["I33"], 360.0 ** 3)
         print(f"B errors against the oracle, {mode}: " + ", ".join(f"B{l} {v:.2e}" for l, v in err.items()))
