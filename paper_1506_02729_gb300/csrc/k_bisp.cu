@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(256) k_counts(const int* __restrict__ ball, co
 
 constexpr int kSP = 8;      // pencils per block
 constexpr int kSNT = 256;   // threads per block: (kSP, 32)
+static_assert(kSNT % kSP == 0, "a thread keeps its pencil across a pass");
 constexpr int kSRL = 16;    // points per thread along a pencil (N <= 512)
 constexpr int kXGap = 16;   // float2 of slack after each FFT buffer of the x shell pass
 
@@ -268,16 +269,22 @@ __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2,
     const int km = sp.kmax[s < sp.S ? s : sp.S - 1];
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    // p fastest: contiguous shared-memory stores, 32-byte row segments read
-    for (int t = tid; t < kSP * N; t += kSNT) {
-      const int p = t % kSP, k = t / kSP;
+    // p fastest: contiguous shared-memory stores, 32-byte row segments read.
+    // A thread's pencil p = tid mod kSP is the same at every k; the shell (and
+    // its reach kmp) is the iteration's unless the iteration straddles two
+    // shells (N^2 not a multiple of 2 kSP)
+    const int p = tid % kSP;
+    const bool valid = p < np;
+    int kmp = km;
+    if (valid && (2 * g0 + 2 * np - 1) / ((long long)N * N) != s) {
+      const int sp0 = (int)((2 * (g0 + p)) / ((long long)N * N));
+      kmp = sp.kmax[sp0 < sp.S ? sp0 : sp.S - 1];
+    }
+    const float2* h0 = stg + (size_t)(2 * p) * m1;
+    const float2* h1 = h0 + m1;
+    for (int k = tid / kSP; k < N; k += kSNT / kSP) {
       float2 v = make_float2(0.f, 0.f);
-      if (p < np) {
-        const long long r0 = 2 * (g0 + p);
-        const int sp0 = (int)(r0 / ((long long)N * N));
-        const int kmp = sp0 == s ? km : sp.kmax[sp0];
-        const float2* h0 = stg + (size_t)(2 * p) * m1;
-        const float2* h1 = h0 + m1;
+      if (valid) {
         float2 x1 = make_float2(0.f, 0.f), x2 = x1;
         if (k == 0) {
           x1 = make_float2(h0[0].x, 0.f);
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(kSNT) k_shell_x(const float2* __restrict__ T2,
         }
         v = make_float2(x1.x - x2.y, x1.y + x2.x);  // x1 + i x2
       }
-      A[t] = v;
+      A[k * kSP + p] = v;
     }
     __syncthreads();
     stage(g0 + (long long)gridDim.x * kSP);
