@@ -16,7 +16,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -162,85 +161,73 @@ struct BispLaunch {
   float2 *T1, *T2;
   float* I;                 // this multipole's S real shell fields
   int xblocks;
-  int nsm;                  // SMs of the device (persistent z and y passes)
 };
 
-// Persistent: blocks walk the work items (one z job each) with the twiddle
-// table loaded once.
 template <int N_>
 __global__ void __launch_bounds__(kSNT) k_shell_z(const float2* __restrict__ E, ShellParams sp, FftPlan fp,
                                                   const float2* __restrict__ twg, const int4* __restrict__ jobs,
-                                                  int njobs, float2* __restrict__ T1) {
+                                                  float2* __restrict__ T1) {
   extern __shared__ float2 sm[];
   const int N = N_ ? N_ : sp.N;
   float2* tw = sm;
   float2* A = sm + N;
   float2* B = A + kSP * N;
   const int tid = threadIdx.y * kSP + threadIdx.x;
-  const int mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1;
+  const int4 job = jobs[blockIdx.x];
+  const int s = job.x, kyp = job.y, kx0 = job.z;
+  const int mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1, ny = kyp - mm;
   for (int i = tid; i < N; i += kSNT) tw[i] = twg[i];
-  for (int w = blockIdx.x; w < njobs; w += gridDim.x) {
-    const int4 job = jobs[w];
-    const int s = job.x, kyp = job.y, kx0 = job.z, ny = kyp - mm;
-    for (int i = tid; i < kSP * N; i += kSNT) A[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    for (int t = tid; t < w2 * kSP; t += kSNT) {
-      const int kzp = t / kSP, c = t - kzp * kSP, kx = kx0 + c;
-      if (kx < m1) {
-        const int nz = kzp - mm;
-        const int n2 = kx * kx + ny * ny + nz * nz;
-        if (n2 < sp.nsh2 && sp.slut[n2] == s) A[wrap_mode(nz, N) * kSP + c] = E[((size_t)kzp * w2 + kyp) * m1 + kx];
-      }
+  for (int i = tid; i < kSP * N; i += kSNT) A[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int t = tid; t < w2 * kSP; t += kSNT) {
+    const int kzp = t / kSP, c = t - kzp * kSP, kx = kx0 + c;
+    if (kx < m1) {
+      const int nz = kzp - mm;
+      const int n2 = kx * kx + ny * ny + nz * nz;
+      if (n2 < sp.nsh2 && sp.slut[n2] == s) A[wrap_mode(nz, N) * kSP + c] = E[((size_t)kzp * w2 + kyp) * m1 + kx];
     }
-    __syncthreads();
-    const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
-    const int c = threadIdx.x, run = threadIdx.y, rl = (N + 31) / 32;
-    if (kx0 + c < m1) {
+  }
+  __syncthreads();
+  const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
+  const int c = threadIdx.x, run = threadIdx.y, rl = (N + 31) / 32;
+  if (kx0 + c < m1) {
 #pragma unroll
-      for (int i = 0; i < kSRL; ++i) {
-        const int z = i * 32 + run;
-        if (i < rl && z < N) T1[(((size_t)s * N + z) * w2 + kyp) * m1 + kx0 + c] = R[z * kSP + c];
-      }
+    for (int i = 0; i < kSRL; ++i) {
+      const int z = i * 32 + run;
+      if (i < rl && z < N) T1[(((size_t)s * N + z) * w2 + kyp) * m1 + kx0 + c] = R[z * kSP + c];
     }
-    __syncthreads();  // R (A or B) is read before the next item clears A
   }
 }
 
-// Persistent: blocks walk the work items (job, z) = (w / N, w mod N) with the
-// twiddle table loaded once.
 template <int N_>
 __global__ void __launch_bounds__(kSNT) k_shell_y(const float2* __restrict__ T1, ShellParams sp, FftPlan fp,
                                                   const float2* __restrict__ twg, const int4* __restrict__ jobs,
-                                                  int njobs, float2* __restrict__ T2) {
+                                                  float2* __restrict__ T2) {
   extern __shared__ float2 sm[];
   const int N = N_ ? N_ : sp.N;
   float2* tw = sm;
   float2* A = sm + N;
   float2* B = A + kSP * N;
   const int tid = threadIdx.y * kSP + threadIdx.x;
+  const int4 job = jobs[blockIdx.x];
+  const int s = job.x, kx0 = job.y, nyr = job.z, z = blockIdx.y;
   const int mm = sp.mm, w2 = 2 * mm + 1, m1 = mm + 1;
   for (int i = tid; i < N; i += kSNT) tw[i] = twg[i];
-  const long long items = (long long)njobs * N;
-  for (long long w = blockIdx.x; w < items; w += gridDim.x) {
-    const int4 job = jobs[w / N];
-    const int s = job.x, kx0 = job.y, nyr = job.z, z = (int)(w % N);
-    for (int i = tid; i < kSP * N; i += kSNT) A[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    for (int t = tid; t < (2 * nyr + 1) * kSP; t += kSNT) {
-      const int j = t / kSP, c = t - j * kSP, ny = j - nyr;
-      if (kx0 + c < m1) A[wrap_mode(ny, N) * kSP + c] = T1[(((size_t)s * N + z) * w2 + ny + mm) * m1 + kx0 + c];
-    }
-    __syncthreads();
-    const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
-    const int c = threadIdx.x, run = threadIdx.y, rl = (N + 31) / 32;
-    if (kx0 + c < m1) {
+  for (int i = tid; i < kSP * N; i += kSNT) A[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int t = tid; t < (2 * nyr + 1) * kSP; t += kSNT) {
+    const int j = t / kSP, c = t - j * kSP, ny = j - nyr;
+    if (kx0 + c < m1) A[wrap_mode(ny, N) * kSP + c] = T1[(((size_t)s * N + z) * w2 + ny + mm) * m1 + kx0 + c];
+  }
+  __syncthreads();
+  const float2* R = fft_any<N_, kSP, kSNT, 1>(A, B, fp, tw);
+  const int c = threadIdx.x, run = threadIdx.y, rl = (N + 31) / 32;
+  if (kx0 + c < m1) {
 #pragma unroll
-      for (int i = 0; i < kSRL; ++i) {
-        const int y = i * 32 + run;
-        if (i < rl && y < N) T2[(((size_t)s * N + z) * N + y) * m1 + kx0 + c] = R[y * kSP + c];
-      }
+    for (int i = 0; i < kSRL; ++i) {
+      const int y = i * 32 + run;
+      if (i < rl && y < N) T2[(((size_t)s * N + z) * N + y) * m1 + kx0 + c] = R[y * kSP + c];
     }
-    __syncthreads();  // R (A or B) is read before the next item clears A
   }
 }
 
@@ -346,23 +333,9 @@ static cudaError_t shell_passes_n(const BispLaunch& L, cudaStream_t s) {
   if ((e = raise_smem_limit((const void*)k_shell_z<N_>, sm)) != cudaSuccess) return e;
   if ((e = raise_smem_limit((const void*)k_shell_y<N_>, sm)) != cudaSuccess) return e;
   const dim3 blk(kSP, kSNT / kSP);
-  // persistent z and y passes: as many blocks as fit on the SMs at once
-  // (queried on the first call for this size, before any graph capture)
-  static std::atomic<int> occ_z{-1}, occ_y{-1};
-  if (occ_z.load() < 0) {
-    int o = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_shell_z<N_>, kSNT, sm)) != cudaSuccess) return e;
-    occ_z.store(o > 0 ? o : 1);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_shell_y<N_>, kSNT, sm)) != cudaSuccess) return e;
-    occ_y.store(o > 0 ? o : 1);
-  }
-  const int resident = L.nsm * occ_z.load();
-  if (L.nz > 0) k_shell_z<N_><<<std::min(L.nz, resident), blk, sm, s>>>(L.E, L.sp, L.fp, L.tw, L.zjobs, L.nz, L.T1);
+  if (L.nz > 0) k_shell_z<N_><<<L.nz, blk, sm, s>>>(L.E, L.sp, L.fp, L.tw, L.zjobs, L.T1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const long long yitems = (long long)L.ny * L.sp.N;
-  const int yres = L.nsm * occ_y.load();
-  if (L.ny > 0)
-    k_shell_y<N_><<<(int)std::min<long long>(yitems, yres), blk, sm, s>>>(L.T1, L.sp, L.fp, L.tw, L.yjobs, L.ny, L.T2);
+  if (L.ny > 0) k_shell_y<N_><<<dim3(L.ny, L.sp.N), blk, sm, s>>>(L.T1, L.sp, L.fp, L.tw, L.yjobs, L.T2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // + the slack after A and B, and the row staging
   const size_t smx = sm + sizeof(float2) * (2 * kXGap + 2 * kSP * (size_t)(L.sp.mm + 1));
@@ -793,7 +766,6 @@ static int enqueue_bisp(Plan* P, const CatDev& g, const CatDev& r, int contracti
     L.T1 = st->d_T1;
     L.T2 = st->d_T2;
     L.xblocks = P->ctx->nsm * 6;
-    L.nsm = P->ctx->nsm;
     for (int li = 0; li < st->nl; ++li) {
       L.E = st->d_E + li * es;
       L.I = st->d_I + (size_t)li * S * N3;
