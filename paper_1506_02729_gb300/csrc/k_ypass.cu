@@ -33,6 +33,10 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
   float2* buf1 = buf0 + tile;
   float2* work = buf1 + tile;
   float2* tw = work + tile;
+  // the polynomial coefficients a[o][j] of every member (in read order) for
+  // this block's 8 columns, [member][o][j][c]: computed once per block instead
+  // of once per member and thread
+  float* coef = reinterpret_cast<float*>(tw + N);
   const int xt = blockIdx.x, z = blockIdx.y;
   const size_t fsz = (size_t)N * NXT * N * kT;
   const size_t gsz = fsz;
@@ -44,9 +48,20 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
     mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
-  __syncthreads();
   int total = 0;
   for (int s = 0; s < mt.nsweeps; ++s) total += mt.s_nmem[s];
+  for (int e = tid; e < total * 10 * kT; e += NT) {
+    const int cc = e % kT, oj = (e / kT) % 10, mi = e / (10 * kT), o = oj / 5, j = oj - 5 * o;
+    int sw = 0, m = mi;
+    while (m >= mt.s_nmem[sw]) m -= mt.s_nmem[sw++];
+    const float nxc = (float)(blockIdx.x * kT + cc);
+    float v = 0.f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+      if (mt.s_j[sw][m][o][t] == j) v += mt.s_c[sw][m][o][t] * powi(nxc, mt.s_i[sw][m][o][t]);
+    coef[e] = v;
+  }
+  __syncthreads();
   auto src_of = [&](int q) { return S1 + (size_t)q * fsz + ((size_t)z * NXT + xt) * tile; };
   if (tid == 0) {
     mbar_expect_tx(&bar[0], bytes);
@@ -55,7 +70,6 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
   const int c = threadIdx.x, run = threadIdx.y;
   const int rl = (N + PassShape<NT>::kRun - 1) / PassShape<NT>::kRun;
   const int kx = xt * kT + c;
-  const float nx = (float)kx;
   int it = 0;
   for (int sw = 0; sw < mt.nsweeps; ++sw) {
     const int nout = mt.s_nout[sw];
@@ -82,13 +96,7 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
 #pragma unroll
       for (int o = 0; o < 2; ++o)
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-          float v = 0.f;
-#pragma unroll
-          for (int t = 0; t < 2; ++t)
-            if (mt.s_j[sw][m][o][t] == j) v += mt.s_c[sw][m][o][t] * powi(nx, mt.s_i[sw][m][o][t]);
-          a[o][j] = v;
-        }
+        for (int j = 0; j < 5; ++j) a[o][j] = coef[(it * 10 + o * 5 + j) * kT + c];
 #pragma unroll
       for (int i = 0; i < PassShape<NT>::kRL; ++i) {
         const int ky = i * PassShape<NT>::kRun + run;
@@ -145,7 +153,9 @@ template <int N_, int NT>
 static cudaError_t yrun_nt(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                            const MomentTable& mt, const FftPlan& fp, const float2* tw, float2* S2, int* err,
                            cudaStream_t s, const MockBatch& mb) {
-  const size_t sm = ysm(g.N);
+  int total = 0;
+  for (int q = 0; q < mt.nsweeps; ++q) total += mt.s_nmem[q];
+  const size_t sm = ysm(g.N) + sizeof(float) * 10 * kT * (size_t)total;
   raise_smem_limit((const void*)k_ypass2<N_, NT>, sm);
   k_ypass2<N_, NT><<<dim3(tiles_x(g.N), g.N, mb.n), dim3(kT, NT / kT), sm, s>>>(S1, gq, gf, g, mt, fp, tw, S2, err,
                                                                                     mb);
