@@ -234,11 +234,15 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
 // pairs: (b, c) of the tile's columns (b < 0 marks padding); part layout
 // [slice][tile][128][256] FP32.
 //
-// Warp-specialised pipeline: warps 0-15 (512 threads) build the operands,
-// warp 16 keeps the ring of raw field chunks filled with bulk copies and one
-// of its lanes issues the MMAs; the two sides meet only on mbarriers, so the
-// operand build of one chunk overlaps the MMAs of the previous one.
-//   ring_full[k]   the bulk copies of the chunk in ring slot k have landed
+// Pipeline on mbarriers, without block barriers: the 16 warps copy the raw
+// field chunks into a 3-slot ring (cp.async, two chunks ahead) and build the
+// operands, and lane 0 of warp 15, after its own share of a chunk, issues the
+// chunk's MMAs once every warp has signalled the stage full; each warp goes on
+// to the next chunk as soon as its own share is done and the stage it writes
+// has been released by the MMAs, so the build of one chunk overlaps the MMAs
+// of the previous one.
+//   ring_full[k]   every builder's copies into ring slot k have landed (512
+//                  cp.async-tracked arrivals)
 //   ring_free[k]   the builders have read ring slot k (512 arrivals)
 //   stage_full[s]  the builders have written operand stage s (512 arrivals)
 //   stage_free[s]  the MMAs that read stage s have completed (tcgen05.commit)
@@ -252,7 +256,8 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
 // whose wait gives up stops working but keeps to the loop, and the host
 // reports the error flag.
 constexpr int kTcBuilders = 512;
-constexpr int kTcThreadsWS = kTcBuilders + 32;
+constexpr int kTcThreadsWS = kTcBuilders;
+constexpr int kTcIssueWarp = 15;  // the warp one of whose lanes issues the MMAs
 
 template <int NS>
 __global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __
   }
   if (tid == 0) {
     for (int k = 0; k < 3; ++k) {
-      mbar_init(&ring_full[k], 1);
+      mbar_init(&ring_full[k], kTcBuilders);
       mbar_init(&ring_free[k], kTcBuilders);
     }
     for (int k = 0; k < 2; ++k) {
@@ -303,67 +308,13 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __
   constexpr int kDrain = tc_drain<NS>();
   bool ok = true;
 
-  if (warp == kTcBuilders / 32) {
-    // ---- control warp: ring producer (all lanes) and MMA issue (lane 0) ----
-    const uint32_t idesc = tc_idesc();
-    // bulk copies of chunk cc's field values into its ring slot (the last
-    // chunk of the last slice may be short; its tail is masked by the builders)
-    auto produce = [&](int cc) {
-      const int slot = cc % 3;
-      const long long x = x0 + (long long)cc * kTcKC;
-      const uint32_t fb = (uint32_t)((xend - x < kTcKC ? xend - x : kTcKC) * 4);
-      if (lane == 0) mbar_expect_tx(&ring_full[slot], fb * (uint32_t)nf);
-      __syncwarp();
-      for (int f = lane; f < nf; f += 32)
-        tma_load_1d(Iring + slot * ring + f * kTcRow, I + (size_t)f * N3 + x, fb, &ring_full[slot]);
-    };
-    for (int cc = 0; cc < 2 && cc < nch; ++cc) produce(cc);
-    for (int c = 0; c < nch; ++c) {
-      // keep the ring two chunks ahead: chunk c + 2 goes into the slot chunk
-      // c - 1 used, once the builders have read it
-      if (c + 2 < nch) {
-        bool w = true;
-        if (c + 2 >= 3) {
-          if (lane == 0 && ok) w = mbar_wait(&ring_free[(c + 2) % 3], (uint32_t)(((c + 2) / 3 - 1) & 1), err, 16);
-          w = __shfl_sync(0xffffffffu, w ? 1 : 0, 0) != 0;
-        }
-        ok = ok && w;
-        if (ok) produce(c + 2);
-      }
-      if (lane == 0 && ok) {
-        const int s = c & 1;
-        ok = mbar_wait(&stage_full[s], (uint32_t)((c >> 1) & 1), err, 16);
-        // the first MMA of a run overwrites the accumulator: the previous run
-        // must have been added to the running sum
-        if (ok && c > 0 && c % kDrain == 0) ok = mbar_wait(acc_free, (uint32_t)((c / kDrain - 1) & 1), err, 16);
-        if (ok) {
-          tc_fence_after();
-          unsigned char* Ap = stage0 + s * kStage;
-          unsigned char* Bp = Ap + NS * kTcABytes;
-          constexpr int NP = NS == 2 ? 3 : 6;
-          constexpr int pi[6] = {0, 0, 1, 0, 2, 1};
-          constexpr int pj[6] = {0, 1, 0, 2, 0, 1};
-#pragma unroll
-          for (int ks = 0; ks < kTcKC / 16; ++ks) {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-              const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 32, 16, 512);
-              const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 32, 16, 512);
-              umma_bf16(taddr, ad, bd, idesc, ((c % kDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
-            }
-          }
-          umma_commit(&stage_free[s]);
-          if ((c + 1) % kDrain == 0 || c == nch - 1) umma_commit(acc_full);
-        }
-      }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-    }
-  } else {
-    // ---- builders (warps 0-15) ----
+  {
+    // ---- every warp builds; lane 0 of warp 15 also issues the MMAs ----
     // this thread's slice of the tile: TMEM lane quarter (warp % 4) and 64 of
     // the 256 columns (warp / 4); its running sum 256 columns further on
     const int q4 = warp & 3, h2 = warp >> 2;
     const uint32_t tcol = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 64);
+    const uint32_t idesc = tc_idesc();
     {
       float z[32];
 #pragma unroll
@@ -381,6 +332,31 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __
     const bool actB = bc.x >= 0;
     const int srcB1 = (actB ? bc.x : 0) * kTcRow + khB * 16, srcB2 = (actB ? bc.y : 0) * kTcRow + khB * 16;
     const int dstB0 = canon_off(rowB, 2 * khB), dstB1 = canon_off(rowB, 2 * khB + 1);
+    // copy slots: fields t / 8 and (t + 512) / 8, points 4 (t % 8) .. + 3
+    const int cf0 = tid >> 3, cf1 = (tid + kTcBuilders) >> 3, ck4 = (tid & 7) * 4;
+    const bool cp0 = cf0 < nf, cp1 = cf1 < nf;
+    const float* csrc0 = I + (size_t)(cp0 ? cf0 : 0) * N3;
+    const float* csrc1 = I + (size_t)(cp1 ? cf1 : 0) * N3;
+    const uint32_t cdst0 = smem_u32(Iring + cf0 * kTcRow + ck4), cdst1 = smem_u32(Iring + cf1 * kTcRow + ck4);
+    // chunk cc's field values into ring slot cc % 3 (16 bytes a copy; points
+    // past the slice end are zero-filled); the slot's mbarrier counts this
+    // thread's arrival when its copies have landed
+    auto prefetch = [&](int cc) {
+      const int slot = cc % 3;
+      const long long x = x0 + (long long)cc * kTcKC + ck4;
+      const int bytes = x + 4 <= xend ? 16 : (x < xend ? (int)(xend - x) * 4 : 0);
+      const long long xs = x < xend ? x : 0;
+      const uint32_t so = (uint32_t)(slot * ring * 4);
+      if (cp0)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(cdst0 + so), "l"(csrc0 + xs), "r"(bytes)
+                     : "memory");
+      if (cp1)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(cdst1 + so), "l"(csrc1 + xs), "r"(bytes)
+                     : "memory");
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&ring_full[slot]))
+                   : "memory");
+    };
+    for (int cc = 0; cc < 2 && cc < nch; ++cc) prefetch(cc);
     // add run r's tile to the running sum once its MMAs have completed (the
     // wait's outcome is made warp-uniform: tcgen05.ld is a warp-collective)
     auto drain = [&](int r) {
@@ -407,6 +383,12 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __
     };
     for (int c = 0; c < nch; ++c) {
       const int s = c & 1, slot = c % 3;
+      // chunk c + 2 goes into the slot chunk c - 1 used, once every builder has
+      // read it
+      if (c + 2 < nch) {
+        if (c + 2 >= 3 && ok) ok = mbar_wait(&ring_free[(c + 2) % 3], (uint32_t)(((c + 2) / 3 - 1) & 1), err, 16);
+        prefetch(c + 2);
+      }
       bool w = ok && mbar_wait(&ring_full[slot], (uint32_t)((c / 3) & 1), err, 16);
       // the MMAs that read this stage two chunks ago must have completed
       if (w && c >= 2) w = mbar_wait(&stage_free[s], (uint32_t)(((c - 2) >> 1) & 1), err, 16);
@@ -415,19 +397,10 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __
         unsigned char* Ap = stage0 + s * kStage;
         unsigned char* Bp = Ap + NS * kTcABytes;
         const float* Ist = Iring + slot * ring;
-        // points of the chunk past the slice end (its last chunk only) hold
-        // stale ring data: they enter as zeros
-        const long long xc = x0 + (long long)c * kTcKC;
-        const bool tail = xc + kTcKC > xend;
         if (actA) {
           const float4 p = *reinterpret_cast<const float4*>(Ist + srcA);
           const float4 q = *reinterpret_cast<const float4*>(Ist + srcA + 4);
-          float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
-          if (tail) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (xc + kgA * 8 + i >= xend) v[i] = 0.f;
-          }
+          const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
           uint4 parts[NS];
           split8<NS>(v, parts);
 #pragma unroll
@@ -440,13 +413,8 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __
             const float4 b1 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h + 4);
             const float4 c0 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h);
             const float4 c1 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h + 4);
-            float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
-                          b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
-            if (tail) {
-#pragma unroll
-              for (int i = 0; i < 8; ++i)
-                if (xc + khB * 16 + 8 * h + i >= xend) v[i] = 0.f;
-            }
+            const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
+                                b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
             uint4 parts[NS];
             split8<NS>(v, parts);
             const int d = h ? dstB1 : dstB0;
@@ -461,8 +429,38 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __
       mbar_arrive(&ring_free[slot]);
       // a run ended with chunk c - 1: its MMAs ran while this chunk was built
       if (c > 0 && c % kDrain == 0) drain(c / kDrain - 1);
+      if (warp == kTcIssueWarp) {
+        bool g = ok;
+        if (lane == 0 && g) {
+          g = mbar_wait(&stage_full[s], (uint32_t)((c >> 1) & 1), err, 16);
+          // the first MMA of a run overwrites the accumulator: the previous
+          // run must have been added to the running sum
+          if (g && c > 0 && c % kDrain == 0) g = mbar_wait(acc_free, (uint32_t)((c / kDrain - 1) & 1), err, 16);
+          if (g) {
+            tc_fence_after();
+            unsigned char* Ap = stage0 + s * kStage;
+            unsigned char* Bp = Ap + NS * kTcABytes;
+            constexpr int NP = NS == 2 ? 3 : 6;
+            constexpr int pi[6] = {0, 0, 1, 0, 2, 1};
+            constexpr int pj[6] = {0, 1, 0, 2, 0, 1};
+#pragma unroll
+            for (int ks = 0; ks < kTcKC / 16; ++ks) {
+#pragma unroll
+              for (int q = 0; q < NP; ++q) {
+                const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 32, 16, 512);
+                const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 32, 16, 512);
+                umma_bf16(taddr, ad, bd, idesc, ((c % kDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
+              }
+            }
+            umma_commit(&stage_free[s]);
+            if ((c + 1) % kDrain == 0 || c == nch - 1) umma_commit(acc_full);
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, g ? 1 : 0, 0) != 0;
+      }
     }
     if (nch > 0) drain((nch - 1) / kDrain);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     // the last drain waited for every MMA of the slice
     float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + lane) * kTcN + h2 * 64;
 #pragma unroll
