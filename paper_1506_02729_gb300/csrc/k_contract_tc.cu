@@ -50,6 +50,7 @@ constexpr int kTcM = 128;              // MMA rows (l, a)
 constexpr int kTcN = 256;              // MMA columns (pairs b >= c) per tile
 constexpr int kTcKC = 32;              // K points per chunk
 constexpr int kTcSliceTarget = 4096;   // chunks per K slice, at most (about)
+constexpr int kTcThreads = 512;
 constexpr int kTcABytes = kTcM * kTcKC * 2;    // one BF16 operand tile: 8 KB
 constexpr int kTcBBytes = kTcN * kTcKC * 2;    // 16 KB
 template <int NS>
@@ -234,243 +235,196 @@ __device__ __forceinline__ void split8(const float* v, uint4* out) {
 // pairs: (b, c) of the tile's columns (b < 0 marks padding); part layout
 // [slice][tile][128][256] FP32.
 //
-// Pipeline on mbarriers, without block barriers: the 16 warps copy the raw
-// field chunks into a 3-slot ring (cp.async, two chunks ahead) and build the
-// operands, and lane 0 of warp 15, after its own share of a chunk, issues the
-// chunk's MMAs once every warp has signalled the stage full; each warp goes on
-// to the next chunk as soon as its own share is done and the stage it writes
-// has been released by the MMAs, so the build of one chunk overlaps the MMAs
-// of the previous one.
-//   ring_full[k]   every builder's copies into ring slot k have landed (512
-//                  cp.async-tracked arrivals)
-//   ring_free[k]   the builders have read ring slot k (512 arrivals)
-//   stage_full[s]  the builders have written operand stage s (512 arrivals)
-//   stage_free[s]  the MMAs that read stage s have completed (tcgen05.commit)
-//   acc_full       the MMAs of an accumulation run have completed (commit)
-//   acc_free       the builders have added the run to the running sum (512)
-// Every builder has a fixed share of each chunk: A row t % 128, k-group t / 128
+// Every thread has a fixed share of each chunk: A row t % 128, k-group t / 128
 // (8 points); B row t % 256, k-groups 2 (t / 256) and 2 (t / 256) + 1 (16
-// points).  Rows of A beyond nf and padding columns of B are zeroed once in
-// both stages and never rewritten.  The running FP32 sum of the drained tiles
-// sits in tensor memory columns 256-511.  Every wait is bounded; a thread
-// whose wait gives up stops working but keeps to the loop, and the host
-// reports the error flag.
-constexpr int kTcBuilders = 512;
-constexpr int kTcThreadsWS = kTcBuilders;
-constexpr int kTcIssueWarp = 15;  // the warp one of whose lanes issues the MMAs
-
+// points); its field copies are f = i / 8, points 4 (i % 8) of i = t, t + 512.
+// Offsets and pair indices are therefore computed once.  Rows of A beyond nf
+// and padding columns of B are zeroed once in both stages and never
+// rewritten.  The running FP32 sum of the drained tiles sits in tensor memory
+// columns 256-511 (each drain: tcgen05.ld tile and sum, add, tcgen05.st), so
+// no accumulator occupies registers through the chunk loop.
 template <int NS>
-__global__ void __launch_bounds__(kTcThreadsWS, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
-                                                                 int S, const short2* __restrict__ pairs,
-                                                                 int npairs, int chunks, float* __restrict__ part,
-                                                                 int* __restrict__ err) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const float* __restrict__ I, long long N3, int nf,
+                                                               int S, const short2* __restrict__ pairs, int npairs,
+                                                               int chunks, float* __restrict__ part,
+                                                               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   constexpr int kStage = tc_stage_bytes<NS>();
   unsigned char* stage0 = smraw;                                  // 2 stages: A parts, then B parts
-  float* Iring = reinterpret_cast<float*>(smraw + 2 * kStage);   // 3 x [nf][kTcRow]
+  float* Iring = reinterpret_cast<float*>(smraw + 2 * kStage);   // 3 x [nf][kTcRow], prefetched 2 chunks ahead
   const int ring = nf * kTcRow;                                   // floats per ring slot
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Iring + 3 * ring);
-  uint64_t* ring_full = bars;        // [3]
-  uint64_t* ring_free = bars + 3;    // [3]
-  uint64_t* stage_full = bars + 6;   // [2]
-  uint64_t* stage_free = bars + 8;   // [2]
-  uint64_t* acc_full = bars + 10;
-  uint64_t* acc_free = bars + 11;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 12);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Iring + 3 * ring);  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int tile = blockIdx.x, slice = blockIdx.y, ntiles = gridDim.x;
-  for (int i = tid; i < 2 * kStage / 16; i += kTcThreadsWS) reinterpret_cast<uint4*>(stage0)[i] = make_uint4(0, 0, 0, 0);
-  fence_proxy_async();  // the zeros that padding rows keep, before any MMA reads them
+  // zero both stages once: rows that are never written stay zero
+  for (int i = tid; i < 2 * kStage / 16; i += kTcThreads) reinterpret_cast<uint4*>(stage0)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) {
     tmem_alloc(tslot, 2 * kTcN);
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int k = 0; k < 3; ++k) {
-      mbar_init(&ring_full[k], kTcBuilders);
-      mbar_init(&ring_free[k], kTcBuilders);
-    }
-    for (int k = 0; k < 2; ++k) {
-      mbar_init(&stage_full[k], kTcBuilders);
-      mbar_init(&stage_free[k], 1);
-    }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_free, kTcBuilders);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *tslot;
+  // this thread's slice of the tile: TMEM lane quarter (warp % 4) and 64 of
+  // the 256 columns (warp / 4); its running sum 256 columns further on
+  const int q4 = warp & 3, h2 = warp >> 2;
+  const uint32_t tcol = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 64);
+  {
+    float z[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z[i] = 0.f;
+    tmem_st32(tcol + kTcN, z);
+    tmem_st32(tcol + kTcN + 32, z);
+  }
   const long long x0 = (long long)slice * kTcKC * chunks;
   const long long xend = (x0 + (long long)kTcKC * chunks < N3) ? x0 + (long long)kTcKC * chunks : N3;
   const int nch = x0 < xend ? (int)((xend - x0 + kTcKC - 1) / kTcKC) : 0;
-  constexpr int kDrain = tc_drain<NS>();
+  const uint32_t idesc = tc_idesc();
+  // fixed roles
+  const int rowA = tid & (kTcM - 1), kgA = tid / kTcM;
+  const bool actA = rowA < nf;
+  const int srcA = rowA * kTcRow + kgA * 8, dstA = canon_off(rowA, kgA);
+  const int rowB = tid & (kTcN - 1), khB = tid / kTcN;
+  short2 bc = make_short2(-1, -1);
+  if (tile * kTcN + rowB < npairs) bc = pairs[tile * kTcN + rowB];
+  const bool actB = bc.x >= 0;
+  const int srcB1 = (actB ? bc.x : 0) * kTcRow + khB * 16, srcB2 = (actB ? bc.y : 0) * kTcRow + khB * 16;
+  const int dstB0 = canon_off(rowB, 2 * khB), dstB1 = canon_off(rowB, 2 * khB + 1);
+  const int cf0 = tid >> 3, cf1 = (tid + kTcThreads) >> 3, ck4 = (tid & 7) * 4;
+  const bool cp0 = cf0 < nf, cp1 = cf1 < nf;
+  const float* csrc0 = I + (size_t)(cp0 ? cf0 : 0) * N3;
+  const float* csrc1 = I + (size_t)(cp1 ? cf1 : 0) * N3;
+  const uint32_t cdst0 = smem_u32(Iring + cf0 * kTcRow + ck4), cdst1 = smem_u32(Iring + cf1 * kTcRow + ck4);
   bool ok = true;
-
-  {
-    // ---- every warp builds; lane 0 of warp 15 also issues the MMAs ----
-    // this thread's slice of the tile: TMEM lane quarter (warp % 4) and 64 of
-    // the 256 columns (warp / 4); its running sum 256 columns further on
-    const int q4 = warp & 3, h2 = warp >> 2;
-    const uint32_t tcol = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h2 * 64);
-    const uint32_t idesc = tc_idesc();
-    {
-      float z[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) z[i] = 0.f;
-      tmem_st32(tcol + kTcN, z);
-      tmem_st32(tcol + kTcN + 32, z);
-    }
-    // fixed roles
-    const int rowA = tid & (kTcM - 1), kgA = tid / kTcM;
-    const bool actA = rowA < nf;
-    const int srcA = rowA * kTcRow + kgA * 8, dstA = canon_off(rowA, kgA);
-    const int rowB = tid & (kTcN - 1), khB = tid / kTcN;
-    short2 bc = make_short2(-1, -1);
-    if (tile * kTcN + rowB < npairs) bc = pairs[tile * kTcN + rowB];
-    const bool actB = bc.x >= 0;
-    const int srcB1 = (actB ? bc.x : 0) * kTcRow + khB * 16, srcB2 = (actB ? bc.y : 0) * kTcRow + khB * 16;
-    const int dstB0 = canon_off(rowB, 2 * khB), dstB1 = canon_off(rowB, 2 * khB + 1);
-    // copy slots: fields t / 8 and (t + 512) / 8, points 4 (t % 8) .. + 3
-    const int cf0 = tid >> 3, cf1 = (tid + kTcBuilders) >> 3, ck4 = (tid & 7) * 4;
-    const bool cp0 = cf0 < nf, cp1 = cf1 < nf;
-    const float* csrc0 = I + (size_t)(cp0 ? cf0 : 0) * N3;
-    const float* csrc1 = I + (size_t)(cp1 ? cf1 : 0) * N3;
-    const uint32_t cdst0 = smem_u32(Iring + cf0 * kTcRow + ck4), cdst1 = smem_u32(Iring + cf1 * kTcRow + ck4);
-    // chunk cc's field values into ring slot cc % 3 (16 bytes a copy; points
-    // past the slice end are zero-filled); the slot's mbarrier counts this
-    // thread's arrival when its copies have landed
-    auto prefetch = [&](int cc) {
-      const int slot = cc % 3;
+  // asynchronous copies of a chunk's field values into its ring slot (16 bytes
+  // each; points past the slice are zero-filled)
+  auto prefetch = [&](int cc) {
+    if (cc < nch) {
       const long long x = x0 + (long long)cc * kTcKC + ck4;
       const int bytes = x + 4 <= xend ? 16 : (x < xend ? (int)(xend - x) * 4 : 0);
       const long long xs = x < xend ? x : 0;
-      const uint32_t so = (uint32_t)(slot * ring * 4);
+      const uint32_t so = (uint32_t)((cc % 3) * ring * 4);
       if (cp0)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(cdst0 + so), "l"(csrc0 + xs), "r"(bytes)
                      : "memory");
       if (cp1)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(cdst1 + so), "l"(csrc1 + xs), "r"(bytes)
                      : "memory");
-      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&ring_full[slot]))
-                   : "memory");
-    };
-    for (int cc = 0; cc < 2 && cc < nch; ++cc) prefetch(cc);
-    // add run r's tile to the running sum once its MMAs have completed (the
-    // wait's outcome is made warp-uniform: tcgen05.ld is a warp-collective)
-    auto drain = [&](int r) {
-      bool w = ok && mbar_wait(acc_full, (uint32_t)(r & 1), err, 16);
-      w = __all_sync(0xffffffffu, w);
-      ok = ok && w;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // drain of the run ending with chunk cl: wait for that chunk's MMAs, add
+  // the tile to the running sum (ok is made block-uniform: tcgen05.ld is a
+  // warp-collective)
+  constexpr int kDrain = tc_drain<NS>();
+  auto drain = [&](int cl) {
+    const bool w = ok && mbar_wait(&bar[cl & 1], (uint32_t)((cl >> 1) & 1), err, 16);
+    ok = __syncthreads_and(w) != 0;
+    tc_fence_after();
+    if (ok) {
+      // per 32 columns: both loads, one wait, add, store; one store wait
+#pragma unroll
+      for (int cg = 0; cg < 2; ++cg) {
+        uint32_t v[32], u[32];
+        tmem_ld32_async(tcol + cg * 32, v);
+        tmem_ld32_async(tcol + kTcN + cg * 32, u);
+        tmem_wait_ld(v);
+        tmem_wait_ld(u);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) u[i] = __float_as_uint(__uint_as_float(u[i]) + __uint_as_float(v[i]));
+        tmem_st32_async(tcol + kTcN + cg * 32, u);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+  };
+  prefetch(0);
+  prefetch(1);
+  for (int c = 0; c < nch; ++c) {
+    const int s = c & 1;
+    unsigned char* st = stage0 + s * kStage;
+    unsigned char* Ap = st;                      // NS tiles of kTcABytes
+    unsigned char* Bp = st + NS * kTcABytes;     // NS tiles of kTcBBytes
+    prefetch(c + 2);
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+    const float* Ist = Iring + (c % 3) * ring;
+    // the MMAs that read this stage two chunks ago must have finished
+    if (c >= 2 && ok) ok = mbar_wait(&bar[s], (uint32_t)(((c - 2) >> 1) & 1), err, 16);
+    ok = __syncthreads_and(ok) != 0;
+    // A: rows (l, a) = field index; a quarter-warp stores 8 consecutive rows
+    // of one k-group (one contiguous, conflict-free 128-byte span)
+    if (actA) {
+      const float4 p = *reinterpret_cast<const float4*>(Ist + srcA);
+      const float4 q = *reinterpret_cast<const float4*>(Ist + srcA + 4);
+      const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+      uint4 parts[NS];
+      split8<NS>(v, parts);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Ap + k * kTcABytes + dstA) = parts[k];
+    }
+    // B: rows = pairs (b, c) of this tile, products of the l = 0 fields
+    if (actB) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 b0 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h);
+        const float4 b1 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h + 4);
+        const float4 c0 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h);
+        const float4 c1 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h + 4);
+        const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
+                            b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
+        uint4 parts[NS];
+        split8<NS>(v, parts);
+        const int d = h ? dstB1 : dstB0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Bp + k * kTcBBytes + d) = parts[k];
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    // a run ended with chunk c - 1: its MMAs ran while this chunk was built,
+    // so the tensor pipe waits only for the drain, not for a build
+    if (c > 0 && c % kDrain == 0) drain(c - 1);
+    if (tid == 0 && ok) {
       tc_fence_after();
-      if (ok) {
+      // products (i, j) of A part i and B part j whose order is at most 2^-16
+      constexpr int NP = NS == 2 ? 3 : 6;
+      constexpr int pi[6] = {0, 0, 1, 0, 2, 1};
+      constexpr int pj[6] = {0, 1, 0, 2, 0, 1};
 #pragma unroll
-        for (int cg = 0; cg < 2; ++cg) {
-          uint32_t v[32], u[32];
-          tmem_ld32_async(tcol + cg * 32, v);
-          tmem_ld32_async(tcol + kTcN + cg * 32, u);
-          tmem_wait_ld(v);
-          tmem_wait_ld(u);
+      for (int ks = 0; ks < kTcKC / 16; ++ks) {
+        // K step ks covers k-groups 2 ks and 2 ks + 1 (32 bytes further along the rows)
 #pragma unroll
-          for (int i = 0; i < 32; ++i) u[i] = __float_as_uint(__uint_as_float(u[i]) + __uint_as_float(v[i]));
-          tmem_st32_async(tcol + kTcN + cg * 32, u);
-        }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      }
-      tc_fence_before();
-      mbar_arrive(acc_free);
-    };
-    for (int c = 0; c < nch; ++c) {
-      const int s = c & 1, slot = c % 3;
-      // chunk c + 2 goes into the slot chunk c - 1 used, once every builder has
-      // read it
-      if (c + 2 < nch) {
-        if (c + 2 >= 3 && ok) ok = mbar_wait(&ring_free[(c + 2) % 3], (uint32_t)(((c + 2) / 3 - 1) & 1), err, 16);
-        prefetch(c + 2);
-      }
-      bool w = ok && mbar_wait(&ring_full[slot], (uint32_t)((c / 3) & 1), err, 16);
-      // the MMAs that read this stage two chunks ago must have completed
-      if (w && c >= 2) w = mbar_wait(&stage_free[s], (uint32_t)(((c - 2) >> 1) & 1), err, 16);
-      ok = ok && w;
-      if (ok) {
-        unsigned char* Ap = stage0 + s * kStage;
-        unsigned char* Bp = Ap + NS * kTcABytes;
-        const float* Ist = Iring + slot * ring;
-        if (actA) {
-          const float4 p = *reinterpret_cast<const float4*>(Ist + srcA);
-          const float4 q = *reinterpret_cast<const float4*>(Ist + srcA + 4);
-          const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
-          uint4 parts[NS];
-          split8<NS>(v, parts);
-#pragma unroll
-          for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Ap + k * kTcABytes + dstA) = parts[k];
-        }
-        if (actB) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float4 b0 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h);
-            const float4 b1 = *reinterpret_cast<const float4*>(Ist + srcB1 + 8 * h + 4);
-            const float4 c0 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h);
-            const float4 c1 = *reinterpret_cast<const float4*>(Ist + srcB2 + 8 * h + 4);
-            const float v[8] = {b0.x * c0.x, b0.y * c0.y, b0.z * c0.z, b0.w * c0.w,
-                                b1.x * c1.x, b1.y * c1.y, b1.z * c1.z, b1.w * c1.w};
-            uint4 parts[NS];
-            split8<NS>(v, parts);
-            const int d = h ? dstB1 : dstB0;
-#pragma unroll
-            for (int k = 0; k < NS; ++k) *reinterpret_cast<uint4*>(Bp + k * kTcBBytes + d) = parts[k];
-          }
+        for (int q = 0; q < NP; ++q) {
+          const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 32, 16, 512);
+          const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 32, 16, 512);
+          umma_bf16(taddr, ad, bd, idesc, ((c % kDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
         }
       }
-      // the stage's generic writes before the MMAs' async-proxy reads
-      fence_proxy_async();
-      mbar_arrive(&stage_full[s]);
-      mbar_arrive(&ring_free[slot]);
-      // a run ended with chunk c - 1: its MMAs ran while this chunk was built
-      if (c > 0 && c % kDrain == 0) drain(c / kDrain - 1);
-      if (warp == kTcIssueWarp) {
-        bool g = ok;
-        if (lane == 0 && g) {
-          g = mbar_wait(&stage_full[s], (uint32_t)((c >> 1) & 1), err, 16);
-          // the first MMA of a run overwrites the accumulator: the previous
-          // run must have been added to the running sum
-          if (g && c > 0 && c % kDrain == 0) g = mbar_wait(acc_free, (uint32_t)((c / kDrain - 1) & 1), err, 16);
-          if (g) {
-            tc_fence_after();
-            unsigned char* Ap = stage0 + s * kStage;
-            unsigned char* Bp = Ap + NS * kTcABytes;
-            constexpr int NP = NS == 2 ? 3 : 6;
-            constexpr int pi[6] = {0, 0, 1, 0, 2, 1};
-            constexpr int pj[6] = {0, 1, 0, 2, 0, 1};
-#pragma unroll
-            for (int ks = 0; ks < kTcKC / 16; ++ks) {
-#pragma unroll
-              for (int q = 0; q < NP; ++q) {
-                const uint64_t ad = sdesc(Ap + pi[q] * kTcABytes + ks * 32, 16, 512);
-                const uint64_t bd = sdesc(Bp + pj[q] * kTcBBytes + ks * 32, 16, 512);
-                umma_bf16(taddr, ad, bd, idesc, ((c % kDrain) > 0 || ks > 0 || q > 0) ? 1u : 0u);
-              }
-            }
-            umma_commit(&stage_free[s]);
-            if ((c + 1) % kDrain == 0 || c == nch - 1) umma_commit(acc_full);
-          }
-        }
-        ok = __shfl_sync(0xffffffffu, g ? 1 : 0, 0) != 0;
-      }
+      umma_commit(&bar[s]);
     }
-    if (nch > 0) drain((nch - 1) / kDrain);
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    // the last drain waited for every MMA of the slice
-    float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + lane) * kTcN + h2 * 64;
+    // No barrier here: the next chunk builds the other stage, which the MMAs
+    // of chunk c - 1 have released (mbarrier wait), and reads a ring slot the
+    // copies of chunk c + 1 filled; stage s is rebuilt only after this commit.
+  }
+  if (nch > 0) drain(nch - 1);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  // the last drain waited for every MMA of the slice
+  float* dst = part + (((size_t)slice * ntiles + tile) * kTcM + q4 * 32 + (tid & 31)) * kTcN + h2 * 64;
 #pragma unroll
-    for (int cg = 0; cg < 2; ++cg) {
-      float u[32];
-      tmem_ld32(tcol + kTcN + cg * 32, u);
+  for (int cg = 0; cg < 2; ++cg) {
+    float u[32];
+    tmem_ld32(tcol + kTcN + cg * 32, u);
 #pragma unroll
-      for (int i = 0; i < 32; i += 4)
-        *reinterpret_cast<float4*>(dst + cg * 32 + i) = make_float4(u[i], u[i + 1], u[i + 2], u[i + 3]);
-    }
+    for (int i = 0; i < 32; i += 4)
+      *reinterpret_cast<float4*>(dst + cg * 32 + i) = make_float4(u[i], u[i + 1], u[i + 2], u[i + 3]);
   }
   tc_fence_before();
   __syncthreads();
@@ -495,7 +449,7 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int nslices, int nti
 
 template <int NS>
 static size_t tc_smem_bytes(int nf) {
-  return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * (size_t)nf * kTcRow + 12 * sizeof(uint64_t) + 16;
+  return 2 * (size_t)tc_stage_bytes<NS>() + 3 * sizeof(float) * (size_t)nf * kTcRow + 2 * sizeof(uint64_t) + 16;
 }
 
 cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, const short2* pairs, int npairs,
@@ -505,11 +459,11 @@ cudaError_t launch_contract_tc(const float* I, long long N3, int nf, int S, cons
   if (nsplit == 2) {
     const size_t sm = tc_smem_bytes<2>(nf);
     raise_smem_limit((const void*)k_contract_tc<2>, sm);
-    k_contract_tc<2><<<grid, kTcThreadsWS, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
+    k_contract_tc<2><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   } else {
     const size_t sm = tc_smem_bytes<3>(nf);
     raise_smem_limit((const void*)k_contract_tc<3>, sm);
-    k_contract_tc<3><<<grid, kTcThreadsWS, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
+    k_contract_tc<3><<<grid, kTcThreads, sm, s>>>(I, N3, nf, S, pairs, npairs, chunks, part, err);
   }
   return cudaGetLastError();
 }
