@@ -36,9 +36,14 @@ def _abs_fields(gal, ran, geom, alpha):
     return A, Aw
 
 
-def _plan(geom):
+def _plan(geom, bisp=True):
+    """A plan with the bispectrum outputs (F and F^w gridded together) or,
+    bisp=False, a power-spectrum plan (F alone: the accumulation kernel's
+    single-grid form)."""
     fkp = _fkp()
     kf = 2 * math.pi / geom["L"]
+    if not bisp:
+        return fkp.Plan(geom, (0.5 * kf, kf, 8))
     return fkp.Plan(geom, (0.5 * kf, kf, 8), bshells=(3, 3, 3, 4), want=B_ALL)
 
 
@@ -79,7 +84,25 @@ def test_grid_matches_oracle_assignment(assign, interlace):
     assert np.count_nonzero(A) > 50000
 
 
-def test_grid_does_not_depend_on_object_order_or_accumulation_form():
+@pytest.mark.parametrize("assign", [2, 3], ids=["cic", "tsc"])
+def test_power_plan_grid_matches_oracle(assign):
+    """A power-spectrum plan grids F alone (the accumulation kernel's
+    single-grid form, the one the power-spectrum path times): cell by cell
+    against the oracle's assignment, and bit for bit the F of a bispectrum
+    plan, which grids F and F^w together."""
+    sv, gal, ran, geom = _exact_setup(assign)
+    F = _plan(geom, bisp=False).grid(_dev(gal), _dev(ran))
+    Fb, _ = _plan(geom).grid(_dev(gal), _dev(ran), with_w=True)
+    assert np.array_equal(F, Fb)
+    Fo, _, sc = op.fkp_grids(gal, ran, geom, with_w2=False)
+    A, _ = _abs_fields(gal, ran, geom, sc["alpha"])
+    assert np.all(np.abs(F * UNIT - Fo) <= REL * A + 1e-11), float(np.max(np.abs(F * UNIT - Fo) - REL * A))
+    assert np.all(F[A == 0] == 0)
+    assert np.count_nonzero(A) > 50000
+
+
+@pytest.mark.parametrize("bisp", [True, False], ids=["F_and_Fw", "F_alone"])
+def test_grid_does_not_depend_on_object_order_or_accumulation_form(bisp):
     """The gridding adds each tap's rounded value as an integer: as two 32-bit
     words, or as one 64-bit word for a work item whose sum of |w| passes 1000.
     Galaxy weights k/1024 (k uniform in 0..250, mean 0.122) and randoms of
@@ -96,19 +119,24 @@ def test_grid_does_not_depend_on_object_order_or_accumulation_form():
     r = np.random.default_rng(1506)
     gal["w"] = (r.integers(0, 251, len(gal["x"])) / 1024.0).astype(np.float32)
     ran["w"] = np.ones(len(ran["x"]), dtype=np.float32)
-    plan = _plan(geom)
-    F1, Fw1 = plan.grid(_dev(gal), _dev(ran), with_w=True)
+    plan = _plan(geom, bisp=bisp)
+
+    def grid(g, rr):
+        return plan.grid(g, rr, with_w=True) if bisp else (plan.grid(g, rr), None)
+
+    F1, Fw1 = grid(_dev(gal), _dev(ran))
     pg, pr = r.permutation(len(gal["x"])), r.permutation(len(ran["x"]))
     gal2 = {k: v[pg] for k, v in gal.items()}
     ran2 = {k: v[pr] for k, v in ran.items()}
-    F2, Fw2 = plan.grid(_dev(gal2), _dev(ran2), with_w=True)
-    F3, Fw3 = plan.grid(gal2, ran2, with_w=True)  # host catalogs
-    assert np.array_equal(F1, F2) and np.array_equal(Fw1, Fw2)
-    assert np.array_equal(F1, F3) and np.array_equal(Fw1, Fw3)
+    F2, Fw2 = grid(_dev(gal2), _dev(ran2))
+    F3, Fw3 = grid(gal2, ran2)  # host catalogs
+    assert np.array_equal(F1, F2) and np.array_equal(F1, F3)
     Fo, Fwo, sc = op.fkp_grids(gal, ran, geom, with_w2=True)
     A, Aw = _abs_fields(gal, ran, geom, sc["alpha"])
     assert np.all(np.abs(F1 * UNIT - Fo) <= REL * A + 1e-11)
-    assert np.all(np.abs(Fw1 * UNIT - Fwo) <= REL * Aw + 1e-11)
+    if bisp:
+        assert np.array_equal(Fw1, Fw2) and np.array_equal(Fw1, Fw3)
+        assert np.all(np.abs(Fw1 * UNIT - Fwo) <= REL * Aw + 1e-11)
 
 
 def test_grid_rejects_bad_requests():
