@@ -294,6 +294,67 @@ __device__ __forceinline__ float2* fft_ct(float2* a, float2* b, const float2* tw
   return fft_ct_run<N, P, NT, DIR, 0, 1, SWZ, RX>(a, b, tw);
 }
 
+// Stages S .. SEND-1 of fft_ct_run; returns the buffer holding their result.
+template <int N, int P, int NT, int DIR, int S, int NS, int SEND>
+__device__ __forceinline__ float2* fft_ct_upto(float2* a, float2* b, const float2* tw) {
+  if constexpr (S == SEND) {
+    return a;
+  } else {
+    constexpr int R = radix_at(N, S);
+    fft_ct_stage<N, P, NT, DIR, R, NS, false>(a, b, tw);
+    __syncthreads();
+    return fft_ct_upto<N, P, NT, DIR, S + 1, NS * R, SEND>(b, a, tw);
+  }
+}
+
+__host__ __device__ constexpr int radix_prod(int n, int s) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= radix_at(n, i);
+  return p;
+}
+
+// Whether fft_ct_fused applies: the last stage's butterflies per pencil (N/R)
+// come in whole rounds of the NT/P threads of a pencil.
+template <int N, int P, int NT>
+__host__ __device__ constexpr bool fft_fusable() {
+  return N > 0 && radix_count(N) >= 2 && (N / radix_at(N, radix_count(N) - 1)) % (NT / P) == 0;
+}
+
+// The transform of fft_ct (natural interleave, no swizzle) whose last stage
+// hands its outputs to the caller instead of storing them: thread (p, y)
+// receives output index y + i NT/P of pencil p as f(i, value), for every i
+// in [0, N P / NT), each exactly once, in registers.  The earlier stages run
+// as in fft_ct and end with a __syncthreads(); the last one does not store,
+// so the caller synchronises before the buffers are reused.
+template <int N, int P, int NT, int DIR, class F>
+__device__ __forceinline__ void fft_ct_fused(float2* a, float2* b, const float2* tw, F&& f) {
+  static_assert(fft_fusable<N, P, NT>(), "the last stage's outputs do not map onto the threads' runs");
+  constexpr int SL = radix_count(N) - 1;
+  constexpr int R = radix_at(N, SL);
+  constexpr int NS = radix_prod(N, SL);  // = N / R
+  constexpr int NB = N / R;
+  constexpr int JT = NT / P;
+  const float2* src = fft_ct_upto<N, P, NT, DIR, 0, 1, SL>(a, b, tw);
+  const int p = threadIdx.x;
+#pragma unroll
+  for (int j0 = 0; j0 < NB; j0 += JT) {
+    // last stage: k = j mod NS = j, outputs j + r NS
+    const int j = j0 + (int)threadIdx.y;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[ilv<P, false>(j + r * NB, p)];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = tw[r * j * (N / (NS * R))];
+      if (DIR > 0) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+    dftR<R, DIR>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) f((j0 + r * NS) / JT, v[r]);
+  }
+}
+
 // Runtime-N version on the same interleaved layout (sizes without a
 // compiled specialisation).
 template <int R, int DIR, bool SWZ>

@@ -89,28 +89,37 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
         mbar_expect_tx(&bar[cur ^ 1], bytes);
         tma_load_1d(cur ? buf0 : buf1, src_of(mt.s_field[s2][m2]), bytes, &bar[cur ^ 1]);
       }
-      mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 4);
-      const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
       // coefficients a[o][j] of n_y^j for this member and column
       float a[2][5];
 #pragma unroll
       for (int o = 0; o < 2; ++o)
 #pragma unroll
         for (int j = 0; j < 5; ++j) a[o][j] = coef[(it * 10 + o * 5 + j) * kT + c];
-#pragma unroll
-      for (int i = 0; i < PassShape<NT>::kRL; ++i) {
+      // the member's value at k_y = i kRun + run, times its polynomials in n_y,
+      // joins the thread's sums
+      auto accumulate = [&](int i, float2 v) {
         const int ky = i * PassShape<NT>::kRun + run;
-        if (i < rl && ky < N) {
-          const float ny = (float)smode(ky, N);
-          const float2 v = R[ky * kT + c];
-          const float s0 = fmaf(fmaf(fmaf(fmaf(a[0][4], ny, a[0][3]), ny, a[0][2]), ny, a[0][1]), ny, a[0][0]);
-          acc0[i].x = fmaf(s0, v.x, acc0[i].x);
-          acc0[i].y = fmaf(s0, v.y, acc0[i].y);
-          if (nout > 1) {
-            const float s1 = fmaf(fmaf(fmaf(fmaf(a[1][4], ny, a[1][3]), ny, a[1][2]), ny, a[1][1]), ny, a[1][0]);
-            acc1[i].x = fmaf(s1, v.x, acc1[i].x);
-            acc1[i].y = fmaf(s1, v.y, acc1[i].y);
-          }
+        const float ny = (float)smode(ky, N);
+        const float s0 = fmaf(fmaf(fmaf(fmaf(a[0][4], ny, a[0][3]), ny, a[0][2]), ny, a[0][1]), ny, a[0][0]);
+        acc0[i].x = fmaf(s0, v.x, acc0[i].x);
+        acc0[i].y = fmaf(s0, v.y, acc0[i].y);
+        if (nout > 1) {
+          const float s1 = fmaf(fmaf(fmaf(fmaf(a[1][4], ny, a[1][3]), ny, a[1][2]), ny, a[1][1]), ny, a[1][0]);
+          acc1[i].x = fmaf(s1, v.x, acc1[i].x);
+          acc1[i].y = fmaf(s1, v.y, acc1[i].y);
+        }
+      };
+      mbar_wait(&bar[cur], (uint32_t)((it >> 1) & 1), err, 4);
+      if constexpr (fft_fusable<N_, kT, NT>()) {
+        // the last FFT stage's butterflies produce exactly this thread's k_y
+        // (y + i kRun): they are summed from registers, never stored
+        fft_ct_fused<N_, kT, NT, -1>(bc, work, tw, accumulate);
+      } else {
+        const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
+#pragma unroll
+        for (int i = 0; i < PassShape<NT>::kRL; ++i) {
+          const int ky = i * PassShape<NT>::kRun + run;
+          if (i < rl && ky < N) accumulate(i, R[ky * kT + c]);
         }
       }
       __syncthreads();
