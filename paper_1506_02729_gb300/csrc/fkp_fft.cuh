@@ -295,15 +295,15 @@ __device__ __forceinline__ float2* fft_ct(float2* a, float2* b, const float2* tw
 }
 
 // Stages S .. SEND-1 of fft_ct_run; returns the buffer holding their result.
-template <int N, int P, int NT, int DIR, int S, int NS, int SEND>
+template <int N, int P, int NT, int DIR, int S, int NS, int SEND, bool SWZ, bool RX>
 __device__ __forceinline__ float2* fft_ct_upto(float2* a, float2* b, const float2* tw) {
   if constexpr (S == SEND) {
     return a;
   } else {
     constexpr int R = radix_at(N, S);
-    fft_ct_stage<N, P, NT, DIR, R, NS, false>(a, b, tw);
+    fft_ct_stage<N, P, NT, DIR, R, NS, SWZ, (RX && (S > 0)), RX>(a, b, tw);
     __syncthreads();
-    return fft_ct_upto<N, P, NT, DIR, S + 1, NS * R, SEND>(b, a, tw);
+    return fft_ct_upto<N, P, NT, DIR, S + 1, NS * R, SEND, SWZ, RX>(b, a, tw);
   }
 }
 
@@ -320,21 +320,24 @@ __host__ __device__ constexpr bool fft_fusable() {
   return N > 0 && radix_count(N) >= 2 && (N / radix_at(N, radix_count(N) - 1)) % (NT / P) == 0;
 }
 
-// The transform of fft_ct (natural interleave, no swizzle) whose last stage
-// hands its outputs to the caller instead of storing them: thread (p, y)
-// receives output index y + i NT/P of pencil p as f(i, value), for every i
-// in [0, N P / NT), each exactly once, in registers.  The earlier stages run
-// as in fft_ct and end with a __syncthreads(); the last one does not store,
-// so the caller synchronises before the buffers are reused.
-template <int N, int P, int NT, int DIR, class F>
-__device__ __forceinline__ void fft_ct_fused(float2* a, float2* b, const float2* tw, F&& f) {
+// The transform of fft_ct<N, P, NT, DIR, SWZ, RX> whose last stage hands its
+// outputs to the caller instead of storing them: thread (p, y) receives
+// output index y + i NT/P of pencil p as f(i, value), for every i in
+// [0, N P / NT), each exactly once, in registers.  The earlier stages run as
+// in fft_ct and end with a __syncthreads(); the last one reads the buffer
+// returned in *last_src and stores nothing, so the other buffer is free and
+// the caller synchronises before either is reused.
+template <int N, int P, int NT, int DIR, bool SWZ, bool RX, class F>
+__device__ __forceinline__ void fft_ct_fused(float2* a, float2* b, const float2* tw, F&& f,
+                                             const float2** last_src = nullptr) {
   static_assert(fft_fusable<N, P, NT>(), "the last stage's outputs do not map onto the threads' runs");
   constexpr int SL = radix_count(N) - 1;
   constexpr int R = radix_at(N, SL);
   constexpr int NS = radix_prod(N, SL);  // = N / R
   constexpr int NB = N / R;
   constexpr int JT = NT / P;
-  const float2* src = fft_ct_upto<N, P, NT, DIR, 0, 1, SL>(a, b, tw);
+  const float2* src = fft_ct_upto<N, P, NT, DIR, 0, 1, SL, SWZ, RX>(a, b, tw);
+  if (last_src) *last_src = src;
   const int p = threadIdx.x;
 #pragma unroll
   for (int j0 = 0; j0 < NB; j0 += JT) {
@@ -342,7 +345,7 @@ __device__ __forceinline__ void fft_ct_fused(float2* a, float2* b, const float2*
     const int j = j0 + (int)threadIdx.y;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[ilv<P, false>(j + r * NB, p)];
+    for (int r = 0; r < R; ++r) v[r] = src[ilvx<P, SWZ, RX>(j + r * NB, p)];
 #pragma unroll
     for (int r = 1; r < R; ++r) {
       float2 w = tw[r * j * (N / (NS * R))];

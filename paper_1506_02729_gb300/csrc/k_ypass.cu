@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(NT, PassShape<NT>::kMinBlocks) k_ypass2(const 
       if constexpr (fft_fusable<N_, kT, NT>()) {
         // the last FFT stage's butterflies produce exactly this thread's k_y
         // (y + i kRun): they are summed from registers, never stored
-        fft_ct_fused<N_, kT, NT, -1>(bc, work, tw, accumulate);
+        fft_ct_fused<N_, kT, NT, -1, false, false>(bc, work, tw, accumulate);
       } else {
         const float2* R = fft_any<N_, kT, NT, -1>(bc, work, fp, tw);
 #pragma unroll

@@ -132,6 +132,38 @@ def test_every_pass_schedule_matches_oracle(small_mock, N):
         plan.set_schedule(3, 256, 512)
 
 
+@pytest.mark.parametrize("N", [128, 256])
+def test_fused_last_stage_sizes_match_oracle(small_mock, N):
+    """At these sizes the y-pass takes its last FFT stage's outputs from
+    registers into the k_y sums: P_l within the tolerance of the oracle for
+    each moment set (P_0 alone, P_0 and P_2, all multipoles: 1, 6 and 16
+    fields, so 1, 3 and 9 k_z-power groups), both y-pass block shapes, and an
+    interlaced PCS pair."""
+    fkp = _fkp()
+    sv0, gal, ran = small_mock
+    sv = mockgen.survey_small(N=N, assign=3)
+    geom = dict(sv.geometry())
+    kf = 2 * math.pi / sv.L
+    bins = (0.5 * kf, kf, 24)
+    ref = _oracle_power(gal, ran, geom, bins)
+    g, r = to_device(gal), to_device(ran)
+    sets = [(fkp.FKP_P0, ("P0",)), (fkp.FKP_P0 | fkp.FKP_P2, ("P0", "P2")),
+            (fkp.FKP_P0 | fkp.FKP_P2 | fkp.FKP_P4 | fkp.FKP_P4B, ("P0", "P2", "P4", "P4b"))]
+    for want, keys in sets:
+        plan = fkp.Plan(geom, bins, want=want)
+        zt = plan.schedule()["z_threads"]
+        for yt in (256, 512):
+            plan.set_schedule(8, yt, zt)
+            err = p_errors(plan.power(g, r), ref, keys)
+            assert max(err.values()) < P_TOL, (want, yt, err)
+    # the second grid of an interlaced pair enters the z-pass sums with its
+    # half-cell phase
+    geom_i = dict(geom, assign=4, interlace=True, periodic=True)
+    ref_i = _oracle_power(gal, ran, geom_i, bins)
+    err = p_errors(fkp.Plan(geom_i, bins).power(g, r), ref_i)
+    assert max(err.values()) < P_TOL, err
+
+
 def test_graph_replay_equals_plain_launches(small_mock):
     """The second call with the same device catalogs captures a CUDA graph and
     later calls replay it; another catalog runs plain launches and the graph
