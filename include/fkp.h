@@ -53,11 +53,24 @@ enum {
  * multipoles by the line-of-sight split of Sec. II.B (the remark after eq.
  * P4fast: the 22 fields of l <= 4 give l = 6 and 8 too).  FKP_B4B: the split
  * hexadecapole bispectrum of eq. Bhexa2 (delta_2 on the two larger sides;
- * a true multipole on zero-area triangles). */
+ * a true multipole on zero-area triangles).
+ *
+ * FKP_XHAT_OBJECT (a modifier, not an output): the moment fields of eqs. Qij,
+ * Qijkl take each object's own line of sight x^ (eq. Qab with x^ of the
+ * object) instead of the grid node's: every moment field is gridded from the
+ * catalogs, sum w x^_a x^_b (...) W, before its FFT, so the estimator is the
+ * gridded form of the direct sum over objects of w L_l(k^.x^) e^{-ik.x}.
+ * Power multipoles of one grid only: fkp_plan_create rejects it with any
+ * FKP_B* flag or an interlaced geometry (FKP_EINVAL), and such plans do not
+ * take fkp_plan_cache_randoms, fkp_power_batch or fkp_power_from_grid
+ * (FKP_ESTATE).  The plan holds one int64 grid per moment field (16 with
+ * FKP_P4, 6 with FKP_P2 alone, 8 N^3 bytes each) and grids the catalogs once
+ * per field. */
 enum {
   FKP_P0 = 1, FKP_P2 = 2, FKP_P4 = 4, FKP_P4B = 8,
   FKP_B0 = 16, FKP_B2 = 32, FKP_B4 = 64,
-  FKP_P6B = 128, FKP_P8B = 256, FKP_B4B = 512
+  FKP_P6B = 128, FKP_P8B = 256, FKP_B4B = 512,
+  FKP_XHAT_OBJECT = 1024
 };
 
 /* One catalog {x_j, w_j, nbar_j} (Sec. III.A, around eq. F0), structure of

@@ -14,7 +14,8 @@ scalars        alpha (Sec. III.A, above eq. F0; weighted reading), I_22 (eq. I22
 assign         interpolation of objects to grid nodes (eq. mapFFT): CIC, TSC or
                PCS; interlaced pairs of grids (Sec. III.A after eq. mapFFT).
 moments        F x^_a x^_b and F x^_a x^_b x^_c x^_d about the observer
-               (eqs. Qij, Qijkl, Qab) with x^ taken at the grid node.
+               (eqs. Qij, Qijkl, Qab) with x^ taken at the grid node, or
+               (xhat="object") sum w x^_a x^_b (...) W with x^ of each object.
 legendre       F_0 (eq. F0), F_2 (eqs. F2, delta2b), F_4 (eqs. delta4, delta4b) from
                one 3-D FFT per moment field, sign e^{-ik.x}.
 bin_power      shell average (eq. shell) in half-open bins and P_0, P_2, P_4
@@ -238,14 +239,16 @@ def window(N, p):
     return (np.sinc(nx / N) * np.sinc(ny / N) * np.sinc(nz / N)) ** p
 
 
-def legendre(grid, geom, lmax=4, compensate=None):
+def legendre(grid, geom, lmax=4, compensate=None, moment=None):
     """F_0, F_2, F_4 on the rfft half-spectrum of a real field.
 
     F_2 = 3/2 sum_ab k^_a k^_b Q_ab - F_0/2            (eqs. F2, delta2b)
     F_4 = 35/8 sum_abcd k^k^k^k^ Q_abcd - 5/2 F_2 - 7/8 F_0   (eqs. delta4, delta4b)
-    with Q the FFT (sign e^{-ik.x}) of grid * x^_a x^_b (...), one FFT per
-    distinct tensor component; n = 0 gets k^ = 0.  Divided by the assignment
-    window when compensating.
+    with Q the FFT (sign e^{-ik.x}) of the moment field of each distinct
+    tensor component (a, b, ...): grid * x^_a x^_b (...) with x^ at the grid
+    node, or moment((a, b, ...)) when given (the per-object fields of
+    object_moments); n = 0 gets k^ = 0.  Divided by the assignment window
+    when compensating.
     """
     g = _geom(geom)
     N = int(g["N"])
@@ -258,16 +261,23 @@ def legendre(grid, geom, lmax=4, compensate=None):
         with np.errstate(divide="ignore", invalid="ignore"):
             inv = np.where(nn > 0, 1.0 / nn, 0.0)
         kh = [nx * inv, ny * inv, nz * inv]
-        xh = node_xhat(g)
+        if moment is None:
+            xh = node_xhat(g)
+
+            def moment(e):
+                out_e = grid
+                for a in e:
+                    out_e = out_e * xh[a]
+                return out_e
         S2 = np.zeros_like(F0)
         for (a, b), m in RANK2:
-            S2 += m * kh[a] * kh[b] * rfftn(grid * xh[a] * xh[b])
+            S2 += m * kh[a] * kh[b] * rfftn(moment((a, b)))
         F2 = 1.5 * S2 - 0.5 * F0
         out[2] = F2
         if lmax >= 4:
             S4 = np.zeros_like(F0)
             for (a, b, c, d), m in RANK4:
-                S4 += m * kh[a] * kh[b] * kh[c] * kh[d] * rfftn(grid * xh[a] * xh[b] * xh[c] * xh[d])
+                S4 += m * kh[a] * kh[b] * kh[c] * kh[d] * rfftn(moment((a, b, c, d)))
             out[4] = 35.0 / 8.0 * S4 - 2.5 * F2 - 7.0 / 8.0 * F0
     if comp:
         W = window(N, int(g["assign"]))
@@ -295,12 +305,36 @@ def interlace_fields(F1, F2, N):
     return {l: 0.5 * (F1[l] + ph * F2[l]) for l in F1}
 
 
+def object_moments(gal, ran, geom, alpha):
+    """The moment fields with x^ taken at each object (eq. Qab read with the
+    object's own line of sight): component e = (a, b, ...) is
+    sum_g w x^_a x^_b (...) W - alpha sum_r w x^_a x^_b (...) W, the
+    products of x^ formed per object before the interpolation."""
+    g = _geom(geom)
+    pg, wg, _ = _cat(gal, g["P_fkp"])
+    pr, wr, _ = _cat(ran, g["P_fkp"])
+    xg, xr = _los_unit(pg, g), _los_unit(pr, g)
+
+    def moment(e):
+        mg, mr = wg.copy(), wr.copy()
+        for a in e:
+            mg = mg * xg[:, a]
+            mr = mr * xr[:, a]
+        return assign(pg, mg, g) - alpha * assign(pr, mr, g)
+    return moment
+
+
 def survey_fields(gal, ran, geom, lmax=4, with_w2=False):
     """F_l (and F^w_l) of a survey: the Legendre fields of its grid, or with
     interlace=True of the interlaced pair of grids, compensated by the
-    window after the average."""
+    window after the average.  xhat="object" in the geometry takes the
+    moments with each object's own x^ (object_moments; one grid, no F^w)."""
     g = _geom(geom)
     F, Fw, sc = fkp_grids(gal, ran, g, with_w2=with_w2)
+    if g.get("xhat", "node") == "object":
+        if g.get("interlace") or with_w2:
+            raise ValueError("per-object moments: one grid and no F^w")
+        return legendre(F, g, lmax=lmax, moment=object_moments(gal, ran, g, sc["alpha"])), None, sc
     if not g.get("interlace"):
         Fl = legendre(F, g, lmax=lmax)
         Fwl = legendre(Fw, g, lmax=lmax) if with_w2 else None

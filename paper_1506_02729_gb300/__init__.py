@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "fkp.h")
 FKP_P0, FKP_P2, FKP_P4, FKP_P4B = 1, 2, 4, 8
 FKP_B0, FKP_B2, FKP_B4 = 16, 32, 64
 FKP_P6B, FKP_P8B, FKP_B4B = 128, 256, 512
+FKP_XHAT_OBJECT = 1024  # modifier: moments with each object's own line of sight
 FKP_CONTRACT_FP32, FKP_CONTRACT_BF16X3, FKP_CONTRACT_BF16X6 = 0, 1, 2
 ERRORS = {-1: "FKP_EINVAL", -2: "FKP_EGEOM", -3: "FKP_ENOMEM", -4: "FKP_ETIMEOUT", -5: "FKP_ECUDA",
           -6: "FKP_ESTATE"}

@@ -420,6 +420,8 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
     if (3.0 * nmax >= N) return set_error(FKP_EGEOM, "3*n_max = %.1f >= N = %d: triangle sums would alias", 3 * nmax, N);
     if (nmax >= N / 2) return set_error(FKP_EGEOM, "shells reach the Nyquist plane");
   }
+  if ((want & FKP_XHAT_OBJECT) && (wantB || geom->interlace))
+    return set_error(FKP_EINVAL, "FKP_XHAT_OBJECT: power multipoles of one grid only (no FKP_B*, no interlace)");
   if (geom->observer_at_infinity) {
     const double l2 = geom->los[0] * geom->los[0] + geom->los[1] * geom->los[1] + geom->los[2] * geom->los[2];
     if (!(l2 > 0)) return set_error(FKP_EINVAL, "los must be nonzero when the observer is at infinity");
@@ -432,6 +434,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   if (bs) P->bs = *bs;
   P->want = want;
   P->wantB = wantB;
+  P->per_object = (want & FKP_XHAT_OBJECT) != 0;
   int lmax = 0;
   if (want & (FKP_P2 | FKP_P4B | FKP_B2 | FKP_B4B)) lmax = 2;
   if (want & (FKP_P4 | FKP_B4 | FKP_P6B | FKP_P8B)) lmax = 4;
@@ -468,6 +471,9 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   g.P_fkp_lo = (float)(geom->P_fkp - (double)g.P_fkp);
   g.alpha_mode = geom->alpha_mode;
   observer_node(g);
+  // with each object's x^ the moment fields obey the trace identity object by
+  // object, so the node at the observer needs no correction
+  if (P->per_object) g.obs_x = g.obs_y = g.obs_z = -1;
   P->interlace = geom->interlace != 0;
   if (P->interlace) {
     // the second grid: nodes at origin + (i + 1/2) H
@@ -531,7 +537,7 @@ extern "C" int fkp_plan_create(void* vctx, const fkp_geometry_t* geom, const fkp
   P->nblk_z = yz_tiles(N) * N;
   bool ok = true;
   auto A = [&](size_t bytes) { void* p = P->alloc(bytes); if (!p) ok = false; return p; };
-  P->d_grid = (unsigned long long*)A(N3 * 8);
+  P->d_grid = (unsigned long long*)A(N3 * 8 * (P->per_object ? (size_t)P->mt.nfields : 1));
   if (wantB) P->d_gridw = (unsigned long long*)A(N3 * 8);
   if (P->interlace) {
     P->d_grid2 = (unsigned long long*)A(N3 * 8);
@@ -708,7 +714,8 @@ static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t
   // zero the grids on the side stream while the counts run
   CK(cudaEventRecord(P->ev_fork, s));
   CK(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
-  CK(cudaMemsetAsync(grid, 0, N3 * 8, P->side));
+  const int ngrid = P->per_object ? P->mt.nfields : 1;  // per object: the moment fields follow F
+  CK(cudaMemsetAsync(grid, 0, N3 * 8 * ngrid, P->side));
   if (gridw) CK(cudaMemsetAsync(gridw, 0, N3 * 8, P->side));
   CK(cudaEventRecord(P->ev_join, P->side));
   int* bh_ran = P->d_bhist + (size_t)nbg * P->ntiles;
@@ -733,6 +740,10 @@ static int grid_pass(Plan* P, const CatDev& gal, const CatDev& ran, cudaStream_t
     CK(launch_lab_finalize(P->d_labpart, ran.n > 0 ? nbr : 0, P->d_ds + DS_COUNT, s));
   }
   CK(launch_tile_accum(geo, P->d_toff, P->d_titem, gal.n + (cached ? 0 : ran.n), P->d_xyzv, vw2, grid, gridw, s));
+  // per-object line of sight: moment field q grids w x^^e[q] with each object's x^
+  for (int q = 1; q < ngrid; ++q)
+    CK(launch_tile_accum(geo, P->d_toff, P->d_titem, gal.n + ran.n, P->d_xyzv, nullptr, grid + (size_t)q * N3,
+                         nullptr, s, P->mt.e[q]));
   if (cached)
     CK(launch_combine_randoms(grid, rgrid, gridw, rgridw, P->d_ds, (long long)N3, P->ctx->nsm, s));
   return FKP_OK;
@@ -821,6 +832,7 @@ static int cache_randoms(Plan* P, const CatDev& ran, cudaStream_t s) {
 extern "C" int fkp_plan_cache_randoms(void* plan, const fkp_catalog_t* ran, void* stream) {
   auto* P = static_cast<Plan*>(plan);
   if (!P || !ran) return set_error(FKP_EINVAL, "NULL plan or catalog");
+  if (P->per_object) return set_error(FKP_ESTATE, "FKP_XHAT_OBJECT plans grid the randoms' moments with each mock");
   CK(cudaSetDevice(P->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CatDev r;
@@ -868,7 +880,8 @@ ZParams fkp::zparams(const Plan* P, int mode) {
 
 int fkp::enqueue_xy(Plan* P, const unsigned long long* gq, const unsigned long long* gq2, const float* gf,
                     cudaStream_t s, bool events) {
-  CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult));
+  CK(launch_xpass(gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S1, P->ctx->nsm, s, P->sched.x_mult, MockBatch(),
+                  P->per_object));
   if (events) CK(record_stage(P->ev[3], s));
   CK(launch_ypass(P->d_S1, gq, gf, P->g, P->mt, P->fp, P->d_tw, P->d_S2, P->d_err + 1, s, P->sched.y_threads));
   if (P->interlace) {
@@ -1150,6 +1163,7 @@ extern "C" int fkp_power_batch(void* plan, int nmock, const fkp_catalog_t* gals,
   if (!P) return set_error(FKP_EINVAL, "NULL plan");
   if (nmock < 1 || nmock > 65535) return set_error(FKP_EINVAL, "nmock = %d (1 .. 65535)", nmock);
   if (P->interlace) return set_error(FKP_EINVAL, "the fused batch does not interlace: use fkp_power per mock");
+  if (P->per_object) return set_error(FKP_ESTATE, "the fused batch forms the moments at the nodes: use fkp_power");
   if (!gals) return set_error(FKP_EINVAL, "NULL catalog array");
   if (!rans && !P->rc_valid) return set_error(FKP_ESTATE, "rans is NULL but the plan has no cached random catalog");
   CK(cudaSetDevice(P->ctx->device));
@@ -1254,6 +1268,7 @@ extern "C" int fkp_power_from_grid(void* plan, const float* F, double I22, doubl
   auto* P = static_cast<Plan*>(plan);
   if (!P || !F) return set_error(FKP_EINVAL, "NULL plan or grid");
   if (P->interlace) return set_error(FKP_EINVAL, "a given field has no interlaced partner: use a plan without interlace");
+  if (P->per_object) return set_error(FKP_ESTATE, "a given field has no objects to take x^ from (FKP_XHAT_OBJECT)");
   CK(cudaSetDevice(P->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int) * 4, s));

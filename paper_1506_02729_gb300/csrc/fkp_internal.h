@@ -37,6 +37,9 @@ struct Plan {
   fkp_bshells_t bs{};
   uint32_t want = 0;
   bool wantB = false;
+  // moments with each object's x^ (FKP_XHAT_OBJECT): d_grid then holds the
+  // mt.nfields moment grids one after the other (field 0 = F)
+  bool per_object = false;
   int lmax = 0;
   MomentTable mt{};
   PassSchedule sched{};
@@ -172,16 +175,22 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
 cudaError_t launch_combine_randoms(unsigned long long* grid, const unsigned long long* rgrid,
                                    unsigned long long* gridw, const unsigned long long* rgridw, const double* ds,
                                    long long n, int nsm, cudaStream_t s);
+// xe: NULL, or the exponents (a, b, c) of a moment field: each object's value
+// is then multiplied by x^_x^a x^_y^b x^_z^c of its own line of sight.
 cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const int* items, long long nobj, const float4* xyzv,
-                              const float* vw2, unsigned long long* grid, unsigned long long* gridw, cudaStream_t s);
+                              const float* vw2, unsigned long long* grid, unsigned long long* gridw, cudaStream_t s,
+                              const unsigned char* xe = nullptr);
 cudaError_t launch_lab_finalize(const double* labpart, int nblk, double* out, cudaStream_t s);
 cudaError_t launch_wait_selftest(unsigned polls, int* flag, cudaStream_t s);
 // xm: x-pass blocks = SMs x resident blocks x xm; nt: threads per y- or
 // z-pass block (256 or 512).  The defaults are the 512^3 choices.  mb: the
 // mocks of one fused launch (blockIdx.z) and their buffer strides.
+// per_object: gq holds mt.nfields gridded moment fields one after the other
+// (N^3 each); the x-pass transforms them instead of forming the moments at
+// the nodes.
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm = 2,
-                         MockBatch mb = MockBatch());
+                         MockBatch mb = MockBatch(), bool per_object = false);
 cudaError_t launch_ypass(const float2* S1, const unsigned long long* gq, const float* gf, const GeomDev& g,
                          const MomentTable& mt, const FftPlan& fp,
                          const float2* tw, float2* S2, int* err, cudaStream_t s, int nt = 256,

@@ -68,11 +68,13 @@ size_t estimate_plan(const fkp_request_t& r) {
   const size_t N3 = (size_t)N * N * N;
   const bool B = (r.want & (FKP_B0 | FKP_B2 | FKP_B4)) != 0;
   int lmax = 0;
-  if (r.want & (FKP_P2 | FKP_P4B | FKP_B2)) lmax = 2;
-  if (r.want & (FKP_P4 | FKP_B4)) lmax = 4;
+  if (r.want & (FKP_P2 | FKP_P4B | FKP_B2 | FKP_B4B)) lmax = 2;
+  if (r.want & (FKP_P4 | FKP_B4 | FKP_P6B | FKP_P8B)) lmax = 4;
   const int nf = lmax >= 4 ? 16 : (lmax >= 2 ? 6 : 1), ng = lmax >= 4 ? 9 : (lmax >= 2 ? 4 : 1);
   const size_t half = field_elems(N) * sizeof(float2);
-  size_t b = N3 * 8 * (B ? 2 : 1) + half * (nf + ng);
+  // one grid (F, and F^w with B), or one per moment field with each object's x^
+  const size_t ngrid = (r.want & FKP_XHAT_OBJECT) ? (size_t)nf : (B ? 2 : 1);
+  size_t b = N3 * 8 * ngrid + half * (nf + ng);
   b += sizeof(double) * (BQ_N + 1) * (size_t)r.pbins.nbins * tiles_x(N) * N;
   // per-block tile counts of the gridding: two rows per SM (256 bounds the SM count)
   const size_t nt = (size_t)assign_tiles_per_axis(N);

@@ -338,6 +338,28 @@ __device__ __forceinline__ void split_fixed(float v, int& h, int& l) {
   l = __float_as_int(fmaf(rem, 524288.0f, kMagic)) - kMagicBits;
 }
 
+// x^_x^ea x^_y^eb x^_z^ec of the object at (o.x, o.y, o.z): its own line of
+// sight about the observer (node 0 sits at origin - observer = (rx, ry, rz)
+// from it), the fixed one for an observer at infinity; x^ = 0 at the
+// observer itself.
+__device__ __forceinline__ float ipow(float v, int e) {
+  float r = 1.f;
+  for (int k = 0; k < e; ++k) r *= v;
+  return r;
+}
+__device__ __forceinline__ float object_moment(const GeomDev& g, const float4& o, int ea, int eb, int ec) {
+  float hx = g.lx, hy = g.ly, hz = g.lz;
+  if (!g.los_inf) {
+    const float dx = (o.x - g.ox) + g.rx, dy = (o.y - g.oy) + g.ry, dz = (o.z - g.oz) + g.rz;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    hx = dx * inv;
+    hy = dy * inv;
+    hz = dz * inv;
+  }
+  return ipow(hx, ea) * ipow(hy, eb) * ipow(hz, ec);
+}
+
 // One block per work item: up to kAccumChunk objects of one tile (items in
 // tile order; items[t] is tile t's first).  The tile's region, from one cell
 // below the tile to the end of its reach (reg_side cells a side), covers the
@@ -363,7 +385,8 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
                                                                         const float4* __restrict__ xyzv,
                                                                         const float* __restrict__ vw2,
                                                                         unsigned long long* __restrict__ grid,
-                                                                        unsigned long long* __restrict__ gridw) {
+                                                                        unsigned long long* __restrict__ gridw,
+                                                                        int ea, int eb, int ec) {
   constexpr int kReg = reg_side<P>(), kReg3 = reg_cells<P>();
   static_assert(kAccumChunk * 262144ll < 2147483648ll, "the low words would wrap");
   extern __shared__ unsigned long long reg[];
@@ -420,8 +443,9 @@ __global__ void __launch_bounds__(kAccumThreads, W2 ? 2 : 4) k_tile_accum(GeomDe
   // the bounds, with room for the rounding of the FP32 sums above
   const bool split = s_abs < 1000.f && __int_as_float(s_max) < 2.f;
   for (int i = a + threadIdx.x; i < b; i += kAccumThreads) {
-    const float4 o = xyzv[i];
+    float4 o = xyzv[i];
     const float wv = W2 ? vw2[i] : 0.f;
+    if (ea >= 0) o.w *= object_moment(g, o, ea, eb, ec);  // |x^ products| <= 1: the bounds hold
     const float ux = (o.x - g.ox) * g.invH, uy = (o.y - g.oy) * g.invH, uz = (o.z - g.oz) * g.invH;
     int ix, iy, iz;
     float wx[P], wy[P], wz[P];
@@ -584,7 +608,9 @@ cudaError_t launch_bin_scatter(const CatDev& c, int is_ran, const GeomDev& g, co
 
 // nobj: the objects scattered into tile order (bounds the number of items).
 cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const int* items, long long nobj, const float4* xyzv,
-                              const float* vw2, unsigned long long* grid, unsigned long long* gridw, cudaStream_t s) {
+                              const float* vw2, unsigned long long* grid, unsigned long long* gridw, cudaStream_t s,
+                              const unsigned char* xe) {
+  const int ea = xe ? xe[0] : -1, eb = xe ? xe[1] : 0, ec = xe ? xe[2] : 0;
   const int ntx = assign_tiles_per_axis(g.N);
   const int ntiles = ntx * ntx * ntx;
   // every non-empty tile has one item that may be partial, the rest are full
@@ -597,7 +623,7 @@ cudaError_t launch_tile_accum(const GeomDev& g, const int* off, const int* items
     const size_t sm = sizeof(unsigned long long) * reg_cells<PP>() * (WW ? 2 : 1);                     \
     raise_smem_limit((const void*)k_tile_accum<PP, WW>, sm);                                           \
     k_tile_accum<PP, WW><<<(int)nitems, kAccumThreads, sm, s>>>(g, ntx, ntiles, off, items, xyzv, vw2, grid, \
-                                                                gridw);                                \
+                                                                gridw, ea, eb, ec);                    \
   } while (0)
   if (g.assign == 2) {
     if (w2) FKP_TA(2, true); else FKP_TA(2, false);

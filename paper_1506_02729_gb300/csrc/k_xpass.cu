@@ -25,7 +25,11 @@ __device__ __forceinline__ void build_pairs(float f, const float (&hx)[5], const
 // threadIdx.y, so no index is divided by NP.  The register cap keeps as many
 // blocks per SM as shared memory allows for the full moment set (4 up to
 // N = 256, 3 above).
-template <int N_, int LMAX>
+// PO (per-object line of sight): gq holds the NF moment fields, gridded from
+// the catalogs with each object's x^, one after the other (N^3 each); the
+// block packs rows of fields 2p and 2p + 1 into pencil p instead of forming
+// the moments at the nodes.
+template <int N_, int LMAX, bool PO = false>
 __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 1 : (N_ > 0 && N_ <= 256 ? 4 : 3))
     k_xpass2(
     const unsigned long long* __restrict__ gq, const float* __restrict__ gf, GeomDev g, FftPlan fp,
@@ -55,6 +59,7 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 
   constexpr int NPRE = (512 + NTX - 1) / NTX;
   float pre[NPRE];
   auto load_row = [&](int row) {
+    if constexpr (PO) return;
 #pragma unroll
     for (int j = 0; j < NPRE; ++j) {
       const int x = tid + j * NTX;
@@ -77,7 +82,19 @@ __global__ void __launch_bounds__(32 * ((nfields_of(LMAX) + 1) / 2), LMAX < 4 ? 
     load_row(row + gridDim.x);
     __syncthreads();
     const float Y = fmaf((float)y, g.H, g.ry), Z = fmaf((float)z, g.H, g.rz);
-    for (int x = tid; x < N; x += NTX) {
+    if constexpr (PO) {
+      const size_t N3 = (size_t)N * N * N, r0 = (size_t)row * N;
+      for (int x = tid; x < N; x += NTX) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const float m0 = (float)(long long)__ldg(gq + (size_t)(2 * p) * N3 + r0 + x) * kFixInvF;
+          const float m1 = 2 * p + 1 < NF ? (float)(long long)__ldg(gq + (size_t)(2 * p + 1) * N3 + r0 + x) * kFixInvF
+                                          : 0.f;
+          A[ilv<NP, SWZ>(x, p)] = make_float2(m0, m1);
+        }
+      }
+    }
+    for (int x = tid; x < N && !PO; x += NTX) {
       float hx[5], hy[5], hz[5];
       if (g.los_inf) {
         hx[1] = g.lx; hy[1] = g.ly; hz[1] = g.lz;
@@ -143,23 +160,26 @@ int yz_tiles(int N) { return tiles_x(N); }
 
 static size_t xsm(int N, int NP) { return sizeof(float2) * (N + N / 2 + 2 * (size_t)NP * N); }
 
-template <int N_, int LMAX>
+template <int N_, int LMAX, bool PO = false>
 static cudaError_t xrun(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
                         const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb) {
   constexpr int NP = (nfields_of(LMAX) + 1) / 2;
   const size_t sm = xsm(g.N, NP);
-  raise_smem_limit((const void*)k_xpass2<N_, LMAX>, sm);
+  raise_smem_limit((const void*)k_xpass2<N_, LMAX, PO>, sm);
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, LMAX>, 32 * NP, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xpass2<N_, LMAX, PO>, 32 * NP, sm);
   int grid = nsm * (occ > 0 ? occ : 1) * (xm > 0 ? xm : 2);
   if (grid > g.N * g.N) grid = g.N * g.N;
-  k_xpass2<N_, LMAX><<<dim3(grid, 1, mb.n), dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1, mb);
+  k_xpass2<N_, LMAX, PO><<<dim3(grid, 1, mb.n), dim3(NP, 32), sm, s>>>(gq, gf, g, fp, tw, S1, mb);
   return cudaGetLastError();
 }
 
 template <int LMAX>
 static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, const GeomDev& g, const FftPlan& fp,
-                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb) {
+                             const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm, const MockBatch& mb,
+                             bool po) {
+  // the per-object variant: the runtime-size kernel, whatever N
+  if (po) return xrun<0, LMAX, true>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
   if (LMAX == 4) {
     switch (g.N) {
       case 512: return xrun<512, LMAX>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
@@ -176,10 +196,11 @@ static cudaError_t xdispatch(const unsigned long long* gq, const float* gf, cons
 
 cudaError_t launch_xpass(const unsigned long long* gq, const float* gf, const GeomDev& g, const MomentTable& mt,
                          const FftPlan& fp, const float2* tw, float2* S1, int nsm, cudaStream_t s, int xm,
-                         MockBatch mb) {
-  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
-  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb);
+                         MockBatch mb, bool per_object) {
+  if (per_object && (!gq || gf || mb.n != 1)) return cudaErrorInvalidValue;
+  if (mt.nfields == nfields_of(4)) return xdispatch<4>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, per_object);
+  if (mt.nfields == nfields_of(2)) return xdispatch<2>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, per_object);
+  return xdispatch<0>(gq, gf, g, fp, tw, S1, nsm, s, xm, mb, per_object);
 }
 
 }  // namespace fkp
