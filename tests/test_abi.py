@@ -29,6 +29,23 @@ def test_header_declares_the_binding_exports():
     assert declared_symbols() == sorted(fkp.EXPORTS)
 
 
+def test_binding_constants_match_the_header():
+    """Every FKP_* enum value of include/fkp.h (output flags, contraction
+    modes, error codes) has the same value in the Python binding."""
+    src = open(os.path.join(ROOT, "include", "fkp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", src):
+        for name, val in re.findall(r"\b(FKP_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            consts[name] = int(val)
+    assert "FKP_XHAT_OBJECT" in consts and "FKP_CONTRACT_BF16X6" in consts
+    for name, val in consts.items():
+        if hasattr(fkp, name):
+            assert getattr(fkp, name) == val, name
+        elif name != "FKP_OK":
+            assert fkp.ERRORS.get(val) == name, name
+
+
 def test_library_exports_every_declared_symbol(built):
     L = ctypes.CDLL(built)
     for s in declared_symbols():
