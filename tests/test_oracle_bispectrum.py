@@ -249,14 +249,32 @@ def test_thin_shell_shot_noise_from_direct_point_sums():
             SQ[(l, 0, s)] = np.mean((F[l] * np.conj(Fw[0])).real)
             SQ[(0, l, s)] = np.mean((F[0] * np.conj(Fw[l])).real)
     scale = max(abs(v) for v in SQ.values()) / I33
+    nclosed = 0
     for t, (a, b, c) in enumerate(ref["tri"]):
-        mu12 = np.clip((cen[c] ** 2 - cen[a] ** 2 - cen[b] ** 2) / (2 * cen[a] * cen[b]), -1, 1)
-        mu13 = np.clip((cen[b] ** 2 - cen[a] ** 2 - cen[c] ** 2) / (2 * cen[a] * cen[c]), -1, 1)
+        A, B, C = cen[a], cen[b], cen[c]
+        if abs(A - B) <= C <= A + B:
+            # the triangle's own vectors: q1 along x, q2 at the angle that
+            # closes |q1 + q2| = C, q3 = -(q1 + q2); cosines by dot products
+            from scipy.optimize import brentq
+            th = brentq(lambda u: np.hypot(A + B * np.cos(u), B * np.sin(u)) - C, 0.0, np.pi) \
+                if A + B > C > abs(A - B) else (0.0 if C == A + B else np.pi)
+            q1 = np.array([A, 0.0, 0.0])
+            q2 = B * np.array([np.cos(th), np.sin(th), 0.0])
+            q3 = -(q1 + q2)
+            mu12 = q1 @ q2 / (A * B)
+            mu13 = q1 @ q3 / (A * np.linalg.norm(q3))
+            nclosed += 1
+        else:
+            # centres that do not close (the shells' widths make N_T > 0):
+            # the cosines clipped to +-1, the oracle's reading
+            mu12 = np.clip((C ** 2 - A ** 2 - B ** 2) / (2 * A * B), -1, 1)
+            mu13 = np.clip((B ** 2 - A ** 2 - C ** 2) / (2 * A * C), -1, 1)
         for l in (0, 2, 4):
             n = (2 * l + 1) / I33 * (SQ[(l, 0, a)] + _leg(l, mu12) * SQ[(0, l, b)] + _leg(l, mu13) * SQ[(0, l, c)])
             if l == 0:
                 n -= 2 * S3 / I33
             assert abs(ref[f"N{l}"][t] - n) < 1e-9 * scale, (l, (a, b, c), ref[f"N{l}"][t], n)
+    assert nclosed >= len(ref["tri"]) // 2
 
 
 def test_counts_for_pair_equals_single_counts():
