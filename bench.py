@@ -232,11 +232,28 @@ def peaks():
 def oracle_full(gal, ran, sv):
     """Wall time of the FP64 oracle (oracle.power.power, as it stands) on one
     whole mock of the workload: scalars, gridding of every galaxy and random,
-    the 22 moment-field FFTs, recombination and binning."""
+    the 22 moment-field FFTs, recombination and binning; and its result."""
     from oracle import power as op
     t0 = time.perf_counter()
-    op.power(gal, ran, sv.geometry(), BINS)
-    return time.perf_counter() - t0
+    ref = op.power(gal, ran, sv.geometry(), BINS)
+    return time.perf_counter() - t0, ref
+
+
+def fp64_errors(got, ref):
+    """Largest error of each output of the GPU path against the FP64 oracle on
+    the same catalogs: P_l per bin with modes relative to max(|P_l|, |P_0|,
+    the raw monopole) (P_2, P_4 and the shot-noise-subtracted P_0 cross zero),
+    the scalars relative to themselves, and whether the mode counts agree."""
+    m = np.asarray(ref["nmodes"]) > 0
+    den = np.maximum(np.abs(ref["P0"][m]), np.abs(ref["mono_raw"][m]))
+    out = {}
+    for k in ("P0", "P2", "P4", "P4b"):
+        d = np.maximum(np.abs(ref[k][m]), den)
+        out[k] = float(np.max(np.abs(np.asarray(got[k])[m] - ref[k][m]) / d))
+    for k in ("alpha", "I22", "N0"):
+        out[k] = float(abs(got[k] / ref[k] - 1.0))
+    out["nmodes_equal"] = bool(np.array_equal(np.asarray(got["nmodes"]), np.asarray(ref["nmodes"])))
+    return out
 
 
 def restrict_cores(n):
@@ -282,7 +299,7 @@ def run_reference(args):
     ts = []
     t_start = time.perf_counter()
     while len(ts) < max(1, args.steps):
-        ts.append(oracle_full(gal, ran, sv))
+        ts.append(oracle_full(gal, ran, sv)[0])
         if time.perf_counter() - t_start + ts[-1] > args.reference_budget:
             break
     t_mock = float(np.mean(ts))
@@ -410,7 +427,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h, "path": f"fkp_server_submit/wait, {args.e2e_slots} slots"
                     if args.e2e_slots > 1 else "fkp_power, one call at a time",
                     "one_call_at_a_time": job_rate(world, sync_s)},
-            "gpu_launches": 12 * args.steps,  # per step: 2 counts, totals, scan, 2 scatters, L^ab, tiles, x, y, z, bins
+            # per step: 2 counts, scalars, tile totals, scan, 2 scatters, L^ab, tiles, x, y, z, bins
+            "gpu_launches": 13 * args.steps,
             "roofline": roof,
             "fft_schedule": plan.schedule(),
             "clocks": ck}
@@ -433,10 +451,15 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         line["fused"] = run_fused(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_mock = oracle_full(gal, ran, sv)
+        t_mock, ref = oracle_full(gal, ran, sv)
         line["cpu_baseline"] = {"value": 1.0 / t_mock, "unit": "mocks/s", "cores": cores_used(), "kind": "oracle",
                                 "sample": f"oracle (numpy/scipy FP64) on one whole mock of the workload (the "
-                                          f"timed catalogs, 512^3): {t_mock:.1f} s"}
+                                          f"timed catalogs, {sv.N}^3): {t_mock:.1f} s"}
+        # the last timed step's outputs against that oracle run
+        try:
+            line["error_vs_fp64"] = fp64_errors(r, ref)
+        except Exception as e:  # the line is printed whatever happens here
+            line["error_vs_fp64"] = {"unavailable": f"{type(e).__name__}: {e}"[:120]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
